@@ -1,0 +1,73 @@
+"""Seeded synthetic inputs for the Chebyshev--Jacobi transform workloads.
+
+This module draws random numbers and nothing else: it holds none of the
+transform's arithmetic, so both the CPU oracle (test infrastructure) and the
+CUDA path can be fed from it without sharing any method code.
+
+Workload recipes follow the paper's own synthetic experiments (Sec. 5: expansion
+coefficients drawn from U(0,1) or U(-1,1) n^-2, Jacobi parameters drawn from
+U(-1/2,1/2)) scaled to the shapes this library is measured on:
+
+* ``decaying_coefficients(N, p, seed)``: c_n = g_n / (n+1)^p, g_n ~ N(0,1).
+* ``jacobi_parameters(seed)``: (alpha, beta) ~ U[-0.45, 0.45]^2.
+* ``batch_workload(count, seed)``: N log-uniform in [64, 65536] (integers, so
+  usually not a power of two), per-item (alpha, beta), direction Bernoulli(1/2),
+  coefficients N(0,1)/(n+1).
+
+All generators use NumPy's PCG64 with base seed 20261203; item t of a
+workload draws from the stream ``seed + t``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BASE_SEED = 20261203
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def decaying_coefficients(N: int, p: float, seed: int = BASE_SEED) -> np.ndarray:
+    """c_n = g_n/(n+1)^p for n = 0..N with g_n i.i.d. standard normal (float64)."""
+    g = rng(seed).standard_normal(N + 1)
+    n = np.arange(N + 1, dtype=np.float64)
+    return g / (n + 1.0) ** p
+
+
+def uniform_coefficients(N: int, seed: int = BASE_SEED) -> np.ndarray:
+    """c_n ~ U(0,1): the paper's 'irregular function' coefficients (Fig. 3)."""
+    return rng(seed).uniform(0.0, 1.0, N + 1)
+
+
+def jacobi_parameters(seed: int = BASE_SEED, lo: float = -0.45, hi: float = 0.45):
+    """(alpha, beta) drawn uniformly from [lo, hi]^2."""
+    r = rng(seed)
+    a, b = r.uniform(lo, hi, 2)
+    return float(a), float(b)
+
+
+def single_workload(Ns=(1 << 12, 1 << 14, 1 << 16, 1 << 18), seed: int = BASE_SEED, p: float = 1.5):
+    """One item per N: (N, alpha, beta, coefficients) with c_n = g_n/(n+1)^p."""
+    items = []
+    for t, N in enumerate(Ns):
+        a, b = jacobi_parameters(seed + 1000 + t)
+        items.append((int(N), a, b, decaying_coefficients(int(N), p, seed + t)))
+    return items
+
+
+def batch_workload(count: int = 4096, seed: int = BASE_SEED, nmin: int = 64, nmax: int = 65536):
+    """Uneven batch: list of (N, alpha, beta, direction, coefficients).
+
+    direction is +1 (forward) or -1 (inverse)."""
+    r = rng(seed)
+    logN = r.uniform(np.log(nmin), np.log(nmax), count)
+    Ns = np.clip(np.rint(np.exp(logN)).astype(np.int64), nmin, nmax)
+    ab = r.uniform(-0.45, 0.45, (count, 2))
+    dirs = np.where(r.uniform(0.0, 1.0, count) < 0.5, 1, -1)
+    items = []
+    for t in range(count):
+        N = int(Ns[t])
+        items.append((N, float(ab[t, 0]), float(ab[t, 1]), int(dirs[t]),
+                      decaying_coefficients(N, 1.0, seed + 1 + t)))
+    return items
