@@ -1,0 +1,180 @@
+/*
+ * cjt.h -- C ABI of the GB300 (sm_103a) Chebyshev--Jacobi transform library.
+ *
+ * The library computes, on one GPU, the forward and inverse Chebyshev--Jacobi
+ * transforms of R. M. Slevinsky, "On the use of Hahn's asymptotic formula and
+ * stabilized recurrence for a fast, simple, and stable Chebyshev--Jacobi
+ * transform" (arXiv:1602.02618):
+ *
+ *   forward  c_cheb = T_N^{-1} P_N^{(alpha,beta)} c_jac        (Eq. "CJT", Sec. 1)
+ *   inverse  c_jac  = P_N^{(alpha,beta)}^{-1} T_N c_cheb       (Eq. "iCJT", Sec. 1)
+ *
+ * where [P_N]_{j,n} = P_n^{(alpha,beta)}(x_j) and [T_N]_{j,k} = T_k(x_j) at the
+ * N+1 Chebyshev--Lobatto points x_j = cos(pi j/N), j = 0..N.  The forward map
+ * evaluates the Jacobi expansion at the Lobatto points by the paper's
+ * partition (Sec. 2.2): Hahn's interior asymptotic formula as a sum of
+ * diagonally scaled DCT-I/DST-I (Eq. "PNASY") inside the boxes, the
+ * Clenshaw--Smith recurrence (Reinsch-modified near x = +-1, Sec. 4.2)
+ * elsewhere, and finishes with the inverse scaled DCT-I.  The inverse map is
+ * the transposed formula on the 2N grid with Clenshaw--Curtis weights
+ * (Eq. "CJTT", Sec. 3.2).
+ *
+ * Conventions shared by every entry point:
+ *  - All coefficient vectors are contiguous IEEE double arrays of length N+1
+ *    (index n = degree).  "_dev" pointers are device pointers on the current
+ *    CUDA device; "_host" pointers are host pointers (pinned memory gives the
+ *    fastest copies, pageable memory works).  The caller owns every I/O buffer;
+ *    input and output may alias (in-place transforms are allowed).
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Device-side calls are asynchronous: they return once the work
+ *    is enqueued; faults surface from cjt_sync or the next CUDA call.
+ *  - A plan owns all its device tables and workspace.  One plan may be in use
+ *    on one stream at a time: a call on a different stream while the plan's
+ *    previous work is still running returns CJT_EBUSY.  Distinct plans are
+ *    independent and may run concurrently.
+ *  - Return values: 0 (CJT_OK) on success, a negative CJT_E* code otherwise;
+ *    cjt_strerror() names it.  No C++ exception crosses this boundary.
+ *  - The library never falls back to a CPU path: every step of a transform
+ *    runs in this library's CUDA kernels.
+ */
+#ifndef CJT_H
+#define CJT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define CJT_OK 0
+#define CJT_EINVAL (-1)      /* null pointer, N < 0, bad option value               */
+#define CJT_EDOMAIN (-2)     /* alpha or beta outside [-1/2, 1/2] (Sec. 2.1)         */
+#define CJT_ENOMEM (-3)      /* device or host allocation failed                     */
+#define CJT_ECUDA (-4)       /* a CUDA runtime call failed (see cjt_last_cuda_error) */
+#define CJT_ETIMEOUT (-5)    /* a bounded device-side wait gave up                   */
+#define CJT_EBUSY (-6)       /* plan still in use on another stream                  */
+#define CJT_EUNSUPPORTED (-7)/* request outside what this build implements          */
+#define CJT_EDIRECTION (-8)  /* plan was not built for the requested direction       */
+
+/* precision of the scaled DCT-I/DST-I bulk (Sec. 2.1, Eq. "PNASY") */
+#define CJT_FP64 0           /* everything in IEEE double                            */
+#define CJT_MIXED 1          /* ASY transforms in float; Hahn coefficients, scalings,
+                                recurrences, accumulation and the final DCT-I in double */
+
+/* directions a plan is built for */
+#define CJT_FWD 1
+#define CJT_INV 2
+
+/* Plan options.  Zero-initialised fields select the defaults noted. */
+typedef struct {
+    int M;            /* terms of Hahn's formula (Eq. "Jacasy"), 1..20; 0 -> 7            */
+    double eps;       /* partition tolerance on each matrix entry (Sec. 2.2); 0 -> 2^-52   */
+    int precision;    /* CJT_FP64 (default) or CJT_MIXED                                   */
+    int directions;   /* CJT_FWD | CJT_INV; 0 -> both                                      */
+    double ratio;     /* block ratio alpha_N of Sec. 2.2 in (0, 1); 0 -> the paper's
+                         min(1/log(N/n_M), 1/2)                                            */
+    int seg_len;      /* degree-segment length of the recurrence work items; 0 -> 2048    */
+    int use_asy;      /* 1 (default when 0): partition as in Sec. 2.2;
+                         -1: recurrence only (no asymptotic blocks)                        */
+} cjt_plan_opts;
+
+/* Summary of a plan (for reports and tests). Sizes are per direction. */
+typedef struct {
+    int64_t N;
+    double alpha, beta;
+    int M, precision, directions;
+    int64_t n_M;             /* Sec. 2.2, from the envelope g_M(pi/2)                  */
+    double ratio;            /* alpha_N actually used                                   */
+    int nblk_fwd, nblk_inv;  /* asymptotic blocks (grid N, grid 2N)                     */
+    int64_t rec_steps_fwd;   /* sum_i J(i): recurrence steps of one forward transform  */
+    int64_t rec_steps_inv;   /* sum_i min(J(i), N+1) on the 2N grid                     */
+    int64_t fft_len_fwd, fft_len_inv;   /* transform lengths used by the ASY blocks     */
+    int64_t nfft_fwd, nfft_inv;         /* complex transforms per execution             */
+    int64_t rec_items_fwd, rec_items_inv;
+    int64_t device_bytes;    /* device memory owned by the plan                        */
+    double plan_ms;          /* wall time of cjt_plan                                  */
+} cjt_plan_info;
+
+typedef struct cjt_plan_s *cjt_plan_t;
+
+/* Fill *opts with the defaults.  Returns CJT_EINVAL if opts is NULL. */
+int cjt_plan_opts_default(cjt_plan_opts *opts);
+
+/*
+ * Build a plan (Sec. 4 "Planification", steps 1a-1e): recurrence tables
+ * (Sec. 1.2, Sec. 4.2 Lemma on r_n^b(+-1)), Hahn coefficients C_{n,m}
+ * (Eq. "Cnmabasy"/"Cnmabrec"), diagonals u_m, v_m (Eq. "Jacasyuv"), the
+ * partition n_M, alpha_N, K, j_k, i_k^1, i_k^2 (Sec. 2.2), transform twiddles,
+ * and for the inverse the Clenshaw--Curtis weights (Eq. "CCweights") and
+ * 1/A_n (Eq. "Anabasy").  Runs on `stream` and synchronises it once (the box
+ * indices are read back to size the launches).
+ *   out    : receives the plan handle (NULL on failure)
+ *   N      : degree, N >= 0 (N = 0 is the identity map); N <= 2^22
+ *   alpha, beta : Jacobi parameters in [-1/2, 1/2] (else CJT_EDOMAIN)
+ *   opts   : NULL for defaults
+ * Errors: CJT_EINVAL, CJT_EDOMAIN, CJT_ENOMEM, CJT_ECUDA, CJT_EUNSUPPORTED.
+ */
+int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_plan_opts *opts,
+             void *stream);
+
+/* Release a plan and all device memory it owns.  NULL is ignored.  The caller
+ * must ensure no work using the plan is still running. */
+void cjt_destroy(cjt_plan_t plan);
+
+/* Copy the plan summary into *info. */
+int cjt_get_info(cjt_plan_t plan, cjt_plan_info *info);
+
+/*
+ * Forward transform (Eq. "CJT"): c_cheb_dev[k], k = 0..N, from c_jac_dev[n].
+ * Both are device arrays of N+1 doubles; they may alias.
+ * Errors: CJT_EINVAL (null), CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA.
+ */
+int cjt_forward(cjt_plan_t plan, const double *c_jac_dev, double *c_cheb_dev, void *stream);
+
+/*
+ * Inverse transform (Eq. "iCJT" through Eq. "CJTT"): c_jac_dev from c_cheb_dev.
+ * Both are device arrays of N+1 doubles; they may alias.
+ * Errors: CJT_EINVAL (null), CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA.
+ */
+int cjt_inverse(cjt_plan_t plan, const double *c_cheb_dev, double *c_jac_dev, void *stream);
+
+/*
+ * End-to-end transform from host memory: copies in_host (N+1 doubles) to the
+ * plan's device staging buffer, runs the forward (direction = CJT_FWD) or
+ * inverse (CJT_INV) transform, copies the result to out_host and waits for
+ * the stream.  in_host and out_host may alias.
+ */
+int cjt_execute_host(cjt_plan_t plan, int direction, const double *in_host, double *out_host,
+                     void *stream);
+
+/*
+ * Batched execution (Sec. 4: the same plan machinery applied to many inputs):
+ * item t uses plans[t] in direction dir[t] (CJT_FWD or CJT_INV) on
+ * in_dev + offsets[t] -> out_dev + offsets[t] (N_t + 1 doubles each, N_t the
+ * degree of plans[t]).  Items may use different N, (alpha, beta) and
+ * precision.  All stages of all items are issued as one sequence of
+ * multi-item launches on `stream` (capturable into a CUDA graph).  A plan may
+ * appear at most once per call.  in_dev and out_dev must not overlap.
+ * Errors: CJT_EINVAL, CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA, CJT_ENOMEM.
+ */
+int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, const int64_t *offsets,
+                        const double *in_dev, double *out_dev, void *stream);
+
+/* Wait for `stream` and report any CUDA error raised by earlier work. */
+int cjt_sync(void *stream);
+
+/* Message for an error code (static string). */
+const char *cjt_strerror(int code);
+
+/* The last CUDA error string seen by the library on this thread ("" if none). */
+const char *cjt_last_cuda_error(void);
+
+/* Library version string. */
+const char *cjt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CJT_H */

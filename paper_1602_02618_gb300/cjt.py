@@ -1,0 +1,218 @@
+"""Thin Python binding of the C ABI in include/cjt.h (argument marshalling only).
+
+Every step of a transform runs in the CUDA library ``_build/libcjt.so``;
+PyTorch is used only to hold device memory and to name CUDA streams.  If the
+library has not been built (``__graft_entry__.build()`` or
+``python paper_1602_02618_gb300/build.py``) every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libcjt.so")
+
+CJT_OK = 0
+CJT_EINVAL = -1
+CJT_EDOMAIN = -2
+CJT_ENOMEM = -3
+CJT_ECUDA = -4
+CJT_ETIMEOUT = -5
+CJT_EBUSY = -6
+CJT_EUNSUPPORTED = -7
+CJT_EDIRECTION = -8
+CJT_FP64 = 0
+CJT_MIXED = 1
+CJT_FWD = 1
+CJT_INV = 2
+
+
+class cjt_plan_opts(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("eps", ctypes.c_double), ("precision", ctypes.c_int),
+                ("directions", ctypes.c_int), ("ratio", ctypes.c_double), ("seg_len", ctypes.c_int),
+                ("use_asy", ctypes.c_int)]
+
+
+class cjt_plan_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("M", ctypes.c_int), ("precision", ctypes.c_int), ("directions", ctypes.c_int),
+                ("n_M", ctypes.c_int64), ("ratio", ctypes.c_double), ("nblk_fwd", ctypes.c_int),
+                ("nblk_inv", ctypes.c_int), ("rec_steps_fwd", ctypes.c_int64), ("rec_steps_inv", ctypes.c_int64),
+                ("fft_len_fwd", ctypes.c_int64), ("fft_len_inv", ctypes.c_int64), ("nfft_fwd", ctypes.c_int64),
+                ("nfft_inv", ctypes.c_int64), ("rec_items_fwd", ctypes.c_int64), ("rec_items_inv", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("plan_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+EXPORTED = ["cjt_plan_opts_default", "cjt_plan", "cjt_destroy", "cjt_get_info", "cjt_forward", "cjt_inverse",
+            "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_strerror", "cjt_last_cuda_error",
+            "cjt_version"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CJTError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        lib = _lib
+        msg = lib.cjt_strerror(code).decode() if lib else str(code)
+        extra = lib.cjt_last_cuda_error().decode() if (lib and code == CJT_ECUDA) else ""
+        super().__init__("%s failed: %s (%d)%s" % (what, msg, code, (" -- " + extra) if extra else ""))
+
+
+def load(path: str = LIB_PATH):
+    """Load libcjt.so and declare its signatures; raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError("CUDA library %s is missing: build it with __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        vp, i64, d, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        lib.cjt_plan_opts_default.argtypes = [ctypes.POINTER(cjt_plan_opts)]
+        lib.cjt_plan.argtypes = [ctypes.POINTER(vp), i64, d, d, ctypes.POINTER(cjt_plan_opts), vp]
+        lib.cjt_destroy.argtypes = [vp]
+        lib.cjt_destroy.restype = None
+        lib.cjt_get_info.argtypes = [vp, ctypes.POINTER(cjt_plan_info)]
+        lib.cjt_forward.argtypes = [vp, vp, vp, vp]
+        lib.cjt_inverse.argtypes = [vp, vp, vp, vp]
+        lib.cjt_execute_host.argtypes = [vp, i, vp, vp, vp]
+        lib.cjt_execute_batched.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int8),
+                                            ctypes.POINTER(i64), vp, vp, vp]
+        lib.cjt_sync.argtypes = [vp]
+        lib.cjt_strerror.argtypes = [i]
+        lib.cjt_strerror.restype = ctypes.c_char_p
+        lib.cjt_last_cuda_error.restype = ctypes.c_char_p
+        lib.cjt_version.restype = ctypes.c_char_p
+        for name in ("cjt_plan_opts_default", "cjt_plan", "cjt_get_info", "cjt_forward", "cjt_inverse",
+                     "cjt_execute_host", "cjt_execute_batched", "cjt_sync"):
+            getattr(lib, name).restype = i
+        _lib = lib
+        return lib
+
+
+def _check(rc, what):
+    if rc != CJT_OK:
+        raise CJTError(rc, what)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if t.numel() < n:
+        raise ValueError("tensor has %d elements, need %d" % (t.numel(), n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_opts() -> cjt_plan_opts:
+    o = cjt_plan_opts()
+    _check(load().cjt_plan_opts_default(ctypes.byref(o)), "cjt_plan_opts_default")
+    return o
+
+
+class Plan:
+    """A cjt_plan_t: device-resident tables for degree N and parameters (alpha, beta)."""
+
+    def __init__(self, N: int, alpha: float, beta: float, M: int = 0, eps: float = 0.0, precision: int = CJT_FP64,
+                 directions: int = 0, ratio: float = 0.0, seg_len: int = 0, use_asy: int = 0, stream=None):
+        lib = load()
+        o = cjt_plan_opts(M, eps, precision, directions, ratio, seg_len, use_asy)
+        h = ctypes.c_void_p()
+        _check(lib.cjt_plan(ctypes.byref(h), int(N), float(alpha), float(beta), ctypes.byref(o),
+                            _stream_handle(stream)), "cjt_plan")
+        self._h = h
+        self.N = int(N)
+        self.alpha = float(alpha)
+        self.beta = float(beta)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = cjt_plan_info()
+        _check(load().cjt_get_info(self._h, ctypes.byref(inf)), "cjt_get_info")
+        return inf.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().cjt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cjt_forward(plan: Plan, c_jac, c_cheb=None, stream=None):
+    """c_cheb = T_N^{-1} P_N c_jac on the device (float64 CUDA tensors of N+1 values)."""
+    import torch
+    n = plan.N + 1
+    if c_cheb is None:
+        c_cheb = torch.empty(n, dtype=torch.float64, device=c_jac.device)
+    _check(load().cjt_forward(plan.handle, _dev_ptr(c_jac, n), _dev_ptr(c_cheb, n), _stream_handle(stream)),
+           "cjt_forward")
+    return c_cheb
+
+
+def cjt_inverse(plan: Plan, c_cheb, c_jac=None, stream=None):
+    """c_jac = P_N^{-1} T_N c_cheb on the device."""
+    import torch
+    n = plan.N + 1
+    if c_jac is None:
+        c_jac = torch.empty(n, dtype=torch.float64, device=c_cheb.device)
+    _check(load().cjt_inverse(plan.handle, _dev_ptr(c_cheb, n), _dev_ptr(c_jac, n), _stream_handle(stream)),
+           "cjt_inverse")
+    return c_jac
+
+
+def cjt_execute_host(plan: Plan, direction: int, x: np.ndarray, out: np.ndarray = None, stream=None):
+    """Host-to-host transform through the library's own staging buffers (synchronous)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.size != plan.N + 1:
+        raise ValueError("expected %d values" % (plan.N + 1))
+    if out is None:
+        out = np.empty_like(x)
+    _check(load().cjt_execute_host(plan.handle, int(direction), ctypes.c_void_p(x.ctypes.data),
+                                   ctypes.c_void_p(out.ctypes.data), _stream_handle(stream)), "cjt_execute_host")
+    return out
+
+
+def cjt_execute_batched(plans, dirs, offsets, x_dev, out_dev, stream=None):
+    """Items t: plans[t] in direction dirs[t] on x_dev[offsets[t]:] -> out_dev[offsets[t]:]."""
+    count = len(plans)
+    arr = (ctypes.c_void_p * count)(*[p.handle.value for p in plans])
+    d = (ctypes.c_int8 * count)(*[int(v) for v in dirs])
+    off = (ctypes.c_int64 * count)(*[int(v) for v in offsets])
+    total = max((int(o) + p.N + 1 for o, p in zip(offsets, plans)), default=0)
+    _check(load().cjt_execute_batched(count, arr, d, off, _dev_ptr(x_dev, total), _dev_ptr(out_dev, total),
+                                      _stream_handle(stream)), "cjt_execute_batched")
+    return out_dev
+
+
+def cjt_sync(stream=None):
+    _check(load().cjt_sync(_stream_handle(stream)), "cjt_sync")
+
+
+def version() -> str:
+    return load().cjt_version().decode()

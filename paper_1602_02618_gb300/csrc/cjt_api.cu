@@ -1,0 +1,250 @@
+// C ABI entry points (include/cjt.h): argument checks, plan lifetime, the
+// one-stream-at-a-time guard, host-buffer execution and error reporting.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "cjt_internal.cuh"
+
+namespace {
+thread_local char g_cuda_err[256] = "";
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int begin_use(cjt_plan_s *p, cudaStream_t st) {
+    if (p->has_pending && p->last_stream != st) {
+        cudaError_t q = cudaEventQuery(p->done);
+        if (q == cudaErrorNotReady) return CJT_EBUSY;
+        if (q != cudaSuccess) {
+            cjt_internal_set_cuda_error(q, "cudaEventQuery");
+            return CJT_ECUDA;
+        }
+    }
+    return CJT_OK;
+}
+
+int end_use(cjt_plan_s *p, cudaStream_t st) {
+    CJT_CUDA_TRY(cudaEventRecord(p->done, st));
+    p->last_stream = st;
+    p->has_pending = true;
+    return CJT_OK;
+}
+
+void free_plan(cjt_plan_s *p) {
+    for (void *v : p->allocs) cudaFree(v);
+    p->allocs.clear();
+    if (p->done) cudaEventDestroy(p->done);
+    delete p;
+}
+}  // namespace
+
+void cjt_internal_set_cuda_error(cudaError_t e, const char *what) {
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+}
+
+extern "C" {
+
+const char *cjt_version(void) { return "cjt-gb300 0.1 (sm_103a)"; }
+
+const char *cjt_last_cuda_error(void) { return g_cuda_err; }
+
+const char *cjt_strerror(int code) {
+    switch (code) {
+        case CJT_OK: return "success";
+        case CJT_EINVAL: return "invalid argument";
+        case CJT_EDOMAIN: return "alpha or beta outside [-1/2, 1/2]";
+        case CJT_ENOMEM: return "out of memory";
+        case CJT_ECUDA: return "CUDA runtime error";
+        case CJT_ETIMEOUT: return "device-side wait timed out";
+        case CJT_EBUSY: return "plan in use on another stream";
+        case CJT_EUNSUPPORTED: return "unsupported request";
+        case CJT_EDIRECTION: return "plan not built for this direction";
+        default: return "unknown error";
+    }
+}
+
+int cjt_plan_opts_default(cjt_plan_opts *o) {
+    if (!o) return CJT_EINVAL;
+    memset(o, 0, sizeof(*o));
+    o->M = 7;
+    o->eps = 0x1p-52;
+    o->precision = CJT_FP64;
+    o->directions = CJT_FWD | CJT_INV;
+    o->ratio = 0.0;
+    o->seg_len = 2048;
+    o->use_asy = 1;
+    return CJT_OK;
+}
+
+int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_plan_opts *opts, void *stream) {
+    if (!out) return CJT_EINVAL;
+    *out = nullptr;
+    if (N < 0) return CJT_EINVAL;
+    if (N > (1LL << 22)) return CJT_EUNSUPPORTED;
+    if (!(alpha >= -0.5 && alpha <= 0.5) || !(beta >= -0.5 && beta <= 0.5)) return CJT_EDOMAIN;
+    cjt_plan_opts o;
+    cjt_plan_opts_default(&o);
+    if (opts) {
+        if (opts->M) o.M = opts->M;
+        if (opts->eps != 0.0) o.eps = opts->eps;
+        o.precision = opts->precision;
+        if (opts->directions) o.directions = opts->directions;
+        o.ratio = opts->ratio;
+        if (opts->seg_len) o.seg_len = opts->seg_len;
+        if (opts->use_asy) o.use_asy = opts->use_asy;
+    }
+    if (o.M < 1 || o.M > 20) return CJT_EINVAL;
+    if (!(o.eps > 0.0 && o.eps < 1.0)) return CJT_EINVAL;
+    if (o.precision != CJT_FP64 && o.precision != CJT_MIXED) return CJT_EINVAL;
+    if (o.directions < 1 || o.directions > 3) return CJT_EINVAL;
+    if (!(o.ratio == 0.0 || (o.ratio > 0.0 && o.ratio < 1.0))) return CJT_EINVAL;
+    if (o.seg_len < 32 || o.seg_len > (1 << 20) || (o.seg_len % 32) != 0) return CJT_EINVAL;
+    if (N > 0 && !is_pow2(N)) return CJT_EUNSUPPORTED;
+
+    cjt_plan_s *p = new (std::nothrow) cjt_plan_s();
+    if (!p) return CJT_ENOMEM;
+    p->N = N;
+    p->alpha = alpha;
+    p->beta = beta;
+    p->opts = o;
+    p->seg_len = o.seg_len;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    int rc;
+    if (N == 0) {
+        rc = CJT_OK;
+        cudaError_t e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+        if (e != cudaSuccess) { cjt_internal_set_cuda_error(e, "cudaEventCreate"); rc = CJT_ECUDA; }
+        if (!rc) {
+            e = cudaMalloc((void **)&p->d_in, 2 * sizeof(double));
+            if (e != cudaSuccess) { cjt_internal_set_cuda_error(e, "cudaMalloc"); rc = CJT_ENOMEM; }
+            else { p->allocs.push_back(p->d_in); p->d_out = p->d_in + 1; }
+        }
+    } else {
+        rc = cjt_plan_build(p, st);
+    }
+    if (rc) {
+        cudaStreamSynchronize(st);
+        free_plan(p);
+        return rc;
+    }
+    p->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return CJT_OK;
+}
+
+void cjt_destroy(cjt_plan_t p) {
+    if (!p) return;
+    if (p->has_pending && p->done) cudaEventSynchronize(p->done);
+    free_plan(p);
+}
+
+int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
+    if (!p || !info) return CJT_EINVAL;
+    memset(info, 0, sizeof(*info));
+    info->N = p->N;
+    info->alpha = p->alpha;
+    info->beta = p->beta;
+    info->M = p->M;
+    info->precision = p->opts.precision;
+    info->directions = p->opts.directions;
+    info->n_M = p->n_M;
+    info->ratio = p->ratio;
+    info->nblk_fwd = p->fw.nblk;
+    info->nblk_inv = p->iv.nblk;
+    info->rec_steps_fwd = p->fw.rec_steps;
+    info->rec_steps_inv = p->iv.rec_steps;
+    info->fft_len_fwd = p->Lf;
+    info->fft_len_inv = p->Li;
+    info->nfft_fwd = p->npair_f + (p->N > 0 ? 1 : 0);
+    info->nfft_inv = p->npair_i + (p->N > 0 ? 1 : 0);
+    info->rec_items_fwd = p->fw.nitems;
+    info->rec_items_inv = p->iv.nitems;
+    info->device_bytes = p->device_bytes;
+    info->plan_ms = p->plan_ms;
+    return CJT_OK;
+}
+
+int cjt_forward(cjt_plan_t p, const double *in, double *out, void *stream) {
+    if (!p || !in || !out) return CJT_EINVAL;
+    if (!(p->opts.directions & CJT_FWD)) return CJT_EDIRECTION;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_use(p, st);
+    if (rc) return rc;
+    rc = cjt_exec_forward(p, in, out, st);
+    if (rc) return rc;
+    return end_use(p, st);
+}
+
+int cjt_inverse(cjt_plan_t p, const double *in, double *out, void *stream) {
+    if (!p || !in || !out) return CJT_EINVAL;
+    if (!(p->opts.directions & CJT_INV)) return CJT_EDIRECTION;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_use(p, st);
+    if (rc) return rc;
+    rc = cjt_exec_inverse(p, in, out, st);
+    if (rc) return rc;
+    return end_use(p, st);
+}
+
+int cjt_execute_host(cjt_plan_t p, int direction, const double *in_host, double *out_host, void *stream) {
+    if (!p || !in_host || !out_host) return CJT_EINVAL;
+    if (direction != CJT_FWD && direction != CJT_INV) return CJT_EINVAL;
+    if (!(p->opts.directions & direction)) return CJT_EDIRECTION;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_use(p, st);
+    if (rc) return rc;
+    const size_t bytes = sizeof(double) * (size_t)(p->N + 1);
+    CJT_CUDA_TRY(cudaMemcpyAsync(p->d_in, in_host, bytes, cudaMemcpyHostToDevice, st));
+    rc = direction == CJT_FWD ? cjt_exec_forward(p, p->d_in, p->d_out, st) : cjt_exec_inverse(p, p->d_in, p->d_out, st);
+    if (rc) return rc;
+    CJT_CUDA_TRY(cudaMemcpyAsync(out_host, p->d_out, bytes, cudaMemcpyDeviceToHost, st));
+    rc = end_use(p, st);
+    if (rc) return rc;
+    CJT_CUDA_TRY(cudaStreamSynchronize(st));
+    return CJT_OK;
+}
+
+int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, const int64_t *offsets,
+                        const double *in_dev, double *out_dev, void *stream) {
+    if (count < 0) return CJT_EINVAL;
+    if (count == 0) return CJT_OK;
+    if (!plans || !dir || !offsets || !in_dev || !out_dev) return CJT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int t = 0; t < count; ++t) {
+        if (!plans[t]) return CJT_EINVAL;
+        if (dir[t] != CJT_FWD && dir[t] != CJT_INV) return CJT_EINVAL;
+        if (!(plans[t]->opts.directions & dir[t])) return CJT_EDIRECTION;
+        int rc = begin_use(plans[t], st);
+        if (rc) return rc;
+    }
+    for (int t = 0; t < count; ++t) {
+        cjt_plan_s *p = plans[t];
+        int rc = dir[t] == CJT_FWD ? cjt_exec_forward(p, in_dev + offsets[t], out_dev + offsets[t], st)
+                                   : cjt_exec_inverse(p, in_dev + offsets[t], out_dev + offsets[t], st);
+        if (rc) return rc;
+        rc = end_use(p, st);
+        if (rc) return rc;
+    }
+    return CJT_OK;
+}
+
+int cjt_sync(void *stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cjt_internal_set_cuda_error(e, "cudaStreamSynchronize");
+        return CJT_ECUDA;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cjt_internal_set_cuda_error(e, "cudaGetLastError");
+        return CJT_ECUDA;
+    }
+    return CJT_OK;
+}
+
+}  // extern "C"

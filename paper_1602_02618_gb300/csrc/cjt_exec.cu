@@ -1,0 +1,422 @@
+// Execution (Sec. 4, steps 2a-2c) of the forward and inverse transforms.
+//
+// forward (Eq. "CJT"):
+//   REC  k_rec_fwd      y_i^REC = sum_{n < J(i)} c_n P_n(x_i): Clenshaw--Smith for
+//                       pi/4 < theta_i < 3pi/4, Reinsch-modified (x0 = +-1) otherwise
+//                       (Sec. 4.2), one warp per (32 rows x degree segment)
+//   ASY  k_asy_pack_fwd a_{k,m}[n] = C_{n,m} c_n on degrees n >= j_k, two (k,m) per complex vector
+//        FFT            DCT-I and DST-I sums at theta_i (Eq. "PNASY")
+//   sum  k_combine_fwd  y_i = REC partials + sum_m u_m Re F - v_m Im F on the deepest box of row i
+//   DCT  FFT + k_dct_finish   c_cheb = T_N^{-1} y (inverse scaled DCT-I)
+// inverse (Eq. "CJTT"):
+//   front  FFT of [c_cheb; 0] -> p_N on the 2N grid, g = w o p_N (Clenshaw--Curtis weights)
+//   ASY^T  k_asy_pack_inv + FFT: Re sum_i (u_m + i v_m) g_i e^{-i n theta_i} per (k,m) box
+//   REC^T  k_rec_inv     forward recurrence g_i P_n(x_i) (Reinsch-modified near +-1), column sums
+//   sum    k_combine_inv y_n = REC^T + sum_m C_{n,m} ASY^T, c_jac_n = y_n / A_n
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "cjt_internal.cuh"
+
+namespace {
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// REC, forward: one warp per item, lane = row
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_rec_fwd(const RecItem *__restrict__ items, int64_t nitems, int64_t Ng,
+                                                RecTables t, const double *__restrict__ c,
+                                                const double *__restrict__ states, double *__restrict__ partials) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nitems) return;
+    const RecItem it = items[w];
+    const int row = it.row0 + min(lane, it.nrows - 1);
+    double P1 = 1.0, P2 = 0.0;
+    if (it.state >= 0) {
+        const double2 sv = reinterpret_cast<const double2 *>(states)[(int64_t)it.state * 32 + lane];
+        P1 = sv.x;
+        P2 = sv.y;
+    }
+    double S;
+    if (it.mode == REC_PLAIN) {
+        const double x = cospi((double)row / (double)Ng);
+        double u1 = 0.0, u2 = 0.0;
+        for (int n = it.b - 1; n >= it.a; --n) {
+            const double w0 = fma(-__ldg(t.C + n + 1), u2, __ldg(c + n));
+            const double u0 = fma(fma(__ldg(t.A + n), x, __ldg(t.B + n)), u1, w0);
+            u2 = u1;
+            u1 = u0;
+        }
+        // segment sum = pi_a u_a - C_a pi_{a-1} u_{a+1}
+        S = fma(P1, u1, -__ldg(t.C + it.a) * P2 * u2);
+    } else {
+        const bool plus = it.mode == REC_REINSCH_P1;
+        double delta;
+        if (plus) {
+            const double s = sinpi((double)row / (2.0 * (double)Ng));
+            delta = -2.0 * s * s;
+        } else {
+            const double s = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
+            delta = 2.0 * s * s;
+        }
+        const double *Cr = plus ? t.Cr_p : t.Cr_m;
+        const double *rbinv = plus ? t.rbinv_p : t.rbinv_m;
+        const double *Ce = plus ? t.Ce_p : t.Ce_m;
+        double u = 0.0, e = 0.0, uprev = 0.0;
+        for (int n = it.b - 1; n >= it.a; --n) {
+            const double wn = fma(__ldg(Cr + n + 1), e, __ldg(c + n));
+            const double en = fma(__ldg(t.A + n) * delta, u, wn);
+            const double un = fma(u, __ldg(rbinv + n), en);
+            uprev = u;
+            u = un;
+            e = en;
+        }
+        // segment sum = pi_a e_a + C_a/r^f_{a-1} u_{a+1} e^f_a
+        S = fma(P1, e, __ldg(Ce + it.a) * uprev * P2);
+    }
+    partials[it.out + lane] = lane < it.nrows ? S : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// REC, inverse (transposed): one warp per item; lane = row; the degree sums
+// over the warp's rows go through a padded shared-memory tile.
+// ---------------------------------------------------------------------------
+constexpr int RI_WARPS = 4;
+__global__ void __launch_bounds__(32 * RI_WARPS) k_rec_inv(const RecItem *__restrict__ items, int64_t nitems,
+                                                          int64_t Ng, RecTables t, const double *__restrict__ g,
+                                                          const double *__restrict__ states,
+                                                          double *__restrict__ partials) {
+    __shared__ double tile[RI_WARPS][32][33];
+    const int wib = threadIdx.x >> 5;
+    const int64_t w = (int64_t)blockIdx.x * RI_WARPS + wib;
+    const int lane = threadIdx.x & 31;
+    if (w >= nitems) return;
+    const RecItem it = items[w];
+    const bool active = lane < it.nrows;
+    const int row = it.row0 + min(lane, it.nrows - 1);
+    const double gi = active ? g[row] : 0.0;
+    double P1 = gi, P2 = 0.0;
+    if (active && it.state >= 0) {
+        const double2 sv = reinterpret_cast<const double2 *>(states)[(int64_t)it.state * 32 + lane];
+        P1 = sv.x * gi;
+        P2 = sv.y * gi;
+    }
+    double(*tl)[33] = tile[wib];
+    double *out = partials + it.out - it.a;
+    if (it.mode == REC_PLAIN) {
+        const double x = cospi((double)row / (double)Ng);
+        double p = P1, pm = P2;
+        for (int n0 = it.a; n0 < it.b; n0 += 32) {
+            const int cnt = min(32, it.b - n0);
+            for (int r = 0; r < cnt; ++r) {
+                const int n = n0 + r;
+                tl[r][lane] = p;
+                const double pn = fma(fma(__ldg(t.A + n), x, __ldg(t.B + n)), p, -__ldg(t.C + n) * pm);
+                pm = p;
+                p = pn;
+            }
+            __syncwarp();
+            if (lane < cnt) {
+                double s = 0.0;
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r) s += tl[lane][r];
+                out[n0 + lane] = s;
+            }
+            __syncwarp();
+        }
+    } else {
+        const bool plus = it.mode == REC_REINSCH_P1;
+        double delta;
+        if (plus) {
+            const double s = sinpi((double)row / (2.0 * (double)Ng));
+            delta = -2.0 * s * s;
+        } else {
+            const double s = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
+            delta = 2.0 * s * s;
+        }
+        const double *Ce = plus ? t.Ce_p : t.Ce_m;
+        const double *rf = plus ? t.rf_p : t.rf_m;
+        double p = P1, e = P2;
+        for (int n0 = it.a; n0 < it.b; n0 += 32) {
+            const int cnt = min(32, it.b - n0);
+            for (int r = 0; r < cnt; ++r) {
+                const int n = n0 + r;
+                tl[r][lane] = p;
+                const double en = fma(__ldg(t.A + n) * delta, p, __ldg(Ce + n) * e);
+                p = fma(p, __ldg(rf + n), en);
+                e = en;
+            }
+            __syncwarp();
+            if (lane < cnt) {
+                double s = 0.0;
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r) s += tl[lane][r];
+                out[n0 + lane] = s;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ASY pack, forward: pair p holds items q = 2p, 2p+1 (q = k*M + m) as re/im
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void k_asy_pack_fwd(int64_t N, int64_t L, int M, int nq, const int *__restrict__ box3,
+                               const double *__restrict__ Cnm, const double *__restrict__ scale,
+                               const double *__restrict__ c, V *__restrict__ buf) {
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (n >= L) return;
+    double v[2] = {0.0, 0.0};
+    if (n <= N) {
+        const double cn = c[n];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int q = 2 * p + s;
+            if (q < nq) {
+                const int k = q / M, m = q - k * M;
+                if (n >= box3[3 * k]) v[s] = Cnm[m * (N + 1) + n] * cn * scale[2 * q];
+            }
+        }
+    }
+    V o;
+    o.x = v[0];
+    o.y = v[1];
+    buf[(int64_t)p * L + n] = o;
+}
+
+// ---------------------------------------------------------------------------
+// combine, forward: REC segment partials + asymptotic terms; writes the even
+// extension of y (length 2N) for the final DCT-I
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void k_combine_fwd(int64_t N, int64_t L, int M, const int *__restrict__ rowk,
+                              const double *__restrict__ scale, const double *__restrict__ u,
+                              const double *__restrict__ v, const V *__restrict__ buf,
+                              const int64_t *__restrict__ row_base, const int *__restrict__ row_nseg,
+                              const double *__restrict__ partials, double2 *__restrict__ ext) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > N) return;
+    const int nseg = row_nseg[i];
+    const int64_t base = row_base[i];
+    double y = 0.0;
+    for (int s = 0; s < nseg; ++s) y += partials[base + (int64_t)s * 32];
+    const int k = rowk[i];
+    if (k >= 0) {
+        const int64_t im = (L - i) & (L - 1);
+        for (int m = 0; m < M; ++m) {
+            const int q = k * M + m, p = q >> 1;
+            const V Z = buf[(int64_t)p * L + i], W = buf[(int64_t)p * L + im];
+            double re, imv;
+            if ((q & 1) == 0) {
+                re = 0.5 * ((double)Z.x + (double)W.x);
+                imv = 0.5 * ((double)Z.y - (double)W.y);
+            } else {
+                re = 0.5 * ((double)Z.y + (double)W.y);
+                imv = 0.5 * ((double)W.x - (double)Z.x);
+            }
+            const double us = scale[2 * q + 1];
+            y = fma(u[m * (N + 1) + i] * us, re, y);
+            y = fma(-v[m * (N + 1) + i] * us, imv, y);
+        }
+    }
+    ext[i] = make_double2(y, 0.0);
+    if (i >= 1 && i < N) ext[2 * N - i] = make_double2(y, 0.0);
+}
+
+// c_k = Re Z(k) / N, halved at k = 0 and k = N (inverse scaled DCT-I)
+__global__ void k_dct_finish(int64_t N, const double2 *__restrict__ Z, double *__restrict__ out) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k > N) return;
+    double v = Z[k].x / (double)N;
+    if (k == 0 || k == N) v *= 0.5;
+    out[k] = v;
+}
+
+// ---------------------------------------------------------------------------
+// inverse front end and transposed blocks
+// ---------------------------------------------------------------------------
+__global__ void k_inv_front_pack(int64_t N, int64_t L, const double *__restrict__ c, double2 *__restrict__ buf) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= L) return;
+    buf[k] = make_double2(k <= N ? c[k] : 0.0, 0.0);
+}
+
+__global__ void k_inv_g(int64_t Ng, const double2 *__restrict__ F, const double *__restrict__ w, double *__restrict__ g) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > Ng) return;
+    g[i] = w[i] * F[i].x;
+}
+
+template <typename V>
+__global__ void k_asy_pack_inv(int64_t Ng, int64_t L, int M, int nq, const int *__restrict__ box3,
+                               const double *__restrict__ scale, const double *__restrict__ u,
+                               const double *__restrict__ v, const double *__restrict__ g, V *__restrict__ buf) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (idx >= L) return;
+    double hr[2] = {0.0, 0.0}, hi[2] = {0.0, 0.0};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int q = 2 * p + s;
+        if (q >= nq) continue;
+        const int k = q / M, m = q - k * M;
+        const int i1 = box3[3 * k + 1], i2 = box3[3 * k + 2];
+        if (idx >= i1 && idx <= i2) {
+            const double gi = 0.5 * scale[2 * q] * g[idx];
+            hr[s] = u[m * (Ng + 1) + idx] * gi;
+            hi[s] = v[m * (Ng + 1) + idx] * gi;
+        } else {
+            const int64_t j = L - idx;
+            if (j >= i1 && j <= i2) {
+                const double gj = 0.5 * scale[2 * q] * g[j];
+                hr[s] = u[m * (Ng + 1) + j] * gj;
+                hi[s] = -v[m * (Ng + 1) + j] * gj;
+            }
+        }
+    }
+    V o;
+    o.x = hr[0] - hi[1];
+    o.y = hi[0] + hr[1];
+    buf[(int64_t)p * L + idx] = o;
+}
+
+template <typename V>
+__global__ void k_combine_inv(int64_t N, int64_t L, int M, int nblk, const int *__restrict__ box3,
+                              const double *__restrict__ scale, const double *__restrict__ Cnm,
+                              const V *__restrict__ buf, int seg_len,
+                              const int64_t *__restrict__ seg_ptr, const int64_t *__restrict__ seg_out,
+                              const int *__restrict__ seg_b, const double *__restrict__ partials,
+                              const double *__restrict__ s_n, double *__restrict__ out) {
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n > N) return;
+    const int64_t s = n / seg_len, off = n - s * seg_len;
+    double y = 0.0;
+    for (int64_t q = seg_ptr[s]; q < seg_ptr[s + 1]; ++q)
+        if (n < seg_b[q]) y += partials[seg_out[q] + off];
+    // degree n belongs to block k when j_k <= n < top_k (top_0 = N+1, top_k = j_{k-1})
+    int k = -1;
+    for (int kk = 0; kk < nblk; ++kk) {
+        const int64_t top = kk == 0 ? N + 1 : box3[3 * (kk - 1)];
+        if (n >= box3[3 * kk] && n < top) k = kk;
+    }
+    if (k >= 0) {
+        for (int m = 0; m < M; ++m) {
+            const int q = k * M + m, p = q >> 1;
+            const V Z = buf[(int64_t)p * L + n];
+            const double R = (q & 1) ? (double)Z.y : (double)Z.x;
+            y = fma(Cnm[m * (N + 1) + n] * scale[2 * q + 1], R, y);
+        }
+    }
+    out[n] = s_n[n] * y;
+}
+
+__global__ void k_copy(int64_t n, const double *__restrict__ in, double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// forward / inverse drivers
+// ---------------------------------------------------------------------------
+int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t st) {
+    const int64_t N = p->N;
+    if (N == 0) {
+        k_copy<<<1, 32, 0, st>>>(1, in, out);
+        CJT_CUDA_TRY(cudaGetLastError());
+        return CJT_OK;
+    }
+    GridWork &gw = p->fw;
+    const bool fp32 = p->opts.precision == CJT_MIXED;
+    const int M = p->M;
+    int rc;
+    // REC
+    if (gw.nitems > 0) {
+        k_rec_fwd<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, gw.Ng, p->rt, in,
+                                                                  gw.d_states, gw.d_partials);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
+    // ASY
+    const int nq = gw.nblk * M;
+    const int64_t L = p->Lf;
+    if (nq > 0) {
+        dim3 gp(blocks_for(L, 256), p->npair_f);
+        if (fp32)
+            k_asy_pack_fwd<float2><<<gp, 256, 0, st>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in, (float2 *)p->d_fft_f);
+        else
+            k_asy_pack_fwd<double2><<<gp, 256, 0, st>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in, (double2 *)p->d_fft_f);
+        CJT_CUDA_TRY(cudaGetLastError());
+        rc = cjt_fft_pow2(p->d_fft_f, p->d_fft_scratch, L, p->npair_f, fp32 ? p->d_tw32 : p->d_tw64, p->Ltab, fp32, st);
+        if (rc) return rc;
+    }
+    double2 *ext = (double2 *)p->d_dct;
+    if (fp32)
+        k_combine_fwd<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
+            N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const float2 *)p->d_fft_f, gw.d_row_base, gw.d_row_nseg,
+            gw.d_partials, ext);
+    else
+        k_combine_fwd<double2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
+            N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const double2 *)p->d_fft_f, gw.d_row_base, gw.d_row_nseg,
+            gw.d_partials, ext);
+    CJT_CUDA_TRY(cudaGetLastError());
+    rc = cjt_fft_pow2(p->d_dct, p->d_dct_scratch, 2 * N, 1, p->d_tw64, p->Ltab, false, st);
+    if (rc) return rc;
+    k_dct_finish<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, (const double2 *)p->d_dct, out);
+    CJT_CUDA_TRY(cudaGetLastError());
+    return CJT_OK;
+}
+
+int cjt_exec_inverse(cjt_plan_s *p, const double *in, double *out, cudaStream_t st) {
+    const int64_t N = p->N;
+    if (N == 0) {
+        k_copy<<<1, 32, 0, st>>>(1, in, out);
+        CJT_CUDA_TRY(cudaGetLastError());
+        return CJT_OK;
+    }
+    GridWork &gw = p->iv;
+    const bool fp32 = p->opts.precision == CJT_MIXED;
+    const int M = p->M;
+    const int64_t Ng = 2 * N, L = p->Li;
+    // front end: p_N on the 2N grid, times the Clenshaw--Curtis weights
+    k_inv_front_pack<<<blocks_for(L, 256), 256, 0, st>>>(N, L, in, (double2 *)p->d_dct);
+    CJT_CUDA_TRY(cudaGetLastError());
+    int rc = cjt_fft_pow2(p->d_dct, p->d_dct_scratch, L, 1, p->d_tw64, p->Ltab, false, st);
+    if (rc) return rc;
+    k_inv_g<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)p->d_dct, p->d_w, p->d_g);
+    CJT_CUDA_TRY(cudaGetLastError());
+    // transposed asymptotic blocks
+    const int nq = gw.nblk * M;
+    if (nq > 0) {
+        dim3 gp(blocks_for(L, 256), p->npair_i);
+        if (fp32)
+            k_asy_pack_inv<float2><<<gp, 256, 0, st>>>(Ng, L, M, nq, gw.d_box, gw.d_scale, gw.d_u, gw.d_v, p->d_g, (float2 *)p->d_fft_i);
+        else
+            k_asy_pack_inv<double2><<<gp, 256, 0, st>>>(Ng, L, M, nq, gw.d_box, gw.d_scale, gw.d_u, gw.d_v, p->d_g, (double2 *)p->d_fft_i);
+        CJT_CUDA_TRY(cudaGetLastError());
+        rc = cjt_fft_pow2(p->d_fft_i, p->d_fft_scratch, L, p->npair_i, fp32 ? p->d_tw32 : p->d_tw64, p->Ltab, fp32, st);
+        if (rc) return rc;
+    }
+    // transposed recurrence
+    if (gw.nitems > 0) {
+        k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt, p->d_g,
+                                                                             gw.d_states, gw.d_partials);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
+    if (fp32)
+        k_combine_inv<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
+            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const float2 *)p->d_fft_i, p->seg_len, gw.d_seg_ptr, gw.d_seg_out,
+            gw.d_seg_b, gw.d_partials, p->d_s, out);
+    else
+        k_combine_inv<double2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
+            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const double2 *)p->d_fft_i, p->seg_len, gw.d_seg_ptr, gw.d_seg_out,
+            gw.d_seg_b, gw.d_partials, p->d_s, out);
+    CJT_CUDA_TRY(cudaGetLastError());
+    return CJT_OK;
+}

@@ -1,0 +1,192 @@
+// Shared-memory radix-4 FFT for sm_103a (FP64 and FP32), used for the
+// diagonally scaled DCT-I/DST-I of the asymptotic blocks (Eq. "PNASY"), the
+// final inverse DCT-I (Sec. 2) and the inverse transform's front end and
+// transposed blocks (Eq. "CJTT").
+//
+// X[k] = sum_n x[n] exp(-2 pi i n k / L), L a power of two, in place, batched.
+//   L <= 4096: one pass, each CTA transforms `tile` sequences held in shared memory.
+//   L  > 4096: four-step  L = L1 * L2  (two passes through global memory / L2):
+//     pass A: L2 columns of length L1 (stride L2), twiddle omega_L^{n2 k1}, store T[k1][n2]
+//     pass B: L1 rows of length L2 (contiguous), store X[k1 + L1 k2]
+// Sub-transforms are decimation-in-frequency radix-4 stages (one radix-2 stage
+// last when log2 is odd) on a padded [column][element] shared-memory tile,
+// with twiddles read from a plan-owned table omega_{Ltab}^j computed by
+// sincospi (exact argument reduction).
+#include <cuda_runtime.h>
+
+#include "cjt_internal.cuh"
+
+namespace {
+
+template <typename T> struct cplx;
+template <> struct cplx<double> { using t = double2; };
+template <> struct cplx<float> { using t = float2; };
+
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { V r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    V r;
+    r.x = fma(a.x, b.x, -a.y * b.y);
+    r.y = fma(a.x, b.y, a.y * b.x);
+    return r;
+}
+// multiply by -i
+template <typename V> __device__ __forceinline__ V cmul_mi(V a) { V r; r.x = a.y; r.y = -a.x; return r; }
+
+constexpr int FFT_THREADS = 256;
+constexpr int SMEM_PAD = 1;
+
+// frequency k -> its position after the DIF stages (mixed-radix digit reversal)
+__device__ __forceinline__ int dif_revinv(int k, int logLs) {
+    int p = 0, lb = logLs;
+    while (lb >= 2) { int q = k & 3; k >>= 2; lb -= 2; p += q << lb; }
+    if (lb == 1) p += k;  // remaining digit (0/1) at weight 1
+    return p;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__restrict__ out, int logLs,
+          int64_t ncols, int tile, int64_t in_es, int64_t in_cs, int64_t in_ts, int64_t out_ks, int64_t out_cs,
+          int64_t out_ts, const typename cplx<R>::t *__restrict__ tw, int logLtab, int post_log) {
+    using V = typename cplx<R>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *s = reinterpret_cast<V *>(smem_raw);
+    const int Ls = 1 << logLs;
+    const int ld = Ls + SMEM_PAD;
+    const int64_t c0 = (int64_t)blockIdx.x * tile;
+    const int64_t t = blockIdx.y;
+    const int ncl = (int)min((int64_t)tile, ncols - c0);
+    const V *src = in + t * in_ts + c0 * in_cs;
+    V *dst = out + t * out_ts + c0 * out_cs;
+
+    // load (natural order); lanes run along the contiguous dimension
+    const int total = ncl * Ls;
+    if (in_es == 1) {
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            int e = idx & (Ls - 1), c = idx >> logLs;
+            s[c * ld + e] = src[c * in_cs + e];
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            int c = idx % ncl, e = idx / ncl;
+            s[c * ld + e] = src[c * in_cs + (int64_t)e * in_es];
+        }
+    }
+    __syncthreads();
+
+    // radix-4 DIF stages
+    const int nb4 = Ls >> 2;
+    int lb = logLs;
+    while (lb >= 2) {
+        const int Lb = 1 << lb, h = Lb >> 2;
+        const int twstep_log = logLtab - lb;  // omega_{Lb}^j = tw[j << (logLtab - lb)]
+        for (int idx = threadIdx.x; idx < ncl * nb4; idx += blockDim.x) {
+            int c = idx / nb4, j = idx - c * nb4;
+            int blk = j >> (lb - 2), n0 = j & (h - 1);
+            V *b = s + c * ld + blk * Lb + n0;
+            V x0 = b[0], x1 = b[h], x2 = b[2 * h], x3 = b[3 * h];
+            V t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = cmul_mi(csub(x1, x3));
+            V y0 = cadd(t0, t2), y2 = csub(t0, t2), y1 = cadd(t1, t3), y3 = csub(t1, t3);
+            if (n0 != 0) {
+                y1 = cmul(y1, tw[(int64_t)n0 << twstep_log]);
+                y2 = cmul(y2, tw[(int64_t)(2 * n0) << twstep_log]);
+                y3 = cmul(y3, tw[(int64_t)(3 * n0) << twstep_log]);
+            }
+            b[0] = y0; b[h] = y1; b[2 * h] = y2; b[3 * h] = y3;
+        }
+        __syncthreads();
+        lb -= 2;
+    }
+    if (lb == 1) {
+        const int nb2 = Ls >> 1;
+        for (int idx = threadIdx.x; idx < ncl * nb2; idx += blockDim.x) {
+            int c = idx / nb2, j = idx - c * nb2;
+            V *b = s + c * ld + 2 * j;
+            V x0 = b[0], x1 = b[1];
+            b[0] = cadd(x0, x1);
+            b[1] = csub(x0, x1);
+        }
+        __syncthreads();
+    }
+
+    // store in natural frequency order, optional four-step twiddle omega_{2^post_log}^{c k}
+    if (out_ks == 1) {
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            int k = idx & (Ls - 1), c = idx >> logLs;
+            V v = s[c * ld + dif_revinv(k, logLs)];
+            if (post_log >= 0) {
+                int64_t ex = ((c0 + c) * (int64_t)k) & ((1LL << post_log) - 1);
+                v = cmul(v, tw[ex << (logLtab - post_log)]);
+            }
+            dst[c * out_cs + k] = v;
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            int c = idx % ncl, k = idx / ncl;
+            V v = s[c * ld + dif_revinv(k, logLs)];
+            if (post_log >= 0) {
+                int64_t ex = ((c0 + c) * (int64_t)k) & ((1LL << post_log) - 1);
+                v = cmul(v, tw[ex << (logLtab - post_log)]);
+            }
+            dst[c * out_cs + (int64_t)k * out_ks] = v;
+        }
+    }
+}
+
+int ilog2(int64_t v) {
+    int r = 0;
+    while ((1LL << r) < v) ++r;
+    return r;
+}
+
+template <typename R>
+int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batch, int64_t in_es, int64_t in_cs,
+               int64_t in_ts, int64_t out_ks, int64_t out_cs, int64_t out_ts, const void *tw, int logLtab,
+               int post_log, cudaStream_t st) {
+    using V = typename cplx<R>::t;
+    const int Ls = 1 << logLs;
+    // tile of columns per CTA: ~64 KB of shared memory
+    int64_t budget_elems = (int64_t)(65536 / sizeof(V));
+    int tile = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(ncols, 64), budget_elems / Ls));
+    size_t smem = (size_t)tile * (Ls + SMEM_PAD) * sizeof(V);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(R) == 8]) {
+        CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set[sizeof(R) == 8] = true;
+    }
+    dim3 grid((unsigned)((ncols + tile - 1) / tile), (unsigned)batch);
+    k_fft_sub<R><<<grid, FFT_THREADS, smem, st>>>((const V *)in, (V *)out, logLs, ncols, tile, in_es, in_cs, in_ts,
+                                                    out_ks, out_cs, out_ts, (const V *)tw, logLtab, post_log);
+    CJT_CUDA_TRY(cudaGetLastError());
+    return CJT_OK;
+}
+
+template <typename R>
+int fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab, cudaStream_t st) {
+    if (L <= 1 || batch <= 0) return CJT_OK;
+    const int logL = ilog2(L), logLtab = ilog2(Ltab);
+    if ((1LL << logL) != L || L > Ltab) return CJT_EINVAL;
+    if (logL <= 12) {
+        // direct: each "column" is one whole transform
+        return launch_sub<R>(data, data, logL, batch, 1, 1, L, 0, 1, L, 0, tw, logLtab, -1, st);
+    }
+    if (logL > 24 || scratch == nullptr) return CJT_EUNSUPPORTED;
+    const int log1 = (logL + 1) / 2, log2 = logL - log1;
+    const int64_t L1 = 1LL << log1, L2 = 1LL << log2;
+    // pass A: columns n2 (L2 of them), elements n1 at stride L2
+    int rc = launch_sub<R>(data, scratch, log1, L2, batch, L2, 1, L, L2, 1, L, tw, logLtab, logL, st);
+    if (rc) return rc;
+    // pass B: rows k1 (L1 of them), elements n2 contiguous, output X[k1 + L1 k2]
+    return launch_sub<R>(scratch, data, log2, L1, batch, 1, L2, L, L1, 1, L, tw, logLtab, -1, st);
+}
+
+}  // namespace
+
+int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab, bool fp32,
+                 cudaStream_t st) {
+    return fp32 ? fft_pow2<float>(data, scratch, L, batch, tw, Ltab, st)
+                : fft_pow2<double>(data, scratch, L, batch, tw, Ltab, st);
+}
+
+int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch) { return L > 4096 ? L * batch : 0; }

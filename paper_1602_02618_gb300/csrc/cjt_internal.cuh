@@ -1,0 +1,213 @@
+// Internal declarations of the Chebyshev--Jacobi transform library (sm_103a).
+//
+// Layout of a plan in device memory (all FP64 unless noted):
+//   recurrence tables, index n = 0..Jcap (Sec. 1.2 and Sec. 4.2):
+//     A, B, C                 plain three-term recurrence
+//     for x0 = +1 and x0 = -1 (Reinsch-modified recurrences, Sec. 4.2):
+//       Cr[n] = C_n r^b_n     rbinv[n] = 1/r^b_n  (backward / Clenshaw--Smith form)
+//       Ce[n] = C_n/r^f_{n-1} rf[n] = r^f_n      (forward form, e_n = d_n r^f_{n-1})
+//   Hahn coefficients  Cnm[m*(N+1) + n], m = 0..M      (Eq. "Cnmab")
+//   diagonals          u[m*(Ng+1) + i], v[...], m < M   (Eq. "Jacasyuv"), per grid
+//   partition          boxes (j_k, i_k^1, i_k^2)        (Sec. 2.2), per grid
+//   recurrence work    warp items over (32 rows) x (degree segment), with the
+//                      forward-recurrence state at every segment start
+//   transform buffers  complex FP64 or FP32, twiddle table omega_{Ltab}^k
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cjt.h"
+
+#define CJT_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) {                             \
+            cjt_internal_set_cuda_error(_e, #expr);          \
+            return CJT_ECUDA;                                \
+        }                                                    \
+    } while (0)
+
+void cjt_internal_set_cuda_error(cudaError_t e, const char *what);
+
+// ---------------------------------------------------------------------------
+// recurrence work items
+// ---------------------------------------------------------------------------
+enum { REC_PLAIN = 0, REC_REINSCH_P1 = 1, REC_REINSCH_M1 = 2 };
+
+struct RecItem {
+    int row0;    // first grid row of the 32-row chunk
+    int nrows;   // rows in the chunk (1..32)
+    int a, b;    // degree segment [a, b)
+    int mode;    // REC_PLAIN / REC_REINSCH_P1 / REC_REINSCH_M1
+    int state;   // state block index (32 lanes x 2 doubles), -1 when a == 0
+    int64_t out; // forward: partial index base (32 values); inverse: base of b-a values
+};
+
+// Recurrence tables for one direction (degrees 0..Jcap).
+struct RecTables {
+    double *A, *B, *C;
+    double *Cr_p, *rbinv_p, *Ce_p, *rf_p;   // x0 = +1
+    double *Cr_m, *rbinv_m, *Ce_m, *rf_m;   // x0 = -1
+};
+
+// Partition and recurrence work of one grid (N points for forward, 2N for inverse).
+struct GridWork {
+    int64_t Ng = 0;        // grid: points x_i = cos(pi i / Ng), i = 0..Ng
+    int64_t Jcap = 0;      // degrees handled: 0..Jcap-1 (= N+1)
+    int nblk = 0;          // asymptotic blocks kept
+    std::vector<int64_t> jk, i1, i2;  // block k: degrees [jk[k], jtop(k)), rows [i1[k], i2[k]]
+    int64_t rec_steps = 0;
+    // device
+    int *d_rowk = nullptr;        // per row: deepest box index k (0-based) or -1
+    int64_t *d_row_base = nullptr;// forward: partial index of segment 0 of each row
+    int *d_row_nseg = nullptr;    // forward: degree segments of each row
+    RecItem *d_items = nullptr;
+    int64_t nitems = 0;
+    double *d_states = nullptr;   // [nstate][32][2]
+    int64_t nstate = 0;
+    double *d_partials = nullptr;
+    int64_t npartials = 0;
+    // state computation rows
+    int *d_srow = nullptr;        // rows needing states: row, J, mode, chunk_state_base, lane, nseg
+    int64_t nsrow = 0;
+    // inverse combine: CSR over degree segments
+    int64_t nsegs = 0;
+    int64_t *d_seg_ptr = nullptr;
+    int64_t *d_seg_out = nullptr; // partial base of each contributing item
+    int *d_seg_b = nullptr;       // item end degree b
+    int64_t nchunks = 0;
+    // diagonals u_m, v_m on this grid
+    double *d_u = nullptr, *d_v = nullptr;
+    int *d_box = nullptr;         // [nblk][3] = j, i1, i2
+    // per asymptotic item q = k*M + m: exact power-of-two scale applied before the
+    // transform (d_scale[2q]) and removed after it (d_scale[2q+1]), so that the two
+    // items sharing one complex transform have comparable magnitudes
+    double *d_scale = nullptr;
+};
+
+struct cjt_plan_s {
+    int64_t N = 0;
+    double alpha = 0, beta = 0;
+    cjt_plan_opts opts{};
+    int M = 7;
+    int64_t n_M = 0;
+    double ratio = 0.5;
+    bool corner = false;          // (alpha, beta) at a corner of the square: Hahn's series terminates
+    int seg_len = 2048;
+
+    RecTables rt{};
+    double *d_tabs = nullptr;     // one allocation holding the recurrence tables
+    int64_t Jcap = 0;
+    double *d_Cnm = nullptr;      // (M+1) x (N+1)
+
+    GridWork fw, iv;
+
+    // transforms
+    int64_t Lf = 0, Li = 0;       // forward ASY/DCT length 2N; inverse 4N
+    int64_t Ltab = 0;
+    void *d_tw64 = nullptr;       // double2[Ltab]
+    void *d_tw32 = nullptr;       // float2[Ltab]
+    int npair_f = 0, npair_i = 0; // complex transforms of ASY item pairs
+    void *d_fft_f = nullptr;      // forward ASY buffers (npair_f x Lf), precision dependent
+    void *d_fft_i = nullptr;      // inverse ASY buffers (npair_i x Li)
+    void *d_fft_scratch = nullptr;// scratch for four-step transforms
+    int64_t scratch_elems = 0;
+    double *d_dct = nullptr;      // complex FP64 buffer of length max(Lf, Li) (DCT-I / front end)
+    double *d_dct_scratch = nullptr;
+    double *d_y = nullptr;        // forward grid values / inverse degree sums
+    double *d_g = nullptr;        // inverse: w_i p_N(x_i) on the 2N grid
+    double *d_w = nullptr;        // inverse: Clenshaw--Curtis weights (2N+1)
+    double *d_s = nullptr;        // inverse: 1/A_n (N+1)
+    double *d_in = nullptr, *d_out = nullptr;  // staging for cjt_execute_host
+
+    // concurrency guard
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool has_pending = false;
+
+    int64_t device_bytes = 0;
+    double plan_ms = 0;
+    std::vector<void *> allocs;
+};
+
+// ---------------------------------------------------------------------------
+// Stirling series and Hahn coefficients (host and device)
+// ---------------------------------------------------------------------------
+#include "stirling_coeffs.h"
+static __constant__ double cjt_stirling_a_dev[CJT_STIRLING_NCOEF] = {CJT_STIRLING_LIST};
+
+// Terms of the truncated Stirling series S_eps(z), z >= 9 (Sec. 4.1, Table "Stirling").
+__host__ __device__ inline int cjt_stirling_terms(double z) {
+    if (z >= 3275) return 4;
+    if (z >= 591) return 5;
+    if (z >= 196) return 6;
+    if (z >= 92) return 7;
+    if (z >= 53) return 8;
+    if (z >= 35) return 9;
+    if (z >= 26) return 10;
+    if (z >= 20) return 11;
+    if (z >= 17) return 12;
+    if (z >= 14) return 13;
+    if (z >= 12) return 14;
+    if (z >= 11) return 15;
+    if (z >= 10) return 16;
+    return 17;
+}
+
+__host__ __device__ inline double cjt_stirling_S(double z) {
+#ifdef __CUDA_ARCH__
+    const double *a = cjt_stirling_a_dev;
+#else
+    const double *a = cjt_stirling_a_host;
+#endif
+    int nt = cjt_stirling_terms(z);
+    double w = 1.0 / z, s = 0.0;
+    for (int k = nt - 1; k >= 0; --k) s = fma(s, w, a[k]);
+    return s;
+}
+
+// C_{n,m} by the Stirling/log1p form Eq. "Cnmabasy"; valid for n + min(a,b) >= 8.
+__host__ __device__ inline double cjt_hahn_C_asy(double n, int m, double a, double b) {
+    const double c = 2.0 * n + a + b + m + 2.0;
+    double t = (n + a + 0.5) * log1p((a - b - m) / c) + (n + b + 0.5) * log1p((b - a - m) / c) -
+               (m + 0.5) * log1p((a + b + m + 2.0) / (2.0 * n));
+    double pre = exp((double)m) * ldexp(1.0, -2 * m) * 0.56418958354775628695;  // e^m / (4^m sqrt(pi))
+    return pre * pow(n, -(m + 0.5)) * exp(t) * cjt_stirling_S(n + a + 1.0) * cjt_stirling_S(n + b + 1.0) /
+           cjt_stirling_S(c);
+}
+
+// C_{n,m} for any n >= 0: Eq. "Cnmabasy" where valid, otherwise the downward
+// recurrence of Eq. "Cnmabrec" from the first valid degree.
+__host__ __device__ inline double cjt_hahn_C(int64_t n, int m, double a, double b) {
+    double mn = a < b ? a : b;
+    int64_t n0 = (int64_t)ceil(8.0 - mn);
+    if (n >= n0) return cjt_hahn_C_asy((double)n, m, a, b);
+    double C = cjt_hahn_C_asy((double)n0, m, a, b);
+    for (int64_t k = n0; k > n; --k) {
+        double kk = (double)k;
+        C = C * (kk + 0.5 * (a + b + m + 1.0)) * (kk + 0.5 * (a + b + m)) / ((kk + a) * (kk + b));
+    }
+    return C;
+}
+
+// h_l(a) = (1/2+a)_l (1/2-a)_l / l!  (the factors of f_m, Eq. "Jacasy")
+__host__ __device__ inline double cjt_hahn_h(int l, double a) {
+    double r = 1.0;
+    for (int k = 0; k < l; ++k) r *= (0.5 + a + k) * (0.5 - a + k) / (k + 1.0);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// launchers implemented in the .cu files
+// ---------------------------------------------------------------------------
+int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab,
+                 bool fp32, cudaStream_t st);
+int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch);
+
+int cjt_plan_build(cjt_plan_s *p, cudaStream_t st);
+int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t st);
+int cjt_exec_inverse(cjt_plan_s *p, const double *in, double *out, cudaStream_t st);

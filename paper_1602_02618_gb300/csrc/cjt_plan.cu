@@ -1,0 +1,629 @@
+// Planification (Sec. 4, steps 1a-1e): everything that depends only on
+// (N, alpha, beta, options) is computed here once, on the GPU, and kept in
+// device memory for every later execution.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "cjt_internal.cuh"
+
+namespace {
+
+constexpr double kSqrtPi = 1.77245385090551602730;
+
+struct HahnH {
+    double ha[21];  // h_l(alpha)
+    double hb[21];  // h_l(beta)
+};
+
+// --------------------------------------------------------------------------
+// 1c: recurrence coefficients (Sec. 1.2) and Reinsch ratios at x0 = +-1 (Sec. 4.2)
+// --------------------------------------------------------------------------
+__global__ void k_rec_tables(int64_t nmax, double a, double b, RecTables t) {
+    int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n > nmax) return;
+    const double nn = (double)n, ab = a + b;
+    double A, B, C;
+    if (n == 0) {
+        // from P_1 = (a-b)/2 + (a+b+2)/2 x (avoids 0/0 when a+b = 0 or -1)
+        A = 0.5 * (ab + 2.0);
+        B = 0.5 * (a - b);
+        C = 0.0;
+    } else {
+        const double t0 = 2.0 * nn + ab, t1 = t0 + 1.0, t2 = t0 + 2.0, s1 = nn + ab + 1.0;
+        A = t1 * t2 / (2.0 * (nn + 1.0) * s1);
+        B = (a - b) * ab * t1 / (2.0 * (nn + 1.0) * s1 * t0);
+        C = (nn + a) * (nn + b) * t2 / ((nn + 1.0) * s1 * t0);
+    }
+    t.A[n] = A;
+    t.B[n] = B;
+    t.C[n] = C;
+    // forward ratios r^f_n(+-1) = pi_{n+1}(+-1)/pi_n(+-1)  (Sec. 4.2)
+    t.rf_p[n] = (nn + a + 1.0) / (nn + 1.0);
+    t.rf_m[n] = -(nn + b + 1.0) / (nn + 1.0);
+    // e-form coefficient Ce_n = C_n / r^f_{n-1}
+    if (n == 0) {
+        t.Ce_p[n] = 0.0;
+        t.Ce_m[n] = 0.0;
+    } else {
+        t.Ce_p[n] = C * nn / (nn + a);
+        t.Ce_m[n] = -C * nn / (nn + b);
+    }
+    // backward ratios r^b_n(+-1) (Lemma of Sec. 4.2); r^b_0 is infinite
+    if (n == 0) {
+        t.Cr_p[n] = 0.0; t.rbinv_p[n] = 0.0;
+        t.Cr_m[n] = 0.0; t.rbinv_m[n] = 0.0;
+    } else {
+        const double common = (nn + 1.0) / nn * (ab + nn + 1.0) * (ab + 2.0 * nn) / (ab + 2.0 * nn + 2.0);
+        const double rbp = common / (nn + b);
+        const double rbm = -common / (nn + a);
+        t.Cr_p[n] = C * rbp; t.rbinv_p[n] = 1.0 / rbp;
+        t.Cr_m[n] = C * rbm; t.rbinv_m[n] = 1.0 / rbm;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Hahn coefficients C_{n,m} (Eq. "Cnmab", computed by Eq. "Cnmabasy"/"Cnmabrec")
+// --------------------------------------------------------------------------
+__global__ void k_hahn_C(int64_t N, int Mp1, double a, double b, double *Cnm) {
+    int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int m = blockIdx.y;
+    if (n > N || m >= Mp1) return;
+    Cnm[m * (N + 1) + n] = cjt_hahn_C(n, m, a, b);
+}
+
+// --------------------------------------------------------------------------
+// diagonals u_m(theta_i), v_m(theta_i) (Eq. "Jacasyuv") on the grid theta_i = pi i / Ng
+// --------------------------------------------------------------------------
+__global__ void k_hahn_uv(int64_t Ng, int M, double a, double b, HahnH h, double *u, double *v) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > Ng) return;
+    if (i == 0 || i == Ng) {
+        for (int m = 0; m < M; ++m) { u[m * (Ng + 1) + i] = 0.0; v[m * (Ng + 1) + i] = 0.0; }
+        return;
+    }
+    const double half = (double)i / (2.0 * (double)Ng);   // theta/(2 pi)... theta/2 = pi * half
+    const double ls = log(sinpi(half)), lc = log(cospi(half));
+    for (int m = 0; m < M; ++m) {
+        double su = 0.0, sv = 0.0;
+        for (int l = 0; l <= m; ++l) {
+            const double coef = h.ha[l] * h.hb[m - l];
+            if (coef == 0.0) continue;
+            const double mag = coef * exp(-(l + a + 0.5) * ls - (m - l + b + 0.5) * lc);
+            // theta_{m,l}/pi = (a + l + 1/2)/2 - (a + b + m + 1) theta / (2 pi)
+            const double ph = 0.5 * (a + l + 0.5) - (a + b + m + 1.0) * half;
+            double s, c;
+            sincospi(ph, &s, &c);
+            su = fma(mag, c, su);
+            sv = fma(mag, s, sv);
+        }
+        u[m * (Ng + 1) + i] = su;
+        v[m * (Ng + 1) + i] = sv;
+    }
+}
+
+// envelope g_M(theta_i) of |f_M| (Sec. 2.2); +inf at the end points
+__global__ void k_envelope(int64_t Ng, int M, double a, double b, HahnH h, double *g) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > Ng) return;
+    if (i == 0 || i == Ng) { g[i] = INFINITY; return; }
+    const double half = (double)i / (2.0 * (double)Ng);
+    const double ls = log(sinpi(half)), lc = log(cospi(half));
+    double s = 0.0;
+    for (int l = 0; l <= M; ++l) {
+        const double coef = h.ha[l] * h.hb[M - l];
+        if (coef == 0.0) continue;
+        s += coef * exp(-(l + a + 0.5) * ls - (M - l + b + 0.5) * lc);
+    }
+    g[i] = s;
+}
+
+__global__ void k_box_init(int nk, int *box) {
+    int k = threadIdx.x;
+    if (k < nk) { box[2 * k] = INT_MAX; box[2 * k + 1] = -1; }
+}
+
+// rows where 2 C_{j_k,M} g_M(theta_i) < eps: the smallest and largest such i per block
+__global__ void k_boxes(int64_t Ng, const double *g, int nk, const double *thr, int *box) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x + 1; i < Ng;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double gi = g[i];
+        for (int k = 0; k < nk; ++k) {
+            if (gi < thr[k]) {
+                atomicMin(&box[2 * k], (int)i);
+                atomicMax(&box[2 * k + 1], (int)i);
+            }
+        }
+    }
+}
+
+// deepest box containing each row (boxes are nested), -1 if none
+__global__ void k_rowk(int64_t Ng, int nblk, const int *box3, int *rowk) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > Ng) return;
+    int kk = -1;
+    for (int k = 0; k < nblk; ++k)
+        if (i >= box3[3 * k + 1] && i <= box3[3 * k + 2]) kk = k;
+    rowk[i] = kk;
+}
+
+// --------------------------------------------------------------------------
+// forward-recurrence state at every degree-segment start (plain or
+// Reinsch-modified forward recurrence, Sec. 4.2).  One thread per row.
+//   srow = {row, J, mode, state_base, lane, nseg}
+// --------------------------------------------------------------------------
+__global__ void k_rec_states(int64_t nrows, const int *srow, int64_t Ng, int seg_len, RecTables t, double *states) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nrows) return;
+    const int *r = srow + 6 * q;
+    const int row = r[0], mode = r[2], base = r[3], lane = r[4], nseg = r[5];
+    const int64_t nend = (int64_t)(nseg - 1) * seg_len;
+    if (mode == REC_PLAIN) {
+        const double x = cospi((double)row / (double)Ng);
+        double pm = 0.0, p = 1.0;
+        for (int64_t n = 0; n < nend; ++n) {
+            const double pn = fma(fma(t.A[n], x, t.B[n]), p, -t.C[n] * pm);
+            pm = p;
+            p = pn;
+            if (((n + 1) % seg_len) == 0) {
+                double *st = states + ((int64_t)(base + (n + 1) / seg_len - 1) * 32 + lane) * 2;
+                st[0] = p;
+                st[1] = pm;
+            }
+        }
+    } else {
+        const bool plus = (mode == REC_REINSCH_P1);
+        // delta = x - x0: -2 sin^2(theta/2) at x0 = 1, 2 cos^2(theta/2) at x0 = -1 (Sec. 4.2)
+        double delta;
+        if (plus) {
+            const double s = sinpi((double)row / (2.0 * (double)Ng));
+            delta = -2.0 * s * s;
+        } else {
+            const double s = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
+            delta = 2.0 * s * s;
+        }
+        const double *Ce = plus ? t.Ce_p : t.Ce_m;
+        const double *rf = plus ? t.rf_p : t.rf_m;
+        double p = 1.0, e = 0.0;
+        for (int64_t n = 0; n < nend; ++n) {
+            const double en = fma(t.A[n] * delta, p, Ce[n] * e);
+            p = fma(p, rf[n], en);
+            e = en;
+            if (((n + 1) % seg_len) == 0) {
+                double *st = states + ((int64_t)(base + (n + 1) / seg_len - 1) * 32 + lane) * 2;
+                st[0] = p;
+                st[1] = e;
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// inverse: modified Chebyshev moments by the three-term recurrence of Sec. 3.1
+// with mu_1 = (beta-alpha)/(alpha+beta+2) mu_0, written as the even extension
+// of length 2*Ng used by the DCT-I of Eq. "CCweights".
+// --------------------------------------------------------------------------
+__global__ void k_moments(int64_t Ng, double a, double b, double mu0, double2 *ext) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const double ab = a + b;
+    double mprev = mu0, mcur = (b - a) / (ab + 2.0) * mu0;
+    ext[0] = make_double2(mu0, 0.0);
+    if (Ng >= 1) {
+        ext[1] = make_double2(mcur, 0.0);
+        if (Ng > 1) ext[2 * Ng - 1] = make_double2(mcur, 0.0);
+    }
+    for (int64_t k = 1; k < Ng; ++k) {
+        const double kk = (double)k;
+        const double mnext = -(2.0 * (a - b) * mcur + (ab - kk + 2.0) * mprev) / (ab + kk + 2.0);
+        mprev = mcur;
+        mcur = mnext;
+        ext[k + 1] = make_double2(mcur, 0.0);
+        if (k + 1 < Ng) ext[2 * Ng - (k + 1)] = make_double2(mcur, 0.0);
+    }
+}
+
+// w_i = (eps_i / Ng) Re DFT_{2Ng}(ext)_i,  eps_0 = eps_Ng = 1/2
+__global__ void k_cc_weights(int64_t Ng, const double2 *F, double *w) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > Ng) return;
+    double v = F[i].x / (double)Ng;
+    if (i == 0 || i == Ng) v *= 0.5;
+    w[i] = v;
+}
+
+// s_n = 1/A_n (Eq. "Anab"), by Eq. "Anabasy" for n + min(a, b, a+b, 0) >= 8
+__global__ void k_inv_norm(int64_t N, double a, double b, double *s) {
+    int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n > N) return;
+    const double ab = a + b, nn = (double)n;
+    const double mn = fmin(fmin(a, b), fmin(ab, 0.0));
+    double A;
+    if (nn + mn >= 8.0) {
+        const double r = nn + ab + 1.0, q = nn + 1.0;
+        const double t = (0.5 * nn + a + 0.25) * log1p(-b / r) + (0.5 * nn + b + 0.25) * log1p(-a / r) +
+                         (0.5 * nn + 0.25) * (log1p(a / q) + log1p(b / q));
+        A = exp2(ab + 1.0) / (2.0 * nn + ab + 1.0) * exp(t) * cjt_stirling_S(nn + a + 1.0) *
+            cjt_stirling_S(nn + b + 1.0) / (cjt_stirling_S(nn + ab + 1.0) * cjt_stirling_S(nn + 1.0));
+    } else if (n == 0) {
+        A = exp2(ab + 1.0) * tgamma(a + 1.0) * tgamma(b + 1.0) / tgamma(ab + 2.0);
+    } else {
+        A = exp2(ab + 1.0) * tgamma(nn + a + 1.0) * tgamma(nn + b + 1.0) /
+            ((2.0 * nn + ab + 1.0) * tgamma(nn + ab + 1.0) * tgamma(nn + 1.0));
+    }
+    s[n] = 1.0 / A;
+}
+
+// twiddles omega_L^k = exp(-2 pi i k / L)
+__global__ void k_twiddles(int64_t L, double2 *tw64, float2 *tw32) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= L) return;
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)L, &s, &c);
+    tw64[k] = make_double2(c, s);
+    if (tw32) tw32[k] = make_float2((float)c, (float)s);
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename T> int dalloc(cjt_plan_s *p, T **ptr, int64_t count) {
+    *ptr = nullptr;
+    if (count <= 0) return CJT_OK;
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) {
+        cjt_internal_set_cuda_error(e, "cudaMalloc");
+        return CJT_ENOMEM;
+    }
+    p->allocs.push_back(v);
+    p->device_bytes += (int64_t)count * (int64_t)sizeof(T);
+    *ptr = (T *)v;
+    return CJT_OK;
+}
+
+#define TRY(x)                 \
+    do {                       \
+        int _rc = (x);         \
+        if (_rc) return _rc;   \
+    } while (0)
+
+// ------------------------------------------------------------------------
+// partition of one grid (Sec. 2.2) and the recurrence work that remains
+// ------------------------------------------------------------------------
+int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const HahnH &h, cudaStream_t st) {
+    const double a = p->alpha, b = p->beta;
+    const int M = p->M;
+    gw.Ng = Ng;
+    gw.Jcap = p->N + 1;
+    const int64_t jtop = Ng + 1;
+    gw.nblk = 0;
+    gw.jk.clear(); gw.i1.clear(); gw.i2.clear();
+
+    bool use_asy = p->opts.use_asy >= 0 && Ng >= 2;
+    if (use_asy && p->corner) {
+        // Hahn's series terminates at m = 0 and is exact for every n >= 0: one
+        // block of all degrees on every interior row.
+        gw.jk.push_back(0); gw.i1.push_back(1); gw.i2.push_back(Ng - 1);
+    } else if (use_asy && p->n_M >= 1 && (double)Ng > (double)p->n_M) {
+        const double lr = std::log((double)Ng / (double)p->n_M);
+        double r = p->opts.ratio > 0 ? p->opts.ratio : std::min(1.0 / lr, 0.5);
+        p->ratio = r;
+        const int K = (int)std::ceil(lr / std::log(1.0 / r));
+        std::vector<int64_t> js;
+        std::vector<double> thr;
+        double pw = 1.0;
+        for (int k = 1; k <= K + 1 && k <= 60; ++k) {
+            pw *= r;
+            int64_t j = (int64_t)std::floor(pw * (double)Ng);
+            if (j <= p->n_M || j < 2) break;
+            js.push_back(j);
+            thr.push_back(p->opts.eps / (2.0 * cjt_hahn_C(j, M, a, b)));
+        }
+        if (!js.empty()) {
+            double *d_g = nullptr, *d_thr = nullptr;
+            int *d_b2 = nullptr;
+            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_g, sizeof(double) * (Ng + 1), st));
+            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_thr, sizeof(double) * thr.size(), st));
+            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_b2, sizeof(int) * 2 * thr.size(), st));
+            k_envelope<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, M, a, b, h, d_g);
+            CJT_CUDA_TRY(cudaMemcpyAsync(d_thr, thr.data(), sizeof(double) * thr.size(), cudaMemcpyHostToDevice, st));
+            k_box_init<<<1, 64, 0, st>>>((int)thr.size(), d_b2);
+            unsigned nb = std::min<unsigned>(blocks_for(Ng, 256), 152 * 8);
+            k_boxes<<<nb, 256, 0, st>>>(Ng, d_g, (int)thr.size(), d_thr, d_b2);
+            CJT_CUDA_TRY(cudaGetLastError());
+            std::vector<int> hb(2 * thr.size());
+            CJT_CUDA_TRY(cudaMemcpyAsync(hb.data(), d_b2, sizeof(int) * hb.size(), cudaMemcpyDeviceToHost, st));
+            CJT_CUDA_TRY(cudaStreamSynchronize(st));
+            cudaFreeAsync(d_g, st); cudaFreeAsync(d_thr, st); cudaFreeAsync(d_b2, st);
+            for (size_t k = 0; k < js.size(); ++k) {
+                int lo = hb[2 * k], hi = hb[2 * k + 1];
+                if (hi < lo) break;   // empty box: this and all deeper blocks dropped
+                gw.jk.push_back(js[k]); gw.i1.push_back(lo); gw.i2.push_back(hi);
+            }
+        }
+    }
+    // inverse: blocks whose degrees all exceed N contribute nothing
+    if (inverse) {
+        std::vector<int64_t> jk, i1, i2;
+        for (size_t k = 0; k < gw.jk.size(); ++k)
+            if (gw.jk[k] < gw.Jcap) { jk.push_back(gw.jk[k]); i1.push_back(gw.i1[k]); i2.push_back(gw.i2[k]); }
+        gw.jk.swap(jk); gw.i1.swap(i1); gw.i2.swap(i2);
+    }
+    gw.nblk = (int)gw.jk.size();
+
+    // deepest-box index per row and the box list on the device
+    TRY(dalloc(p, &gw.d_rowk, Ng + 1));
+    if (gw.nblk > 0) {
+        std::vector<int> box3(3 * gw.nblk);
+        for (int k = 0; k < gw.nblk; ++k) {
+            box3[3 * k] = (int)gw.jk[k]; box3[3 * k + 1] = (int)gw.i1[k]; box3[3 * k + 2] = (int)gw.i2[k];
+        }
+        TRY(dalloc(p, &gw.d_box, 3 * gw.nblk));
+        CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_box, box3.data(), sizeof(int) * box3.size(), cudaMemcpyHostToDevice, st));
+        TRY(dalloc(p, &gw.d_u, (int64_t)M * (Ng + 1)));
+        TRY(dalloc(p, &gw.d_v, (int64_t)M * (Ng + 1)));
+        k_hahn_uv<<<blocks_for(Ng + 1, 128), 128, 0, st>>>(Ng, M, a, b, h, gw.d_u, gw.d_v);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
+    if (gw.nblk > 0) {
+        // Item scales.  Forward: the transform input C_{n,m} c_n on degrees n >= j_k is
+        // at most C_{j_k,m} |c| (C_{n,m} decreases in n, Lemma of Sec. 2.2).  Inverse:
+        // the input (u_m + i v_m) g on rows [i1, i2] is bounded by the envelope g_m
+        // (Sec. 2.2), which is unimodal, so its maximum over the box is at an end row.
+        std::vector<double> sc(2 * (size_t)gw.nblk * M);
+        for (int k = 0; k < gw.nblk; ++k) {
+            for (int m = 0; m < M; ++m) {
+                double mag;
+                if (!inverse) {
+                    mag = cjt_hahn_C(gw.jk[k], m, a, b);
+                } else {
+                    auto gm = [&](int64_t i) {
+                        const double half = (double)i / (2.0 * (double)Ng);
+                        const double ls = std::log(std::sin(M_PI * half)), lc = std::log(std::cos(M_PI * half));
+                        double s = 0.0;
+                        for (int l = 0; l <= m; ++l)
+                            s += h.ha[l] * h.hb[m - l] * std::exp(-(l + a + 0.5) * ls - (m - l + b + 0.5) * lc);
+                        return s;
+                    };
+                    mag = std::max(gm(gw.i1[k]), gm(gw.i2[k]));
+                }
+                int e = 0;
+                if (mag > 0 && std::isfinite(mag)) std::frexp(mag, &e);
+                sc[2 * ((size_t)k * M + m)] = std::ldexp(1.0, -e);
+                sc[2 * ((size_t)k * M + m) + 1] = std::ldexp(1.0, e);
+            }
+        }
+        TRY(dalloc(p, &gw.d_scale, (int64_t)sc.size()));
+        CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_scale, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, st));
+        CJT_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    k_rowk<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, gw.nblk, gw.d_box, gw.d_rowk);
+    CJT_CUDA_TRY(cudaGetLastError());
+
+    // ---- recurrence work: J(i) per row, chunks of <= 32 rows, degree segments
+    const int S = p->seg_len;
+    auto J_of = [&](int64_t i) -> int64_t {
+        int64_t J = jtop;
+        for (int k = 0; k < gw.nblk; ++k)
+            if (i >= gw.i1[k] && i <= gw.i2[k]) J = gw.jk[k];
+        return std::min(J, gw.Jcap);
+    };
+    auto mode_of = [&](int64_t i) -> int {
+        if (4 * i <= Ng) return REC_REINSCH_P1;
+        if (4 * i >= 3 * Ng) return REC_REINSCH_M1;
+        return REC_PLAIN;
+    };
+    struct Chunk { int64_t row0; int nrows; int64_t J; int mode; };
+    std::vector<Chunk> chunks;
+    for (int64_t i = 0; i <= Ng;) {
+        int64_t J = J_of(i);
+        int md = mode_of(i);
+        Chunk c{i, 1, J, md};
+        int64_t k = i + 1;
+        while (k <= Ng && c.nrows < 32 && J_of(k) == J && mode_of(k) == md) { ++c.nrows; ++k; }
+        chunks.push_back(c);
+        i = k;
+    }
+    gw.nchunks = (int64_t)chunks.size();
+    std::vector<RecItem> items;
+    std::vector<int> row_nseg(Ng + 1);
+    std::vector<int64_t> row_base(Ng + 1);
+    std::vector<int> srow;
+    int64_t out_f = 0, out_i = 0, nstate = 0, steps = 0;
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        const Chunk &ch = chunks[c];
+        int nseg = (int)((ch.J + S - 1) / S);
+        for (int r = 0; r < ch.nrows; ++r) {
+            row_nseg[ch.row0 + r] = nseg;
+            row_base[ch.row0 + r] = out_f + r;
+        }
+        steps += ch.J * ch.nrows;
+        int state_base = (int)nstate;
+        for (int s = 0; s < nseg; ++s) {
+            RecItem it;
+            it.row0 = (int)ch.row0;
+            it.nrows = ch.nrows;
+            it.a = s * S;
+            it.b = (int)std::min<int64_t>((int64_t)(s + 1) * S, ch.J);
+            it.mode = ch.mode;
+            it.state = s == 0 ? -1 : state_base + s - 1;
+            if (!inverse) {
+                it.out = out_f + (int64_t)s * 32;
+            } else {
+                it.out = out_i;
+                out_i += it.b - it.a;
+            }
+            items.push_back(it);
+        }
+        if (nseg > 1) {
+            for (int r = 0; r < ch.nrows; ++r) {
+                int row = (int)(ch.row0 + r);
+                int v[6] = {row, (int)ch.J, ch.mode, state_base, r, nseg};
+                srow.insert(srow.end(), v, v + 6);
+            }
+            nstate += nseg - 1;
+        }
+        out_f += (int64_t)nseg * 32;
+    }
+    gw.rec_steps = steps;
+    gw.nstate = nstate;
+    gw.nsrow = (int64_t)srow.size() / 6;
+    gw.npartials = inverse ? out_i : out_f;
+
+    // inverse: contributions to each degree segment, in a fixed order
+    if (inverse) {
+        gw.nsegs = (gw.Jcap + S - 1) / S;
+        std::vector<std::vector<size_t>> per(gw.nsegs);
+        for (size_t q = 0; q < items.size(); ++q) per[items[q].a / S].push_back(q);
+        std::vector<int64_t> ptr(gw.nsegs + 1, 0), sout;
+        std::vector<int> sb;
+        for (int64_t s = 0; s < gw.nsegs; ++s) {
+            for (size_t q : per[s]) { sout.push_back(items[q].out); sb.push_back(items[q].b); }
+            ptr[s + 1] = (int64_t)sout.size();
+        }
+        TRY(dalloc(p, &gw.d_seg_ptr, gw.nsegs + 1));
+        TRY(dalloc(p, &gw.d_seg_out, (int64_t)sout.size()));
+        TRY(dalloc(p, &gw.d_seg_b, (int64_t)sb.size()));
+        CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_seg_ptr, ptr.data(), sizeof(int64_t) * ptr.size(), cudaMemcpyHostToDevice, st));
+        if (!sout.empty()) {
+            CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_seg_out, sout.data(), sizeof(int64_t) * sout.size(), cudaMemcpyHostToDevice, st));
+            CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_seg_b, sb.data(), sizeof(int) * sb.size(), cudaMemcpyHostToDevice, st));
+        }
+        CJT_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        TRY(dalloc(p, &gw.d_row_base, Ng + 1));
+        TRY(dalloc(p, &gw.d_row_nseg, Ng + 1));
+        CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_row_base, row_base.data(), sizeof(int64_t) * row_base.size(),
+                                     cudaMemcpyHostToDevice, st));
+        CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_row_nseg, row_nseg.data(), sizeof(int) * row_nseg.size(),
+                                     cudaMemcpyHostToDevice, st));
+        CJT_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    // longest items first: the block scheduler then balances the SMs
+    std::stable_sort(items.begin(), items.end(),
+                     [](const RecItem &x, const RecItem &y) { return (x.b - x.a) > (y.b - y.a); });
+    gw.nitems = (int64_t)items.size();
+    TRY(dalloc(p, &gw.d_items, gw.nitems));
+    if (gw.nitems)
+        CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_items, items.data(), sizeof(RecItem) * items.size(), cudaMemcpyHostToDevice, st));
+    TRY(dalloc(p, &gw.d_partials, std::max<int64_t>(gw.npartials, 1)));
+    TRY(dalloc(p, &gw.d_states, std::max<int64_t>(nstate * 64, 1)));
+    CJT_CUDA_TRY(cudaMemsetAsync(gw.d_states, 0, sizeof(double) * std::max<int64_t>(nstate * 64, 1), st));
+    if (gw.nsrow > 0) {
+        TRY(dalloc(p, &gw.d_srow, (int64_t)srow.size()));
+        CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_srow, srow.data(), sizeof(int) * srow.size(), cudaMemcpyHostToDevice, st));
+        // one row per thread; 32-thread blocks spread the long chains over the SMs
+        k_rec_states<<<blocks_for(gw.nsrow, 32), 32, 0, st>>>(gw.nsrow, gw.d_srow, Ng, S, p->rt, gw.d_states);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
+    CJT_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope
+    return CJT_OK;
+}
+
+}  // namespace
+
+int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
+    const int64_t N = p->N;
+    const double a = p->alpha, b = p->beta;
+    p->corner = (std::fabs(std::fabs(a) - 0.5) == 0.0) && (std::fabs(std::fabs(b) - 0.5) == 0.0);
+    p->M = p->corner ? 1 : p->opts.M;
+    const int M = p->M;
+
+    HahnH h;
+    for (int l = 0; l <= 20; ++l) { h.ha[l] = cjt_hahn_h(l, a); h.hb[l] = cjt_hahn_h(l, b); }
+    // n_M from the envelope at pi/2 (Sec. 2.2): g_M(pi/2) = sum_l h_l(a) h_{M-l}(b) 2^{(M+a+b+1)/2}
+    {
+        double gh = 0.0;
+        for (int l = 0; l <= M; ++l) gh += h.ha[l] * h.hb[M - l];
+        gh *= std::pow(2.0, 0.5 * (M + a + b + 1.0));
+        if (gh > 0) {
+            double v = std::pow(p->opts.eps * std::ldexp(1.0, 2 * M - 1) * kSqrtPi / gh, -1.0 / (M + 0.5));
+            p->n_M = (int64_t)std::floor(v);
+        } else {
+            p->n_M = 0;
+        }
+    }
+
+    // 1c: recurrence tables for degrees 0..N+1
+    p->Jcap = N + 1;
+    const int64_t nt = N + 2;
+    TRY(dalloc(p, &p->d_tabs, 11 * nt));
+    double *q = p->d_tabs;
+    p->rt.A = q; p->rt.B = q + nt; p->rt.C = q + 2 * nt;
+    p->rt.Cr_p = q + 3 * nt; p->rt.rbinv_p = q + 4 * nt; p->rt.Ce_p = q + 5 * nt; p->rt.rf_p = q + 6 * nt;
+    p->rt.Cr_m = q + 7 * nt; p->rt.rbinv_m = q + 8 * nt; p->rt.Ce_m = q + 9 * nt; p->rt.rf_m = q + 10 * nt;
+    k_rec_tables<<<blocks_for(nt, 256), 256, 0, st>>>(nt - 1, a, b, p->rt);
+    CJT_CUDA_TRY(cudaGetLastError());
+
+    // Hahn coefficients for m = 0..M (row M is the partition's remainder term)
+    TRY(dalloc(p, &p->d_Cnm, (int64_t)(M + 1) * (N + 1)));
+    {
+        dim3 g(blocks_for(N + 1, 256), M + 1);
+        k_hahn_C<<<g, 256, 0, st>>>(N, M + 1, a, b, p->d_Cnm);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
+
+    const bool fwd = p->opts.directions & CJT_FWD, inv = p->opts.directions & CJT_INV;
+    if (fwd) TRY(build_grid(p, p->fw, N, false, h, st));
+    if (inv) TRY(build_grid(p, p->iv, 2 * N, true, h, st));
+
+    // transforms: forward ASY/DCT length 2N, inverse 4N
+    const bool fp32 = p->opts.precision == CJT_MIXED;
+    p->Lf = fwd ? 2 * N : 0;
+    p->Li = inv ? 4 * N : 0;
+    p->Ltab = std::max<int64_t>(std::max(p->Lf, p->Li), 2);
+    TRY(dalloc(p, (double2 **)&p->d_tw64, p->Ltab));
+    if (fp32) TRY(dalloc(p, (float2 **)&p->d_tw32, p->Ltab));
+    k_twiddles<<<blocks_for(p->Ltab, 256), 256, 0, st>>>(p->Ltab, (double2 *)p->d_tw64, (float2 *)p->d_tw32);
+    CJT_CUDA_TRY(cudaGetLastError());
+
+    const size_t csz = fp32 ? sizeof(float2) : sizeof(double2);
+    p->npair_f = (p->fw.nblk * M + 1) / 2;
+    p->npair_i = (p->iv.nblk * M + 1) / 2;
+    int64_t scratch = 0;
+    if (p->npair_f) {
+        void *v;
+        CJT_CUDA_TRY(cudaMalloc(&v, csz * p->npair_f * p->Lf));
+        p->allocs.push_back(v); p->device_bytes += csz * p->npair_f * p->Lf; p->d_fft_f = v;
+        scratch = std::max(scratch, cjt_fft_scratch_elems(p->Lf, p->npair_f));
+    }
+    if (p->npair_i) {
+        void *v;
+        CJT_CUDA_TRY(cudaMalloc(&v, csz * p->npair_i * p->Li));
+        p->allocs.push_back(v); p->device_bytes += csz * p->npair_i * p->Li; p->d_fft_i = v;
+        scratch = std::max(scratch, cjt_fft_scratch_elems(p->Li, p->npair_i));
+    }
+    if (scratch) {
+        void *v;
+        CJT_CUDA_TRY(cudaMalloc(&v, csz * scratch));
+        p->allocs.push_back(v); p->device_bytes += csz * scratch; p->d_fft_scratch = v;
+        p->scratch_elems = scratch;
+    }
+    const int64_t Ld = std::max<int64_t>(std::max(p->Lf, p->Li), 2);
+    TRY(dalloc(p, (double2 **)&p->d_dct, Ld));
+    if (Ld > 4096) TRY(dalloc(p, (double2 **)&p->d_dct_scratch, Ld));
+    TRY(dalloc(p, &p->d_y, 2 * N + 2));
+    TRY(dalloc(p, &p->d_in, N + 1));
+    TRY(dalloc(p, &p->d_out, N + 1));
+
+    if (inv && N >= 1) {
+        const int64_t Ng = 2 * N;
+        TRY(dalloc(p, &p->d_g, Ng + 1));
+        TRY(dalloc(p, &p->d_w, Ng + 1));
+        TRY(dalloc(p, &p->d_s, N + 1));
+        const double mu0 = std::exp2(a + b + 1.0) * std::tgamma(a + 1.0) * std::tgamma(b + 1.0) / std::tgamma(a + b + 2.0);
+        CJT_CUDA_TRY(cudaMemsetAsync(p->d_dct, 0, sizeof(double2) * 2 * Ng, st));
+        k_moments<<<1, 1, 0, st>>>(Ng, a, b, mu0, (double2 *)p->d_dct);
+        CJT_CUDA_TRY(cudaGetLastError());
+        TRY(cjt_fft_pow2(p->d_dct, p->d_dct_scratch, 2 * Ng, 1, p->d_tw64, p->Ltab, false, st));
+        k_cc_weights<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)p->d_dct, p->d_w);
+        k_inv_norm<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, a, b, p->d_s);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
+    CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
+    CJT_CUDA_TRY(cudaStreamSynchronize(st));
+    return CJT_OK;
+}

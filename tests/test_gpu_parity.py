@@ -1,0 +1,196 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerance (forward and inverse, FP64 form): max |c_gpu - c_oracle| <= 1e-12 * ||c_in||_1,
+the bound stated for this library.  At full size (N = 2^16, 2^18) the oracle
+evaluates sampled grid values in double-double; the GPU result is checked
+through the identities that hold at any size:
+  forward:  sum_k c_cheb_k T_k(x_j) = sum_n c_jac_n P_n(x_j) at sampled x_j
+  inverse:  sum_n c_jac_n P_n(x_j)  = sum_k c_cheb_k T_k(x_j) at sampled x_j
+and by the round trip inverse(forward(c)) = c.
+"""
+import numpy as np
+import pytest
+
+from paper_1602_02618_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+PARAMS = [(0.1, -0.3), (0.45, 0.45), (-0.45, 0.2), (0.0, 0.0), (0.125, 0.375), (-0.5, -0.5), (0.5, 0.5),
+          (0.5, -0.5), (-0.5, 0.3), (0.37, -0.5)]
+
+
+@pytest.fixture(scope="module")
+def cjt():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1602_02618_gb300 import cjt as mod
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return mod
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def l1(c):
+    return float(np.abs(c).sum())
+
+
+def run_fwd(cjt, plan, c):
+    y = cjt.cjt_forward(plan, dev(c))
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def run_inv(cjt, plan, c):
+    y = cjt.cjt_inverse(plan, dev(c))
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+@pytest.mark.parametrize("alpha,beta", PARAMS)
+@pytest.mark.parametrize("N", [1, 2, 4, 8, 64, 256, 1024, 4096])
+def test_forward_matches_oracle(cjt, orc, N, alpha, beta):
+    c = inputs.decaying_coefficients(N, 1.0, inputs.BASE_SEED + N)
+    plan = cjt.Plan(N, alpha, beta)
+    got = run_fwd(cjt, plan, c)
+    ref = orc.forward(c, alpha, beta)
+    assert np.max(np.abs(got - ref)) <= TOL * l1(c)
+
+
+@pytest.mark.parametrize("alpha,beta", PARAMS)
+@pytest.mark.parametrize("N", [1, 2, 4, 8, 64, 256, 1024, 4096])
+def test_inverse_matches_oracle(cjt, orc, N, alpha, beta):
+    c = inputs.decaying_coefficients(N, 1.0, inputs.BASE_SEED + 7 * N)
+    plan = cjt.Plan(N, alpha, beta)
+    got = run_inv(cjt, plan, c)
+    ref = orc.inverse(c, alpha, beta)
+    assert np.max(np.abs(got - ref)) <= TOL * l1(c)
+
+
+@pytest.mark.parametrize("opts", [dict(M=3), dict(M=5), dict(M=10), dict(M=13), dict(M=20), dict(use_asy=-1),
+                                  dict(seg_len=32), dict(seg_len=96), dict(ratio=0.5), dict(ratio=0.2),
+                                  dict(M=13, seg_len=64)])
+def test_options_do_not_change_the_result(cjt, orc, opts):
+    """The partition, M and the work split change only the rounding (Sec. 2.2)."""
+    N, a, b = 4096, 0.1, -0.3
+    c = inputs.decaying_coefficients(N, 1.5, 99)
+    plan = cjt.Plan(N, a, b, **opts)
+    info = plan.info()
+    assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, a, b))) <= TOL * l1(c), info
+    assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, a, b))) <= TOL * l1(c), info
+
+
+def test_partition_matches_paper_shape(cjt):
+    """N = 1024, (0.1, -0.3), M = 7: two asymptotic blocks and most of the matrix by ASY."""
+    plan = cjt.Plan(1024, 0.1, -0.3, M=7)
+    info = plan.info()
+    assert info["n_M"] > 50 and info["nblk_fwd"] >= 1
+    assert info["rec_steps_fwd"] < 0.6 * 1025 ** 2
+
+
+@pytest.mark.parametrize("N", [1 << 14])
+def test_forward_inverse_16384_elementwise(cjt, orc, N):
+    a, b = inputs.jacobi_parameters(inputs.BASE_SEED + 1001)
+    c = inputs.decaying_coefficients(N, 1.5, inputs.BASE_SEED + 1)
+    plan = cjt.Plan(N, a, b)
+    assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, a, b))) <= TOL * l1(c)
+    assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, a, b))) <= TOL * l1(c)
+
+
+def test_forward_inverse_65536_elementwise(cjt, orc):
+    N = 1 << 16
+    a, b = inputs.jacobi_parameters(inputs.BASE_SEED + 1002)
+    c = inputs.decaying_coefficients(N, 1.5, inputs.BASE_SEED + 2)
+    plan = cjt.Plan(N, a, b)
+    assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, a, b))) <= TOL * l1(c)
+    assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, a, b))) <= TOL * l1(c)
+
+
+@pytest.mark.parametrize("logN", [16, 18])
+def test_full_size_properties(cjt, orc, logN):
+    """At any size: value-space identities at sampled Lobatto points (double-double oracle),
+    the exact first inverse coefficient c_jac_0 = sum_k c_k mu_k / mu_0 (Eq. cjintdefn, n = 0),
+    and the round trip inverse(forward(c)) = c."""
+    N = 1 << logN
+    a, b = inputs.jacobi_parameters(inputs.BASE_SEED + 1000 + logN)
+    c = inputs.decaying_coefficients(N, 1.5, inputs.BASE_SEED + logN)
+    plan = cjt.Plan(N, a, b)
+    rng = inputs.rng(5)
+    j = np.unique(np.concatenate([np.arange(0, 40), N - np.arange(0, 40), rng.integers(0, N + 1, 400)]))
+    # forward: sum_k c_cheb_k T_k(x_j) = sum_n c_n P_n(x_j)
+    fwd = run_fwd(cjt, plan, c)
+    y_ref = orc.jacobi_series(c, a, b, j, N)
+    y_got = orc.cheb_series(fwd, j, N)
+    assert np.max(np.abs(y_got - y_ref)) <= TOL * l1(c)
+    # inverse: sum_n c_jac_n P_n(x_j) = sum_k c_k T_k(x_j).  A coefficient error within the
+    # tolerance moves the value at x_j by at most TOL ||c||_1 sum_n |P_n(x_j)|.
+    inv = run_inv(cjt, plan, c)
+    v_ref = orc.cheb_series(c, j, N)
+    v_got = orc.jacobi_series(inv, a, b, j, N)
+    for q in range(0, j.size, 37):
+        bound = TOL * l1(c) * np.abs(orc.jacobi_values(N, a, b, int(j[q]), N)).sum()
+        assert abs(v_got[q] - v_ref[q]) <= bound
+    mu = orc.moments(N, a, b)
+    assert abs(inv[0] - np.dot(c, mu) / mu[0]) <= TOL * l1(c)
+    # round trips
+    back = run_inv(cjt, plan, fwd)
+    assert np.max(np.abs(back - c)) <= TOL * l1(c)
+    again = run_fwd(cjt, plan, inv)
+    assert np.max(np.abs(again - c)) <= TOL * l1(c)
+
+
+def test_in_place_and_determinism(cjt, orc):
+    N, a, b = 2048, 0.3, -0.2
+    c = inputs.decaying_coefficients(N, 1.0, 3)
+    plan = cjt.Plan(N, a, b)
+    x = dev(c)
+    y1 = cjt.cjt_forward(plan, x).cpu().numpy()
+    y2 = cjt.cjt_forward(plan, x).cpu().numpy()
+    assert np.array_equal(y1, y2)
+    z = dev(c)
+    cjt.cjt_forward(plan, z, z)   # aliasing input and output
+    torch.cuda.synchronize()
+    assert np.array_equal(z.cpu().numpy(), y1)
+    w = dev(c)
+    cjt.cjt_inverse(plan, w, w)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(w.cpu().numpy() - orc.inverse(c, a, b))) <= TOL * l1(c)
+
+
+def test_execute_host_matches_device(cjt):
+    N, a, b = 1024, -0.2, 0.4
+    c = inputs.decaying_coefficients(N, 1.0, 4)
+    plan = cjt.Plan(N, a, b)
+    h = cjt.cjt_execute_host(plan, cjt.CJT_FWD, c)
+    d = run_fwd(cjt, plan, c)
+    assert np.array_equal(h, d)
+    h = cjt.cjt_execute_host(plan, cjt.CJT_INV, c)
+    d = run_inv(cjt, plan, c)
+    assert np.array_equal(h, d)
+
+
+def test_error_codes(cjt):
+    with pytest.raises(cjt.CJTError) as e:
+        cjt.Plan(64, 0.6, 0.0)
+    assert e.value.code == cjt.CJT_EDOMAIN
+    with pytest.raises(cjt.CJTError) as e:
+        cjt.Plan(-1, 0.0, 0.0)
+    assert e.value.code == cjt.CJT_EINVAL
+    with pytest.raises(cjt.CJTError) as e:
+        cjt.Plan(64, 0.0, 0.0, M=21)
+    assert e.value.code == cjt.CJT_EINVAL
+    p = cjt.Plan(64, 0.0, 0.0, directions=cjt.CJT_FWD)
+    with pytest.raises(cjt.CJTError) as e:
+        cjt.cjt_inverse(p, dev(np.zeros(65)))
+    assert e.value.code == cjt.CJT_EDIRECTION
+
+
+def test_identity_at_N0(cjt):
+    p = cjt.Plan(0, 0.2, 0.1)
+    assert run_fwd(cjt, p, np.array([2.5]))[0] == 2.5
+    assert run_inv(cjt, p, np.array([-1.5]))[0] == -1.5
