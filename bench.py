@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the Chebyshev--Jacobi transform library on GB300.
+
+Workload (one "step"): the forward and the inverse transform, one transform
+per call, of each of N in {2^12, 2^14, 2^16, 2^18} with its own
+(alpha, beta) ~ U[-0.45, 0.45]^2 and coefficients c_n = g_n/(n+1)^1.5,
+g_n ~ N(0,1) (seeded; see paper_1602_02618_gb300/inputs.py).  The forward
+transform maps c; the inverse maps the forward result back (round trip).
+Plans are built (and autotuned) before the timed region; inputs are resident
+in HBM when it starts.  The L2 cache is flushed (a 512 MiB write) between
+timed steps, outside the timed events.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead
+(rank 0 only), on a bounded sample of the same workload.
+
+Multi-GPU: transforms are independent, so `--gpus N` under torchrun runs N
+replicas of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "transform coeffs/sec (batched, mixed-precision vs plain FP64) at stated error; p50/p99"
+LOGNS = (12, 14, 16, 18)
+FP64_PEAK_DERIVED = 152 * 2070e6 * 4.0   # 152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM (1.25 TFLOP/s nominal)
+
+
+def workload():
+    from paper_1602_02618_gb300 import inputs
+    return inputs.single_workload(Ns=tuple(1 << k for k in LOGNS))
+
+
+def workload_desc(precision):
+    return ("forward+inverse CJT singly, %s, N in {2^12,2^14,2^16,2^18}, alpha,beta~U[-0.45,0.45] per transform, "
+            "c_n=g_n/(n+1)^1.5, g~N(0,1)" % ("FP64" if precision == "fp64" else "mixed (FP32 ASY transforms)"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": float(np.median(power)) if power else None}
+
+
+def run_reference(args):
+    """The CPU oracle on the host cores: each step runs the oracle's forward and inverse
+    transform on the N = 2^12 and N = 2^14 items of the workload (full transforms) and
+    extrapolates the N = 2^16 and 2^18 items by the oracle's exact O(N^2) cost."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    orc.build()
+    items = workload()
+    coeffs = 2 * sum(N + 1 for N, _, _, _ in items)
+    small = [it for it in items if it[0] <= (1 << 14)]
+    def step():
+        t = {}
+        for N, a, b, c in small:
+            t0 = time.perf_counter()
+            f = orc.forward(c, a, b)
+            orc.inverse(f, a, b)
+            t[N] = time.perf_counter() - t0
+        Nmax = max(t)
+        return sum(t[N] if N in t else t[Nmax] * (N / Nmax) ** 2 for N, _, _, _ in items)
+    for _ in range(args.warmup):
+        step()
+    times = [step() for _ in range(args.steps)]
+    total = float(np.sum(times))
+    value = coeffs * len(times) / total
+    cores = os.cpu_count()
+    sample = ("oracle forward+inverse (double-double, O(N^2)) run in full at N=2^12 and 2^14; N=2^16, 2^18 "
+              "extrapolated as t(2^14)*(N/2^14)^2")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (double-double)",
+        "data": "synthetic", "config": {"workload": workload_desc("fp64")},
+        "cpu_baseline": {"value": value, "unit": "coeffs/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "coeffs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def cpu_baseline_sample():
+    """The oracle as it stands, timed once on the host cores (same sample as --impl reference)."""
+    from oracle import oracle as orc
+    orc.build()
+    items = workload()
+    coeffs = 2 * sum(N + 1 for N, _, _, _ in items)
+    t = {}
+    for N, a, b, c in items:
+        if N > (1 << 14):
+            continue
+        t0 = time.perf_counter()
+        f = orc.forward(c, a, b)
+        orc.inverse(f, a, b)
+        t[N] = time.perf_counter() - t0
+    Nmax = max(t)
+    total = sum(t[N] if N in t else t[Nmax] * (N / Nmax) ** 2 for N, _, _, _ in items)
+    return {"value": coeffs / total, "unit": "coeffs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle forward+inverse (double-double) in full at N=2^12, 2^14; N=2^16, 2^18 extrapolated "
+                      "as t(2^14)*(N/2^14)^2; total %.1f s measured" % sum(t.values())}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--fixed-options", default="", help="e.g. M=13,seg_len=1024 (applied to every N; no autotune)")
+    ap.add_argument("--only-logn", type=int, default=0, help="profile runs: one size of the workload only")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1602_02618_gb300 import autotune, cjt
+
+    precision = cjt.CJT_FP64 if args.precision == "fp64" else cjt.CJT_MIXED
+    items = workload()
+    if args.only_logn:
+        items = [it for it in items if it[0] == (1 << args.only_logn)]
+    fixed = {}
+    for kv in filter(None, args.fixed_options.split(",")):
+        k, v = kv.split("=")
+        fixed[k.strip()] = int(v)
+    plans, xs, ys, zs, chosen = [], [], [], [], []
+    for N, a, b, c in items:
+        opts = dict(fixed) if (fixed or args.no_autotune) else autotune.best_options(N, a, b, precision)
+        plans.append(cjt.Plan(N, a, b, precision=precision, **opts))
+        chosen.append(opts)
+        xs.append(torch.from_numpy(c).to(dev))
+        ys.append(torch.empty_like(xs[-1]))
+        zs.append(torch.empty_like(xs[-1]))
+    coeffs_per_step = 2 * sum(N + 1 for N, _, _, _ in items)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for p, x, y, z in zip(plans, xs, ys, zs):
+            cjt.cjt_forward(p, x, y)
+            cjt.cjt_inverse(p, y, z)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for p in plans:
+        p.set_profiling(True)
+        p.profile()  # clear
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        torch.cuda.nvtx.range_push("timed")
+        step()
+        torch.cuda.nvtx.range_pop()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
+    total_s = float(step_ms.sum()) / 1e3
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+    value = coeffs_per_step * args.steps * world / total_s
+
+    # stage times measured live during the timed region
+    prof = {}
+    launches = 0
+    infos = [p.info() for p in plans]
+    for p, inf in zip(plans, infos):
+        for st, (ms, cnt) in p.profile().items():
+            a = prof.setdefault(st, [0.0, 0, 0.0])
+            a[0] += ms
+            a[1] += cnt
+        launches += (inf["kernels_fwd"] + inf["kernels_inv"]) * args.steps
+    for p in plans:
+        p.set_profiling(False)
+    # algorithmic work per launch: 8 flops per recurrence step (sum_i J(i)), 2.5 L log2 L per length-L transform
+    rec_flops = {"fwd_rec": sum(8.0 * inf["rec_steps_fwd"] for inf in infos) * args.steps,
+                 "inv_rec": sum(8.0 * inf["rec_steps_inv"] for inf in infos) * args.steps}
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    try:
+        fp64_meas = cjt.microbench_fma(True)
+    except Exception:
+        fp64_meas = None
+    roof = None
+    if dom in rec_flops:
+        achieved = rec_flops[dom] / (prof[dom][0] * 1e-3)
+        peak = FP64_PEAK_DERIVED
+        roof = {"kernel": "k_rec_fwd" if dom == "fwd_rec" else "k_rec_inv", "bound": "alu",
+                "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": "derived FP64 pipe peak (152 SMs x 2.07 GHz x 2 DFMA/clk)",
+                "fp64_fma_measured_tflops": fp64_meas / 1e12 if fp64_meas else None,
+                "time_share": prof[dom][0] / sum(v[0] for v in prof.values())}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_DERIVED / 1e12,
+                "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "fp64_fma_measured_tflops": fp64_meas / 1e12 if fp64_meas else None}
+    try:
+        roof["fp32_fma_measured_tflops"] = cjt.microbench_fma(False) / 1e12
+    except Exception:
+        pass
+
+    # accuracy of the round trip (one step)
+    err = max(float((z - x).abs().max()) / float(x.abs().sum()) for x, z in zip(xs, zs))
+
+    # end to end through the C ABI from pinned host memory
+    hx = [torch.from_numpy(c).pin_memory() for _, _, _, c in items]
+    hy = [torch.empty_like(h).pin_memory() for h in hx]
+    hz = [torch.empty_like(h).pin_memory() for h in hx]
+    def e2e_step():
+        for p, x, y, z in zip(plans, hx, hy, hz):
+            cjt.cjt_execute_host(p, cjt.CJT_FWD, x.numpy(), y.numpy())
+            cjt.cjt_execute_host(p, cjt.CJT_INV, y.numpy(), z.numpy())
+    ksteps = max(3, min(args.steps, 20))
+    e2e_s = float("nan")
+    if not args.no_e2e:
+        e2e_step()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            e2e_step()
+        e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    bytes_io = 2 * sum(8 * (N + 1) for N, _, _, _ in items)
+
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline_sample()
+        out = {
+            "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(step_ms.mean()),
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == cjt.CJT_FP64 else "f32 ASY transforms + f64",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(args.precision), "N": [1 << k for k in LOGNS],
+                       "options": chosen, "l2": "flushed between steps (512 MiB write, outside timed events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "error": {"round_trip_max_abs_over_l1": err},
+            "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": (coeffs_per_step * ksteps * world / e2e_s) if e2e_s == e2e_s else None, "unit": "coeffs/s",
+                    "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

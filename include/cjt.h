@@ -95,7 +95,21 @@ typedef struct {
     int64_t rec_items_fwd, rec_items_inv;
     int64_t device_bytes;    /* device memory owned by the plan                        */
     double plan_ms;          /* wall time of cjt_plan                                  */
+    int64_t kernels_fwd, kernels_inv;   /* kernel launches of one execution              */
 } cjt_plan_info;
+
+/* Stages reported by cjt_get_profile (forward 0-4, inverse 5-9). */
+#define CJT_STAGE_FWD_REC 0      /* Clenshaw--Smith / Reinsch recurrence           */
+#define CJT_STAGE_FWD_PACK 1     /* C_{n,m} c_n scaling and packing                */
+#define CJT_STAGE_FWD_FFT 2      /* DCT-I/DST-I transforms of the blocks           */
+#define CJT_STAGE_FWD_COMBINE 3  /* diagonal scalings u_m, v_m and accumulation    */
+#define CJT_STAGE_FWD_DCT 4      /* final inverse DCT-I                            */
+#define CJT_STAGE_INV_FRONT 5    /* T_2N^T [c; 0] and Clenshaw--Curtis weights     */
+#define CJT_STAGE_INV_PACK 6     /* (u_m + i v_m) g packing                        */
+#define CJT_STAGE_INV_FFT 7      /* transposed DCT-I/DST-I transforms              */
+#define CJT_STAGE_INV_REC 8      /* transposed (forward) recurrence                */
+#define CJT_STAGE_INV_COMBINE 9  /* C_{n,m} scaling, accumulation, 1/A_n           */
+#define CJT_NSTAGE 10
 
 typedef struct cjt_plan_s *cjt_plan_t;
 
@@ -161,6 +175,24 @@ int cjt_execute_host(cjt_plan_t plan, int direction, const double *in_host, doub
  */
 int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, const int64_t *offsets,
                         const double *in_dev, double *out_dev, void *stream);
+
+/*
+ * Stage profiling.  cjt_set_profiling(plan, 1) makes every later execution of
+ * the plan record a CUDA event pair around each stage on the launching stream;
+ * cjt_get_profile waits for those events and returns, per stage s < n, the
+ * summed milliseconds ms[s] and the number of timed launches counts[s]
+ * (either pointer may be NULL), then clears the record.  Profiling adds one
+ * event record per stage boundary and is off by default.
+ */
+int cjt_set_profiling(cjt_plan_t plan, int on);
+int cjt_get_profile(cjt_plan_t plan, double *ms, int64_t *counts, int n);
+
+/*
+ * Peak arithmetic microbenchmark (diagnostic, no counterpart in the paper):
+ * dependent-chain fused multiply-adds on every SM, FP64 (fp64 = 1) or FP32
+ * (fp64 = 0).  Writes the measured rate in FLOP/s to *flops (2 per FMA).
+ */
+int cjt_microbench_fma(int fp64, double *flops, void *stream);
 
 /* Wait for `stream` and report any CUDA error raised by earlier work. */
 int cjt_sync(void *stream);

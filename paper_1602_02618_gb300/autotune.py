@@ -1,0 +1,104 @@
+"""Plan autotuner: picks the number of Hahn terms M and the recurrence work
+split (degree-segment length) for a given N and precision by timing candidate
+plans on the current GPU (forward + inverse, CUDA events), and caches the
+choice in a JSON file.
+
+Every candidate computes the same transform to within the stated tolerance
+(the partition only moves work between the asymptotic blocks and the
+recurrence, Sec. 2.2); only the time differs.  On GB300 the FP64 pipe is the
+bottleneck of both parts, so the balance point differs from the paper's
+CPU setting.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+CANDIDATES_M = (7, 10, 13, 16)
+CANDIDATES_SEG = (256, 1024)
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("CJT_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "cjt_gb300_autotune.json"))
+
+
+def _load():
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save(d):
+    path = cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def _key(N, precision, directions):
+    import torch
+    return "%s|N=%d|prec=%d|dir=%d" % (torch.cuda.get_device_name(), N, precision, directions)
+
+
+def time_plan(plan, x, y, reps=3):
+    """Average milliseconds of forward + inverse (CUDA events on the current stream)."""
+    import torch
+    from . import cjt
+    info = plan.info()
+    def run():
+        if info["directions"] & cjt.CJT_FWD:
+            cjt.cjt_forward(plan, x, y)
+        if info["directions"] & cjt.CJT_INV:
+            cjt.cjt_inverse(plan, x, y)
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def best_options(N: int, alpha: float, beta: float, precision: int = 0, directions: int = 3,
+                 refresh: bool = False) -> dict:
+    """Options dict (M, seg_len) for cjt.Plan, from the cache or by timing the candidates."""
+    import numpy as np
+    import torch
+    from . import cjt
+    if N < 256:
+        return {"M": 7, "seg_len": 256}
+    key = _key(N, precision, directions)
+    with _lock:
+        cache = _load()
+        if not refresh and key in cache:
+            return dict(cache[key]["options"])
+    rng = np.random.default_rng(N)
+    x = torch.from_numpy(rng.standard_normal(N + 1) / np.arange(1, N + 2)).cuda()
+    y = torch.empty_like(x)
+    results = []
+    for M in CANDIDATES_M:
+        for seg in CANDIDATES_SEG:
+            opts = {"M": M, "seg_len": seg}
+            p = cjt.Plan(N, alpha, beta, precision=precision, directions=directions, **opts)
+            results.append((time_plan(p, x, y), opts))
+            p.close()
+    results.sort(key=lambda r: r[0])
+    best = results[0][1]
+    with _lock:
+        cache = _load()
+        cache[key] = {"options": best, "ms": results[0][0],
+                      "candidates": [{"options": o, "ms": t} for t, o in results]}
+        _save(cache)
+    return dict(best)

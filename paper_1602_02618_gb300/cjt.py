@@ -44,7 +44,8 @@ class cjt_plan_info(ctypes.Structure):
                 ("nblk_inv", ctypes.c_int), ("rec_steps_fwd", ctypes.c_int64), ("rec_steps_inv", ctypes.c_int64),
                 ("fft_len_fwd", ctypes.c_int64), ("fft_len_inv", ctypes.c_int64), ("nfft_fwd", ctypes.c_int64),
                 ("nfft_inv", ctypes.c_int64), ("rec_items_fwd", ctypes.c_int64), ("rec_items_inv", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("plan_ms", ctypes.c_double)]
+                ("device_bytes", ctypes.c_int64), ("plan_ms", ctypes.c_double), ("kernels_fwd", ctypes.c_int64),
+                ("kernels_inv", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -52,7 +53,10 @@ class cjt_plan_info(ctypes.Structure):
 
 EXPORTED = ["cjt_plan_opts_default", "cjt_plan", "cjt_destroy", "cjt_get_info", "cjt_forward", "cjt_inverse",
             "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_strerror", "cjt_last_cuda_error",
-            "cjt_version"]
+            "cjt_version", "cjt_set_profiling", "cjt_get_profile", "cjt_microbench_fma"]
+
+STAGES = ["fwd_rec", "fwd_pack", "fwd_fft", "fwd_combine", "fwd_dct", "inv_front", "inv_pack", "inv_fft",
+          "inv_rec", "inv_combine"]
 
 _lock = threading.Lock()
 _lib = None
@@ -88,12 +92,16 @@ def load(path: str = LIB_PATH):
         lib.cjt_execute_batched.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int8),
                                             ctypes.POINTER(i64), vp, vp, vp]
         lib.cjt_sync.argtypes = [vp]
+        lib.cjt_set_profiling.argtypes = [vp, i]
+        lib.cjt_get_profile.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64), i]
+        lib.cjt_microbench_fma.argtypes = [i, ctypes.POINTER(d), vp]
         lib.cjt_strerror.argtypes = [i]
         lib.cjt_strerror.restype = ctypes.c_char_p
         lib.cjt_last_cuda_error.restype = ctypes.c_char_p
         lib.cjt_version.restype = ctypes.c_char_p
         for name in ("cjt_plan_opts_default", "cjt_plan", "cjt_get_info", "cjt_forward", "cjt_inverse",
-                     "cjt_execute_host", "cjt_execute_batched", "cjt_sync"):
+                     "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_set_profiling", "cjt_get_profile",
+                     "cjt_microbench_fma"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -151,6 +159,17 @@ class Plan:
         inf = cjt_plan_info()
         _check(load().cjt_get_info(self._h, ctypes.byref(inf)), "cjt_get_info")
         return inf.as_dict()
+
+    def set_profiling(self, on: bool = True):
+        _check(load().cjt_set_profiling(self._h, 1 if on else 0), "cjt_set_profiling")
+
+    def profile(self):
+        """{stage: (total ms, launches)} of the executions since the last call."""
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        _check(load().cjt_get_profile(self._h, ms, cnt, n), "cjt_get_profile")
+        return {STAGES[s]: (ms[s], cnt[s]) for s in range(n)}
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -212,6 +231,14 @@ def cjt_execute_batched(plans, dirs, offsets, x_dev, out_dev, stream=None):
 
 def cjt_sync(stream=None):
     _check(load().cjt_sync(_stream_handle(stream)), "cjt_sync")
+
+
+def microbench_fma(fp64: bool = True, stream=None) -> float:
+    """Measured dependent-FMA throughput of the device in FLOP/s (FP64 or FP32)."""
+    v = ctypes.c_double()
+    _check(load().cjt_microbench_fma(1 if fp64 else 0, ctypes.byref(v), _stream_handle(stream)),
+           "cjt_microbench_fma")
+    return v.value
 
 
 def version() -> str:

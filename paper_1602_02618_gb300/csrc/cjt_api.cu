@@ -34,7 +34,11 @@ int end_use(cjt_plan_s *p, cudaStream_t st) {
     return CJT_OK;
 }
 
+int fft_launches(int64_t L) { return L <= 1 ? 0 : (L <= 4096 ? 1 : 2); }
+
 void free_plan(cjt_plan_s *p) {
+    for (auto &r : p->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : p->prof_pool) cudaEventDestroy(e);
     for (void *v : p->allocs) cudaFree(v);
     p->allocs.clear();
     if (p->done) cudaEventDestroy(p->done);
@@ -166,7 +170,50 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
     info->rec_items_inv = p->iv.nitems;
     info->device_bytes = p->device_bytes;
     info->plan_ms = p->plan_ms;
+    if (p->N == 0) {
+        info->kernels_fwd = info->kernels_inv = 1;
+    } else {
+        const int nqf = p->fw.nblk * p->M, nqi = p->iv.nblk * p->M;
+        info->kernels_fwd = (p->fw.nitems > 0) + (nqf > 0 ? 1 + fft_launches(p->Lf) : 0) + 1 +
+                            fft_launches(2 * p->N) + 1;
+        info->kernels_inv = 1 + fft_launches(p->Li) + 1 + (nqi > 0 ? 1 + fft_launches(p->Li) : 0) +
+                            (p->iv.nitems > 0) + 2;
+        if (!(p->opts.directions & CJT_FWD)) info->kernels_fwd = 0;
+        if (!(p->opts.directions & CJT_INV)) info->kernels_inv = 0;
+    }
     return CJT_OK;
+}
+
+int cjt_set_profiling(cjt_plan_t p, int on) {
+    if (!p) return CJT_EINVAL;
+    p->prof = on != 0;
+    return CJT_OK;
+}
+
+int cjt_get_profile(cjt_plan_t p, double *ms, int64_t *counts, int n) {
+    if (!p || n < 0) return CJT_EINVAL;
+    for (int s = 0; s < n; ++s) {
+        if (ms) ms[s] = 0.0;
+        if (counts) counts[s] = 0;
+    }
+    int rc = CJT_OK;
+    for (auto &r : p->prof_pending) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) {
+            cjt_internal_set_cuda_error(e, "cudaEventElapsedTime");
+            rc = CJT_ECUDA;
+        }
+        if (r.stage < n) {
+            if (ms) ms[r.stage] += t;
+            if (counts) counts[r.stage] += 1;
+        }
+        p->prof_pool.push_back(r.a);
+        p->prof_pool.push_back(r.b);
+    }
+    p->prof_pending.clear();
+    return rc;
 }
 
 int cjt_forward(cjt_plan_t p, const double *in, double *out, void *stream) {

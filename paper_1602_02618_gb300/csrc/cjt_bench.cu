@@ -1,0 +1,57 @@
+// Peak arithmetic microbenchmark: independent dependent-FMA chains on every SM.
+// Used to state the FP64 / FP32 pipe peak that the recurrence and transform
+// kernels are compared against.
+#include <cuda_runtime.h>
+
+#include "cjt_internal.cuh"
+
+namespace {
+constexpr int kChains = 8;
+constexpr int kIters = 4096;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_chain(T *out, T a, T b) {
+    T x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+    for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    if (s == (T)12345.678) out[0] = s;  // keeps the chains live
+}
+
+template <typename T>
+int run(double *flops, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    CJT_CUDA_TRY(cudaGetDevice(&dev));
+    CJT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    T *out = nullptr;
+    CJT_CUDA_TRY(cudaMallocAsync((void **)&out, sizeof(T), st));
+    const int blocks = sms * 8, threads = 256;
+    cudaEvent_t e0, e1;
+    CJT_CUDA_TRY(cudaEventCreate(&e0));
+    CJT_CUDA_TRY(cudaEventCreate(&e1));
+    k_fma_chain<T><<<blocks, threads, 0, st>>>(out, (T)0.999999, (T)1e-7);  // warm-up
+    CJT_CUDA_TRY(cudaEventRecord(e0, st));
+    const int reps = sizeof(T) == 8 ? 2 : 20;
+    for (int r = 0; r < reps; ++r) k_fma_chain<T><<<blocks, threads, 0, st>>>(out, (T)0.999999, (T)1e-7);
+    CJT_CUDA_TRY(cudaEventRecord(e1, st));
+    CJT_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CJT_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, st);
+    *flops = 2.0 * kChains * (double)kIters * blocks * threads * reps / (ms * 1e-3);
+    return CJT_OK;
+}
+}  // namespace
+
+extern "C" int cjt_microbench_fma(int fp64, double *flops, void *stream) {
+    if (!flops) return CJT_EINVAL;
+    return fp64 ? run<double>(flops, (cudaStream_t)stream) : run<float>(flops, (cudaStream_t)stream);
+}

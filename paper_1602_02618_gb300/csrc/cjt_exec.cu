@@ -286,19 +286,49 @@ __global__ void k_asy_pack_inv(int64_t Ng, int64_t L, int M, int nq, const int *
     buf[(int64_t)p * L + idx] = o;
 }
 
+// Sum of the recurrence partials of every item covering degree n (fixed order:
+// warp w takes items w, w+32, ...; four interleaved accumulators; the 32 warp
+// sums are added in warp order).  One block per 32 consecutive degrees.
+constexpr int RED_WARPS = 32;
+__global__ void __launch_bounds__(32 * RED_WARPS) k_inv_reduce(int64_t N, int seg_len,
+                                                               const int64_t *__restrict__ seg_ptr,
+                                                               const int64_t *__restrict__ seg_out,
+                                                               const int *__restrict__ seg_b,
+                                                               const double *__restrict__ partials,
+                                                               double *__restrict__ y) {
+    __shared__ double red[RED_WARPS][33];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n0 = (int64_t)blockIdx.x * 32, n = n0 + lane;
+    const int64_t s = n0 / seg_len, off = n - s * seg_len;
+    const int64_t q0 = seg_ptr[s], q1 = seg_ptr[s + 1];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t q = q0 + w;
+    for (; q + 3 * RED_WARPS < q1; q += 4 * RED_WARPS) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t qq = q + j * RED_WARPS;
+            if (n < seg_b[qq]) acc[j] += partials[seg_out[qq] + off];
+        }
+    }
+    for (int j = 0; q < q1; q += RED_WARPS, ++j)
+        if (n < seg_b[q]) acc[j & 3] += partials[seg_out[q] + off];
+    red[w][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    __syncthreads();
+    if (w == 0 && n <= N) {
+        double t = 0.0;
+        for (int k = 0; k < RED_WARPS; ++k) t += red[k][lane];
+        y[n] = t;
+    }
+}
+
 template <typename V>
 __global__ void k_combine_inv(int64_t N, int64_t L, int M, int nblk, const int *__restrict__ box3,
                               const double *__restrict__ scale, const double *__restrict__ Cnm,
-                              const V *__restrict__ buf, int seg_len,
-                              const int64_t *__restrict__ seg_ptr, const int64_t *__restrict__ seg_out,
-                              const int *__restrict__ seg_b, const double *__restrict__ partials,
+                              const V *__restrict__ buf, const double *__restrict__ yrec,
                               const double *__restrict__ s_n, double *__restrict__ out) {
     const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (n > N) return;
-    const int64_t s = n / seg_len, off = n - s * seg_len;
-    double y = 0.0;
-    for (int64_t q = seg_ptr[s]; q < seg_ptr[s + 1]; ++q)
-        if (n < seg_b[q]) y += partials[seg_out[q] + off];
+    double y = yrec[n];
     // degree n belongs to block k when j_k <= n < top_k (top_0 = N+1, top_k = j_{k-1})
     int k = -1;
     for (int kk = 0; kk < nblk; ++kk) {
@@ -339,6 +369,7 @@ int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
     int rc;
     // REC
     if (gw.nitems > 0) {
+        StageTimer tm(p, st, CJT_STAGE_FWD_REC);
         k_rec_fwd<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, gw.Ng, p->rt, in,
                                                                   gw.d_states, gw.d_partials);
         CJT_CUDA_TRY(cudaGetLastError());
@@ -348,15 +379,21 @@ int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
     const int64_t L = p->Lf;
     if (nq > 0) {
         dim3 gp(blocks_for(L, 256), p->npair_f);
+        StageTimer tm(p, st, CJT_STAGE_FWD_PACK);
         if (fp32)
             k_asy_pack_fwd<float2><<<gp, 256, 0, st>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in, (float2 *)p->d_fft_f);
         else
             k_asy_pack_fwd<double2><<<gp, 256, 0, st>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in, (double2 *)p->d_fft_f);
         CJT_CUDA_TRY(cudaGetLastError());
+    }
+    if (nq > 0) {
+        StageTimer tm(p, st, CJT_STAGE_FWD_FFT);
         rc = cjt_fft_pow2(p->d_fft_f, p->d_fft_scratch, L, p->npair_f, fp32 ? p->d_tw32 : p->d_tw64, p->Ltab, fp32, st);
         if (rc) return rc;
     }
     double2 *ext = (double2 *)p->d_dct;
+    {
+    StageTimer tm(p, st, CJT_STAGE_FWD_COMBINE);
     if (fp32)
         k_combine_fwd<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
             N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const float2 *)p->d_fft_f, gw.d_row_base, gw.d_row_nseg,
@@ -366,6 +403,8 @@ int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
             N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const double2 *)p->d_fft_f, gw.d_row_base, gw.d_row_nseg,
             gw.d_partials, ext);
     CJT_CUDA_TRY(cudaGetLastError());
+    }
+    StageTimer tm(p, st, CJT_STAGE_FWD_DCT);
     rc = cjt_fft_pow2(p->d_dct, p->d_dct_scratch, 2 * N, 1, p->d_tw64, p->Ltab, false, st);
     if (rc) return rc;
     k_dct_finish<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, (const double2 *)p->d_dct, out);
@@ -385,38 +424,49 @@ int cjt_exec_inverse(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
     const int M = p->M;
     const int64_t Ng = 2 * N, L = p->Li;
     // front end: p_N on the 2N grid, times the Clenshaw--Curtis weights
+    int rc;
+    {
+    StageTimer tm(p, st, CJT_STAGE_INV_FRONT);
     k_inv_front_pack<<<blocks_for(L, 256), 256, 0, st>>>(N, L, in, (double2 *)p->d_dct);
     CJT_CUDA_TRY(cudaGetLastError());
-    int rc = cjt_fft_pow2(p->d_dct, p->d_dct_scratch, L, 1, p->d_tw64, p->Ltab, false, st);
+    rc = cjt_fft_pow2(p->d_dct, p->d_dct_scratch, L, 1, p->d_tw64, p->Ltab, false, st);
     if (rc) return rc;
     k_inv_g<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)p->d_dct, p->d_w, p->d_g);
     CJT_CUDA_TRY(cudaGetLastError());
+    }
     // transposed asymptotic blocks
     const int nq = gw.nblk * M;
     if (nq > 0) {
         dim3 gp(blocks_for(L, 256), p->npair_i);
+        StageTimer tm(p, st, CJT_STAGE_INV_PACK);
         if (fp32)
             k_asy_pack_inv<float2><<<gp, 256, 0, st>>>(Ng, L, M, nq, gw.d_box, gw.d_scale, gw.d_u, gw.d_v, p->d_g, (float2 *)p->d_fft_i);
         else
             k_asy_pack_inv<double2><<<gp, 256, 0, st>>>(Ng, L, M, nq, gw.d_box, gw.d_scale, gw.d_u, gw.d_v, p->d_g, (double2 *)p->d_fft_i);
         CJT_CUDA_TRY(cudaGetLastError());
+    }
+    if (nq > 0) {
+        StageTimer tm(p, st, CJT_STAGE_INV_FFT);
         rc = cjt_fft_pow2(p->d_fft_i, p->d_fft_scratch, L, p->npair_i, fp32 ? p->d_tw32 : p->d_tw64, p->Ltab, fp32, st);
         if (rc) return rc;
     }
     // transposed recurrence
     if (gw.nitems > 0) {
+        StageTimer tm(p, st, CJT_STAGE_INV_REC);
         k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt, p->d_g,
                                                                              gw.d_states, gw.d_partials);
         CJT_CUDA_TRY(cudaGetLastError());
     }
+    StageTimer tm(p, st, CJT_STAGE_INV_COMBINE);
+    k_inv_reduce<<<blocks_for(N + 1, 32), 32 * RED_WARPS, 0, st>>>(N, p->seg_len, gw.d_seg_ptr, gw.d_seg_out,
+                                                                     gw.d_seg_b, gw.d_partials, p->d_y);
+    CJT_CUDA_TRY(cudaGetLastError());
     if (fp32)
         k_combine_inv<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const float2 *)p->d_fft_i, p->seg_len, gw.d_seg_ptr, gw.d_seg_out,
-            gw.d_seg_b, gw.d_partials, p->d_s, out);
+            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const float2 *)p->d_fft_i, p->d_y, p->d_s, out);
     else
         k_combine_inv<double2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const double2 *)p->d_fft_i, p->seg_len, gw.d_seg_ptr, gw.d_seg_out,
-            gw.d_seg_b, gw.d_partials, p->d_s, out);
+            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const double2 *)p->d_fft_i, p->d_y, p->d_s, out);
     CJT_CUDA_TRY(cudaGetLastError());
     return CJT_OK;
 }

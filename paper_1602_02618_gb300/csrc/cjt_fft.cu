@@ -146,17 +146,28 @@ int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batc
                int post_log, cudaStream_t st) {
     using V = typename cplx<R>::t;
     const int Ls = 1 << logLs;
-    // tile of columns per CTA: ~64 KB of shared memory
-    int64_t budget_elems = (int64_t)(65536 / sizeof(V));
-    int tile = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(ncols, 64), budget_elems / Ls));
+    // Columns per CTA: at most ~64 KB of shared memory, and few enough that the
+    // launch spreads over every SM (>= 2 CTAs per SM when there is enough work).
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    const int64_t budget_elems = (int64_t)(65536 / sizeof(V));
+    int64_t tile64 = std::min<int64_t>(std::min<int64_t>(ncols, 64), std::max<int64_t>(1, budget_elems / Ls));
+    tile64 = std::min<int64_t>(tile64, std::max<int64_t>(1, ncols * batch / (2 * sms)));
+    const int tile = (int)std::max<int64_t>(1, tile64);
     size_t smem = (size_t)tile * (Ls + SMEM_PAD) * sizeof(V);
+    const int threads = (int)std::min<int64_t>(FFT_THREADS, std::max<int64_t>(32, ((int64_t)tile * Ls / 4 + 31) / 32 * 32));
     static bool attr_set[2] = {false, false};
     if (!attr_set[sizeof(R) == 8]) {
         CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr_set[sizeof(R) == 8] = true;
     }
     dim3 grid((unsigned)((ncols + tile - 1) / tile), (unsigned)batch);
-    k_fft_sub<R><<<grid, FFT_THREADS, smem, st>>>((const V *)in, (V *)out, logLs, ncols, tile, in_es, in_cs, in_ts,
+    k_fft_sub<R><<<grid, threads, smem, st>>>((const V *)in, (V *)out, logLs, ncols, tile, in_es, in_cs, in_ts,
                                                     out_ks, out_cs, out_ts, (const V *)tw, logLtab, post_log);
     CJT_CUDA_TRY(cudaGetLastError());
     return CJT_OK;

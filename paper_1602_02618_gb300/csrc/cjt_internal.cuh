@@ -132,6 +132,41 @@ struct cjt_plan_s {
     int64_t device_bytes = 0;
     double plan_ms = 0;
     std::vector<void *> allocs;
+
+    // stage profiling (CUDA events on the launching stream)
+    bool prof = false;
+    struct ProfRec { int stage; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+};
+
+// Records an event pair around a stage when the plan is being profiled.
+struct StageTimer {
+    cjt_plan_s *p;
+    cudaStream_t st;
+    int stage;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageTimer(cjt_plan_s *p_, cudaStream_t st_, int stage_) : p(p_), st(st_), stage(stage_) {
+        if (!p->prof) return;
+        a = take();
+        b = take();
+        if (a) cudaEventRecord(a, st);
+    }
+    ~StageTimer() {
+        if (!p->prof || !a || !b) return;
+        cudaEventRecord(b, st);
+        p->prof_pending.push_back({stage, a, b});
+    }
+    cudaEvent_t take() {
+        if (!p->prof_pool.empty()) {
+            cudaEvent_t e = p->prof_pool.back();
+            p->prof_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
 };
 
 // ---------------------------------------------------------------------------
