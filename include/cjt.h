@@ -194,6 +194,27 @@ int cjt_get_profile(cjt_plan_t plan, double *ms, int64_t *counts, int n);
  */
 int cjt_microbench_fma(int fp64, double *flops, void *stream);
 
+/*
+ * Allocation-free Chebyshev coefficients from values (no counterpart in the
+ * paper; it is the forward transform's last step, c = T_N^{-1} y, offered for
+ * callers that cannot call cudaMalloc: code running under a host framework's
+ * pool allocator that owns the device memory, latency-critical paths where an
+ * allocation may block or synchronise the device, and plug-ins whose host has
+ * reserved nearly all device memory).
+ *   values_dev : device array of N+1 doubles, y_j at x_j = cos(pi j/N)
+ *   c_cheb_dev : device array of N+1 doubles receiving c_k with y_j = sum_k c_k T_k(x_j)
+ * Needs no plan and allocates nothing: its working memory is a fixed device
+ * array of 3 * 2 * CJT_NOALLOC_MAX_N complex doubles (6 MiB), reserved on every
+ * GPU that loads the library until the process exits.  N must be 0 or a power
+ * of two no larger than CJT_NOALLOC_MAX_N, else CJT_EUNSUPPORTED; CJT_EINVAL for
+ * null pointers or N < 0.  The first call on a device looks up the array's
+ * address on that device; make it before capturing a stream into a graph.  All
+ * calls share the array: calls whose work overlaps on the GPU (other streams or
+ * threads) race and must be serialised by the caller.
+ */
+#define CJT_NOALLOC_MAX_N 65536
+int cjt_cheb_coeffs_noalloc(int64_t N, const double *values_dev, double *c_cheb_dev, void *stream);
+
 /* Wait for `stream` and report any CUDA error raised by earlier work. */
 int cjt_sync(void *stream);
 

@@ -53,7 +53,9 @@ class cjt_plan_info(ctypes.Structure):
 
 EXPORTED = ["cjt_plan_opts_default", "cjt_plan", "cjt_destroy", "cjt_get_info", "cjt_forward", "cjt_inverse",
             "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_strerror", "cjt_last_cuda_error",
-            "cjt_version", "cjt_set_profiling", "cjt_get_profile", "cjt_microbench_fma"]
+            "cjt_version", "cjt_set_profiling", "cjt_get_profile", "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc"]
+
+NOALLOC_MAX_N = 65536
 
 STAGES = ["fwd_rec", "fwd_pack", "fwd_fft", "fwd_combine", "fwd_dct", "inv_front", "inv_pack", "inv_fft",
           "inv_rec", "inv_combine"]
@@ -95,13 +97,14 @@ def load(path: str = LIB_PATH):
         lib.cjt_set_profiling.argtypes = [vp, i]
         lib.cjt_get_profile.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64), i]
         lib.cjt_microbench_fma.argtypes = [i, ctypes.POINTER(d), vp]
+        lib.cjt_cheb_coeffs_noalloc.argtypes = [i64, vp, vp, vp]
         lib.cjt_strerror.argtypes = [i]
         lib.cjt_strerror.restype = ctypes.c_char_p
         lib.cjt_last_cuda_error.restype = ctypes.c_char_p
         lib.cjt_version.restype = ctypes.c_char_p
         for name in ("cjt_plan_opts_default", "cjt_plan", "cjt_get_info", "cjt_forward", "cjt_inverse",
                      "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_set_profiling", "cjt_get_profile",
-                     "cjt_microbench_fma"):
+                     "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -231,6 +234,16 @@ def cjt_execute_batched(plans, dirs, offsets, x_dev, out_dev, stream=None):
 
 def cjt_sync(stream=None):
     _check(load().cjt_sync(_stream_handle(stream)), "cjt_sync")
+
+
+def cjt_cheb_coeffs_noalloc(values, c_cheb, stream=None):
+    """Chebyshev coefficients from values at the N+1 Lobatto points through the
+    allocation-free entry point (working memory in a fixed device array; both
+    tensors must already exist, N = values.numel() - 1 a power of two <= 65536)."""
+    n = values.numel()
+    _check(load().cjt_cheb_coeffs_noalloc(n - 1, _dev_ptr(values, n), _dev_ptr(c_cheb, n), _stream_handle(stream)),
+           "cjt_cheb_coeffs_noalloc")
+    return c_cheb
 
 
 def microbench_fma(fp64: bool = True, stream=None) -> float:
