@@ -35,6 +35,7 @@ int end_use(cjt_plan_s *p, cudaStream_t st) {
 }
 
 int fft_launches(int64_t L) { return L <= 1 ? 0 : (L <= 4096 ? 1 : 2); }
+int dft_launches(const Dft &d) { return d.L <= 1 ? 0 : (d.P ? 3 + 2 * fft_launches(d.P) : fft_launches(d.L)); }
 
 void free_plan(cjt_plan_s *p) {
     for (auto &r : p->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -107,7 +108,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     if (o.directions < 1 || o.directions > 3) return CJT_EINVAL;
     if (!(o.ratio == 0.0 || (o.ratio > 0.0 && o.ratio < 1.0))) return CJT_EINVAL;
     if (o.seg_len < 32 || o.seg_len > (1 << 20) || (o.seg_len % 32) != 0) return CJT_EINVAL;
-    if (N > 0 && !is_pow2(N)) return CJT_EUNSUPPORTED;
+    if (N > (1LL << 21) && !is_pow2(N)) return CJT_EUNSUPPORTED;   // Bluestein lengths stay <= 2^24
 
     cjt_plan_s *p = new (std::nothrow) cjt_plan_s();
     if (!p) return CJT_ENOMEM;
@@ -174,9 +175,9 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
         info->kernels_fwd = info->kernels_inv = 1;
     } else {
         const int nqf = p->fw.nblk * p->M, nqi = p->iv.nblk * p->M;
-        info->kernels_fwd = (p->fw.nitems > 0) + (nqf > 0 ? 1 + fft_launches(p->Lf) : 0) + 1 +
-                            fft_launches(2 * p->N) + 1;
-        info->kernels_inv = 1 + fft_launches(p->Li) + 1 + (nqi > 0 ? 1 + fft_launches(p->Li) : 0) +
+        info->kernels_fwd = (p->fw.nitems > 0) + (nqf > 0 ? 1 + dft_launches(p->dft_f) : 0) + 1 +
+                            dft_launches(p->dft_dct) + 1;
+        info->kernels_inv = 1 + dft_launches(p->dft_front) + 1 + (nqi > 0 ? 1 + dft_launches(p->dft_i) : 0) +
                             (p->iv.nitems > 0) + 2;
         if (!(p->opts.directions & CJT_FWD)) info->kernels_fwd = 0;
         if (!(p->opts.directions & CJT_INV)) info->kernels_inv = 0;

@@ -208,7 +208,7 @@ __global__ void k_combine_fwd(int64_t N, int64_t L, int M, const int *__restrict
     for (int s = 0; s < nseg; ++s) y += partials[base + (int64_t)s * 32];
     const int k = rowk[i];
     if (k >= 0) {
-        const int64_t im = (L - i) & (L - 1);
+        const int64_t im = i == 0 ? 0 : L - i;
         for (int m = 0; m < M; ++m) {
             const int q = k * M + m, p = q >> 1;
             const V Z = buf[(int64_t)p * L + i], W = buf[(int64_t)p * L + im];
@@ -388,7 +388,8 @@ int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
     }
     if (nq > 0) {
         StageTimer tm(p, st, CJT_STAGE_FWD_FFT);
-        rc = cjt_fft_pow2(p->d_fft_f, p->d_fft_scratch, L, p->npair_f, fp32 ? p->d_tw32 : p->d_tw64, p->Ltab, fp32, st);
+        rc = cjt_dft_exec(p->dft_f, p->d_fft_f, p->d_work, p->d_fft_scratch, p->npair_f, fp32 ? p->d_tw32 : p->d_tw64,
+                          p->Ltab, st);
         if (rc) return rc;
     }
     double2 *ext = (double2 *)p->d_dct;
@@ -405,7 +406,7 @@ int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
     CJT_CUDA_TRY(cudaGetLastError());
     }
     StageTimer tm(p, st, CJT_STAGE_FWD_DCT);
-    rc = cjt_fft_pow2(p->d_dct, p->d_dct_scratch, 2 * N, 1, p->d_tw64, p->Ltab, false, st);
+    rc = cjt_dft_exec(p->dft_dct, p->d_dct, p->d_work, p->d_fft_scratch, 1, p->d_tw64, p->Ltab, st);
     if (rc) return rc;
     k_dct_finish<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, (const double2 *)p->d_dct, out);
     CJT_CUDA_TRY(cudaGetLastError());
@@ -429,7 +430,7 @@ int cjt_exec_inverse(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
     StageTimer tm(p, st, CJT_STAGE_INV_FRONT);
     k_inv_front_pack<<<blocks_for(L, 256), 256, 0, st>>>(N, L, in, (double2 *)p->d_dct);
     CJT_CUDA_TRY(cudaGetLastError());
-    rc = cjt_fft_pow2(p->d_dct, p->d_dct_scratch, L, 1, p->d_tw64, p->Ltab, false, st);
+    rc = cjt_dft_exec(p->dft_front, p->d_dct, p->d_work, p->d_fft_scratch, 1, p->d_tw64, p->Ltab, st);
     if (rc) return rc;
     k_inv_g<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)p->d_dct, p->d_w, p->d_g);
     CJT_CUDA_TRY(cudaGetLastError());
@@ -447,7 +448,8 @@ int cjt_exec_inverse(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
     }
     if (nq > 0) {
         StageTimer tm(p, st, CJT_STAGE_INV_FFT);
-        rc = cjt_fft_pow2(p->d_fft_i, p->d_fft_scratch, L, p->npair_i, fp32 ? p->d_tw32 : p->d_tw64, p->Ltab, fp32, st);
+        rc = cjt_dft_exec(p->dft_i, p->d_fft_i, p->d_work, p->d_fft_scratch, p->npair_i, fp32 ? p->d_tw32 : p->d_tw64,
+                          p->Ltab, st);
         if (rc) return rc;
     }
     // transposed recurrence

@@ -12,7 +12,12 @@
 // last when log2 is odd) on a padded [column][element] shared-memory tile,
 // with twiddles read from a plan-owned table omega_{Ltab}^j computed by
 // sincospi (exact argument reduction).
+//
+// Lengths that are not powers of two (N not a power of two) go through
+// Bluestein's chirp-z form on top of the power-of-two transform.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "cjt_internal.cuh"
 
@@ -192,7 +197,142 @@ int fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw
     return launch_sub<R>(scratch, data, log2, L1, batch, 1, L2, L, L1, 1, L, tw, logLtab, -1, st);
 }
 
+// ---------------------------------------------------------------------------
+// Bluestein
+// ---------------------------------------------------------------------------
+template <typename V> __device__ __forceinline__ V cconj(V a) { a.y = -a.y; return a; }
+
+template <typename V>
+__global__ void k_blue_pre(int64_t L, int64_t S, int64_t P, const V *__restrict__ data, const V *__restrict__ chirp,
+                           V *__restrict__ work) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t b = blockIdx.y;
+    if (i >= P) return;
+    V v;
+    v.x = 0;
+    v.y = 0;
+    if (i < S) v = cmul(data[b * L + i], chirp[i]);
+    work[b * P + i] = v;
+}
+
+template <typename V>
+__global__ void k_blue_mid(int64_t P, const V *__restrict__ bhat, V *__restrict__ work) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t b = blockIdx.y;
+    if (i >= P) return;
+    work[b * P + i] = cconj(cmul(work[b * P + i], bhat[i]));
+}
+
+template <typename V, typename R>
+__global__ void k_blue_post(int64_t L, int64_t K, int64_t P, const V *__restrict__ work, const V *__restrict__ chirp,
+                            V *__restrict__ data, R invP) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t b = blockIdx.y;
+    if (k >= K) return;
+    V v = cconj(work[b * P + k]);
+    v.x *= invP;
+    v.y *= invP;
+    data[b * L + k] = cmul(v, chirp[k]);
+}
+
+// w_m = exp(-i pi m^2 / L), the square reduced exactly modulo 2L
+__global__ void k_blue_chirp(int64_t L, int64_t n, double2 *w64, float2 *w32) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const int64_t r = (m * m) % (2 * L);
+    double sv, cv;
+    sincospi(-(double)r / (double)L, &sv, &cv);
+    if (w64) w64[m] = make_double2(cv, sv);
+    if (w32) w32[m] = make_float2((float)cv, (float)sv);
+}
+
+// cyclic arrangement of conj(w_m) for m in (-(S-1), K-1]
+__global__ void k_blue_b(int64_t S, int64_t K, int64_t P, const double2 *__restrict__ w, double2 *__restrict__ b) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= P) return;
+    double2 v = make_double2(0.0, 0.0);
+    if (j < K) v = make_double2(w[j].x, -w[j].y);
+    else if (P - j < S) v = make_double2(w[P - j].x, -w[P - j].y);
+    b[j] = v;
+}
+
+__global__ void k_to_f32(int64_t n, const double2 *__restrict__ a, float2 *__restrict__ b) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename R>
+int dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const void *tw, int64_t Ltab,
+             cudaStream_t st) {
+    using V = typename cplx<R>::t;
+    if (batch <= 0 || d.L <= 1) return CJT_OK;
+    if (!d.P) return fft_pow2<R>(data, scratch, d.L, batch, tw, Ltab, st);
+    dim3 g(nblk(d.P, 256), (unsigned)batch);
+    k_blue_pre<V><<<g, 256, 0, st>>>(d.L, d.S, d.P, (const V *)data, (const V *)d.chirp, (V *)work);
+    CJT_CUDA_TRY(cudaGetLastError());
+    int rc = fft_pow2<R>(work, scratch, d.P, batch, tw, Ltab, st);
+    if (rc) return rc;
+    k_blue_mid<V><<<g, 256, 0, st>>>(d.P, (const V *)d.bhat, (V *)work);
+    CJT_CUDA_TRY(cudaGetLastError());
+    rc = fft_pow2<R>(work, scratch, d.P, batch, tw, Ltab, st);
+    if (rc) return rc;
+    dim3 g2(nblk(d.K, 256), (unsigned)batch);
+    k_blue_post<V, R><<<g2, 256, 0, st>>>(d.L, d.K, d.P, (const V *)work, (const V *)d.chirp, (V *)data,
+                                          (R)(1.0 / (double)d.P));
+    CJT_CUDA_TRY(cudaGetLastError());
+    return CJT_OK;
+}
+
 }  // namespace
+
+int64_t cjt_dft_padded(int64_t L, int64_t S, int64_t K) {
+    if (L <= 1 || (L & (L - 1)) == 0) return 0;
+    int64_t P = 1;
+    while (P < S + K - 1) P <<= 1;
+    return P;
+}
+
+int64_t cjt_dft_work_bytes(const Dft &d, int64_t batch) {
+    return d.P ? d.P * batch * (int64_t)(d.fp32 ? sizeof(float2) : sizeof(double2)) : 0;
+}
+
+int64_t cjt_dft_scratch_bytes(const Dft &d, int64_t batch) {
+    return cjt_fft_scratch_elems(d.fft_len(), batch) * (int64_t)(d.fp32 ? sizeof(float2) : sizeof(double2));
+}
+
+int cjt_dft_setup(Dft &d, const void *tw64, int64_t Ltab, cudaStream_t st) {
+    if (!d.P) return CJT_OK;
+    const int64_t nw = std::max(d.S, d.K);
+    double2 *w64 = nullptr, *b64 = nullptr, *scr = nullptr;
+    CJT_CUDA_TRY(cudaMallocAsync((void **)&w64, sizeof(double2) * nw, st));
+    CJT_CUDA_TRY(cudaMallocAsync((void **)&b64, sizeof(double2) * d.P, st));
+    if (d.P > 4096) CJT_CUDA_TRY(cudaMallocAsync((void **)&scr, sizeof(double2) * d.P, st));
+    k_blue_chirp<<<nblk(nw, 256), 256, 0, st>>>(d.L, nw, w64, nullptr);
+    k_blue_b<<<nblk(d.P, 256), 256, 0, st>>>(d.S, d.K, d.P, w64, b64);
+    CJT_CUDA_TRY(cudaGetLastError());
+    int rc = fft_pow2<double>(b64, scr, d.P, 1, tw64, Ltab, st);
+    if (rc) return rc;
+    if (d.fp32) {
+        k_to_f32<<<nblk(nw, 256), 256, 0, st>>>(nw, w64, (float2 *)d.chirp);
+        k_to_f32<<<nblk(d.P, 256), 256, 0, st>>>(d.P, b64, (float2 *)d.bhat);
+    } else {
+        CJT_CUDA_TRY(cudaMemcpyAsync(d.chirp, w64, sizeof(double2) * nw, cudaMemcpyDeviceToDevice, st));
+        CJT_CUDA_TRY(cudaMemcpyAsync(d.bhat, b64, sizeof(double2) * d.P, cudaMemcpyDeviceToDevice, st));
+    }
+    CJT_CUDA_TRY(cudaGetLastError());
+    cudaFreeAsync(w64, st);
+    cudaFreeAsync(b64, st);
+    if (scr) cudaFreeAsync(scr, st);
+    return CJT_OK;
+}
+
+int cjt_dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const void *tw, int64_t Ltab,
+                 cudaStream_t st) {
+    return d.fp32 ? dft_exec<float>(d, data, work, scratch, batch, tw, Ltab, st)
+                  : dft_exec<double>(d, data, work, scratch, batch, tw, Ltab, st);
+}
 
 int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab, bool fp32,
                  cudaStream_t st) {

@@ -89,6 +89,18 @@ struct GridWork {
     double *d_scale = nullptr;
 };
 
+// A discrete Fourier transform X_k = sum_{n<S} x_n exp(-2 pi i n k / L), k < K, batched over
+// rows of length L.  L a power of two: direct radix-4 FFT (P = 0).  Otherwise Bluestein's
+// chirp-z form: X_k = w_k sum_n (x_n w_n) conj(w_{k-n}), w_m = exp(-i pi m^2 / L), as a cyclic
+// convolution of power-of-two length P >= S + K - 1.
+struct Dft {
+    int64_t L = 0, S = 0, K = 0, P = 0;
+    bool fp32 = false;
+    void *chirp = nullptr;  // w_m, m < max(S, K)
+    void *bhat = nullptr;   // FFT_P of the cyclically arranged conj(w)
+    int64_t fft_len() const { return P ? P : L; }
+};
+
 struct cjt_plan_s {
     int64_t N = 0;
     double alpha = 0, beta = 0;
@@ -114,10 +126,12 @@ struct cjt_plan_s {
     int npair_f = 0, npair_i = 0; // complex transforms of ASY item pairs
     void *d_fft_f = nullptr;      // forward ASY buffers (npair_f x Lf), precision dependent
     void *d_fft_i = nullptr;      // inverse ASY buffers (npair_i x Li)
-    void *d_fft_scratch = nullptr;// scratch for four-step transforms
-    int64_t scratch_elems = 0;
+    void *d_fft_scratch = nullptr;// scratch for four-step transforms (bytes: scratch_bytes)
+    int64_t scratch_bytes = 0;
+    void *d_work = nullptr;       // Bluestein work rows (bytes: work_bytes)
+    int64_t work_bytes = 0;
+    Dft dft_f, dft_dct, dft_front, dft_i, dft_cc;
     double *d_dct = nullptr;      // complex FP64 buffer of length max(Lf, Li) (DCT-I / front end)
-    double *d_dct_scratch = nullptr;
     double *d_y = nullptr;        // forward grid values / inverse degree sums
     double *d_g = nullptr;        // inverse: w_i p_N(x_i) on the 2N grid
     double *d_w = nullptr;        // inverse: Clenshaw--Curtis weights (2N+1)
@@ -242,6 +256,14 @@ __host__ __device__ inline double cjt_hahn_h(int l, double a) {
 int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab,
                  bool fp32, cudaStream_t st);
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch);
+// Bluestein length (0 when L is a power of two)
+int64_t cjt_dft_padded(int64_t L, int64_t S, int64_t K);
+// chirp and bhat for a Bluestein transform; tw64 must cover P
+int cjt_dft_setup(Dft &d, const void *tw64, int64_t Ltab, cudaStream_t st);
+int cjt_dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const void *tw, int64_t Ltab,
+                 cudaStream_t st);
+int64_t cjt_dft_work_bytes(const Dft &d, int64_t batch);
+int64_t cjt_dft_scratch_bytes(const Dft &d, int64_t batch);
 
 int cjt_plan_build(cjt_plan_s *p, cudaStream_t st);
 int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t st);

@@ -570,41 +570,74 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     if (fwd) TRY(build_grid(p, p->fw, N, false, h, st));
     if (inv) TRY(build_grid(p, p->iv, 2 * N, true, h, st));
 
-    // transforms: forward ASY/DCT length 2N, inverse 4N
+    // transforms: forward ASY/DCT length 2N, inverse 4N; Bluestein when N is not a power of two
     const bool fp32 = p->opts.precision == CJT_MIXED;
     p->Lf = fwd ? 2 * N : 0;
     p->Li = inv ? 4 * N : 0;
-    p->Ltab = std::max<int64_t>(std::max(p->Lf, p->Li), 2);
+    p->npair_f = (p->fw.nblk * M + 1) / 2;
+    p->npair_i = (p->iv.nblk * M + 1) / 2;
+    auto mk = [](Dft &d, int64_t L, int64_t S, int64_t K, bool f32) {
+        d.L = L; d.S = S; d.K = K; d.fp32 = f32; d.P = cjt_dft_padded(L, S, K);
+    };
+    std::vector<std::pair<Dft *, int64_t>> used;   // transform and its batch
+    if (fwd) {
+        mk(p->dft_f, 2 * N, N + 1, 2 * N, fp32);   // both Z(i) and Z(L-i) are read by the pair separation
+        mk(p->dft_dct, 2 * N, 2 * N, N + 1, false);
+        if (p->npair_f) used.push_back({&p->dft_f, p->npair_f});
+        used.push_back({&p->dft_dct, 1});
+    }
+    if (inv) {
+        mk(p->dft_front, 4 * N, N + 1, 2 * N + 1, false);
+        mk(p->dft_i, 4 * N, 4 * N, N + 1, fp32);
+        mk(p->dft_cc, 4 * N, 4 * N, 2 * N + 1, false);
+        used.push_back({&p->dft_front, 1});
+        if (p->npair_i) used.push_back({&p->dft_i, p->npair_i});
+        used.push_back({&p->dft_cc, 1});
+    }
+    p->Ltab = 2;
+    for (auto &u : used) p->Ltab = std::max(p->Ltab, u.first->fft_len());
     TRY(dalloc(p, (double2 **)&p->d_tw64, p->Ltab));
     if (fp32) TRY(dalloc(p, (float2 **)&p->d_tw32, p->Ltab));
     k_twiddles<<<blocks_for(p->Ltab, 256), 256, 0, st>>>(p->Ltab, (double2 *)p->d_tw64, (float2 *)p->d_tw32);
     CJT_CUDA_TRY(cudaGetLastError());
-
+    int64_t work = 0, scratch = 0;
+    for (auto &u : used) {
+        Dft &d = *u.first;
+        if (d.P) {
+            const int64_t nw = std::max(d.S, d.K);
+            if (d.fp32) {
+                TRY(dalloc(p, (float2 **)&d.chirp, nw));
+                TRY(dalloc(p, (float2 **)&d.bhat, d.P));
+            } else {
+                TRY(dalloc(p, (double2 **)&d.chirp, nw));
+                TRY(dalloc(p, (double2 **)&d.bhat, d.P));
+            }
+            TRY(cjt_dft_setup(d, p->d_tw64, p->Ltab, st));
+        }
+        work = std::max(work, cjt_dft_work_bytes(d, u.second));
+        scratch = std::max(scratch, cjt_dft_scratch_bytes(d, u.second));
+    }
     const size_t csz = fp32 ? sizeof(float2) : sizeof(double2);
-    p->npair_f = (p->fw.nblk * M + 1) / 2;
-    p->npair_i = (p->iv.nblk * M + 1) / 2;
-    int64_t scratch = 0;
     if (p->npair_f) {
         void *v;
         CJT_CUDA_TRY(cudaMalloc(&v, csz * p->npair_f * p->Lf));
         p->allocs.push_back(v); p->device_bytes += csz * p->npair_f * p->Lf; p->d_fft_f = v;
-        scratch = std::max(scratch, cjt_fft_scratch_elems(p->Lf, p->npair_f));
     }
     if (p->npair_i) {
         void *v;
         CJT_CUDA_TRY(cudaMalloc(&v, csz * p->npair_i * p->Li));
         p->allocs.push_back(v); p->device_bytes += csz * p->npair_i * p->Li; p->d_fft_i = v;
-        scratch = std::max(scratch, cjt_fft_scratch_elems(p->Li, p->npair_i));
     }
     if (scratch) {
-        void *v;
-        CJT_CUDA_TRY(cudaMalloc(&v, csz * scratch));
-        p->allocs.push_back(v); p->device_bytes += csz * scratch; p->d_fft_scratch = v;
-        p->scratch_elems = scratch;
+        TRY(dalloc(p, (unsigned char **)&p->d_fft_scratch, scratch));
+        p->scratch_bytes = scratch;
+    }
+    if (work) {
+        TRY(dalloc(p, (unsigned char **)&p->d_work, work));
+        p->work_bytes = work;
     }
     const int64_t Ld = std::max<int64_t>(std::max(p->Lf, p->Li), 2);
     TRY(dalloc(p, (double2 **)&p->d_dct, Ld));
-    if (Ld > 4096) TRY(dalloc(p, (double2 **)&p->d_dct_scratch, Ld));
     TRY(dalloc(p, &p->d_y, 2 * N + 2));
     TRY(dalloc(p, &p->d_in, N + 1));
     TRY(dalloc(p, &p->d_out, N + 1));
@@ -618,7 +651,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         CJT_CUDA_TRY(cudaMemsetAsync(p->d_dct, 0, sizeof(double2) * 2 * Ng, st));
         k_moments<<<1, 1, 0, st>>>(Ng, a, b, mu0, (double2 *)p->d_dct);
         CJT_CUDA_TRY(cudaGetLastError());
-        TRY(cjt_fft_pow2(p->d_dct, p->d_dct_scratch, 2 * Ng, 1, p->d_tw64, p->Ltab, false, st));
+        TRY(cjt_dft_exec(p->dft_cc, p->d_dct, p->d_work, p->d_fft_scratch, 1, p->d_tw64, p->Ltab, st));
         k_cc_weights<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)p->d_dct, p->d_w);
         k_inv_norm<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, a, b, p->d_s);
         CJT_CUDA_TRY(cudaGetLastError());

@@ -194,3 +194,32 @@ def test_identity_at_N0(cjt):
     p = cjt.Plan(0, 0.2, 0.1)
     assert run_fwd(cjt, p, np.array([2.5]))[0] == 2.5
     assert run_inv(cjt, p, np.array([-1.5]))[0] == -1.5
+
+
+@pytest.mark.parametrize("alpha,beta", [(0.1, -0.3), (0.45, 0.45), (-0.5, 0.5)])
+@pytest.mark.parametrize("N", [3, 5, 6, 7, 100, 1000, 1023, 1025, 3001, 10007])
+def test_general_N_matches_oracle(cjt, orc, N, alpha, beta):
+    """N not a power of two: the DCT-I/DST-I sums go through Bluestein's chirp-z form."""
+    c = inputs.decaying_coefficients(N, 1.0, inputs.BASE_SEED + 3 * N)
+    plan = cjt.Plan(N, alpha, beta)
+    assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, alpha, beta))) <= TOL * l1(c)
+    assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, alpha, beta))) <= TOL * l1(c)
+
+
+# Mixed form (FP32 transforms of the asymptotic blocks, everything else FP64): stated bounds
+MIXED_TOL_FWD = 1e-9
+MIXED_TOL_INV = 1e-5
+
+
+@pytest.mark.parametrize("N,M", [(1024, 7), (4096, 13), (3001, 10), (16384, 16), (65536, 16)])
+def test_mixed_precision_within_stated_bound(cjt, orc, N, M):
+    a, b = inputs.jacobi_parameters(inputs.BASE_SEED + 77 + N)
+    c = inputs.decaying_coefficients(N, 1.0, inputs.BASE_SEED + 5 * N)
+    plan = cjt.Plan(N, a, b, M=M, precision=cjt.CJT_MIXED)
+    if N <= 16384:
+        assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, a, b))) <= MIXED_TOL_FWD * l1(c)
+        assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, a, b))) <= MIXED_TOL_INV * l1(c)
+    # against the FP64 GPU form at any size
+    p64 = cjt.Plan(N, a, b, M=M)
+    assert np.max(np.abs(run_fwd(cjt, plan, c) - run_fwd(cjt, p64, c))) <= MIXED_TOL_FWD * l1(c)
+    assert np.max(np.abs(run_inv(cjt, plan, c) - run_inv(cjt, p64, c))) <= MIXED_TOL_INV * l1(c)
