@@ -7,6 +7,8 @@
 #include <chrono>
 #include <climits>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "cjt_internal.cuh"
@@ -161,43 +163,48 @@ __global__ void k_rec_states(int64_t nrows, const int *srow, int64_t Ng, int seg
     if (q >= nrows) return;
     const int *r = srow + 6 * q;
     const int row = r[0], mode = r[2], base = r[3], lane = r[4], nseg = r[5];
-    const int64_t nend = (int64_t)(nseg - 1) * seg_len;
     if (mode == REC_PLAIN) {
         const double x = cospi((double)row / (double)Ng);
         double pm = 0.0, p = 1.0;
-        for (int64_t n = 0; n < nend; ++n) {
-            const double pn = fma(fma(t.A[n], x, t.B[n]), p, -t.C[n] * pm);
-            pm = p;
-            p = pn;
-            if (((n + 1) % seg_len) == 0) {
-                double *st = states + ((int64_t)(base + (n + 1) / seg_len - 1) * 32 + lane) * 2;
-                st[0] = p;
-                st[1] = pm;
+        for (int s = 1; s < nseg; ++s) {
+            const int64_t n0 = (int64_t)(s - 1) * seg_len;
+#pragma unroll 8
+            for (int k = 0; k < seg_len; ++k) {
+                const int64_t n = n0 + k;
+                const double pn = fma(fma(__ldg(t.A + n), x, __ldg(t.B + n)), p, -__ldg(t.C + n) * pm);
+                pm = p;
+                p = pn;
             }
+            double *st = states + ((int64_t)(base + s - 1) * 32 + lane) * 2;
+            st[0] = p;
+            st[1] = pm;
         }
     } else {
         const bool plus = (mode == REC_REINSCH_P1);
         // delta = x - x0: -2 sin^2(theta/2) at x0 = 1, 2 cos^2(theta/2) at x0 = -1 (Sec. 4.2)
         double delta;
         if (plus) {
-            const double s = sinpi((double)row / (2.0 * (double)Ng));
-            delta = -2.0 * s * s;
+            const double sv = sinpi((double)row / (2.0 * (double)Ng));
+            delta = -2.0 * sv * sv;
         } else {
-            const double s = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
-            delta = 2.0 * s * s;
+            const double sv = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
+            delta = 2.0 * sv * sv;
         }
         const double *Ce = plus ? t.Ce_p : t.Ce_m;
         const double *rf = plus ? t.rf_p : t.rf_m;
         double p = 1.0, e = 0.0;
-        for (int64_t n = 0; n < nend; ++n) {
-            const double en = fma(t.A[n] * delta, p, Ce[n] * e);
-            p = fma(p, rf[n], en);
-            e = en;
-            if (((n + 1) % seg_len) == 0) {
-                double *st = states + ((int64_t)(base + (n + 1) / seg_len - 1) * 32 + lane) * 2;
-                st[0] = p;
-                st[1] = e;
+        for (int s = 1; s < nseg; ++s) {
+            const int64_t n0 = (int64_t)(s - 1) * seg_len;
+#pragma unroll 8
+            for (int k = 0; k < seg_len; ++k) {
+                const int64_t n = n0 + k;
+                const double en = fma(__ldg(t.A + n) * delta, p, __ldg(Ce + n) * e);
+                p = fma(p, __ldg(rf + n), en);
+                e = en;
             }
+            double *st = states + ((int64_t)(base + s - 1) * 32 + lane) * 2;
+            st[0] = p;
+            st[1] = e;
         }
     }
 }
@@ -207,22 +214,68 @@ __global__ void k_rec_states(int64_t nrows, const int *srow, int64_t Ng, int seg
 // with mu_1 = (beta-alpha)/(alpha+beta+2) mu_0, written as the even extension
 // of length 2*Ng used by the DCT-I of Eq. "CCweights".
 // --------------------------------------------------------------------------
-__global__ void k_moments(int64_t Ng, double a, double b, double mu0, double2 *ext) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    const double ab = a + b;
-    double mprev = mu0, mcur = (b - a) / (ab + 2.0) * mu0;
-    ext[0] = make_double2(mu0, 0.0);
-    if (Ng >= 1) {
-        ext[1] = make_double2(mcur, 0.0);
-        if (Ng > 1) ext[2 * Ng - 1] = make_double2(mcur, 0.0);
+// The recurrence for k >= 1 is the linear map (mu_{k-1}, mu_k) -> (mu_k, mu_{k+1}) with
+//   mu_{k+1} = c1_k mu_k + c0_k mu_{k-1},  c1_k = -2(a-b)/(a+b+k+2),  c0_k = -(a+b-k+2)/(a+b+k+2).
+// It is evaluated as a chunked scan: each chunk of kMomChunk steps forms its 2x2 transfer
+// matrix in parallel, one thread carries the true state across the chunks, and every chunk
+// then reruns its steps from that state.  The forward recurrence is stable in the square
+// (Sec. 3.1), so the basis solutions carried by the transfer matrices do not outgrow mu.
+constexpr int kMomChunk = 64;
+
+__device__ __forceinline__ void mom_coeffs(double ab, double amb, int64_t k, double *c0, double *c1) {
+    const double inv = 1.0 / (ab + (double)k + 2.0);
+    *c1 = -2.0 * amb * inv;
+    *c0 = -(ab - (double)k + 2.0) * inv;
+}
+
+__global__ void k_mom_transfer(int64_t Ng, double a, double b, int64_t nchunk, double4 *T) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nchunk) return;
+    const double ab = a + b, amb = a - b;
+    double x0 = 1.0, y0 = 0.0, x1 = 0.0, y1 = 1.0;   // columns: state (mu_{k-1}, mu_k)
+    const int64_t k0 = 1 + c * kMomChunk, k1 = min(k0 + kMomChunk, Ng);
+    for (int64_t k = k0; k < k1; ++k) {
+        double c0, c1;
+        mom_coeffs(ab, amb, k, &c0, &c1);
+        const double nx = fma(c1, y0, c0 * x0), ny = fma(c1, y1, c0 * x1);
+        x0 = y0; y0 = nx;
+        x1 = y1; y1 = ny;
     }
-    for (int64_t k = 1; k < Ng; ++k) {
-        const double kk = (double)k;
-        const double mnext = -(2.0 * (a - b) * mcur + (ab - kk + 2.0) * mprev) / (ab + kk + 2.0);
-        mprev = mcur;
-        mcur = mnext;
-        ext[k + 1] = make_double2(mcur, 0.0);
-        if (k + 1 < Ng) ext[2 * Ng - (k + 1)] = make_double2(mcur, 0.0);
+    T[c] = make_double4(x0, x1, y0, y1);   // [[x0, x1], [y0, y1]]
+}
+
+__global__ void k_mom_carry(int64_t nchunk, double mu0, double mu1, const double4 *T, double2 *start) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double u = mu0, v = mu1;
+    for (int64_t c = 0; c < nchunk; ++c) {
+        start[c] = make_double2(u, v);
+        const double4 m = T[c];
+        const double nu = fma(m.x, u, m.y * v), nv = fma(m.z, u, m.w * v);
+        u = nu;
+        v = nv;
+    }
+}
+
+// writes the even extension of length 2 Ng used by the DCT-I of Eq. "CCweights"
+__global__ void k_mom_fill(int64_t Ng, double a, double b, int64_t nchunk, const double2 *start, double2 *ext) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nchunk) return;
+    const double ab = a + b, amb = a - b;
+    double u = start[c].x, v = start[c].y;   // (mu_{k0-1}, mu_{k0})
+    const int64_t k0 = 1 + c * kMomChunk, k1 = min(k0 + kMomChunk, Ng);
+    if (c == 0) {
+        ext[0] = make_double2(u, 0.0);
+        ext[1] = make_double2(v, 0.0);
+        if (Ng > 1) ext[2 * Ng - 1] = make_double2(v, 0.0);
+    }
+    for (int64_t k = k0; k < k1; ++k) {
+        double c0, c1;
+        mom_coeffs(ab, amb, k, &c0, &c1);
+        const double w = fma(c1, v, c0 * u);
+        u = v;
+        v = w;
+        ext[k + 1] = make_double2(w, 0.0);
+        if (k + 1 < Ng) ext[2 * Ng - (k + 1)] = make_double2(w, 0.0);
     }
 }
 
@@ -269,6 +322,21 @@ __global__ void k_twiddles(int64_t L, double2 *tw64, float2 *tw32) {
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// CJT_PLAN_TRACE=1: print the wall time of each planning step (synchronising after each)
+struct PlanTrace {
+    bool on;
+    cudaStream_t st;
+    std::chrono::steady_clock::time_point t;
+    explicit PlanTrace(cudaStream_t s) : on(getenv("CJT_PLAN_TRACE") != nullptr), st(s), t(std::chrono::steady_clock::now()) {}
+    void mark(const char *what) {
+        if (!on) return;
+        cudaStreamSynchronize(st);
+        auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "[cjt plan] %-28s %8.3f ms\n", what, std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
+
 template <typename T> int dalloc(cjt_plan_s *p, T **ptr, int64_t count) {
     *ptr = nullptr;
     if (count <= 0) return CJT_OK;
@@ -294,6 +362,7 @@ template <typename T> int dalloc(cjt_plan_s *p, T **ptr, int64_t count) {
 // partition of one grid (Sec. 2.2) and the recurrence work that remains
 // ------------------------------------------------------------------------
 int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const HahnH &h, cudaStream_t st) {
+    PlanTrace tr(st);
     const double a = p->alpha, b = p->beta;
     const int M = p->M;
     gw.Ng = Ng;
@@ -353,6 +422,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
         gw.jk.swap(jk); gw.i1.swap(i1); gw.i2.swap(i2);
     }
     gw.nblk = (int)gw.jk.size();
+    tr.mark(inverse ? "inv: partition" : "fwd: partition");
 
     // deepest-box index per row and the box list on the device
     TRY(dalloc(p, &gw.d_rowk, Ng + 1));
@@ -403,6 +473,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
     k_rowk<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, gw.nblk, gw.d_box, gw.d_rowk);
     CJT_CUDA_TRY(cudaGetLastError());
 
+    tr.mark(inverse ? "inv: u,v tables, scales" : "fwd: u,v tables, scales");
     // ---- recurrence work: J(i) per row, chunks of <= 32 rows, degree segments
     const int S = p->seg_len;
     auto J_of = [&](int64_t i) -> int64_t {
@@ -502,6 +573,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
                                      cudaMemcpyHostToDevice, st));
         CJT_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    tr.mark(inverse ? "inv: host work lists" : "fwd: host work lists");
     // longest items first: the block scheduler then balances the SMs
     std::stable_sort(items.begin(), items.end(),
                      [](const RecItem &x, const RecItem &y) { return (x.b - x.a) > (y.b - y.a); });
@@ -520,12 +592,14 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
         CJT_CUDA_TRY(cudaGetLastError());
     }
     CJT_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope
+    tr.mark(inverse ? "inv: segment states" : "fwd: segment states");
     return CJT_OK;
 }
 
 }  // namespace
 
 int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
+    PlanTrace tr(st);
     const int64_t N = p->N;
     const double a = p->alpha, b = p->beta;
     p->corner = (std::fabs(std::fabs(a) - 0.5) == 0.0) && (std::fabs(std::fabs(b) - 0.5) == 0.0);
@@ -566,6 +640,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         CJT_CUDA_TRY(cudaGetLastError());
     }
 
+    tr.mark("tables: recurrence, C_nm");
     const bool fwd = p->opts.directions & CJT_FWD, inv = p->opts.directions & CJT_INV;
     if (fwd) TRY(build_grid(p, p->fw, N, false, h, st));
     if (inv) TRY(build_grid(p, p->iv, 2 * N, true, h, st));
@@ -636,6 +711,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         TRY(dalloc(p, (unsigned char **)&p->d_work, work));
         p->work_bytes = work;
     }
+    tr.mark("transforms: twiddles, chirps");
     const int64_t Ld = std::max<int64_t>(std::max(p->Lf, p->Li), 2);
     TRY(dalloc(p, (double2 **)&p->d_dct, Ld));
     TRY(dalloc(p, &p->d_y, 2 * N + 2));
@@ -648,14 +724,25 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         TRY(dalloc(p, &p->d_w, Ng + 1));
         TRY(dalloc(p, &p->d_s, N + 1));
         const double mu0 = std::exp2(a + b + 1.0) * std::tgamma(a + 1.0) * std::tgamma(b + 1.0) / std::tgamma(a + b + 2.0);
-        CJT_CUDA_TRY(cudaMemsetAsync(p->d_dct, 0, sizeof(double2) * 2 * Ng, st));
-        k_moments<<<1, 1, 0, st>>>(Ng, a, b, mu0, (double2 *)p->d_dct);
+        // modified moments mu_0..mu_Ng (Sec. 3.1, mu_1 with the sign of the weight's mean)
+        const double mu1 = (b - a) / (a + b + 2.0) * mu0;
+        const int64_t nchunk = std::max<int64_t>(1, (Ng - 1 + kMomChunk - 1) / kMomChunk);
+        double4 *T = nullptr;
+        double2 *start = nullptr;
+        CJT_CUDA_TRY(cudaMallocAsync((void **)&T, sizeof(double4) * nchunk, st));
+        CJT_CUDA_TRY(cudaMallocAsync((void **)&start, sizeof(double2) * nchunk, st));
+        k_mom_transfer<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, T);
+        k_mom_carry<<<1, 1, 0, st>>>(nchunk, mu0, mu1, T, start);
+        k_mom_fill<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, start, (double2 *)p->d_dct);
         CJT_CUDA_TRY(cudaGetLastError());
+        cudaFreeAsync(T, st);
+        cudaFreeAsync(start, st);
         TRY(cjt_dft_exec(p->dft_cc, p->d_dct, p->d_work, p->d_fft_scratch, 1, p->d_tw64, p->Ltab, st));
         k_cc_weights<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)p->d_dct, p->d_w);
         k_inv_norm<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, a, b, p->d_s);
         CJT_CUDA_TRY(cudaGetLastError());
     }
+    tr.mark("buffers, inverse weights");
     CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
     CJT_CUDA_TRY(cudaStreamSynchronize(st));
     return CJT_OK;
