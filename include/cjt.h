@@ -78,6 +78,10 @@ typedef struct {
     int seg_len;      /* degree-segment length of the recurrence work items; 0 -> 2048    */
     int use_asy;      /* 1 (default when 0): partition as in Sec. 2.2;
                          -1: recurrence only (no asymptotic blocks)                        */
+    int shared_workspace; /* 0: the plan owns its execution workspace (default);
+                         1: it owns only its tables, and executions borrow a workspace
+                         (cjt_forward_ws / cjt_inverse_ws, or the batched executor), so
+                         that thousands of plans fit in device memory                      */
 } cjt_plan_opts;
 
 /* Summary of a plan (for reports and tests). Sizes are per direction. */
@@ -96,6 +100,7 @@ typedef struct {
     int64_t device_bytes;    /* device memory owned by the plan                        */
     double plan_ms;          /* wall time of cjt_plan                                  */
     int64_t kernels_fwd, kernels_inv;   /* kernel launches of one execution              */
+    int64_t workspace_bytes;            /* execution workspace one execution needs       */
 } cjt_plan_info;
 
 /* Stages reported by cjt_get_profile (forward 0-4, inverse 5-9). */
@@ -155,6 +160,18 @@ int cjt_forward(cjt_plan_t plan, const double *c_jac_dev, double *c_cheb_dev, vo
 int cjt_inverse(cjt_plan_t plan, const double *c_cheb_dev, double *c_jac_dev, void *stream);
 
 /*
+ * Forward / inverse transform with a caller-supplied workspace: workspace_dev is
+ * a device buffer of at least cjt_plan_info.workspace_bytes bytes (256-byte
+ * aligned), used only for the duration of the call's work on `stream`.
+ * Works for every plan; required for plans built with shared_workspace = 1
+ * (cjt_forward / cjt_inverse return CJT_EINVAL for those).
+ */
+int cjt_forward_ws(cjt_plan_t plan, const double *c_jac_dev, double *c_cheb_dev, void *workspace_dev,
+                   size_t workspace_bytes, void *stream);
+int cjt_inverse_ws(cjt_plan_t plan, const double *c_cheb_dev, double *c_jac_dev, void *workspace_dev,
+                   size_t workspace_bytes, void *stream);
+
+/*
  * End-to-end transform from host memory: copies in_host (N+1 doubles) to the
  * plan's device staging buffer, runs the forward (direction = CJT_FWD) or
  * inverse (CJT_INV) transform, copies the result to out_host and waits for
@@ -164,17 +181,35 @@ int cjt_execute_host(cjt_plan_t plan, int direction, const double *in_host, doub
                      void *stream);
 
 /*
- * Batched execution (Sec. 4: the same plan machinery applied to many inputs):
+ * Batched execution (Sec. 4: one plan machinery applied to many inputs):
  * item t uses plans[t] in direction dir[t] (CJT_FWD or CJT_INV) on
  * in_dev + offsets[t] -> out_dev + offsets[t] (N_t + 1 doubles each, N_t the
- * degree of plans[t]).  Items may use different N, (alpha, beta) and
- * precision.  All stages of all items are issued as one sequence of
- * multi-item launches on `stream` (capturable into a CUDA graph).  A plan may
- * appear at most once per call.  in_dev and out_dev must not overlap.
+ * degree of plans[t]).  Items may mix N, (alpha, beta), precision and
+ * direction.  The items are spread, longest first, over a set of internal
+ * streams that fork from and join back to `stream` through events, so the
+ * call is ordered like any other work on `stream`.  Plans built with
+ * shared_workspace borrow per-stream workspace arenas owned by the library
+ * (grown on demand; the growing call must not be under stream capture).  A
+ * plan may appear at most once per call; in_dev and out_dev must not overlap.
  * Errors: CJT_EINVAL, CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA, CJT_ENOMEM.
  */
 int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, const int64_t *offsets,
                         const double *in_dev, double *out_dev, void *stream);
+
+/*
+ * A captured batch: cjt_batch_create sizes private workspace arenas for the
+ * items (nstreams concurrent lanes, 0 -> 16), captures the whole batched
+ * execution of the given items and buffers into one CUDA graph and
+ * instantiates it; cjt_batch_launch replays it on `stream` with a single graph
+ * launch.  Plans and buffers must outlive the batch.  cjt_batch_info reports
+ * the number of kernel nodes and the arena bytes.
+ */
+typedef struct cjt_batch_s *cjt_batch_t;
+int cjt_batch_create(cjt_batch_t *out, int count, const cjt_plan_t *plans, const int8_t *dir,
+                     const int64_t *offsets, const double *in_dev, double *out_dev, int nstreams);
+int cjt_batch_launch(cjt_batch_t batch, void *stream);
+int cjt_batch_info(cjt_batch_t batch, int64_t *kernels, int64_t *arena_bytes);
+void cjt_batch_destroy(cjt_batch_t batch);
 
 /*
  * Stage profiling.  cjt_set_profiling(plan, 1) makes every later execution of

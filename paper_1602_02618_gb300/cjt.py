@@ -34,7 +34,7 @@ CJT_INV = 2
 class cjt_plan_opts(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("eps", ctypes.c_double), ("precision", ctypes.c_int),
                 ("directions", ctypes.c_int), ("ratio", ctypes.c_double), ("seg_len", ctypes.c_int),
-                ("use_asy", ctypes.c_int)]
+                ("use_asy", ctypes.c_int), ("shared_workspace", ctypes.c_int)]
 
 
 class cjt_plan_info(ctypes.Structure):
@@ -45,7 +45,7 @@ class cjt_plan_info(ctypes.Structure):
                 ("fft_len_fwd", ctypes.c_int64), ("fft_len_inv", ctypes.c_int64), ("nfft_fwd", ctypes.c_int64),
                 ("nfft_inv", ctypes.c_int64), ("rec_items_fwd", ctypes.c_int64), ("rec_items_inv", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("plan_ms", ctypes.c_double), ("kernels_fwd", ctypes.c_int64),
-                ("kernels_inv", ctypes.c_int64)]
+                ("kernels_inv", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -53,7 +53,9 @@ class cjt_plan_info(ctypes.Structure):
 
 EXPORTED = ["cjt_plan_opts_default", "cjt_plan", "cjt_destroy", "cjt_get_info", "cjt_forward", "cjt_inverse",
             "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_strerror", "cjt_last_cuda_error",
-            "cjt_version", "cjt_set_profiling", "cjt_get_profile", "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc"]
+            "cjt_version", "cjt_set_profiling", "cjt_get_profile", "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc",
+            "cjt_forward_ws", "cjt_inverse_ws", "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info",
+            "cjt_batch_destroy"]
 
 NOALLOC_MAX_N = 65536
 
@@ -98,13 +100,22 @@ def load(path: str = LIB_PATH):
         lib.cjt_get_profile.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64), i]
         lib.cjt_microbench_fma.argtypes = [i, ctypes.POINTER(d), vp]
         lib.cjt_cheb_coeffs_noalloc.argtypes = [i64, vp, vp, vp]
+        lib.cjt_forward_ws.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
+        lib.cjt_inverse_ws.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
+        lib.cjt_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int8),
+                                         ctypes.POINTER(i64), vp, vp, i]
+        lib.cjt_batch_launch.argtypes = [vp, vp]
+        lib.cjt_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.cjt_batch_destroy.argtypes = [vp]
+        lib.cjt_batch_destroy.restype = None
         lib.cjt_strerror.argtypes = [i]
         lib.cjt_strerror.restype = ctypes.c_char_p
         lib.cjt_last_cuda_error.restype = ctypes.c_char_p
         lib.cjt_version.restype = ctypes.c_char_p
         for name in ("cjt_plan_opts_default", "cjt_plan", "cjt_get_info", "cjt_forward", "cjt_inverse",
                      "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_set_profiling", "cjt_get_profile",
-                     "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc"):
+                     "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc", "cjt_forward_ws", "cjt_inverse_ws",
+                     "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -143,9 +154,10 @@ class Plan:
     """A cjt_plan_t: device-resident tables for degree N and parameters (alpha, beta)."""
 
     def __init__(self, N: int, alpha: float, beta: float, M: int = 0, eps: float = 0.0, precision: int = CJT_FP64,
-                 directions: int = 0, ratio: float = 0.0, seg_len: int = 0, use_asy: int = 0, stream=None):
+                 directions: int = 0, ratio: float = 0.0, seg_len: int = 0, use_asy: int = 0,
+                 shared_workspace: bool = False, stream=None):
         lib = load()
-        o = cjt_plan_opts(M, eps, precision, directions, ratio, seg_len, use_asy)
+        o = cjt_plan_opts(M, eps, precision, directions, ratio, seg_len, use_asy, 1 if shared_workspace else 0)
         h = ctypes.c_void_p()
         _check(lib.cjt_plan(ctypes.byref(h), int(N), float(alpha), float(beta), ctypes.byref(o),
                             _stream_handle(stream)), "cjt_plan")
@@ -230,6 +242,58 @@ def cjt_execute_batched(plans, dirs, offsets, x_dev, out_dev, stream=None):
     _check(load().cjt_execute_batched(count, arr, d, off, _dev_ptr(x_dev, total), _dev_ptr(out_dev, total),
                                       _stream_handle(stream)), "cjt_execute_batched")
     return out_dev
+
+
+def cjt_forward_ws(plan: Plan, c_jac, c_cheb, workspace, stream=None):
+    """Forward transform borrowing `workspace` (a CUDA tensor of >= workspace_bytes bytes)."""
+    n = plan.N + 1
+    _check(load().cjt_forward_ws(plan.handle, _dev_ptr(c_jac, n), _dev_ptr(c_cheb, n),
+                                 ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
+                                 _stream_handle(stream)), "cjt_forward_ws")
+    return c_cheb
+
+
+def cjt_inverse_ws(plan: Plan, c_cheb, c_jac, workspace, stream=None):
+    n = plan.N + 1
+    _check(load().cjt_inverse_ws(plan.handle, _dev_ptr(c_cheb, n), _dev_ptr(c_jac, n),
+                                 ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
+                                 _stream_handle(stream)), "cjt_inverse_ws")
+    return c_jac
+
+
+class Batch:
+    """cjt_batch_t: a batched execution captured into one CUDA graph."""
+
+    def __init__(self, plans, dirs, offsets, x_dev, out_dev, nstreams: int = 0):
+        count = len(plans)
+        arr = (ctypes.c_void_p * count)(*[p.handle.value for p in plans])
+        d = (ctypes.c_int8 * count)(*[int(v) for v in dirs])
+        off = (ctypes.c_int64 * count)(*[int(v) for v in offsets])
+        total = max(int(o) + p.N + 1 for o, p in zip(offsets, plans))
+        h = ctypes.c_void_p()
+        _check(load().cjt_batch_create(ctypes.byref(h), count, arr, d, off, _dev_ptr(x_dev, total),
+                                       _dev_ptr(out_dev, total), int(nstreams)), "cjt_batch_create")
+        self._h = h
+        self._keep = (plans, x_dev, out_dev)
+
+    def launch(self, stream=None):
+        _check(load().cjt_batch_launch(self._h, _stream_handle(stream)), "cjt_batch_launch")
+
+    def info(self):
+        k, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().cjt_batch_info(self._h, ctypes.byref(k), ctypes.byref(b)), "cjt_batch_info")
+        return {"kernels": k.value, "arena_bytes": b.value}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().cjt_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cjt_sync(stream=None):

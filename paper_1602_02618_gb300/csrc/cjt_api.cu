@@ -15,7 +15,9 @@ thread_local char g_cuda_err[256] = "";
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
-int begin_use(cjt_plan_s *p, cudaStream_t st) {
+}  // namespace
+
+int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st) {
     if (p->has_pending && p->last_stream != st) {
         cudaError_t q = cudaEventQuery(p->done);
         if (q == cudaErrorNotReady) return CJT_EBUSY;
@@ -27,12 +29,14 @@ int begin_use(cjt_plan_s *p, cudaStream_t st) {
     return CJT_OK;
 }
 
-int end_use(cjt_plan_s *p, cudaStream_t st) {
+int cjt_internal_end_use(cjt_plan_s *p, cudaStream_t st) {
     CJT_CUDA_TRY(cudaEventRecord(p->done, st));
     p->last_stream = st;
     p->has_pending = true;
     return CJT_OK;
 }
+
+namespace {
 
 int fft_launches(int64_t L) { return L <= 1 ? 0 : (L <= 4096 ? 1 : 2); }
 int dft_launches(const Dft &d) { return d.L <= 1 ? 0 : (d.P ? 3 + 2 * fft_launches(d.P) : fft_launches(d.L)); }
@@ -101,6 +105,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
         o.ratio = opts->ratio;
         if (opts->seg_len) o.seg_len = opts->seg_len;
         if (opts->use_asy) o.use_asy = opts->use_asy;
+        o.shared_workspace = opts->shared_workspace;
     }
     if (o.M < 1 || o.M > 20) return CJT_EINVAL;
     if (!(o.eps > 0.0 && o.eps < 1.0)) return CJT_EINVAL;
@@ -171,6 +176,7 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
     info->rec_items_inv = p->iv.nitems;
     info->device_bytes = p->device_bytes;
     info->plan_ms = p->plan_ms;
+    info->workspace_bytes = p->ws_bytes;
     if (p->N == 0) {
         info->kernels_fwd = info->kernels_inv = 1;
     } else {
@@ -217,67 +223,54 @@ int cjt_get_profile(cjt_plan_t p, double *ms, int64_t *counts, int n) {
     return rc;
 }
 
-int cjt_forward(cjt_plan_t p, const double *in, double *out, void *stream) {
+static int run_one(cjt_plan_t p, int direction, const double *in, double *out, const Workspace &ws, void *stream) {
     if (!p || !in || !out) return CJT_EINVAL;
-    if (!(p->opts.directions & CJT_FWD)) return CJT_EDIRECTION;
+    if (!(p->opts.directions & direction)) return CJT_EDIRECTION;
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = begin_use(p, st);
+    int rc = cjt_internal_begin_use(p, st);
     if (rc) return rc;
-    rc = cjt_exec_forward(p, in, out, st);
+    rc = direction == CJT_FWD ? cjt_exec_forward(p, ws, in, out, st) : cjt_exec_inverse(p, ws, in, out, st);
     if (rc) return rc;
-    return end_use(p, st);
+    return cjt_internal_end_use(p, st);
+}
+
+int cjt_forward(cjt_plan_t p, const double *in, double *out, void *stream) {
+    if (p && p->shared_ws && p->N > 0) return CJT_EINVAL;
+    return p ? run_one(p, CJT_FWD, in, out, p->ws, stream) : CJT_EINVAL;
 }
 
 int cjt_inverse(cjt_plan_t p, const double *in, double *out, void *stream) {
-    if (!p || !in || !out) return CJT_EINVAL;
-    if (!(p->opts.directions & CJT_INV)) return CJT_EDIRECTION;
-    cudaStream_t st = (cudaStream_t)stream;
-    int rc = begin_use(p, st);
-    if (rc) return rc;
-    rc = cjt_exec_inverse(p, in, out, st);
-    if (rc) return rc;
-    return end_use(p, st);
+    if (p && p->shared_ws && p->N > 0) return CJT_EINVAL;
+    return p ? run_one(p, CJT_INV, in, out, p->ws, stream) : CJT_EINVAL;
+}
+
+int cjt_forward_ws(cjt_plan_t p, const double *in, double *out, void *ws, size_t bytes, void *stream) {
+    if (!p || (!ws && p->ws_bytes > 0) || (int64_t)bytes < p->ws_bytes) return CJT_EINVAL;
+    return run_one(p, CJT_FWD, in, out, cjt_carve(p, ws), stream);
+}
+
+int cjt_inverse_ws(cjt_plan_t p, const double *in, double *out, void *ws, size_t bytes, void *stream) {
+    if (!p || (!ws && p->ws_bytes > 0) || (int64_t)bytes < p->ws_bytes) return CJT_EINVAL;
+    return run_one(p, CJT_INV, in, out, cjt_carve(p, ws), stream);
 }
 
 int cjt_execute_host(cjt_plan_t p, int direction, const double *in_host, double *out_host, void *stream) {
     if (!p || !in_host || !out_host) return CJT_EINVAL;
     if (direction != CJT_FWD && direction != CJT_INV) return CJT_EINVAL;
     if (!(p->opts.directions & direction)) return CJT_EDIRECTION;
+    if (p->shared_ws && p->N > 0) return CJT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = begin_use(p, st);
+    int rc = cjt_internal_begin_use(p, st);
     if (rc) return rc;
     const size_t bytes = sizeof(double) * (size_t)(p->N + 1);
     CJT_CUDA_TRY(cudaMemcpyAsync(p->d_in, in_host, bytes, cudaMemcpyHostToDevice, st));
-    rc = direction == CJT_FWD ? cjt_exec_forward(p, p->d_in, p->d_out, st) : cjt_exec_inverse(p, p->d_in, p->d_out, st);
+    rc = direction == CJT_FWD ? cjt_exec_forward(p, p->ws, p->d_in, p->d_out, st)
+                              : cjt_exec_inverse(p, p->ws, p->d_in, p->d_out, st);
     if (rc) return rc;
     CJT_CUDA_TRY(cudaMemcpyAsync(out_host, p->d_out, bytes, cudaMemcpyDeviceToHost, st));
-    rc = end_use(p, st);
+    rc = cjt_internal_end_use(p, st);
     if (rc) return rc;
     CJT_CUDA_TRY(cudaStreamSynchronize(st));
-    return CJT_OK;
-}
-
-int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, const int64_t *offsets,
-                        const double *in_dev, double *out_dev, void *stream) {
-    if (count < 0) return CJT_EINVAL;
-    if (count == 0) return CJT_OK;
-    if (!plans || !dir || !offsets || !in_dev || !out_dev) return CJT_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
-    for (int t = 0; t < count; ++t) {
-        if (!plans[t]) return CJT_EINVAL;
-        if (dir[t] != CJT_FWD && dir[t] != CJT_INV) return CJT_EINVAL;
-        if (!(plans[t]->opts.directions & dir[t])) return CJT_EDIRECTION;
-        int rc = begin_use(plans[t], st);
-        if (rc) return rc;
-    }
-    for (int t = 0; t < count; ++t) {
-        cjt_plan_s *p = plans[t];
-        int rc = dir[t] == CJT_FWD ? cjt_exec_forward(p, in_dev + offsets[t], out_dev + offsets[t], st)
-                                   : cjt_exec_inverse(p, in_dev + offsets[t], out_dev + offsets[t], st);
-        if (rc) return rc;
-        rc = end_use(p, st);
-        if (rc) return rc;
-    }
     return CJT_OK;
 }
 

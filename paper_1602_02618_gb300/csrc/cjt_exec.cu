@@ -356,7 +356,7 @@ __global__ void k_copy(int64_t n, const double *__restrict__ in, double *__restr
 // ---------------------------------------------------------------------------
 // forward / inverse drivers
 // ---------------------------------------------------------------------------
-int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t st) {
+int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st) {
     const int64_t N = p->N;
     if (N == 0) {
         k_copy<<<1, 32, 0, st>>>(1, in, out);
@@ -371,7 +371,7 @@ int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
     if (gw.nitems > 0) {
         StageTimer tm(p, st, CJT_STAGE_FWD_REC);
         k_rec_fwd<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, gw.Ng, p->rt, in,
-                                                                  gw.d_states, gw.d_partials);
+                                                                  gw.d_states, ws.part_f);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     // ASY
@@ -381,39 +381,39 @@ int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
         dim3 gp(blocks_for(L, 256), p->npair_f);
         StageTimer tm(p, st, CJT_STAGE_FWD_PACK);
         if (fp32)
-            k_asy_pack_fwd<float2><<<gp, 256, 0, st>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in, (float2 *)p->d_fft_f);
+            k_asy_pack_fwd<float2><<<gp, 256, 0, st>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in, (float2 *)ws.fft_f);
         else
-            k_asy_pack_fwd<double2><<<gp, 256, 0, st>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in, (double2 *)p->d_fft_f);
+            k_asy_pack_fwd<double2><<<gp, 256, 0, st>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in, (double2 *)ws.fft_f);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     if (nq > 0) {
         StageTimer tm(p, st, CJT_STAGE_FWD_FFT);
-        rc = cjt_dft_exec(p->dft_f, p->d_fft_f, p->d_work, p->d_fft_scratch, p->npair_f, fp32 ? p->d_tw32 : p->d_tw64,
+        rc = cjt_dft_exec(p->dft_f, ws.fft_f, ws.work, ws.scratch, p->npair_f, fp32 ? p->d_tw32 : p->d_tw64,
                           p->Ltab, st);
         if (rc) return rc;
     }
-    double2 *ext = (double2 *)p->d_dct;
+    double2 *ext = (double2 *)ws.dct;
     {
     StageTimer tm(p, st, CJT_STAGE_FWD_COMBINE);
     if (fp32)
         k_combine_fwd<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const float2 *)p->d_fft_f, gw.d_row_base, gw.d_row_nseg,
-            gw.d_partials, ext);
+            N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const float2 *)ws.fft_f, gw.d_row_base, gw.d_row_nseg,
+            ws.part_f, ext);
     else
         k_combine_fwd<double2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const double2 *)p->d_fft_f, gw.d_row_base, gw.d_row_nseg,
-            gw.d_partials, ext);
+            N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const double2 *)ws.fft_f, gw.d_row_base, gw.d_row_nseg,
+            ws.part_f, ext);
     CJT_CUDA_TRY(cudaGetLastError());
     }
     StageTimer tm(p, st, CJT_STAGE_FWD_DCT);
-    rc = cjt_dft_exec(p->dft_dct, p->d_dct, p->d_work, p->d_fft_scratch, 1, p->d_tw64, p->Ltab, st);
+    rc = cjt_dft_exec(p->dft_dct, ws.dct, ws.work, ws.scratch, 1, p->d_tw64, p->Ltab, st);
     if (rc) return rc;
-    k_dct_finish<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, (const double2 *)p->d_dct, out);
+    k_dct_finish<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, (const double2 *)ws.dct, out);
     CJT_CUDA_TRY(cudaGetLastError());
     return CJT_OK;
 }
 
-int cjt_exec_inverse(cjt_plan_s *p, const double *in, double *out, cudaStream_t st) {
+int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st) {
     const int64_t N = p->N;
     if (N == 0) {
         k_copy<<<1, 32, 0, st>>>(1, in, out);
@@ -428,11 +428,11 @@ int cjt_exec_inverse(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
     int rc;
     {
     StageTimer tm(p, st, CJT_STAGE_INV_FRONT);
-    k_inv_front_pack<<<blocks_for(L, 256), 256, 0, st>>>(N, L, in, (double2 *)p->d_dct);
+    k_inv_front_pack<<<blocks_for(L, 256), 256, 0, st>>>(N, L, in, (double2 *)ws.dct);
     CJT_CUDA_TRY(cudaGetLastError());
-    rc = cjt_dft_exec(p->dft_front, p->d_dct, p->d_work, p->d_fft_scratch, 1, p->d_tw64, p->Ltab, st);
+    rc = cjt_dft_exec(p->dft_front, ws.dct, ws.work, ws.scratch, 1, p->d_tw64, p->Ltab, st);
     if (rc) return rc;
-    k_inv_g<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)p->d_dct, p->d_w, p->d_g);
+    k_inv_g<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)ws.dct, p->d_w, ws.g);
     CJT_CUDA_TRY(cudaGetLastError());
     }
     // transposed asymptotic blocks
@@ -441,34 +441,34 @@ int cjt_exec_inverse(cjt_plan_s *p, const double *in, double *out, cudaStream_t 
         dim3 gp(blocks_for(L, 256), p->npair_i);
         StageTimer tm(p, st, CJT_STAGE_INV_PACK);
         if (fp32)
-            k_asy_pack_inv<float2><<<gp, 256, 0, st>>>(Ng, L, M, nq, gw.d_box, gw.d_scale, gw.d_u, gw.d_v, p->d_g, (float2 *)p->d_fft_i);
+            k_asy_pack_inv<float2><<<gp, 256, 0, st>>>(Ng, L, M, nq, gw.d_box, gw.d_scale, gw.d_u, gw.d_v, ws.g, (float2 *)ws.fft_i);
         else
-            k_asy_pack_inv<double2><<<gp, 256, 0, st>>>(Ng, L, M, nq, gw.d_box, gw.d_scale, gw.d_u, gw.d_v, p->d_g, (double2 *)p->d_fft_i);
+            k_asy_pack_inv<double2><<<gp, 256, 0, st>>>(Ng, L, M, nq, gw.d_box, gw.d_scale, gw.d_u, gw.d_v, ws.g, (double2 *)ws.fft_i);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     if (nq > 0) {
         StageTimer tm(p, st, CJT_STAGE_INV_FFT);
-        rc = cjt_dft_exec(p->dft_i, p->d_fft_i, p->d_work, p->d_fft_scratch, p->npair_i, fp32 ? p->d_tw32 : p->d_tw64,
+        rc = cjt_dft_exec(p->dft_i, ws.fft_i, ws.work, ws.scratch, p->npair_i, fp32 ? p->d_tw32 : p->d_tw64,
                           p->Ltab, st);
         if (rc) return rc;
     }
     // transposed recurrence
     if (gw.nitems > 0) {
         StageTimer tm(p, st, CJT_STAGE_INV_REC);
-        k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt, p->d_g,
-                                                                             gw.d_states, gw.d_partials);
+        k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt, ws.g,
+                                                                             gw.d_states, ws.part_i);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     StageTimer tm(p, st, CJT_STAGE_INV_COMBINE);
     k_inv_reduce<<<blocks_for(N + 1, 32), 32 * RED_WARPS, 0, st>>>(N, p->seg_len, gw.d_seg_ptr, gw.d_seg_out,
-                                                                     gw.d_seg_b, gw.d_partials, p->d_y);
+                                                                     gw.d_seg_b, ws.part_i, ws.y);
     CJT_CUDA_TRY(cudaGetLastError());
     if (fp32)
         k_combine_inv<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const float2 *)p->d_fft_i, p->d_y, p->d_s, out);
+            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const float2 *)ws.fft_i, ws.y, p->d_s, out);
     else
         k_combine_inv<double2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const double2 *)p->d_fft_i, p->d_y, p->d_s, out);
+            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const double2 *)ws.fft_i, ws.y, p->d_s, out);
     CJT_CUDA_TRY(cudaGetLastError());
     return CJT_OK;
 }

@@ -21,6 +21,8 @@
 
 #include "cjt_internal.cuh"
 
+int cjt_fft_prime();
+
 namespace {
 
 template <typename T> struct cplx;
@@ -166,11 +168,8 @@ int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batc
     const int tile = (int)std::max<int64_t>(1, tile64);
     size_t smem = (size_t)tile * (Ls + SMEM_PAD) * sizeof(V);
     const int threads = (int)std::min<int64_t>(FFT_THREADS, std::max<int64_t>(32, ((int64_t)tile * Ls / 4 + 31) / 32 * 32));
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(R) == 8]) {
-        CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr_set[sizeof(R) == 8] = true;
-    }
+    int prc = cjt_fft_prime();
+    if (prc) return prc;
     dim3 grid((unsigned)((ncols + tile - 1) / tile), (unsigned)batch);
     k_fft_sub<R><<<grid, threads, smem, st>>>((const V *)in, (V *)out, logLs, ncols, tile, in_es, in_cs, in_ts,
                                                     out_ks, out_cs, out_ts, (const V *)tw, logLtab, post_log);
@@ -341,3 +340,14 @@ int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void
 }
 
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch) { return L > 4096 ? L * batch : 0; }
+
+// One-time function attributes, so that later launches (possibly under stream capture)
+// make no configuration calls.
+int cjt_fft_prime() {
+    static bool done = false;
+    if (done) return CJT_OK;
+    CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    done = true;
+    return CJT_OK;
+}

@@ -32,6 +32,9 @@
     } while (0)
 
 void cjt_internal_set_cuda_error(cudaError_t e, const char *what);
+struct cjt_plan_s;
+int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st);
+int cjt_internal_end_use(cjt_plan_s *p, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // recurrence work items
@@ -69,8 +72,7 @@ struct GridWork {
     int64_t nitems = 0;
     double *d_states = nullptr;   // [nstate][32][2]
     int64_t nstate = 0;
-    double *d_partials = nullptr;
-    int64_t npartials = 0;
+    int64_t npartials = 0;        // recurrence partial sums (in the workspace)
     // state computation rows
     int *d_srow = nullptr;        // rows needing states: row, J, mode, chunk_state_base, lane, nseg
     int64_t nsrow = 0;
@@ -101,6 +103,15 @@ struct Dft {
     int64_t fft_len() const { return P ? P : L; }
 };
 
+// Execution workspace of a plan: one arena carved into these buffers.  A plan owns
+// one unless it was built with shared_workspace, in which case the caller (or the
+// batched executor) supplies the arena.
+struct Workspace {
+    void *fft_f = nullptr, *fft_i = nullptr, *scratch = nullptr, *work = nullptr;
+    double *dct = nullptr, *y = nullptr, *g = nullptr, *part_f = nullptr, *part_i = nullptr;
+};
+enum { WS_FFT_F, WS_FFT_I, WS_SCRATCH, WS_WORK, WS_DCT, WS_Y, WS_G, WS_PART_F, WS_PART_I, WS_COUNT };
+
 struct cjt_plan_s {
     int64_t N = 0;
     double alpha = 0, beta = 0;
@@ -124,16 +135,13 @@ struct cjt_plan_s {
     void *d_tw64 = nullptr;       // double2[Ltab]
     void *d_tw32 = nullptr;       // float2[Ltab]
     int npair_f = 0, npair_i = 0; // complex transforms of ASY item pairs
-    void *d_fft_f = nullptr;      // forward ASY buffers (npair_f x Lf), precision dependent
-    void *d_fft_i = nullptr;      // inverse ASY buffers (npair_i x Li)
-    void *d_fft_scratch = nullptr;// scratch for four-step transforms (bytes: scratch_bytes)
-    int64_t scratch_bytes = 0;
-    void *d_work = nullptr;       // Bluestein work rows (bytes: work_bytes)
-    int64_t work_bytes = 0;
     Dft dft_f, dft_dct, dft_front, dft_i, dft_cc;
-    double *d_dct = nullptr;      // complex FP64 buffer of length max(Lf, Li) (DCT-I / front end)
-    double *d_y = nullptr;        // forward grid values / inverse degree sums
-    double *d_g = nullptr;        // inverse: w_i p_N(x_i) on the 2N grid
+    // workspace layout (byte offsets and sizes within the arena) and the owned workspace
+    int64_t ws_off[WS_COUNT] = {0};
+    int64_t ws_size[WS_COUNT] = {0};
+    int64_t ws_bytes = 0;
+    bool shared_ws = false;
+    Workspace ws{};
     double *d_w = nullptr;        // inverse: Clenshaw--Curtis weights (2N+1)
     double *d_s = nullptr;        // inverse: 1/A_n (N+1)
     double *d_in = nullptr, *d_out = nullptr;  // staging for cjt_execute_host
@@ -256,6 +264,7 @@ __host__ __device__ inline double cjt_hahn_h(int l, double a) {
 int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab,
                  bool fp32, cudaStream_t st);
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch);
+int cjt_fft_prime();
 // Bluestein length (0 when L is a power of two)
 int64_t cjt_dft_padded(int64_t L, int64_t S, int64_t K);
 // chirp and bhat for a Bluestein transform; tw64 must cover P
@@ -266,5 +275,6 @@ int64_t cjt_dft_work_bytes(const Dft &d, int64_t batch);
 int64_t cjt_dft_scratch_bytes(const Dft &d, int64_t batch);
 
 int cjt_plan_build(cjt_plan_s *p, cudaStream_t st);
-int cjt_exec_forward(cjt_plan_s *p, const double *in, double *out, cudaStream_t st);
-int cjt_exec_inverse(cjt_plan_s *p, const double *in, double *out, cudaStream_t st);
+Workspace cjt_carve(const cjt_plan_s *p, void *base);
+int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st);
+int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st);

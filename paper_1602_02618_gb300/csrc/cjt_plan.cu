@@ -581,7 +581,6 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
     TRY(dalloc(p, &gw.d_items, gw.nitems));
     if (gw.nitems)
         CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_items, items.data(), sizeof(RecItem) * items.size(), cudaMemcpyHostToDevice, st));
-    TRY(dalloc(p, &gw.d_partials, std::max<int64_t>(gw.npartials, 1)));
     TRY(dalloc(p, &gw.d_states, std::max<int64_t>(nstate * 64, 1)));
     CJT_CUDA_TRY(cudaMemsetAsync(gw.d_states, 0, sizeof(double) * std::max<int64_t>(nstate * 64, 1), st));
     if (gw.nsrow > 0) {
@@ -600,6 +599,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
 
 int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     PlanTrace tr(st);
+    TRY(cjt_fft_prime());
     const int64_t N = p->N;
     const double a = p->alpha, b = p->beta;
     p->corner = (std::fabs(std::fabs(a) - 0.5) == 0.0) && (std::fabs(std::fabs(b) - 0.5) == 0.0);
@@ -692,35 +692,44 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         work = std::max(work, cjt_dft_work_bytes(d, u.second));
         scratch = std::max(scratch, cjt_dft_scratch_bytes(d, u.second));
     }
-    const size_t csz = fp32 ? sizeof(float2) : sizeof(double2);
-    if (p->npair_f) {
-        void *v;
-        CJT_CUDA_TRY(cudaMalloc(&v, csz * p->npair_f * p->Lf));
-        p->allocs.push_back(v); p->device_bytes += csz * p->npair_f * p->Lf; p->d_fft_f = v;
-    }
-    if (p->npair_i) {
-        void *v;
-        CJT_CUDA_TRY(cudaMalloc(&v, csz * p->npair_i * p->Li));
-        p->allocs.push_back(v); p->device_bytes += csz * p->npair_i * p->Li; p->d_fft_i = v;
-    }
-    if (scratch) {
-        TRY(dalloc(p, (unsigned char **)&p->d_fft_scratch, scratch));
-        p->scratch_bytes = scratch;
-    }
-    if (work) {
-        TRY(dalloc(p, (unsigned char **)&p->d_work, work));
-        p->work_bytes = work;
-    }
     tr.mark("transforms: twiddles, chirps");
-    const int64_t Ld = std::max<int64_t>(std::max(p->Lf, p->Li), 2);
-    TRY(dalloc(p, (double2 **)&p->d_dct, Ld));
-    TRY(dalloc(p, &p->d_y, 2 * N + 2));
+    // execution workspace layout
+    {
+        const int64_t csz = fp32 ? (int64_t)sizeof(float2) : (int64_t)sizeof(double2);
+        const int64_t Ld = std::max<int64_t>(std::max(p->Lf, p->Li), 2);
+        p->ws_size[WS_FFT_F] = csz * p->npair_f * p->Lf;
+        p->ws_size[WS_FFT_I] = csz * p->npair_i * p->Li;
+        p->ws_size[WS_SCRATCH] = scratch;
+        p->ws_size[WS_WORK] = work;
+        p->ws_size[WS_DCT] = (int64_t)sizeof(double2) * Ld;
+        p->ws_size[WS_Y] = (int64_t)sizeof(double) * (2 * N + 2);
+        p->ws_size[WS_G] = inv ? (int64_t)sizeof(double) * (2 * N + 1) : 0;
+        p->ws_size[WS_PART_F] = (int64_t)sizeof(double) * (fwd ? std::max<int64_t>(p->fw.npartials, 1) : 0);
+        p->ws_size[WS_PART_I] = (int64_t)sizeof(double) * (inv ? std::max<int64_t>(p->iv.npartials, 1) : 0);
+        int64_t off = 0;
+        for (int k = 0; k < WS_COUNT; ++k) {
+            p->ws_off[k] = off;
+            off += (p->ws_size[k] + 255) / 256 * 256;
+        }
+        p->ws_bytes = off;
+    }
+    p->shared_ws = p->opts.shared_workspace != 0;
+    void *tmp_ws = nullptr;
+    if (!p->shared_ws) {
+        unsigned char *arena = nullptr;
+        TRY(dalloc(p, &arena, p->ws_bytes));
+        p->ws = cjt_carve(p, arena);
+    }
     TRY(dalloc(p, &p->d_in, N + 1));
     TRY(dalloc(p, &p->d_out, N + 1));
 
     if (inv && N >= 1) {
         const int64_t Ng = 2 * N;
-        TRY(dalloc(p, &p->d_g, Ng + 1));
+        Workspace ws = p->ws;
+        if (p->shared_ws) {   // a temporary arena for the weights
+            CJT_CUDA_TRY(cudaMallocAsync(&tmp_ws, p->ws_bytes, st));
+            ws = cjt_carve(p, tmp_ws);
+        }
         TRY(dalloc(p, &p->d_w, Ng + 1));
         TRY(dalloc(p, &p->d_s, N + 1));
         const double mu0 = std::exp2(a + b + 1.0) * std::tgamma(a + 1.0) * std::tgamma(b + 1.0) / std::tgamma(a + b + 2.0);
@@ -733,17 +742,35 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         CJT_CUDA_TRY(cudaMallocAsync((void **)&start, sizeof(double2) * nchunk, st));
         k_mom_transfer<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, T);
         k_mom_carry<<<1, 1, 0, st>>>(nchunk, mu0, mu1, T, start);
-        k_mom_fill<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, start, (double2 *)p->d_dct);
+        k_mom_fill<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, start, (double2 *)ws.dct);
         CJT_CUDA_TRY(cudaGetLastError());
         cudaFreeAsync(T, st);
         cudaFreeAsync(start, st);
-        TRY(cjt_dft_exec(p->dft_cc, p->d_dct, p->d_work, p->d_fft_scratch, 1, p->d_tw64, p->Ltab, st));
-        k_cc_weights<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)p->d_dct, p->d_w);
+        TRY(cjt_dft_exec(p->dft_cc, ws.dct, ws.work, ws.scratch, 1, p->d_tw64, p->Ltab, st));
+        k_cc_weights<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)ws.dct, p->d_w);
         k_inv_norm<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, a, b, p->d_s);
         CJT_CUDA_TRY(cudaGetLastError());
     }
+    if (tmp_ws) cudaFreeAsync(tmp_ws, st);
     tr.mark("buffers, inverse weights");
     CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
     CJT_CUDA_TRY(cudaStreamSynchronize(st));
     return CJT_OK;
+}
+
+Workspace cjt_carve(const cjt_plan_s *p, void *base) {
+    Workspace w;
+    if (!base) return w;
+    unsigned char *b = (unsigned char *)base;
+    auto at = [&](int k) -> void * { return p->ws_size[k] ? (void *)(b + p->ws_off[k]) : nullptr; };
+    w.fft_f = at(WS_FFT_F);
+    w.fft_i = at(WS_FFT_I);
+    w.scratch = at(WS_SCRATCH);
+    w.work = at(WS_WORK);
+    w.dct = (double *)at(WS_DCT);
+    w.y = (double *)at(WS_Y);
+    w.g = (double *)at(WS_G);
+    w.part_f = (double *)at(WS_PART_F);
+    w.part_i = (double *)at(WS_PART_I);
+    return w;
 }
