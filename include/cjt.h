@@ -28,10 +28,12 @@
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *    stream.  Device-side calls are asynchronous: they return once the work
  *    is enqueued; faults surface from cjt_sync or the next CUDA call.
- *  - A plan owns all its device tables and workspace.  One plan may be in use
- *    on one stream at a time: a call on a different stream while the plan's
- *    previous work is still running returns CJT_EBUSY.  Distinct plans are
- *    independent and may run concurrently.
+ *  - A plan owns all its device tables and, by default, its workspace.  A plan
+ *    with its own workspace may be in use on one stream at a time: a call on a
+ *    different stream while the plan's previous work is still running returns
+ *    CJT_EBUSY.  A plan built with shared_workspace holds only read-only tables
+ *    and may run on any number of streams at once, each execution with its own
+ *    workspace.  Distinct plans are independent and may run concurrently.
  *  - Return values: 0 (CJT_OK) on success, a negative CJT_E* code otherwise;
  *    cjt_strerror() names it.  No C++ exception crosses this boundary.
  *  - The library never falls back to a CPU path: every step of a transform

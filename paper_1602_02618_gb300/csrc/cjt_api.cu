@@ -18,6 +18,9 @@ bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 }  // namespace
 
 int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st) {
+    // a shared-workspace plan holds only read-only tables: any number of streams may use
+    // it at once, each with its own workspace
+    if (p->shared_ws) return CJT_OK;
     if (p->has_pending && p->last_stream != st) {
         cudaError_t q = cudaEventQuery(p->done);
         if (q == cudaErrorNotReady) return CJT_EBUSY;

@@ -71,3 +71,16 @@ def batch_workload(count: int = 4096, seed: int = BASE_SEED, nmin: int = 64, nma
         items.append((N, float(ab[t, 0]), float(ab[t, 1]), int(dirs[t]),
                       decaying_coefficients(N, 1.0, seed + 1 + t)))
     return items
+
+
+def serving_requests(count: int, seed: int = BASE_SEED, nmin: int = 128, nmax: int = 1 << 18):
+    """Request stream: N log-uniform in [nmin, nmax], (alpha, beta) ~ U[-0.45, 0.45]^2,
+    direction Bernoulli(1/2) (+1 forward, -1 inverse), c_n = g_n/(n+1)."""
+    r = rng(seed)
+    out = []
+    for t in range(count):
+        N = int(np.clip(np.rint(np.exp(r.uniform(np.log(nmin), np.log(nmax)))), nmin, nmax))
+        a, b = r.uniform(-0.45, 0.45, 2)
+        d = 1 if r.uniform() < 0.5 else -1
+        out.append((N, float(a), float(b), d, decaying_coefficients(N, 1.0, seed + 7 + t)))
+    return out
