@@ -421,27 +421,44 @@ def main():
         launches += (inf["kernels_fwd"] + inf["kernels_inv"]) * args.steps
     for p in plans:
         p.set_profiling(False)
-    # algorithmic work per launch: 8 flops per recurrence step (sum_i J(i)), 2.5 L log2 L per length-L transform
-    rec_flops = {"fwd_rec": sum(8.0 * inf["rec_steps_fwd"] for inf in infos) * args.steps,
-                 "inv_rec": sum(8.0 * inf["rec_steps_inv"] for inf in infos) * args.steps}
+    # Algorithmic work per stage (flop per launch x launches in the timed region):
+    #   recurrence: 8 flop per step (sum_i J(i)) when it runs at execution, 2 flop (one FMA)
+    #   per stored value when the plan keeps the values (rec_store);
+    #   asymptotic blocks: 2.5 L log2 L per (block, m) item, L = 2N forward, 4N inverse;
+    #   final DCT-I / inverse front end: 2.5 L log2 L with L = 2N / 4N.
+    def lg(v):
+        return max(np.log2(max(v, 2)), 1.0)
+    alg = {k: 0.0 for k in cjt.STAGES}
+    for inf, opt in zip(infos, chosen):
+        store = opt.get("rec_store", 0)
+        N, Lf, Li, M = inf["N"], inf["fft_len_fwd"], inf["fft_len_inv"], inf["M"]
+        alg["fwd_rec"] += (2.0 if store else 8.0) * inf["rec_steps_fwd"]
+        alg["inv_rec"] += (2.0 if store else 8.0) * inf["rec_steps_inv"]
+        alg["fwd_fft"] += inf["nblk_fwd"] * M * 2.5 * Lf * lg(Lf)
+        alg["inv_fft"] += inf["nblk_inv"] * M * 2.5 * Li * lg(Li)
+        alg["fwd_dct"] += 2.5 * Lf * lg(Lf)
+        alg["inv_front"] += 2.5 * Li * lg(Li)
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
     try:
         fp64_meas = cjt.microbench_fma(True)
     except Exception:
         fp64_meas = None
-    roof = None
-    if dom in rec_flops:
-        achieved = rec_flops[dom] / (prof[dom][0] * 1e-3)
-        peak = FP64_PEAK_DERIVED
-        roof = {"kernel": "k_rec_fwd" if dom == "fwd_rec" else "k_rec_inv", "bound": "alu",
-                "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": "derived FP64 pipe peak (152 SMs x 2.07 GHz x 2 DFMA/clk)",
-                "fp64_fma_measured_tflops": fp64_meas / 1e12 if fp64_meas else None,
-                "time_share": prof[dom][0] / sum(v[0] for v in prof.values())}
+    kernel_of = {"fwd_rec": "k_rec_fwd_stored / k_rec_fwd", "inv_rec": "k_rec_inv_stored / k_rec_inv",
+                 "fwd_fft": "k_fft_sub (forward ASY transforms)", "inv_fft": "k_fft_sub (transposed ASY transforms)",
+                 "fwd_dct": "k_fft_sub (final DCT-I)", "inv_front": "k_fft_sub (front end)"}
+    roof = {"kernel": kernel_of.get(dom, dom), "stage": dom, "bound": "alu", "peak": FP64_PEAK_DERIVED / 1e12,
+            "unit": "TFLOP/s", "traffic": None,
+            "peak_source": "derived FP64 pipe peak: 152 SMs x 2.07 GHz x 2 DFMA/clk (ncu: 2 DFMA/clk/SM)",
+            "fp64_fma_measured_tflops": fp64_meas / 1e12 if fp64_meas else None,
+            "time_share": prof[dom][0] / sum(v[0] for v in prof.values())}
+    if alg.get(dom, 0.0) > 0.0:
+        achieved = alg[dom] * args.steps / (prof[dom][0] * 1e-3)
+        roof.update({"achieved": achieved / 1e12, "frac": achieved / FP64_PEAK_DERIVED,
+                     "algorithmic_flop_per_step": alg[dom]})
     else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_DERIVED / 1e12,
-                "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "fp64_fma_measured_tflops": fp64_meas / 1e12 if fp64_meas else None}
+        roof.update({"achieved": None, "frac": None})
+    roof["stages_frac_of_peak"] = {k: (alg[k] * args.steps / (prof[k][0] * 1e-3)) / FP64_PEAK_DERIVED
+                                   for k in alg if alg[k] > 0 and prof.get(k, (0, 0))[0] > 0}
     try:
         roof["fp32_fma_measured_tflops"] = cjt.microbench_fma(False) / 1e12
     except Exception:

@@ -84,6 +84,11 @@ typedef struct {
                          1: it owns only its tables, and executions borrow a workspace
                          (cjt_forward_ws / cjt_inverse_ws, or the batched executor), so
                          that thousands of plans fit in device memory                      */
+    int rec_store;    /* 0 (default): the recurrences run at each execution (Sec. 4.2).
+                         1: the plan evaluates the recurrence part of the matrix once, with
+                         the same stabilised forward recurrences, and keeps it in device
+                         memory (8 bytes per recurrence step, rec_store_bytes); executions
+                         then apply it with one fused multiply-add per entry             */
 } cjt_plan_opts;
 
 /* Summary of a plan (for reports and tests). Sizes are per direction. */
@@ -103,6 +108,7 @@ typedef struct {
     double plan_ms;          /* wall time of cjt_plan                                  */
     int64_t kernels_fwd, kernels_inv;   /* kernel launches of one execution              */
     int64_t workspace_bytes;            /* execution workspace one execution needs       */
+    int64_t rec_store_bytes;            /* stored recurrence values (rec_store = 1)      */
 } cjt_plan_info;
 
 /* Stages reported by cjt_get_profile (forward 0-4, inverse 5-9). */

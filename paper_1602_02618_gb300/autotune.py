@@ -1,7 +1,8 @@
-"""Plan autotuner: picks the number of Hahn terms M and the recurrence work
-split (degree-segment length) for a given N and precision by timing candidate
-plans on the current GPU (forward + inverse, CUDA events), and caches the
-choice in a JSON file.
+"""Plan autotuner: picks the number of Hahn terms M, the recurrence work
+split (degree-segment length) and whether the recurrence values are stored in
+the plan (rec_store) for a given N and precision by timing candidate plans on
+the current GPU (forward + inverse, CUDA events), and caches the choice in a
+JSON file.
 
 Every candidate computes the same transform to within the stated tolerance
 (the partition only moves work between the asymptotic blocks and the
@@ -17,6 +18,7 @@ import threading
 
 CANDIDATES_M = (7, 10, 13, 16)
 CANDIDATES_SEG = (256, 1024)
+CANDIDATES_STORE = (0, 1)
 _lock = threading.Lock()
 
 
@@ -87,13 +89,18 @@ def best_options(N: int, alpha: float, beta: float, precision: int = 0, directio
     rng = np.random.default_rng(N)
     x = torch.from_numpy(rng.standard_normal(N + 1) / np.arange(1, N + 2)).cuda()
     y = torch.empty_like(x)
+    max_store = float(os.environ.get("CJT_AUTOTUNE_MAX_STORE_GB", "40")) * 1e9
     results = []
-    for M in CANDIDATES_M:
-        for seg in CANDIDATES_SEG:
-            opts = {"M": M, "seg_len": seg}
-            p = cjt.Plan(N, alpha, beta, precision=precision, directions=directions, **opts)
-            results.append((time_plan(p, x, y), opts))
-            p.close()
+    for store in CANDIDATES_STORE:
+        for M in CANDIDATES_M:
+            for seg in CANDIDATES_SEG:
+                opts = {"M": M, "seg_len": seg, "rec_store": store}
+                p = cjt.Plan(N, alpha, beta, precision=precision, directions=directions, **opts)
+                if store and p.info()["rec_store_bytes"] > max_store:
+                    p.close()
+                    continue
+                results.append((time_plan(p, x, y), opts))
+                p.close()
     results.sort(key=lambda r: r[0])
     best = results[0][1]
     with _lock:

@@ -109,12 +109,14 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
         if (opts->seg_len) o.seg_len = opts->seg_len;
         if (opts->use_asy) o.use_asy = opts->use_asy;
         o.shared_workspace = opts->shared_workspace;
+        o.rec_store = opts->rec_store;
     }
     if (o.M < 1 || o.M > 20) return CJT_EINVAL;
     if (!(o.eps > 0.0 && o.eps < 1.0)) return CJT_EINVAL;
     if (o.precision != CJT_FP64 && o.precision != CJT_MIXED) return CJT_EINVAL;
     if (o.directions < 1 || o.directions > 3) return CJT_EINVAL;
     if (!(o.ratio == 0.0 || (o.ratio > 0.0 && o.ratio < 1.0))) return CJT_EINVAL;
+    if (o.rec_store != 0 && o.rec_store != 1) return CJT_EINVAL;
     if (o.seg_len < 32 || o.seg_len > (1 << 20) || (o.seg_len % 32) != 0) return CJT_EINVAL;
     if (N > (1LL << 21) && !is_pow2(N)) return CJT_EUNSUPPORTED;   // Bluestein lengths stay <= 2^24
 
@@ -180,6 +182,7 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
     info->device_bytes = p->device_bytes;
     info->plan_ms = p->plan_ms;
     info->workspace_bytes = p->ws_bytes;
+    info->rec_store_bytes = 8 * ((p->fw.d_E ? p->fw.nE : 0) + (p->iv.d_E ? p->iv.nE : 0));
     if (p->N == 0) {
         info->kernels_fwd = info->kernels_inv = 1;
     } else {

@@ -163,6 +163,52 @@ __global__ void __launch_bounds__(32 * RI_WARPS) k_rec_inv(const RecItem *__rest
 }
 
 // ---------------------------------------------------------------------------
+// REC with stored values (rec_store): one fused multiply-add per entry
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_rec_fwd_stored(const RecItem *__restrict__ items, int64_t nitems,
+                                                       const double *__restrict__ c, const double *__restrict__ E,
+                                                       double *__restrict__ partials) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nitems) return;
+    const RecItem it = items[w];
+    const int len = it.b - it.a;
+    const double *e = E + it.eoff + lane;
+    const double *cc = c + it.a;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int k = 0;
+    for (; k + 4 <= len; k += 4) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = fma(__ldg(e + (int64_t)(k + j) * 32), __ldg(cc + k + j), acc[j]);
+    }
+    for (; k < len; ++k) acc[k & 3] = fma(__ldg(e + (int64_t)k * 32), __ldg(cc + k), acc[k & 3]);
+    partials[it.out + lane] = lane < it.nrows ? (acc[0] + acc[1]) + (acc[2] + acc[3]) : 0.0;
+}
+
+__global__ void __launch_bounds__(128) k_rec_inv_stored(const RecItem *__restrict__ items, int64_t nitems,
+                                                       const double *__restrict__ g, const double *__restrict__ E,
+                                                       double *__restrict__ partials) {
+    __shared__ double gs[4][32];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * 4 + wib;
+    if (w >= nitems) return;
+    const RecItem it = items[w];
+    gs[wib][lane] = lane < it.nrows ? g[it.row0 + lane] : 0.0;
+    __syncwarp();
+    const int len = it.b - it.a;
+    const double *e = E + it.eoff;
+    double *out = partials + it.out;
+    for (int k0 = 0; k0 < len; k0 += 32) {
+        const int k = k0 + lane;
+        if (k < len) {
+            double acc = 0.0;
+            for (int r = 0; r < it.nrows; ++r) acc = fma(gs[wib][r], __ldg(e + (int64_t)r * len + k), acc);
+            out[k] = acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // ASY pack, forward: pair p holds items q = 2p, 2p+1 (q = k*M + m) as re/im
 // ---------------------------------------------------------------------------
 template <typename V>
@@ -370,8 +416,12 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     // REC
     if (gw.nitems > 0) {
         StageTimer tm(p, st, CJT_STAGE_FWD_REC);
-        k_rec_fwd<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, gw.Ng, p->rt, in,
-                                                                  gw.d_states, ws.part_f);
+        if (gw.d_E)
+            k_rec_fwd_stored<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, in, gw.d_E,
+                                                                             ws.part_f);
+        else
+            k_rec_fwd<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, gw.Ng, p->rt, in,
+                                                                      gw.d_states, ws.part_f);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     // ASY
@@ -455,8 +505,11 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     // transposed recurrence
     if (gw.nitems > 0) {
         StageTimer tm(p, st, CJT_STAGE_INV_REC);
-        k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt, ws.g,
-                                                                             gw.d_states, ws.part_i);
+        if (gw.d_E)
+            k_rec_inv_stored<<<blocks_for(gw.nitems, 4), 128, 0, st>>>(gw.d_items, gw.nitems, ws.g, gw.d_E, ws.part_i);
+        else
+            k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt,
+                                                                                 ws.g, gw.d_states, ws.part_i);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     StageTimer tm(p, st, CJT_STAGE_INV_COMBINE);

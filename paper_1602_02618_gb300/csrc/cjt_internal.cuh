@@ -48,6 +48,7 @@ struct RecItem {
     int mode;    // REC_PLAIN / REC_REINSCH_P1 / REC_REINSCH_M1
     int state;   // state block index (32 lanes x 2 doubles), -1 when a == 0
     int64_t out; // forward: partial index base (32 values); inverse: base of b-a values
+    int64_t eoff;// stored recurrence values of this item (rec_store): 32 x (b-a) doubles
 };
 
 // Recurrence tables for one direction (degrees 0..Jcap).
@@ -82,6 +83,9 @@ struct GridWork {
     int64_t *d_seg_out = nullptr; // partial base of each contributing item
     int *d_seg_b = nullptr;       // item end degree b
     int64_t nchunks = 0;
+    // stored recurrence values (rec_store): forward [item][k][lane], inverse [item][lane][k]
+    double *d_E = nullptr;
+    int64_t nE = 0;
     // diagonals u_m, v_m on this grid
     double *d_u = nullptr, *d_v = nullptr;
     int *d_box = nullptr;         // [nblk][3] = j, i1, i2

@@ -210,6 +210,65 @@ __global__ void k_rec_states(int64_t nrows, const int *srow, int64_t Ng, int seg
 }
 
 // --------------------------------------------------------------------------
+// rec_store: the values P_n(x_i) of each recurrence item, by the same forward
+// recurrences (plain, or Reinsch-modified near x = +-1, Sec. 4.2) from the item's
+// segment state.  layout 0: [k][lane] (forward matvec), 1: [lane][k] (transposed).
+// --------------------------------------------------------------------------
+__global__ void k_rec_fill(const RecItem *__restrict__ items, int64_t nitems, int64_t Ng, RecTables t,
+                           const double *__restrict__ states, double *__restrict__ E, int layout) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nitems) return;
+    const RecItem it = items[w];
+    const bool active = lane < it.nrows;
+    const int row = it.row0 + min(lane, it.nrows - 1);
+    double P1 = 1.0, P2 = 0.0;
+    if (active && it.state >= 0) {
+        const double2 sv = reinterpret_cast<const double2 *>(states)[(int64_t)it.state * 32 + lane];
+        P1 = sv.x;
+        P2 = sv.y;
+    }
+    const int len = it.b - it.a;
+    double *e = E + it.eoff;
+    auto put = [&](int k, double v) {
+        v = active ? v : 0.0;
+        if (layout == 0) e[(int64_t)k * 32 + lane] = v;
+        else e[(int64_t)lane * len + k] = v;
+    };
+    if (it.mode == REC_PLAIN) {
+        const double x = cospi((double)row / (double)Ng);
+        double p = P1, pm = P2;
+        for (int k = 0; k < len; ++k) {
+            const int n = it.a + k;
+            put(k, p);
+            const double pn = fma(fma(__ldg(t.A + n), x, __ldg(t.B + n)), p, -__ldg(t.C + n) * pm);
+            pm = p;
+            p = pn;
+        }
+    } else {
+        const bool plus = it.mode == REC_REINSCH_P1;
+        double delta;
+        if (plus) {
+            const double sv = sinpi((double)row / (2.0 * (double)Ng));
+            delta = -2.0 * sv * sv;
+        } else {
+            const double sv = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
+            delta = 2.0 * sv * sv;
+        }
+        const double *Ce = plus ? t.Ce_p : t.Ce_m;
+        const double *rf = plus ? t.rf_p : t.rf_m;
+        double p = P1, ee = P2;
+        for (int k = 0; k < len; ++k) {
+            const int n = it.a + k;
+            put(k, p);
+            const double en = fma(__ldg(t.A + n) * delta, p, __ldg(Ce + n) * ee);
+            p = fma(p, __ldg(rf + n), en);
+            ee = en;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
 // inverse: modified Chebyshev moments by the three-term recurrence of Sec. 3.1
 // with mu_1 = (beta-alpha)/(alpha+beta+2) mu_0, written as the even extension
 // of length 2*Ng used by the DCT-I of Eq. "CCweights".
@@ -503,7 +562,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
     std::vector<int> row_nseg(Ng + 1);
     std::vector<int64_t> row_base(Ng + 1);
     std::vector<int> srow;
-    int64_t out_f = 0, out_i = 0, nstate = 0, steps = 0;
+    int64_t out_f = 0, out_i = 0, nstate = 0, steps = 0, eoff = 0;
     for (size_t c = 0; c < chunks.size(); ++c) {
         const Chunk &ch = chunks[c];
         int nseg = (int)((ch.J + S - 1) / S);
@@ -521,6 +580,8 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
             it.b = (int)std::min<int64_t>((int64_t)(s + 1) * S, ch.J);
             it.mode = ch.mode;
             it.state = s == 0 ? -1 : state_base + s - 1;
+            it.eoff = eoff;
+            eoff += 32 * (int64_t)(it.b - it.a);
             if (!inverse) {
                 it.out = out_f + (int64_t)s * 32;
             } else {
@@ -588,6 +649,13 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
         CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_srow, srow.data(), sizeof(int) * srow.size(), cudaMemcpyHostToDevice, st));
         // one row per thread; 32-thread blocks spread the long chains over the SMs
         k_rec_states<<<blocks_for(gw.nsrow, 32), 32, 0, st>>>(gw.nsrow, gw.d_srow, Ng, S, p->rt, gw.d_states);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
+    gw.nE = eoff;
+    if (p->opts.rec_store && gw.nitems > 0) {
+        TRY(dalloc(p, &gw.d_E, std::max<int64_t>(gw.nE, 1)));
+        k_rec_fill<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt, gw.d_states,
+                                                                   gw.d_E, inverse ? 1 : 0);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     CJT_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope

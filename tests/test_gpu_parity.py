@@ -74,7 +74,8 @@ def test_inverse_matches_oracle(cjt, orc, N, alpha, beta):
 
 @pytest.mark.parametrize("opts", [dict(M=3), dict(M=5), dict(M=10), dict(M=13), dict(M=20), dict(use_asy=-1),
                                   dict(seg_len=32), dict(seg_len=96), dict(ratio=0.5), dict(ratio=0.2),
-                                  dict(M=13, seg_len=64)])
+                                  dict(M=13, seg_len=64), dict(rec_store=1), dict(rec_store=1, seg_len=64, M=5),
+                                  dict(rec_store=1, use_asy=-1)])
 def test_options_do_not_change_the_result(cjt, orc, opts):
     """The partition, M and the work split change only the rounding (Sec. 2.2)."""
     N, a, b = 4096, 0.1, -0.3
@@ -223,3 +224,16 @@ def test_mixed_precision_within_stated_bound(cjt, orc, N, M):
     p64 = cjt.Plan(N, a, b, M=M)
     assert np.max(np.abs(run_fwd(cjt, plan, c) - run_fwd(cjt, p64, c))) <= MIXED_TOL_FWD * l1(c)
     assert np.max(np.abs(run_inv(cjt, plan, c) - run_inv(cjt, p64, c))) <= MIXED_TOL_INV * l1(c)
+
+
+@pytest.mark.parametrize("N", [1 << 16, 3001, 100])
+def test_stored_recurrence_values(cjt, orc, N):
+    """rec_store = 1 keeps the recurrence part of the matrix in device memory."""
+    a, b = 0.3, -0.4
+    c = inputs.decaying_coefficients(N, 1.5, 123)
+    plan = cjt.Plan(N, a, b, rec_store=1, M=10)
+    info = plan.info()
+    # one double per recurrence step (padded to whole 32-row chunks)
+    assert info["rec_store_bytes"] >= 8 * (info["rec_steps_fwd"] + info["rec_steps_inv"]) > 0
+    assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, a, b))) <= TOL * l1(c)
+    assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, a, b))) <= TOL * l1(c)
