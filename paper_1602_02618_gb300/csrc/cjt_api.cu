@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "cjt_internal.cuh"
 
@@ -32,6 +34,25 @@ int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st) {
     return CJT_OK;
 }
 
+int cjt_internal_side_stream(cudaStream_t *out) {
+    static std::mutex mu;
+    static std::vector<cudaStream_t> pool[64];
+    static unsigned next[64] = {0};
+    int dev = 0;
+    CJT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return CJT_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(mu);
+    if (pool[dev].empty()) {
+        for (int k = 0; k < 32; ++k) {
+            cudaStream_t s;
+            CJT_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            pool[dev].push_back(s);
+        }
+    }
+    *out = pool[dev][next[dev]++ % pool[dev].size()];
+    return CJT_OK;
+}
+
 int cjt_internal_end_use(cjt_plan_s *p, cudaStream_t st) {
     CJT_CUDA_TRY(cudaEventRecord(p->done, st));
     p->last_stream = st;
@@ -50,6 +71,8 @@ void free_plan(cjt_plan_s *p) {
     for (void *v : p->allocs) cudaFree(v);
     p->allocs.clear();
     if (p->done) cudaEventDestroy(p->done);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     delete p;
 }
 }  // namespace

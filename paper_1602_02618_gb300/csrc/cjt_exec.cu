@@ -236,6 +236,49 @@ __global__ void k_asy_pack_fwd(int64_t N, int64_t L, int M, int nq, const int *_
     buf[(int64_t)p * L + n] = o;
 }
 
+// Packs with the pre-scaled tables: arithmetic in the transform precision R.
+template <typename V, typename R>
+__global__ void k_asy_pack_fwd_s(int64_t N, int64_t L, int nq, const R *__restrict__ Cs, const double *__restrict__ c,
+                                 V *__restrict__ buf) {
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (n >= L) return;
+    V o;
+    o.x = 0;
+    o.y = 0;
+    if (n <= N) {
+        const R cn = (R)c[n];
+        const int q = 2 * p;
+        o.x = Cs[(int64_t)q * (N + 1) + n] * cn;
+        if (q + 1 < nq) o.y = Cs[(int64_t)(q + 1) * (N + 1) + n] * cn;
+    }
+    buf[(int64_t)p * L + n] = o;
+}
+
+template <typename V, typename R>
+__global__ void k_asy_pack_inv_s(int64_t Ng, int64_t L, int nq, const R *__restrict__ Us, const R *__restrict__ Vs,
+                                 const double *__restrict__ g, V *__restrict__ buf) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (idx >= L) return;
+    // H(idx) = (z(idx) + conj z(L - idx)) / 2: the box rows lie in [1, Ng - 1]
+    const bool lo = idx <= Ng;
+    const int64_t i = lo ? idx : L - idx;
+    const R gi = (R)g[i];
+    const R sgn = lo ? (R)1 : (R)-1;
+    const int q = 2 * p;
+    const R h0r = Us[(int64_t)q * (Ng + 1) + i] * gi, h0i = sgn * Vs[(int64_t)q * (Ng + 1) + i] * gi;
+    R h1r = 0, h1i = 0;
+    if (q + 1 < nq) {
+        h1r = Us[(int64_t)(q + 1) * (Ng + 1) + i] * gi;
+        h1i = sgn * Vs[(int64_t)(q + 1) * (Ng + 1) + i] * gi;
+    }
+    V o;
+    o.x = h0r - h1i;
+    o.y = h0i + h1r;
+    buf[(int64_t)p * L + idx] = o;
+}
+
 // ---------------------------------------------------------------------------
 // combine, forward: REC segment partials + asymptotic terms; writes the even
 // extension of y (length 2N) for the final DCT-I
@@ -413,6 +456,31 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     const bool fp32 = p->opts.precision == CJT_MIXED;
     const int M = p->M;
     int rc;
+    const int nq = gw.nblk * M;
+    const int64_t L = p->Lf;
+    // the asymptotic transforms run on a side stream, concurrently with the recurrence
+    const bool ovl = nq > 0 && p->side;
+    cudaStream_t sa = ovl ? p->side : st;
+    if (ovl) {
+        CJT_CUDA_TRY(cudaEventRecord(p->ev_fork, st));
+        CJT_CUDA_TRY(cudaStreamWaitEvent(sa, p->ev_fork, 0));
+    }
+    if (nq > 0) {
+        dim3 gp(blocks_for(L, 256), p->npair_f);
+        StageTimer tm(p, sa, CJT_STAGE_FWD_PACK);
+        if (fp32)
+            k_asy_pack_fwd_s<float2, float><<<gp, 256, 0, sa>>>(N, L, nq, (const float *)gw.d_Cs, in, (float2 *)ws.fft_f);
+        else
+            k_asy_pack_fwd_s<double2, double><<<gp, 256, 0, sa>>>(N, L, nq, (const double *)gw.d_Cs, in,
+                                                                 (double2 *)ws.fft_f);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
+    if (nq > 0) {
+        StageTimer tm(p, sa, CJT_STAGE_FWD_FFT);
+        rc = cjt_dft_exec(p->dft_f, ws.fft_f, ws.work, ws.scratch, p->npair_f, fp32 ? p->d_tw32 : p->d_tw64,
+                          p->Ltab, sa);
+        if (rc) return rc;
+    }
     // REC
     if (gw.nitems > 0) {
         StageTimer tm(p, st, CJT_STAGE_FWD_REC);
@@ -424,23 +492,9 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
                                                                       gw.d_states, ws.part_f);
         CJT_CUDA_TRY(cudaGetLastError());
     }
-    // ASY
-    const int nq = gw.nblk * M;
-    const int64_t L = p->Lf;
-    if (nq > 0) {
-        dim3 gp(blocks_for(L, 256), p->npair_f);
-        StageTimer tm(p, st, CJT_STAGE_FWD_PACK);
-        if (fp32)
-            k_asy_pack_fwd<float2><<<gp, 256, 0, st>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in, (float2 *)ws.fft_f);
-        else
-            k_asy_pack_fwd<double2><<<gp, 256, 0, st>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in, (double2 *)ws.fft_f);
-        CJT_CUDA_TRY(cudaGetLastError());
-    }
-    if (nq > 0) {
-        StageTimer tm(p, st, CJT_STAGE_FWD_FFT);
-        rc = cjt_dft_exec(p->dft_f, ws.fft_f, ws.work, ws.scratch, p->npair_f, fp32 ? p->d_tw32 : p->d_tw64,
-                          p->Ltab, st);
-        if (rc) return rc;
+    if (ovl) {
+        CJT_CUDA_TRY(cudaEventRecord(p->ev_join, sa));
+        CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
     }
     double2 *ext = (double2 *)ws.dct;
     {
@@ -485,37 +539,52 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     k_inv_g<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)ws.dct, p->d_w, ws.g);
     CJT_CUDA_TRY(cudaGetLastError());
     }
-    // transposed asymptotic blocks
+    // transposed asymptotic blocks, on a side stream concurrently with the recurrence
     const int nq = gw.nblk * M;
+    const bool ovl = nq > 0 && p->side;
+    cudaStream_t sa = ovl ? p->side : st;
+    if (ovl) {
+        CJT_CUDA_TRY(cudaEventRecord(p->ev_fork, st));
+        CJT_CUDA_TRY(cudaStreamWaitEvent(sa, p->ev_fork, 0));
+    }
     if (nq > 0) {
         dim3 gp(blocks_for(L, 256), p->npair_i);
-        StageTimer tm(p, st, CJT_STAGE_INV_PACK);
+        StageTimer tm(p, sa, CJT_STAGE_INV_PACK);
         if (fp32)
-            k_asy_pack_inv<float2><<<gp, 256, 0, st>>>(Ng, L, M, nq, gw.d_box, gw.d_scale, gw.d_u, gw.d_v, ws.g, (float2 *)ws.fft_i);
+            k_asy_pack_inv_s<float2, float><<<gp, 256, 0, sa>>>(Ng, L, nq, (const float *)gw.d_Us,
+                                                                (const float *)gw.d_Vs, ws.g, (float2 *)ws.fft_i);
         else
-            k_asy_pack_inv<double2><<<gp, 256, 0, st>>>(Ng, L, M, nq, gw.d_box, gw.d_scale, gw.d_u, gw.d_v, ws.g, (double2 *)ws.fft_i);
+            k_asy_pack_inv_s<double2, double><<<gp, 256, 0, sa>>>(Ng, L, nq, (const double *)gw.d_Us,
+                                                                  (const double *)gw.d_Vs, ws.g, (double2 *)ws.fft_i);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     if (nq > 0) {
-        StageTimer tm(p, st, CJT_STAGE_INV_FFT);
+        StageTimer tm(p, sa, CJT_STAGE_INV_FFT);
         rc = cjt_dft_exec(p->dft_i, ws.fft_i, ws.work, ws.scratch, p->npair_i, fp32 ? p->d_tw32 : p->d_tw64,
-                          p->Ltab, st);
+                          p->Ltab, sa);
         if (rc) return rc;
     }
-    // transposed recurrence
-    if (gw.nitems > 0) {
+    // transposed recurrence and the fixed-order sums over the items of each degree
+    {
         StageTimer tm(p, st, CJT_STAGE_INV_REC);
-        if (gw.d_E)
-            k_rec_inv_stored<<<blocks_for(gw.nitems, 4), 128, 0, st>>>(gw.d_items, gw.nitems, ws.g, gw.d_E, ws.part_i);
-        else
-            k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt,
-                                                                                 ws.g, gw.d_states, ws.part_i);
+        if (gw.nitems > 0) {
+            if (gw.d_E)
+                k_rec_inv_stored<<<blocks_for(gw.nitems, 4), 128, 0, st>>>(gw.d_items, gw.nitems, ws.g, gw.d_E,
+                                                                            ws.part_i);
+            else
+                k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt,
+                                                                                     ws.g, gw.d_states, ws.part_i);
+            CJT_CUDA_TRY(cudaGetLastError());
+        }
+        k_inv_reduce<<<blocks_for(N + 1, 32), 32 * RED_WARPS, 0, st>>>(N, p->seg_len, gw.d_seg_ptr, gw.d_seg_out,
+                                                                         gw.d_seg_b, ws.part_i, ws.y);
         CJT_CUDA_TRY(cudaGetLastError());
     }
+    if (ovl) {
+        CJT_CUDA_TRY(cudaEventRecord(p->ev_join, sa));
+        CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
+    }
     StageTimer tm(p, st, CJT_STAGE_INV_COMBINE);
-    k_inv_reduce<<<blocks_for(N + 1, 32), 32 * RED_WARPS, 0, st>>>(N, p->seg_len, gw.d_seg_ptr, gw.d_seg_out,
-                                                                     gw.d_seg_b, ws.part_i, ws.y);
-    CJT_CUDA_TRY(cudaGetLastError());
     if (fp32)
         k_combine_inv<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
             N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const float2 *)ws.fft_i, ws.y, p->d_s, out);

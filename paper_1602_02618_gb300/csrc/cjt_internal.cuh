@@ -35,6 +35,7 @@ void cjt_internal_set_cuda_error(cudaError_t e, const char *what);
 struct cjt_plan_s;
 int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st);
 int cjt_internal_end_use(cjt_plan_s *p, cudaStream_t st);
+int cjt_internal_side_stream(cudaStream_t *out);   // round-robin pool of non-blocking streams per device
 
 // ---------------------------------------------------------------------------
 // recurrence work items
@@ -93,6 +94,10 @@ struct GridWork {
     // transform (d_scale[2q]) and removed after it (d_scale[2q+1]), so that the two
     // items sharing one complex transform have comparable magnitudes
     double *d_scale = nullptr;
+    // transform inputs pre-scaled per item, in the transform precision:
+    //   forward  Cs[q][n] = s_q C_{n,m} for n >= j_k (0 below)            (q x (N+1))
+    //   inverse  Us[q][i] = s_q u_m(theta_i)/2, Vs = s_q v_m(theta_i)/2 on box rows (q x (Ng+1))
+    void *d_Cs = nullptr, *d_Us = nullptr, *d_Vs = nullptr;
 };
 
 // A discrete Fourier transform X_k = sum_{n<S} x_n exp(-2 pi i n k / L), k < K, batched over
@@ -149,6 +154,11 @@ struct cjt_plan_s {
     double *d_w = nullptr;        // inverse: Clenshaw--Curtis weights (2N+1)
     double *d_s = nullptr;        // inverse: 1/A_n (N+1)
     double *d_in = nullptr, *d_out = nullptr;  // staging for cjt_execute_host
+
+    // overlap of the asymptotic transforms with the recurrence: a side stream from the
+    // device pool and a fork/join event pair
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // concurrency guard
     cudaStream_t last_stream = nullptr;

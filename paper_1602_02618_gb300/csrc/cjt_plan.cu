@@ -210,6 +210,33 @@ __global__ void k_rec_states(int64_t nrows, const int *srow, int64_t Ng, int seg
 }
 
 // --------------------------------------------------------------------------
+// pre-scaled transform inputs (the scale of each item is an exact power of two)
+// --------------------------------------------------------------------------
+template <typename R>
+__global__ void k_scaled_C(int64_t N, int M, int nq, const int *__restrict__ box3, const double *__restrict__ Cnm,
+                           const double *__restrict__ scale, R *__restrict__ out) {
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (n > N || q >= nq) return;
+    const int k = q / M, m = q - k * M;
+    out[(int64_t)q * (N + 1) + n] = n >= box3[3 * k] ? (R)(Cnm[m * (N + 1) + n] * scale[2 * q]) : (R)0;
+}
+
+template <typename R>
+__global__ void k_scaled_uv(int64_t Ng, int M, int nq, const int *__restrict__ box3, const double *__restrict__ u,
+                            const double *__restrict__ v, const double *__restrict__ scale, R *__restrict__ U,
+                            R *__restrict__ V) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (i > Ng || q >= nq) return;
+    const int k = q / M, m = q - k * M;
+    const bool in = i >= box3[3 * k + 1] && i <= box3[3 * k + 2];
+    const double sc = 0.5 * scale[2 * q];
+    U[(int64_t)q * (Ng + 1) + i] = in ? (R)(sc * u[m * (Ng + 1) + i]) : (R)0;
+    V[(int64_t)q * (Ng + 1) + i] = in ? (R)(sc * v[m * (Ng + 1) + i]) : (R)0;
+}
+
+// --------------------------------------------------------------------------
 // rec_store: the values P_n(x_i) of each recurrence item, by the same forward
 // recurrences (plain, or Reinsch-modified near x = +-1, Sec. 4.2) from the item's
 // segment state.  layout 0: [k][lane] (forward matvec), 1: [lane][k] (transposed).
@@ -527,6 +554,32 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
         }
         TRY(dalloc(p, &gw.d_scale, (int64_t)sc.size()));
         CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_scale, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, st));
+        const int nq = gw.nblk * M;
+        const bool f32 = p->opts.precision == CJT_MIXED;
+        if (!inverse) {
+            dim3 g(blocks_for(p->N + 1, 256), nq);
+            if (f32) {
+                TRY(dalloc(p, (float **)&gw.d_Cs, (int64_t)nq * (p->N + 1)));
+                k_scaled_C<float><<<g, 256, 0, st>>>(p->N, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, (float *)gw.d_Cs);
+            } else {
+                TRY(dalloc(p, (double **)&gw.d_Cs, (int64_t)nq * (p->N + 1)));
+                k_scaled_C<double><<<g, 256, 0, st>>>(p->N, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, (double *)gw.d_Cs);
+            }
+        } else {
+            dim3 g(blocks_for(Ng + 1, 256), nq);
+            if (f32) {
+                TRY(dalloc(p, (float **)&gw.d_Us, (int64_t)nq * (Ng + 1)));
+                TRY(dalloc(p, (float **)&gw.d_Vs, (int64_t)nq * (Ng + 1)));
+                k_scaled_uv<float><<<g, 256, 0, st>>>(Ng, M, nq, gw.d_box, gw.d_u, gw.d_v, gw.d_scale,
+                                                      (float *)gw.d_Us, (float *)gw.d_Vs);
+            } else {
+                TRY(dalloc(p, (double **)&gw.d_Us, (int64_t)nq * (Ng + 1)));
+                TRY(dalloc(p, (double **)&gw.d_Vs, (int64_t)nq * (Ng + 1)));
+                k_scaled_uv<double><<<g, 256, 0, st>>>(Ng, M, nq, gw.d_box, gw.d_u, gw.d_v, gw.d_scale,
+                                                       (double *)gw.d_Us, (double *)gw.d_Vs);
+            }
+        }
+        CJT_CUDA_TRY(cudaGetLastError());
         CJT_CUDA_TRY(cudaStreamSynchronize(st));
     }
     k_rowk<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, gw.nblk, gw.d_box, gw.d_rowk);
@@ -822,6 +875,11 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     if (tmp_ws) cudaFreeAsync(tmp_ws, st);
     tr.mark("buffers, inverse weights");
     CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
+    if (p->fw.nblk > 0 || p->iv.nblk > 0) {
+        TRY(cjt_internal_side_stream(&p->side));
+        CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+        CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    }
     CJT_CUDA_TRY(cudaStreamSynchronize(st));
     return CJT_OK;
 }

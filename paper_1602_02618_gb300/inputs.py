@@ -84,3 +84,14 @@ def serving_requests(count: int, seed: int = BASE_SEED, nmin: int = 128, nmax: i
         d = 1 if r.uniform() < 0.5 else -1
         out.append((N, float(a), float(b), d, decaying_coefficients(N, 1.0, seed + 7 + t)))
     return out
+
+
+def mixed_large_workload(count: int = 64, N: int = 1 << 20, seed: int = BASE_SEED):
+    """count transforms of degree N, (alpha, beta) ~ U[-0.45, 0.45]^2 each, forward and
+    inverse alternating, c_n = g_n/(n+1)."""
+    r = rng(seed + 5000)
+    out = []
+    for t in range(count):
+        a, b = r.uniform(-0.45, 0.45, 2)
+        out.append((N, float(a), float(b), 1 if t % 2 == 0 else -1, decaying_coefficients(N, 1.0, seed + 6000 + t)))
+    return out
