@@ -391,7 +391,7 @@ def main():
     fixed = {}
     for kv in filter(None, args.fixed_options.split(",")):
         k, v = kv.split("=")
-        fixed[k.strip()] = int(v)
+        fixed[k.strip()] = float(v) if k.strip() in ("ratio", "eps") else int(v)
     plans, xs, ys, zs, chosen = [], [], [], [], []
     for N, a, b, c in items:
         opts = dict(fixed) if (fixed or args.no_autotune) else autotune.best_options(N, a, b, precision)

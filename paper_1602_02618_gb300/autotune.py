@@ -18,7 +18,24 @@ import threading
 
 CANDIDATES_M = (7, 10, 13, 16)
 CANDIDATES_SEG = (256, 1024)
-CANDIDATES_STORE = (0, 1)
+
+
+def candidates(N: int, max_store_bytes: float):
+    """Options to time: the recurrence at execution over M and the segment length; the
+    stored recurrence values over M, the segment length and a coarser block ratio (fewer
+    transforms, more recurrence); and no asymptotic blocks at all when the stored matrix
+    (8 (N+1)^2 bytes per direction) fits the memory cap."""
+    out = []
+    for M in CANDIDATES_M:
+        for seg in CANDIDATES_SEG:
+            out.append({"M": M, "seg_len": seg, "rec_store": 0})
+    for M in (5, 7, 10, 13):
+        for seg in CANDIDATES_SEG:
+            out.append({"M": M, "seg_len": seg, "rec_store": 1})
+        out.append({"M": M, "seg_len": 1024, "rec_store": 1, "ratio": 0.05})
+    if 3 * 8.0 * (N + 1) ** 2 <= max_store_bytes:
+        out.append({"M": 7, "seg_len": 1024, "rec_store": 1, "use_asy": -1})
+    return out
 _lock = threading.Lock()
 
 
@@ -75,7 +92,8 @@ def time_plan(plan, x, y, reps=3):
 
 def best_options(N: int, alpha: float, beta: float, precision: int = 0, directions: int = 3,
                  refresh: bool = False) -> dict:
-    """Options dict (M, seg_len) for cjt.Plan, from the cache or by timing the candidates."""
+    """Options dict for cjt.Plan (M, seg_len, rec_store, ratio, use_asy), from the cache or by
+    timing the candidates."""
     import numpy as np
     import torch
     from . import cjt
@@ -91,16 +109,16 @@ def best_options(N: int, alpha: float, beta: float, precision: int = 0, directio
     y = torch.empty_like(x)
     max_store = float(os.environ.get("CJT_AUTOTUNE_MAX_STORE_GB", "40")) * 1e9
     results = []
-    for store in CANDIDATES_STORE:
-        for M in CANDIDATES_M:
-            for seg in CANDIDATES_SEG:
-                opts = {"M": M, "seg_len": seg, "rec_store": store}
-                p = cjt.Plan(N, alpha, beta, precision=precision, directions=directions, **opts)
-                if store and p.info()["rec_store_bytes"] > max_store:
-                    p.close()
-                    continue
-                results.append((time_plan(p, x, y), opts))
-                p.close()
+    for opts in candidates(N, max_store):
+        try:
+            p = cjt.Plan(N, alpha, beta, precision=precision, directions=directions, **opts)
+        except cjt.CJTError:
+            continue
+        if opts.get("rec_store") and p.info()["rec_store_bytes"] > max_store:
+            p.close()
+            continue
+        results.append((time_plan(p, x, y), opts))
+        p.close()
     results.sort(key=lambda r: r[0])
     best = results[0][1]
     with _lock:

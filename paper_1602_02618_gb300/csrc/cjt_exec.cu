@@ -175,14 +175,22 @@ __global__ void __launch_bounds__(128) k_rec_fwd_stored(const RecItem *__restric
     const int len = it.b - it.a;
     const double *e = E + it.eoff + lane;
     const double *cc = c + it.a;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    // eight independent streaming loads and accumulators per lane keep enough bytes in flight
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     int k = 0;
-    for (; k + 4 <= len; k += 4) {
+    for (; k + 8 <= len; k += 8) {
+        double v[8], cv[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j] = fma(__ldg(e + (int64_t)(k + j) * 32), __ldg(cc + k + j), acc[j]);
+        for (int j = 0; j < 8; ++j) {
+            v[j] = __ldcs(e + (int64_t)(k + j) * 32);
+            cv[j] = __ldg(cc + k + j);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = fma(v[j], cv[j], acc[j]);
     }
-    for (; k < len; ++k) acc[k & 3] = fma(__ldg(e + (int64_t)k * 32), __ldg(cc + k), acc[k & 3]);
-    partials[it.out + lane] = lane < it.nrows ? (acc[0] + acc[1]) + (acc[2] + acc[3]) : 0.0;
+    for (; k < len; ++k) acc[k & 7] = fma(__ldcs(e + (int64_t)k * 32), __ldg(cc + k), acc[k & 7]);
+    const double S = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    partials[it.out + lane] = lane < it.nrows ? S : 0.0;
 }
 
 __global__ void __launch_bounds__(128) k_rec_inv_stored(const RecItem *__restrict__ items, int64_t nitems,
