@@ -41,9 +41,27 @@ def workload():
     return inputs.single_workload(Ns=tuple(1 << k for k in LOGNS))
 
 
+PREC_NAMES = {"fp64": "FP64", "mixed": "mixed (FP32 ASY transforms)",
+              "df": "double-float (f32x2 ASY transforms and stored recurrence, FP64 error bound)"}
+DTYPES = {"fp64": "f64", "mixed": "f32 ASY transforms + f64",
+          "df": "f32x2 double-float ASY transforms and stored recurrence + f64"}
+
+
+def precision_code(cjt, name):
+    return {"fp64": cjt.CJT_FP64, "mixed": cjt.CJT_MIXED, "df": cjt.CJT_DFLOAT}[name]
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured HBM copy bandwidth (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback HBM bandwidth 6.8 TB/s"
+
+
 def workload_desc(precision):
     return ("forward+inverse CJT singly, %s, N in {2^12,2^14,2^16,2^18}, alpha,beta~U[-0.45,0.45] per transform, "
-            "c_n=g_n/(n+1)^1.5, g~N(0,1)" % ("FP64" if precision == "fp64" else "mixed (FP32 ASY transforms)"))
+            "c_n=g_n/(n+1)^1.5, g~N(0,1)" % PREC_NAMES[precision])
 
 
 class ClockSampler:
@@ -173,7 +191,7 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
         precision = cjt.CJT_MIXED
     else:
         items = inputs.batch_workload(args.batch_count)
-        precision = cjt.CJT_FP64 if args.precision == "fp64" else cjt.CJT_MIXED
+        precision = precision_code(cjt, args.precision)
     t0 = time.perf_counter()
     plans = []
     for N, a, b, d, c in items:
@@ -274,13 +292,14 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
             "warmup": args.warmup, "ms_per_step": float(step_ms.mean()),
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if precision == cjt.CJT_FP64 else "f32 ASY transforms + f64", "data": "synthetic",
+            "dtype": DTYPES["mixed" if big else args.precision], "data": "synthetic",
             "config": {"workload": ("mixed precision: 64 transforms at N=2^20, alpha,beta~U[-0.45,0.45] each, "
                                     "forward/inverse alternating, c_n=g_n/(n+1); FP32 ASY transforms, FP64 "
                                     "recurrences, scalings and accumulation; one captured CUDA graph per step")
                        if big else
                        ("batched: %d transforms, N log-uniform in [64, 65536], alpha,beta~U[-0.45,0.45] "
-                        "each, random forward/inverse, c_n=g_n/(n+1); one captured CUDA graph per step" % len(items)),
+                        "each, random forward/inverse, c_n=g_n/(n+1); %s; one captured CUDA graph per step"
+                        % (len(items), PREC_NAMES[args.precision])),
                        "coefficients_per_step": coeffs, "lanes": args.lanes,
                        "l2": "inputs (%.0f MB) exceed L2; flushed between steps" % (coeffs * 8 / 1e6)},
             "error": ({"vs_fp64_gpu_max_abs_over_l1": max(err64) if err64 else None,
@@ -302,7 +321,7 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
 def run_serving(args, torch, cjt, rank):
     """configs[4]: Poisson arrivals at swept rates, continuous batching, 40 GB budget."""
     from paper_1602_02618_gb300 import inputs, serve
-    precision = cjt.CJT_FP64 if args.precision == "fp64" else cjt.CJT_MIXED
+    precision = precision_code(cjt, args.precision)
     rates = [float(r) for r in args.rates.split(",")]
     results = []
     for k, rate in enumerate(rates):
@@ -325,7 +344,7 @@ def run_serving(args, torch, cjt, rank):
             "metric": METRIC, "value": best["coeffs_per_s"], "unit": "coeffs/s", "n_gpus": 1,
             "steps": args.requests, "warmup": 0, "ms_per_step": best["mean_ms"],
             "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if precision == cjt.CJT_FP64 else "f32 ASY transforms + f64",
+            "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": "serving: Poisson arrivals, %d requests per rate, N log-uniform in [128, 2^18], "
                                    "alpha,beta~U[-0.45,0.45], random direction, c_n=g_n/(n+1); plan built per "
@@ -341,7 +360,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "df"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--fixed-options", default="", help="e.g. M=13,seg_len=1024 (applied to every N; no autotune)")
@@ -384,7 +403,7 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
-    precision = cjt.CJT_FP64 if args.precision == "fp64" else cjt.CJT_MIXED
+    precision = precision_code(cjt, args.precision)
     items = workload()
     if args.only_logn:
         items = [it for it in items if it[0] == (1 << args.only_logn)]
@@ -452,55 +471,77 @@ def main():
         launches += (inf["kernels_fwd"] + inf["kernels_inv"]) * args.steps
     for p in plans:
         p.set_profiling(False)
-    # Algorithmic work per stage (flop per launch x launches in the timed region):
-    #   recurrence: 8 flop per step (sum_i J(i)) when it runs at execution, 2 flop (one FMA)
-    #   per stored value when the plan keeps the values (rec_store);
-    #   asymptotic blocks: 2.5 L log2 L per (block, m) item, L = 2N forward, 4N inverse;
-    #   final DCT-I / inverse front end: 2.5 L log2 L with L = 2N / 4N.
+    # Roofline per stage.  Algorithmic work of one plan per step, and the peak it is held to:
+    #   recurrence at execution: 8 flop per step (sum_i J(i)), FP64 pipe;
+    #   stored recurrence values (rec_store): one multiply-add per value, 2 flop on the FP64
+    #   pipe, or, in the double-float form, 8 bytes read per value against HBM bandwidth;
+    #   asymptotic blocks: 2.5 L log2 L flop per (block, m) item, L = 2N forward, 4N inverse,
+    #   on the FP64 pipe, the FP32 pipe (mixed form) or at the measured double-float rate;
+    #   final DCT-I / inverse front end: 2.5 L log2 L flop with L = 2N / 4N, FP64 pipe.
+    # A stage's fraction of peak = (sum over plans of work / peak) / measured stage time.
     def lg(v):
         return max(np.log2(max(v, 2)), 1.0)
-    alg = {k: 0.0 for k in cjt.STAGES}
+    try:
+        fp64_meas = cjt.microbench_fma(1)
+    except Exception:
+        fp64_meas = None
+    try:
+        fp32_meas = cjt.microbench_fma(0)
+    except Exception:
+        fp32_meas = None
+    try:
+        df_meas = cjt.microbench_fma(2) if precision == cjt.CJT_DFLOAT else None
+    except Exception:
+        df_meas = None
+    hbm_gbs, hbm_src = measured_hbm_gbs()
+    P64 = ("alu", "TFLOP/s", FP64_PEAK_DERIVED, "derived FP64 pipe peak: 152 SMs x 2.07 GHz x 2 DFMA/clk "
+           "(ncu: 2 DFMA/clk/SM)")
+    P32 = ("alu", "TFLOP/s", fp32_meas or 77e12, "measured FP32 FMA rate (cjt_microbench_fma)")
+    PDF = ("alu", "TFLOP/s", df_meas or 4.5e12, "measured double-float multiply-add rate (cjt_microbench_fma kind 2)")
+    PHBM = ("hbm", "GB/s", hbm_gbs * 1e9, hbm_src)
+    ideal = {k: 0.0 for k in cjt.STAGES}
+    model = {}
     for inf, opt in zip(infos, chosen):
         store = opt.get("rec_store", 0)
         N, Lf, Li, M = inf["N"], inf["fft_len_fwd"], inf["fft_len_inv"], inf["M"]
-        alg["fwd_rec"] += (2.0 if store else 8.0) * inf["rec_steps_fwd"]
-        alg["inv_rec"] += (2.0 if store else 8.0) * inf["rec_steps_inv"]
-        alg["fwd_fft"] += inf["nblk_fwd"] * M * 2.5 * Lf * lg(Lf)
-        alg["inv_fft"] += inf["nblk_inv"] * M * 2.5 * Li * lg(Li)
-        alg["fwd_dct"] += 2.5 * Lf * lg(Lf)
-        alg["inv_front"] += 2.5 * Li * lg(Li)
+        work = {}
+        for st, steps in (("fwd_rec", inf["rec_steps_fwd"]), ("inv_rec", inf["rec_steps_inv"])):
+            if store and precision == cjt.CJT_DFLOAT:
+                work[st] = (8.0 * steps, PHBM)
+            else:
+                work[st] = ((2.0 if store else 8.0) * steps, P64)
+        asy = PDF if precision == cjt.CJT_DFLOAT else (P32 if precision == cjt.CJT_MIXED else P64)
+        work["fwd_fft"] = (inf["nblk_fwd"] * M * 2.5 * Lf * lg(Lf), asy)
+        work["inv_fft"] = (inf["nblk_inv"] * M * 2.5 * Li * lg(Li), asy)
+        work["fwd_dct"] = (2.5 * Lf * lg(Lf), P64)
+        work["inv_front"] = (2.5 * Li * lg(Li), P64)
+        for st, (w, pk) in work.items():
+            ideal[st] += w / pk[2]
+            if w > 0:
+                model[st] = pk   # the largest N (last plan) names the stage's bound
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
-    try:
-        fp64_meas = cjt.microbench_fma(True)
-    except Exception:
-        fp64_meas = None
-    kernel_of = {"fwd_rec": "k_rec_fwd_stored / k_rec_fwd", "inv_rec": "k_rec_inv_stored / k_rec_inv",
+    kernel_of = {"fwd_rec": "k_rec_fwd_stored(_df) / k_rec_fwd", "inv_rec": "k_rec_inv_stored(_df) / k_rec_inv",
                  "fwd_fft": "k_fft_sub (forward ASY transforms)", "inv_fft": "k_fft_sub (transposed ASY transforms)",
                  "fwd_dct": "k_fft_sub (final DCT-I)", "inv_front": "k_fft_sub (front end)"}
-    roof = {"kernel": kernel_of.get(dom, dom), "stage": dom, "bound": "alu", "peak": FP64_PEAK_DERIVED / 1e12,
-            "unit": "TFLOP/s", "traffic": None,
-            "peak_source": "derived FP64 pipe peak: 152 SMs x 2.07 GHz x 2 DFMA/clk (ncu: 2 DFMA/clk/SM)",
+    def frac_of(st):
+        t = prof.get(st, (0.0, 0))[0] * 1e-3
+        return ideal[st] * args.steps / t if t > 0 and ideal[st] > 0 else None
+    roof = {"kernel": kernel_of.get(dom, dom), "stage": dom, "traffic": None,
+            "time_share": prof[dom][0] / sum(v[0] for v in prof.values()),
             "fp64_fma_measured_tflops": fp64_meas / 1e12 if fp64_meas else None,
-            "time_share": prof[dom][0] / sum(v[0] for v in prof.values())}
-    try:
-        fp32_meas = cjt.microbench_fma(False)
-    except Exception:
-        fp32_meas = None
-    roof["fp32_fma_measured_tflops"] = fp32_meas / 1e12 if fp32_meas else None
-    # in the mixed form the asymptotic transforms run on the FP32 pipe
-    def peak_of(stage):
-        if precision == cjt.CJT_MIXED and stage in ("fwd_fft", "inv_fft") and fp32_meas:
-            return fp32_meas, "measured FP32 FMA peak (cjt_microbench_fma)"
-        return FP64_PEAK_DERIVED, roof["peak_source"]
-    if alg.get(dom, 0.0) > 0.0:
-        achieved = alg[dom] * args.steps / (prof[dom][0] * 1e-3)
-        pk, src = peak_of(dom)
-        roof.update({"achieved": achieved / 1e12, "frac": achieved / pk, "peak": pk / 1e12, "peak_source": src,
-                     "algorithmic_flop_per_step": alg[dom]})
+            "fp32_fma_measured_tflops": fp32_meas / 1e12 if fp32_meas else None,
+            "df_fma_measured_tflops": df_meas / 1e12 if df_meas else None}
+    f = frac_of(dom)
+    if f is not None and dom in model:
+        bound, unit, pk, src = model[dom]
+        scale = 1e9 if unit == "GB/s" else 1e12
+        roof.update({"bound": bound, "unit": unit, "peak": pk / scale, "achieved": f * pk / scale, "frac": f,
+                     "peak_source": src})
     else:
-        roof.update({"achieved": None, "frac": None})
-    roof["stages_frac_of_peak"] = {k: (alg[k] * args.steps / (prof[k][0] * 1e-3)) / peak_of(k)[0]
-                                   for k in alg if alg[k] > 0 and prof.get(k, (0, 0))[0] > 0}
+        roof.update({"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_DERIVED / 1e12, "achieved": None,
+                     "frac": None, "peak_source": P64[3]})
+    roof["stages_frac_of_peak"] = {k: frac_of(k) for k in cjt.STAGES if frac_of(k) is not None}
+    roof["stages_bound"] = {k: "%s (%s)" % (model[k][0], model[k][3]) for k in model}
 
     # accuracy of the round trip (one step)
     err = max(float((z - x).abs().max()) / float(x.abs().sum()) for x, z in zip(xs, zs))
@@ -536,7 +577,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": float(step_ms.mean()),
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if precision == cjt.CJT_FP64 else "f32 ASY transforms + f64",
+            "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": workload_desc(args.precision), "N": [1 << k for k in LOGNS],
                        "options": chosen, "l2": "flushed between steps (512 MiB write, outside timed events)",

@@ -64,6 +64,12 @@ extern "C" {
 #define CJT_FP64 0           /* everything in IEEE double                            */
 #define CJT_MIXED 1          /* ASY transforms in float; Hahn coefficients, scalings,
                                 recurrences, accumulation and the final DCT-I in double */
+#define CJT_DFLOAT 2         /* ASY transforms and their inputs, and the stored recurrence
+                                values (rec_store), in double-float arithmetic (pairs of
+                                floats, about 48 significant bits, on the FP32 pipe); Hahn
+                                coefficients, scalings, recurrences, accumulation and the
+                                final DCT-I in double.  Meets the FP64 error bound
+                                1e-12 ||c||_1 of this library's tests.                  */
 
 /* directions a plan is built for */
 #define CJT_FWD 1
@@ -73,7 +79,7 @@ extern "C" {
 typedef struct {
     int M;            /* terms of Hahn's formula (Eq. "Jacasy"), 1..20; 0 -> 7            */
     double eps;       /* partition tolerance on each matrix entry (Sec. 2.2); 0 -> 2^-52   */
-    int precision;    /* CJT_FP64 (default) or CJT_MIXED                                   */
+    int precision;    /* CJT_FP64 (default), CJT_MIXED or CJT_DFLOAT                       */
     int directions;   /* CJT_FWD | CJT_INV; 0 -> both                                      */
     double ratio;     /* block ratio alpha_N of Sec. 2.2 in (0, 1); 0 -> the paper's
                          min(1/log(N/n_M), 1/2)                                            */
@@ -232,10 +238,12 @@ int cjt_get_profile(cjt_plan_t plan, double *ms, int64_t *counts, int n);
 
 /*
  * Peak arithmetic microbenchmark (diagnostic, no counterpart in the paper):
- * dependent-chain fused multiply-adds on every SM, FP64 (fp64 = 1) or FP32
- * (fp64 = 0).  Writes the measured rate in FLOP/s to *flops (2 per FMA).
+ * dependent-chain multiply-adds on every SM in FP32 (kind = 0), FP64 (kind = 1)
+ * or double-float arithmetic (kind = 2: x <- x*a + b with a double-float product
+ * and sum, the operations of the CJT_DFLOAT transforms).  Writes the measured rate
+ * in FLOP/s to *flops (2 per multiply-add).  Other kinds: CJT_EINVAL.
  */
-int cjt_microbench_fma(int fp64, double *flops, void *stream);
+int cjt_microbench_fma(int kind, double *flops, void *stream);
 
 /*
  * Allocation-free Chebyshev coefficients from values (no counterpart in the

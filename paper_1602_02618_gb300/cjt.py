@@ -27,6 +27,7 @@ CJT_EUNSUPPORTED = -7
 CJT_EDIRECTION = -8
 CJT_FP64 = 0
 CJT_MIXED = 1
+CJT_DFLOAT = 2
 CJT_FWD = 1
 CJT_INV = 2
 
@@ -312,10 +313,11 @@ def cjt_cheb_coeffs_noalloc(values, c_cheb, stream=None):
     return c_cheb
 
 
-def microbench_fma(fp64: bool = True, stream=None) -> float:
-    """Measured dependent-FMA throughput of the device in FLOP/s (FP64 or FP32)."""
+def microbench_fma(kind=True, stream=None) -> float:
+    """Measured dependent multiply-add throughput of the device in FLOP/s: kind True/1 FP64,
+    False/0 FP32, 2 double-float."""
     v = ctypes.c_double()
-    _check(load().cjt_microbench_fma(1 if fp64 else 0, ctypes.byref(v), _stream_handle(stream)),
+    _check(load().cjt_microbench_fma(int(kind), ctypes.byref(v), _stream_handle(stream)),
            "cjt_microbench_fma")
     return v.value
 

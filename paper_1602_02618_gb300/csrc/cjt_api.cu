@@ -136,7 +136,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     }
     if (o.M < 1 || o.M > 20) return CJT_EINVAL;
     if (!(o.eps > 0.0 && o.eps < 1.0)) return CJT_EINVAL;
-    if (o.precision != CJT_FP64 && o.precision != CJT_MIXED) return CJT_EINVAL;
+    if (o.precision != CJT_FP64 && o.precision != CJT_MIXED && o.precision != CJT_DFLOAT) return CJT_EINVAL;
     if (o.directions < 1 || o.directions > 3) return CJT_EINVAL;
     if (!(o.ratio == 0.0 || (o.ratio > 0.0 && o.ratio < 1.0))) return CJT_EINVAL;
     if (o.rec_store != 0 && o.rec_store != 1) return CJT_EINVAL;
@@ -211,7 +211,8 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
     } else {
         const int nqf = p->fw.nblk * p->M, nqi = p->iv.nblk * p->M;
         info->kernels_fwd = (p->fw.nitems > 0) + (nqf > 0 ? 1 + dft_launches(p->dft_f) : 0) + 1 +
-                            dft_launches(p->dft_dct) + 1;
+                            dft_launches(p->dft_dct) + 1 +
+                            (p->prec_asy == PREC_DF && (nqf > 0 || p->fw.E_df) ? 1 : 0);   // input to double-float
         info->kernels_inv = 1 + dft_launches(p->dft_front) + 1 + (nqi > 0 ? 1 + dft_launches(p->dft_i) : 0) +
                             (p->iv.nitems > 0) + 2;
         if (!(p->opts.directions & CJT_FWD)) info->kernels_fwd = 0;

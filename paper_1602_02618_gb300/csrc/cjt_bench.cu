@@ -1,8 +1,9 @@
 // Peak arithmetic microbenchmark: independent dependent-FMA chains on every SM.
-// Used to state the FP64 / FP32 pipe peak that the recurrence and transform
-// kernels are compared against.
+// Used to state the FP64 / FP32 pipe peak, and the double-float rate, that the
+// recurrence and transform kernels are compared against.
 #include <cuda_runtime.h>
 
+#include "cjt_df.cuh"
 #include "cjt_internal.cuh"
 
 namespace {
@@ -24,21 +25,46 @@ __global__ void __launch_bounds__(256) k_fma_chain(T *out, T a, T b) {
     if (s == (T)12345.678) out[0] = s;  // keeps the chains live
 }
 
+__global__ void __launch_bounds__(256) k_df_chain(float *out, float ah, float al, float bh, float bl) {
+    const dfs a = df_make(ah, al), b = df_make(bh, bl);
+    dfs x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = df_make((float)(threadIdx.x + c) * 1e-3f, 0.f);
+    for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = df_add(df_mul(x[c], a), b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c].h + x[c].l;
+    if (s == 12345.678f) out[0] = s;  // keeps the chains live
+}
+
+template <typename T>
+void launch_chain(int blocks, int threads, T *out, cudaStream_t st) {
+    k_fma_chain<T><<<blocks, threads, 0, st>>>(out, (T)0.999999, (T)1e-7);
+}
+struct DfTag {};
+template <>
+void launch_chain<DfTag>(int blocks, int threads, DfTag *out, cudaStream_t st) {
+    k_df_chain<<<blocks, threads, 0, st>>>((float *)out, 0.999999f, 1e-9f, 1e-7f, 1e-15f);
+}
+
 template <typename T>
 int run(double *flops, cudaStream_t st) {
     int dev = 0, sms = 0;
     CJT_CUDA_TRY(cudaGetDevice(&dev));
     CJT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     T *out = nullptr;
-    CJT_CUDA_TRY(cudaMallocAsync((void **)&out, sizeof(T), st));
+    CJT_CUDA_TRY(cudaMallocAsync((void **)&out, 8, st));
     const int blocks = sms * 8, threads = 256;
     cudaEvent_t e0, e1;
     CJT_CUDA_TRY(cudaEventCreate(&e0));
     CJT_CUDA_TRY(cudaEventCreate(&e1));
-    k_fma_chain<T><<<blocks, threads, 0, st>>>(out, (T)0.999999, (T)1e-7);  // warm-up
+    launch_chain<T>(blocks, threads, out, st);  // warm-up
     CJT_CUDA_TRY(cudaEventRecord(e0, st));
-    const int reps = sizeof(T) == 8 ? 2 : 20;
-    for (int r = 0; r < reps; ++r) k_fma_chain<T><<<blocks, threads, 0, st>>>(out, (T)0.999999, (T)1e-7);
+    const int reps = sizeof(T) == 8 ? 2 : (sizeof(T) == 4 ? 20 : 4);
+    for (int r = 0; r < reps; ++r) launch_chain<T>(blocks, threads, out, st);
     CJT_CUDA_TRY(cudaEventRecord(e1, st));
     CJT_CUDA_TRY(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -51,7 +77,10 @@ int run(double *flops, cudaStream_t st) {
 }
 }  // namespace
 
-extern "C" int cjt_microbench_fma(int fp64, double *flops, void *stream) {
+extern "C" int cjt_microbench_fma(int kind, double *flops, void *stream) {
     if (!flops) return CJT_EINVAL;
-    return fp64 ? run<double>(flops, (cudaStream_t)stream) : run<float>(flops, (cudaStream_t)stream);
+    if (kind == 0) return run<float>(flops, (cudaStream_t)stream);
+    if (kind == 1) return run<double>(flops, (cudaStream_t)stream);
+    if (kind == 2) return run<DfTag>(flops, (cudaStream_t)stream);
+    return CJT_EINVAL;
 }

@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "cjt_df.cuh"
 #include "cjt_internal.cuh"
 
 namespace {
@@ -217,34 +218,10 @@ __global__ void __launch_bounds__(128) k_rec_inv_stored(const RecItem *__restric
 }
 
 // ---------------------------------------------------------------------------
-// ASY pack, forward: pair p holds items q = 2p, 2p+1 (q = k*M + m) as re/im
+// ASY packs: pair p holds items q = 2p, 2p+1 (q = k*M + m) as the real and imaginary
+// parts of one complex transform input, from the pre-scaled tables; arithmetic in the
+// transform precision R.
 // ---------------------------------------------------------------------------
-template <typename V>
-__global__ void k_asy_pack_fwd(int64_t N, int64_t L, int M, int nq, const int *__restrict__ box3,
-                               const double *__restrict__ Cnm, const double *__restrict__ scale,
-                               const double *__restrict__ c, V *__restrict__ buf) {
-    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int p = blockIdx.y;
-    if (n >= L) return;
-    double v[2] = {0.0, 0.0};
-    if (n <= N) {
-        const double cn = c[n];
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const int q = 2 * p + s;
-            if (q < nq) {
-                const int k = q / M, m = q - k * M;
-                if (n >= box3[3 * k]) v[s] = Cnm[m * (N + 1) + n] * cn * scale[2 * q];
-            }
-        }
-    }
-    V o;
-    o.x = v[0];
-    o.y = v[1];
-    buf[(int64_t)p * L + n] = o;
-}
-
-// Packs with the pre-scaled tables: arithmetic in the transform precision R.
 template <typename V, typename R>
 __global__ void k_asy_pack_fwd_s(int64_t N, int64_t L, int nq, const R *__restrict__ Cs, const double *__restrict__ c,
                                  V *__restrict__ buf) {
@@ -287,6 +264,115 @@ __global__ void k_asy_pack_inv_s(int64_t Ng, int64_t L, int nq, const R *__restr
     buf[(int64_t)p * L + idx] = o;
 }
 
+// double-float packs (CJT_DFLOAT): the input as double-floats (xdf), tables as double-floats
+__global__ void k_to_dfs(int64_t n, const double *__restrict__ x, dfs *__restrict__ xdf) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) xdf[i] = df_from(x[i]);
+}
+
+__global__ void k_asy_pack_fwd_df(int64_t N, int64_t L, int nq, const dfs *__restrict__ Cs,
+                                  const dfs *__restrict__ cdf, dfc *__restrict__ buf) {
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (n >= L) return;
+    dfs re = df_make(0.f, 0.f), im = df_make(0.f, 0.f);
+    if (n <= N) {
+        const dfs cn = cdf[n];
+        const int q = 2 * p;
+        re = df_mul(Cs[(int64_t)q * (N + 1) + n], cn);
+        if (q + 1 < nq) im = df_mul(Cs[(int64_t)(q + 1) * (N + 1) + n], cn);
+    }
+    buf[(int64_t)p * L + n] = dfc_make(re, im);
+}
+
+__global__ void k_asy_pack_inv_df(int64_t Ng, int64_t L, int nq, const dfs *__restrict__ Us,
+                                  const dfs *__restrict__ Vs, const dfs *__restrict__ gdf, dfc *__restrict__ buf) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (idx >= L) return;
+    // H(idx) = (z(idx) + conj z(L - idx)) / 2: the box rows lie in [1, Ng - 1]
+    const bool lo = idx <= Ng;
+    const int64_t i = lo ? idx : L - idx;
+    const dfs gi = gdf[i];
+    const int q = 2 * p;
+    const dfs h0r = df_mul(Us[(int64_t)q * (Ng + 1) + i], gi);
+    dfs h0i = df_mul(Vs[(int64_t)q * (Ng + 1) + i], gi);
+    dfs h1r = df_make(0.f, 0.f), h1i = df_make(0.f, 0.f);
+    if (q + 1 < nq) {
+        h1r = df_mul(Us[(int64_t)(q + 1) * (Ng + 1) + i], gi);
+        h1i = df_mul(Vs[(int64_t)(q + 1) * (Ng + 1) + i], gi);
+    }
+    if (!lo) {
+        h0i = df_neg(h0i);
+        h1i = df_neg(h1i);
+    }
+    buf[(int64_t)p * L + idx] = dfc_make(df_sub(h0r, h1i), df_add(h0i, h1r));
+}
+
+// REC with stored double-float values: one double-float multiply-add per entry,
+// renormalised at every step (an unnormalised low part would let its own rounding
+// errors grow with the segment length)
+__global__ void __launch_bounds__(128) k_rec_fwd_stored_df(const RecItem *__restrict__ items, int64_t nitems,
+                                                          const dfs *__restrict__ cdf, const dfs *__restrict__ E,
+                                                          double *__restrict__ partials) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nitems) return;
+    const RecItem it = items[w];
+    const int len = it.b - it.a;
+    const dfs *e = E + it.eoff + lane;
+    const dfs *cc = cdf + it.a;
+    dfs acc[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = df_make(0.f, 0.f);
+    int k = 0;
+    for (; k + 4 <= len; k += 4) {
+        dfs v[4], cv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 t = __ldcs(reinterpret_cast<const float2 *>(e + (int64_t)(k + j) * 32));
+            v[j] = df_make(t.x, t.y);
+            cv[j] = cc[k + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = df_mac(acc[j], v[j], cv[j]);
+    }
+    for (; k < len; ++k) acc[k & 3] = df_mac(acc[k & 3], e[(int64_t)k * 32], cc[k]);
+    const dfs S = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
+    partials[it.out + lane] = lane < it.nrows ? df_to(S) : 0.0;
+}
+
+__global__ void __launch_bounds__(128) k_rec_inv_stored_df(const RecItem *__restrict__ items, int64_t nitems,
+                                                          const dfs *__restrict__ gdf, const dfs *__restrict__ E,
+                                                          double *__restrict__ partials) {
+    __shared__ dfs gs[4][32];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * 4 + wib;
+    if (w >= nitems) return;
+    const RecItem it = items[w];
+    gs[wib][lane] = lane < it.nrows ? gdf[it.row0 + lane] : df_make(0.f, 0.f);
+    __syncwarp();
+    const int len = it.b - it.a;
+    const dfs *e = E + it.eoff;
+    double *out = partials + it.out;
+    for (int k0 = 0; k0 < len; k0 += 32) {
+        const int k = k0 + lane;
+        if (k < len) {
+            dfs acc = df_make(0.f, 0.f);
+            for (int r = 0; r < it.nrows; ++r) acc = df_mac(acc, gs[wib][r], e[(int64_t)r * len + k]);
+            out[k] = df_to(acc);
+        }
+    }
+}
+
+// transform output components as doubles
+__device__ __forceinline__ double re_d(double2 v) { return v.x; }
+__device__ __forceinline__ double im_d(double2 v) { return v.y; }
+__device__ __forceinline__ double re_d(float2 v) { return (double)v.x; }
+__device__ __forceinline__ double im_d(float2 v) { return (double)v.y; }
+__device__ __forceinline__ double re_d(dfc v) { return df_to(dfc_re(v)); }
+__device__ __forceinline__ double im_d(dfc v) { return df_to(dfc_im(v)); }
+
 // ---------------------------------------------------------------------------
 // combine, forward: REC segment partials + asymptotic terms; writes the even
 // extension of y (length 2N) for the final DCT-I
@@ -311,11 +397,11 @@ __global__ void k_combine_fwd(int64_t N, int64_t L, int M, const int *__restrict
             const V Z = buf[(int64_t)p * L + i], W = buf[(int64_t)p * L + im];
             double re, imv;
             if ((q & 1) == 0) {
-                re = 0.5 * ((double)Z.x + (double)W.x);
-                imv = 0.5 * ((double)Z.y - (double)W.y);
+                re = 0.5 * (re_d(Z) + re_d(W));
+                imv = 0.5 * (im_d(Z) - im_d(W));
             } else {
-                re = 0.5 * ((double)Z.y + (double)W.y);
-                imv = 0.5 * ((double)W.x - (double)Z.x);
+                re = 0.5 * (im_d(Z) + im_d(W));
+                imv = 0.5 * (re_d(W) - re_d(Z));
             }
             const double us = scale[2 * q + 1];
             y = fma(u[m * (N + 1) + i] * us, re, y);
@@ -344,43 +430,13 @@ __global__ void k_inv_front_pack(int64_t N, int64_t L, const double *__restrict_
     buf[k] = make_double2(k <= N ? c[k] : 0.0, 0.0);
 }
 
-__global__ void k_inv_g(int64_t Ng, const double2 *__restrict__ F, const double *__restrict__ w, double *__restrict__ g) {
+__global__ void k_inv_g(int64_t Ng, const double2 *__restrict__ F, const double *__restrict__ w, double *__restrict__ g,
+                        dfs *__restrict__ gdf) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i > Ng) return;
-    g[i] = w[i] * F[i].x;
-}
-
-template <typename V>
-__global__ void k_asy_pack_inv(int64_t Ng, int64_t L, int M, int nq, const int *__restrict__ box3,
-                               const double *__restrict__ scale, const double *__restrict__ u,
-                               const double *__restrict__ v, const double *__restrict__ g, V *__restrict__ buf) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int p = blockIdx.y;
-    if (idx >= L) return;
-    double hr[2] = {0.0, 0.0}, hi[2] = {0.0, 0.0};
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const int q = 2 * p + s;
-        if (q >= nq) continue;
-        const int k = q / M, m = q - k * M;
-        const int i1 = box3[3 * k + 1], i2 = box3[3 * k + 2];
-        if (idx >= i1 && idx <= i2) {
-            const double gi = 0.5 * scale[2 * q] * g[idx];
-            hr[s] = u[m * (Ng + 1) + idx] * gi;
-            hi[s] = v[m * (Ng + 1) + idx] * gi;
-        } else {
-            const int64_t j = L - idx;
-            if (j >= i1 && j <= i2) {
-                const double gj = 0.5 * scale[2 * q] * g[j];
-                hr[s] = u[m * (Ng + 1) + j] * gj;
-                hi[s] = -v[m * (Ng + 1) + j] * gj;
-            }
-        }
-    }
-    V o;
-    o.x = hr[0] - hi[1];
-    o.y = hi[0] + hr[1];
-    buf[(int64_t)p * L + idx] = o;
+    const double v = w[i] * F[i].x;
+    g[i] = v;
+    if (gdf) gdf[i] = df_from(v);
 }
 
 // Sum of the recurrence partials of every item covering degree n (fixed order:
@@ -436,7 +492,7 @@ __global__ void k_combine_inv(int64_t N, int64_t L, int M, int nblk, const int *
         for (int m = 0; m < M; ++m) {
             const int q = k * M + m, p = q >> 1;
             const V Z = buf[(int64_t)p * L + n];
-            const double R = (q & 1) ? (double)Z.y : (double)Z.x;
+            const double R = (q & 1) ? im_d(Z) : re_d(Z);
             y = fma(Cnm[m * (N + 1) + n] * scale[2 * q + 1], R, y);
         }
     }
@@ -461,11 +517,17 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         return CJT_OK;
     }
     GridWork &gw = p->fw;
-    const bool fp32 = p->opts.precision == CJT_MIXED;
+    const bool fp32 = p->prec_asy == PREC_F32, dfm = p->prec_asy == PREC_DF;
+    const void *tw_asy = fp32 ? p->d_tw32 : dfm ? p->d_twdf : p->d_tw64;
     const int M = p->M;
     int rc;
     const int nq = gw.nblk * M;
     const int64_t L = p->Lf;
+    dfs *cdf = (dfs *)ws.xdf;
+    if (dfm && (nq > 0 || gw.E_df)) {
+        k_to_dfs<<<blocks_for(N + 1, 256), 256, 0, st>>>(N + 1, in, cdf);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
     // the asymptotic transforms run on a side stream, concurrently with the recurrence
     const bool ovl = nq > 0 && p->side;
     cudaStream_t sa = ovl ? p->side : st;
@@ -476,7 +538,9 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     if (nq > 0) {
         dim3 gp(blocks_for(L, 256), p->npair_f);
         StageTimer tm(p, sa, CJT_STAGE_FWD_PACK);
-        if (fp32)
+        if (dfm)
+            k_asy_pack_fwd_df<<<gp, 256, 0, sa>>>(N, L, nq, (const dfs *)gw.d_Cs, cdf, (dfc *)ws.fft_f);
+        else if (fp32)
             k_asy_pack_fwd_s<float2, float><<<gp, 256, 0, sa>>>(N, L, nq, (const float *)gw.d_Cs, in, (float2 *)ws.fft_f);
         else
             k_asy_pack_fwd_s<double2, double><<<gp, 256, 0, sa>>>(N, L, nq, (const double *)gw.d_Cs, in,
@@ -485,14 +549,16 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     if (nq > 0) {
         StageTimer tm(p, sa, CJT_STAGE_FWD_FFT);
-        rc = cjt_dft_exec(p->dft_f, ws.fft_f, ws.work, ws.scratch, p->npair_f, fp32 ? p->d_tw32 : p->d_tw64,
-                          p->Ltab, sa);
+        rc = cjt_dft_exec(p->dft_f, ws.fft_f, ws.work, ws.scratch, p->npair_f, tw_asy, p->Ltab, sa);
         if (rc) return rc;
     }
     // REC
     if (gw.nitems > 0) {
         StageTimer tm(p, st, CJT_STAGE_FWD_REC);
-        if (gw.d_E)
+        if (gw.d_E && gw.E_df)
+            k_rec_fwd_stored_df<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, cdf,
+                                                                                (const dfs *)gw.d_E, ws.part_f);
+        else if (gw.d_E)
             k_rec_fwd_stored<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, in, gw.d_E,
                                                                              ws.part_f);
         else
@@ -507,7 +573,11 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     double2 *ext = (double2 *)ws.dct;
     {
     StageTimer tm(p, st, CJT_STAGE_FWD_COMBINE);
-    if (fp32)
+    if (dfm)
+        k_combine_fwd<dfc><<<blocks_for(N + 1, 256), 256, 0, st>>>(
+            N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const dfc *)ws.fft_f, gw.d_row_base, gw.d_row_nseg,
+            ws.part_f, ext);
+    else if (fp32)
         k_combine_fwd<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
             N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const float2 *)ws.fft_f, gw.d_row_base, gw.d_row_nseg,
             ws.part_f, ext);
@@ -533,7 +603,9 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         return CJT_OK;
     }
     GridWork &gw = p->iv;
-    const bool fp32 = p->opts.precision == CJT_MIXED;
+    const bool fp32 = p->prec_asy == PREC_F32, dfm = p->prec_asy == PREC_DF;
+    const void *tw_asy = fp32 ? p->d_tw32 : dfm ? p->d_twdf : p->d_tw64;
+    dfs *gdf = dfm ? (dfs *)ws.xdf : nullptr;
     const int M = p->M;
     const int64_t Ng = 2 * N, L = p->Li;
     // front end: p_N on the 2N grid, times the Clenshaw--Curtis weights
@@ -544,7 +616,7 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     CJT_CUDA_TRY(cudaGetLastError());
     rc = cjt_dft_exec(p->dft_front, ws.dct, ws.work, ws.scratch, 1, p->d_tw64, p->Ltab, st);
     if (rc) return rc;
-    k_inv_g<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)ws.dct, p->d_w, ws.g);
+    k_inv_g<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)ws.dct, p->d_w, ws.g, gdf);
     CJT_CUDA_TRY(cudaGetLastError());
     }
     // transposed asymptotic blocks, on a side stream concurrently with the recurrence
@@ -558,7 +630,10 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     if (nq > 0) {
         dim3 gp(blocks_for(L, 256), p->npair_i);
         StageTimer tm(p, sa, CJT_STAGE_INV_PACK);
-        if (fp32)
+        if (dfm)
+            k_asy_pack_inv_df<<<gp, 256, 0, sa>>>(Ng, L, nq, (const dfs *)gw.d_Us, (const dfs *)gw.d_Vs, gdf,
+                                                  (dfc *)ws.fft_i);
+        else if (fp32)
             k_asy_pack_inv_s<float2, float><<<gp, 256, 0, sa>>>(Ng, L, nq, (const float *)gw.d_Us,
                                                                 (const float *)gw.d_Vs, ws.g, (float2 *)ws.fft_i);
         else
@@ -568,15 +643,17 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     if (nq > 0) {
         StageTimer tm(p, sa, CJT_STAGE_INV_FFT);
-        rc = cjt_dft_exec(p->dft_i, ws.fft_i, ws.work, ws.scratch, p->npair_i, fp32 ? p->d_tw32 : p->d_tw64,
-                          p->Ltab, sa);
+        rc = cjt_dft_exec(p->dft_i, ws.fft_i, ws.work, ws.scratch, p->npair_i, tw_asy, p->Ltab, sa);
         if (rc) return rc;
     }
     // transposed recurrence and the fixed-order sums over the items of each degree
     {
         StageTimer tm(p, st, CJT_STAGE_INV_REC);
         if (gw.nitems > 0) {
-            if (gw.d_E)
+            if (gw.d_E && gw.E_df)
+                k_rec_inv_stored_df<<<blocks_for(gw.nitems, 4), 128, 0, st>>>(gw.d_items, gw.nitems, gdf,
+                                                                               (const dfs *)gw.d_E, ws.part_i);
+            else if (gw.d_E)
                 k_rec_inv_stored<<<blocks_for(gw.nitems, 4), 128, 0, st>>>(gw.d_items, gw.nitems, ws.g, gw.d_E,
                                                                             ws.part_i);
             else
@@ -593,7 +670,10 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
     }
     StageTimer tm(p, st, CJT_STAGE_INV_COMBINE);
-    if (fp32)
+    if (dfm)
+        k_combine_inv<dfc><<<blocks_for(N + 1, 256), 256, 0, st>>>(
+            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const dfc *)ws.fft_i, ws.y, p->d_s, out);
+    else if (fp32)
         k_combine_inv<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
             N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const float2 *)ws.fft_i, ws.y, p->d_s, out);
     else

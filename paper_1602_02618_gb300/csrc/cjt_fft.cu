@@ -1,4 +1,4 @@
-// Shared-memory radix-4 FFT for sm_103a (FP64 and FP32), used for the
+// Shared-memory radix-4 FFT for sm_103a (FP64, FP32 and double-float), used for the
 // diagonally scaled DCT-I/DST-I of the asymptotic blocks (Eq. "PNASY"), the
 // final inverse DCT-I (Sec. 2) and the inverse transform's front end and
 // transposed blocks (Eq. "CJTT").
@@ -19,15 +19,18 @@
 
 #include <algorithm>
 
+#include "cjt_df.cuh"
 #include "cjt_internal.cuh"
 
 int cjt_fft_prime();
 
 namespace {
 
+struct dfloat {};   // tag of the double-float transform (complex type dfc)
 template <typename T> struct cplx;
 template <> struct cplx<double> { using t = double2; };
 template <> struct cplx<float> { using t = float2; };
+template <> struct cplx<dfloat> { using t = dfc; };
 
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { V r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
@@ -39,6 +42,21 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
 }
 // multiply by -i
 template <typename V> __device__ __forceinline__ V cmul_mi(V a) { V r; r.x = a.y; r.y = -a.x; return r; }
+template <typename V> __device__ __forceinline__ V czero() { V r; r.x = 0; r.y = 0; return r; }
+template <typename V> __device__ __forceinline__ V cconj(V a) { a.y = -a.y; return a; }
+// times a power of two (exact)
+template <typename V> __device__ __forceinline__ V cscale(V a, double s) {
+    a.x = a.x * (decltype(a.x))s;
+    a.y = a.y * (decltype(a.y))s;
+    return a;
+}
+template <> __device__ __forceinline__ dfc cadd(dfc a, dfc b) { return dfc_add(a, b); }
+template <> __device__ __forceinline__ dfc csub(dfc a, dfc b) { return dfc_sub(a, b); }
+template <> __device__ __forceinline__ dfc cmul(dfc a, dfc b) { return dfc_mul(a, b); }
+template <> __device__ __forceinline__ dfc cmul_mi(dfc a) { return dfc_mul_mi(a); }
+template <> __device__ __forceinline__ dfc czero<dfc>() { return dfc_zero(); }
+template <> __device__ __forceinline__ dfc cconj(dfc a) { return dfc_conj(a); }
+template <> __device__ __forceinline__ dfc cscale(dfc a, double s) { return dfc_scale_pow2(a, (float)s); }
 
 constexpr int FFT_THREADS = 256;
 constexpr int SMEM_PAD = 1;
@@ -199,17 +217,13 @@ int fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw
 // ---------------------------------------------------------------------------
 // Bluestein
 // ---------------------------------------------------------------------------
-template <typename V> __device__ __forceinline__ V cconj(V a) { a.y = -a.y; return a; }
-
 template <typename V>
 __global__ void k_blue_pre(int64_t L, int64_t S, int64_t P, const V *__restrict__ data, const V *__restrict__ chirp,
                            V *__restrict__ work) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t b = blockIdx.y;
     if (i >= P) return;
-    V v;
-    v.x = 0;
-    v.y = 0;
+    V v = czero<V>();
     if (i < S) v = cmul(data[b * L + i], chirp[i]);
     work[b * P + i] = v;
 }
@@ -222,15 +236,13 @@ __global__ void k_blue_mid(int64_t P, const V *__restrict__ bhat, V *__restrict_
     work[b * P + i] = cconj(cmul(work[b * P + i], bhat[i]));
 }
 
-template <typename V, typename R>
+template <typename V>
 __global__ void k_blue_post(int64_t L, int64_t K, int64_t P, const V *__restrict__ work, const V *__restrict__ chirp,
-                            V *__restrict__ data, R invP) {
+                            V *__restrict__ data, double invP) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t b = blockIdx.y;
     if (k >= K) return;
-    V v = cconj(work[b * P + k]);
-    v.x *= invP;
-    v.y *= invP;
+    const V v = cscale(cconj(work[b * P + k]), invP);   // 1/P is a power of two
     data[b * L + k] = cmul(v, chirp[k]);
 }
 
@@ -260,6 +272,11 @@ __global__ void k_to_f32(int64_t n, const double2 *__restrict__ a, float2 *__res
     if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
+__global__ void k_to_dfc(int64_t n, const double2 *__restrict__ a, dfc *__restrict__ b) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = dfc_make(df_from(a[i].x), df_from(a[i].y));
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <typename R>
@@ -278,8 +295,8 @@ int dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch,
     rc = fft_pow2<R>(work, scratch, d.P, batch, tw, Ltab, st);
     if (rc) return rc;
     dim3 g2(nblk(d.K, 256), (unsigned)batch);
-    k_blue_post<V, R><<<g2, 256, 0, st>>>(d.L, d.K, d.P, (const V *)work, (const V *)d.chirp, (V *)data,
-                                          (R)(1.0 / (double)d.P));
+    k_blue_post<V><<<g2, 256, 0, st>>>(d.L, d.K, d.P, (const V *)work, (const V *)d.chirp, (V *)data,
+                                       1.0 / (double)d.P);
     CJT_CUDA_TRY(cudaGetLastError());
     return CJT_OK;
 }
@@ -294,11 +311,11 @@ int64_t cjt_dft_padded(int64_t L, int64_t S, int64_t K) {
 }
 
 int64_t cjt_dft_work_bytes(const Dft &d, int64_t batch) {
-    return d.P ? d.P * batch * (int64_t)(d.fp32 ? sizeof(float2) : sizeof(double2)) : 0;
+    return d.P ? d.P * batch * prec_cbytes(d.prec) : 0;
 }
 
 int64_t cjt_dft_scratch_bytes(const Dft &d, int64_t batch) {
-    return cjt_fft_scratch_elems(d.fft_len(), batch) * (int64_t)(d.fp32 ? sizeof(float2) : sizeof(double2));
+    return cjt_fft_scratch_elems(d.fft_len(), batch) * prec_cbytes(d.prec);
 }
 
 int cjt_dft_setup(Dft &d, const void *tw64, int64_t Ltab, cudaStream_t st) {
@@ -313,9 +330,12 @@ int cjt_dft_setup(Dft &d, const void *tw64, int64_t Ltab, cudaStream_t st) {
     CJT_CUDA_TRY(cudaGetLastError());
     int rc = fft_pow2<double>(b64, scr, d.P, 1, tw64, Ltab, st);
     if (rc) return rc;
-    if (d.fp32) {
+    if (d.prec == PREC_F32) {
         k_to_f32<<<nblk(nw, 256), 256, 0, st>>>(nw, w64, (float2 *)d.chirp);
         k_to_f32<<<nblk(d.P, 256), 256, 0, st>>>(d.P, b64, (float2 *)d.bhat);
+    } else if (d.prec == PREC_DF) {
+        k_to_dfc<<<nblk(nw, 256), 256, 0, st>>>(nw, w64, (dfc *)d.chirp);
+        k_to_dfc<<<nblk(d.P, 256), 256, 0, st>>>(d.P, b64, (dfc *)d.bhat);
     } else {
         CJT_CUDA_TRY(cudaMemcpyAsync(d.chirp, w64, sizeof(double2) * nw, cudaMemcpyDeviceToDevice, st));
         CJT_CUDA_TRY(cudaMemcpyAsync(d.bhat, b64, sizeof(double2) * d.P, cudaMemcpyDeviceToDevice, st));
@@ -329,14 +349,16 @@ int cjt_dft_setup(Dft &d, const void *tw64, int64_t Ltab, cudaStream_t st) {
 
 int cjt_dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const void *tw, int64_t Ltab,
                  cudaStream_t st) {
-    return d.fp32 ? dft_exec<float>(d, data, work, scratch, batch, tw, Ltab, st)
-                  : dft_exec<double>(d, data, work, scratch, batch, tw, Ltab, st);
+    if (d.prec == PREC_F32) return dft_exec<float>(d, data, work, scratch, batch, tw, Ltab, st);
+    if (d.prec == PREC_DF) return dft_exec<dfloat>(d, data, work, scratch, batch, tw, Ltab, st);
+    return dft_exec<double>(d, data, work, scratch, batch, tw, Ltab, st);
 }
 
-int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab, bool fp32,
+int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab, int prec,
                  cudaStream_t st) {
-    return fp32 ? fft_pow2<float>(data, scratch, L, batch, tw, Ltab, st)
-                : fft_pow2<double>(data, scratch, L, batch, tw, Ltab, st);
+    if (prec == PREC_F32) return fft_pow2<float>(data, scratch, L, batch, tw, Ltab, st);
+    if (prec == PREC_DF) return fft_pow2<dfloat>(data, scratch, L, batch, tw, Ltab, st);
+    return fft_pow2<double>(data, scratch, L, batch, tw, Ltab, st);
 }
 
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch) { return L > 4096 ? L * batch : 0; }
@@ -348,6 +370,7 @@ int cjt_fft_prime() {
     if (done) return CJT_OK;
     CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     done = true;
     return CJT_OK;
 }

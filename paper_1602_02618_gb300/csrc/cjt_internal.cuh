@@ -11,7 +11,8 @@
 //   partition          boxes (j_k, i_k^1, i_k^2)        (Sec. 2.2), per grid
 //   recurrence work    warp items over (32 rows) x (degree segment), with the
 //                      forward-recurrence state at every segment start
-//   transform buffers  complex FP64 or FP32, twiddle table omega_{Ltab}^k
+//   transform buffers  complex FP64, FP32 or double-float (cjt_df.cuh), twiddle
+//                      table omega_{Ltab}^k in each precision the plan uses
 #pragma once
 
 #include <cuda_runtime.h>
@@ -84,8 +85,10 @@ struct GridWork {
     int64_t *d_seg_out = nullptr; // partial base of each contributing item
     int *d_seg_b = nullptr;       // item end degree b
     int64_t nchunks = 0;
-    // stored recurrence values (rec_store): forward [item][k][lane], inverse [item][lane][k]
+    // stored recurrence values (rec_store): forward [item][k][lane], inverse [item][lane][k];
+    // doubles, or double-floats (dfs, same 8 bytes) when E_df
     double *d_E = nullptr;
+    bool E_df = false;
     int64_t nE = 0;
     // diagonals u_m, v_m on this grid
     double *d_u = nullptr, *d_v = nullptr;
@@ -104,9 +107,11 @@ struct GridWork {
 // rows of length L.  L a power of two: direct radix-4 FFT (P = 0).  Otherwise Bluestein's
 // chirp-z form: X_k = w_k sum_n (x_n w_n) conj(w_{k-n}), w_m = exp(-i pi m^2 / L), as a cyclic
 // convolution of power-of-two length P >= S + K - 1.
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_DF = 2 };   // element type of a transform
+inline int64_t prec_cbytes(int prec) { return prec == PREC_F32 ? 8 : 16; }   // bytes of one complex
 struct Dft {
     int64_t L = 0, S = 0, K = 0, P = 0;
-    bool fp32 = false;
+    int prec = PREC_F64;
     void *chirp = nullptr;  // w_m, m < max(S, K)
     void *bhat = nullptr;   // FFT_P of the cyclically arranged conj(w)
     int64_t fft_len() const { return P ? P : L; }
@@ -118,8 +123,9 @@ struct Dft {
 struct Workspace {
     void *fft_f = nullptr, *fft_i = nullptr, *scratch = nullptr, *work = nullptr;
     double *dct = nullptr, *y = nullptr, *g = nullptr, *part_f = nullptr, *part_i = nullptr;
+    void *xdf = nullptr;   // CJT_DFLOAT: the input c (forward) or g (inverse) as double-floats
 };
-enum { WS_FFT_F, WS_FFT_I, WS_SCRATCH, WS_WORK, WS_DCT, WS_Y, WS_G, WS_PART_F, WS_PART_I, WS_COUNT };
+enum { WS_FFT_F, WS_FFT_I, WS_SCRATCH, WS_WORK, WS_DCT, WS_Y, WS_G, WS_PART_F, WS_PART_I, WS_XDF, WS_COUNT };
 
 struct cjt_plan_s {
     int64_t N = 0;
@@ -143,6 +149,8 @@ struct cjt_plan_s {
     int64_t Ltab = 0;
     void *d_tw64 = nullptr;       // double2[Ltab]
     void *d_tw32 = nullptr;       // float2[Ltab]
+    void *d_twdf = nullptr;       // dfc[Ltab]
+    int prec_asy = PREC_F64;      // element type of the asymptotic transforms
     int npair_f = 0, npair_i = 0; // complex transforms of ASY item pairs
     Dft dft_f, dft_dct, dft_front, dft_i, dft_cc;
     // workspace layout (byte offsets and sizes within the arena) and the owned workspace
@@ -276,12 +284,12 @@ __host__ __device__ inline double cjt_hahn_h(int l, double a) {
 // launchers implemented in the .cu files
 // ---------------------------------------------------------------------------
 int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab,
-                 bool fp32, cudaStream_t st);
+                 int prec, cudaStream_t st);
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch);
 int cjt_fft_prime();
 // Bluestein length (0 when L is a power of two)
 int64_t cjt_dft_padded(int64_t L, int64_t S, int64_t K);
-// chirp and bhat for a Bluestein transform; tw64 must cover P
+// chirp and bhat for a Bluestein transform (in d.prec); tw64 must cover P
 int cjt_dft_setup(Dft &d, const void *tw64, int64_t Ltab, cudaStream_t st);
 int cjt_dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const void *tw, int64_t Ltab,
                  cudaStream_t st);

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "cjt_df.cuh"
 #include "cjt_internal.cuh"
 
 namespace {
@@ -212,6 +213,9 @@ __global__ void k_rec_states(int64_t nrows, const int *srow, int64_t Ng, int seg
 // --------------------------------------------------------------------------
 // pre-scaled transform inputs (the scale of each item is an exact power of two)
 // --------------------------------------------------------------------------
+template <typename R> __device__ __forceinline__ R to_prec(double v) { return (R)v; }
+template <> __device__ __forceinline__ dfs to_prec<dfs>(double v) { return df_from(v); }
+
 template <typename R>
 __global__ void k_scaled_C(int64_t N, int M, int nq, const int *__restrict__ box3, const double *__restrict__ Cnm,
                            const double *__restrict__ scale, R *__restrict__ out) {
@@ -219,7 +223,7 @@ __global__ void k_scaled_C(int64_t N, int M, int nq, const int *__restrict__ box
     const int q = blockIdx.y;
     if (n > N || q >= nq) return;
     const int k = q / M, m = q - k * M;
-    out[(int64_t)q * (N + 1) + n] = n >= box3[3 * k] ? (R)(Cnm[m * (N + 1) + n] * scale[2 * q]) : (R)0;
+    out[(int64_t)q * (N + 1) + n] = to_prec<R>(n >= box3[3 * k] ? Cnm[m * (N + 1) + n] * scale[2 * q] : 0.0);
 }
 
 template <typename R>
@@ -232,8 +236,8 @@ __global__ void k_scaled_uv(int64_t Ng, int M, int nq, const int *__restrict__ b
     const int k = q / M, m = q - k * M;
     const bool in = i >= box3[3 * k + 1] && i <= box3[3 * k + 2];
     const double sc = 0.5 * scale[2 * q];
-    U[(int64_t)q * (Ng + 1) + i] = in ? (R)(sc * u[m * (Ng + 1) + i]) : (R)0;
-    V[(int64_t)q * (Ng + 1) + i] = in ? (R)(sc * v[m * (Ng + 1) + i]) : (R)0;
+    U[(int64_t)q * (Ng + 1) + i] = to_prec<R>(in ? sc * u[m * (Ng + 1) + i] : 0.0);
+    V[(int64_t)q * (Ng + 1) + i] = to_prec<R>(in ? sc * v[m * (Ng + 1) + i] : 0.0);
 }
 
 // --------------------------------------------------------------------------
@@ -397,13 +401,22 @@ __global__ void k_inv_norm(int64_t N, double a, double b, double *s) {
 }
 
 // twiddles omega_L^k = exp(-2 pi i k / L)
-__global__ void k_twiddles(int64_t L, double2 *tw64, float2 *tw32) {
+__global__ void k_twiddles(int64_t L, double2 *tw64, float2 *tw32, dfc *twdf) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= L) return;
     double s, c;
     sincospi(-2.0 * (double)k / (double)L, &s, &c);
     tw64[k] = make_double2(c, s);
     if (tw32) tw32[k] = make_float2((float)c, (float)s);
+    if (twdf) twdf[k] = dfc_make(df_from(c), df_from(s));
+}
+
+// stored recurrence values, doubles -> double-floats in place (same 8 bytes per entry)
+__global__ void k_E_to_df(int64_t n, double *E) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = E[i];
+    reinterpret_cast<dfs *>(E)[i] = df_from(v);
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -555,10 +568,13 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
         TRY(dalloc(p, &gw.d_scale, (int64_t)sc.size()));
         CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_scale, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, st));
         const int nq = gw.nblk * M;
-        const bool f32 = p->opts.precision == CJT_MIXED;
+        const bool f32 = p->opts.precision == CJT_MIXED, df = p->opts.precision == CJT_DFLOAT;
         if (!inverse) {
             dim3 g(blocks_for(p->N + 1, 256), nq);
-            if (f32) {
+            if (df) {
+                TRY(dalloc(p, (double **)&gw.d_Cs, (int64_t)nq * (p->N + 1)));   // dfs: 8 bytes
+                k_scaled_C<dfs><<<g, 256, 0, st>>>(p->N, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, (dfs *)gw.d_Cs);
+            } else if (f32) {
                 TRY(dalloc(p, (float **)&gw.d_Cs, (int64_t)nq * (p->N + 1)));
                 k_scaled_C<float><<<g, 256, 0, st>>>(p->N, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, (float *)gw.d_Cs);
             } else {
@@ -567,7 +583,12 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
             }
         } else {
             dim3 g(blocks_for(Ng + 1, 256), nq);
-            if (f32) {
+            if (df) {
+                TRY(dalloc(p, (double **)&gw.d_Us, (int64_t)nq * (Ng + 1)));
+                TRY(dalloc(p, (double **)&gw.d_Vs, (int64_t)nq * (Ng + 1)));
+                k_scaled_uv<dfs><<<g, 256, 0, st>>>(Ng, M, nq, gw.d_box, gw.d_u, gw.d_v, gw.d_scale,
+                                                    (dfs *)gw.d_Us, (dfs *)gw.d_Vs);
+            } else if (f32) {
                 TRY(dalloc(p, (float **)&gw.d_Us, (int64_t)nq * (Ng + 1)));
                 TRY(dalloc(p, (float **)&gw.d_Vs, (int64_t)nq * (Ng + 1)));
                 k_scaled_uv<float><<<g, 256, 0, st>>>(Ng, M, nq, gw.d_box, gw.d_u, gw.d_v, gw.d_scale,
@@ -710,6 +731,11 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
         k_rec_fill<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt, gw.d_states,
                                                                    gw.d_E, inverse ? 1 : 0);
         CJT_CUDA_TRY(cudaGetLastError());
+        if (p->opts.precision == CJT_DFLOAT) {
+            k_E_to_df<<<blocks_for(gw.nE, 256), 256, 0, st>>>(gw.nE, gw.d_E);
+            CJT_CUDA_TRY(cudaGetLastError());
+            gw.E_df = true;
+        }
     }
     CJT_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors go out of scope
     tr.mark(inverse ? "inv: segment states" : "fwd: segment states");
@@ -767,25 +793,26 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     if (inv) TRY(build_grid(p, p->iv, 2 * N, true, h, st));
 
     // transforms: forward ASY/DCT length 2N, inverse 4N; Bluestein when N is not a power of two
-    const bool fp32 = p->opts.precision == CJT_MIXED;
+    p->prec_asy = p->opts.precision == CJT_MIXED ? PREC_F32 : p->opts.precision == CJT_DFLOAT ? PREC_DF : PREC_F64;
+    const int pa = p->prec_asy;
     p->Lf = fwd ? 2 * N : 0;
     p->Li = inv ? 4 * N : 0;
     p->npair_f = (p->fw.nblk * M + 1) / 2;
     p->npair_i = (p->iv.nblk * M + 1) / 2;
-    auto mk = [](Dft &d, int64_t L, int64_t S, int64_t K, bool f32) {
-        d.L = L; d.S = S; d.K = K; d.fp32 = f32; d.P = cjt_dft_padded(L, S, K);
+    auto mk = [](Dft &d, int64_t L, int64_t S, int64_t K, int prec) {
+        d.L = L; d.S = S; d.K = K; d.prec = prec; d.P = cjt_dft_padded(L, S, K);
     };
     std::vector<std::pair<Dft *, int64_t>> used;   // transform and its batch
     if (fwd) {
-        mk(p->dft_f, 2 * N, N + 1, 2 * N, fp32);   // both Z(i) and Z(L-i) are read by the pair separation
-        mk(p->dft_dct, 2 * N, 2 * N, N + 1, false);
+        mk(p->dft_f, 2 * N, N + 1, 2 * N, pa);   // both Z(i) and Z(L-i) are read by the pair separation
+        mk(p->dft_dct, 2 * N, 2 * N, N + 1, PREC_F64);
         if (p->npair_f) used.push_back({&p->dft_f, p->npair_f});
         used.push_back({&p->dft_dct, 1});
     }
     if (inv) {
-        mk(p->dft_front, 4 * N, N + 1, 2 * N + 1, false);
-        mk(p->dft_i, 4 * N, 4 * N, N + 1, fp32);
-        mk(p->dft_cc, 4 * N, 4 * N, 2 * N + 1, false);
+        mk(p->dft_front, 4 * N, N + 1, 2 * N + 1, PREC_F64);
+        mk(p->dft_i, 4 * N, 4 * N, N + 1, pa);
+        mk(p->dft_cc, 4 * N, 4 * N, 2 * N + 1, PREC_F64);
         used.push_back({&p->dft_front, 1});
         if (p->npair_i) used.push_back({&p->dft_i, p->npair_i});
         used.push_back({&p->dft_cc, 1});
@@ -793,18 +820,20 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     p->Ltab = 2;
     for (auto &u : used) p->Ltab = std::max(p->Ltab, u.first->fft_len());
     TRY(dalloc(p, (double2 **)&p->d_tw64, p->Ltab));
-    if (fp32) TRY(dalloc(p, (float2 **)&p->d_tw32, p->Ltab));
-    k_twiddles<<<blocks_for(p->Ltab, 256), 256, 0, st>>>(p->Ltab, (double2 *)p->d_tw64, (float2 *)p->d_tw32);
+    if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_tw32, p->Ltab));
+    if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_twdf, p->Ltab));   // dfc: 16 bytes
+    k_twiddles<<<blocks_for(p->Ltab, 256), 256, 0, st>>>(p->Ltab, (double2 *)p->d_tw64, (float2 *)p->d_tw32,
+                                                         (dfc *)p->d_twdf);
     CJT_CUDA_TRY(cudaGetLastError());
     int64_t work = 0, scratch = 0;
     for (auto &u : used) {
         Dft &d = *u.first;
         if (d.P) {
             const int64_t nw = std::max(d.S, d.K);
-            if (d.fp32) {
+            if (d.prec == PREC_F32) {
                 TRY(dalloc(p, (float2 **)&d.chirp, nw));
                 TRY(dalloc(p, (float2 **)&d.bhat, d.P));
-            } else {
+            } else {   // double2 or dfc: 16 bytes
                 TRY(dalloc(p, (double2 **)&d.chirp, nw));
                 TRY(dalloc(p, (double2 **)&d.bhat, d.P));
             }
@@ -816,7 +845,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     tr.mark("transforms: twiddles, chirps");
     // execution workspace layout
     {
-        const int64_t csz = fp32 ? (int64_t)sizeof(float2) : (int64_t)sizeof(double2);
+        const int64_t csz = prec_cbytes(pa);
         const int64_t Ld = std::max<int64_t>(std::max(p->Lf, p->Li), 2);
         p->ws_size[WS_FFT_F] = csz * p->npair_f * p->Lf;
         p->ws_size[WS_FFT_I] = csz * p->npair_i * p->Li;
@@ -827,6 +856,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         p->ws_size[WS_G] = inv ? (int64_t)sizeof(double) * (2 * N + 1) : 0;
         p->ws_size[WS_PART_F] = (int64_t)sizeof(double) * (fwd ? std::max<int64_t>(p->fw.npartials, 1) : 0);
         p->ws_size[WS_PART_I] = (int64_t)sizeof(double) * (inv ? std::max<int64_t>(p->iv.npartials, 1) : 0);
+        p->ws_size[WS_XDF] = pa == PREC_DF ? (int64_t)sizeof(dfs) * (inv ? 2 * N + 1 : N + 1) : 0;
         int64_t off = 0;
         for (int k = 0; k < WS_COUNT; ++k) {
             p->ws_off[k] = off;
@@ -898,5 +928,6 @@ Workspace cjt_carve(const cjt_plan_s *p, void *base) {
     w.g = (double *)at(WS_G);
     w.part_f = (double *)at(WS_PART_F);
     w.part_i = (double *)at(WS_PART_I);
+    w.xdf = at(WS_XDF);
     return w;
 }
