@@ -212,9 +212,9 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
         const int nqf = p->fw.nblk * p->M, nqi = p->iv.nblk * p->M;
         info->kernels_fwd = (p->fw.nitems > 0) + (nqf > 0 ? 1 + dft_launches(p->dft_f) : 0) + 1 +
                             dft_launches(p->dft_dct) + 1 +
-                            (p->prec_asy == PREC_DF && (nqf > 0 || p->fw.E_df) ? 1 : 0);   // input to double-float
+                            (p->prec_asy == PREC_DF ? 2 : 0);   // input scaling to double-float
         info->kernels_inv = 1 + dft_launches(p->dft_front) + 1 + (nqi > 0 ? 1 + dft_launches(p->dft_i) : 0) +
-                            (p->iv.nitems > 0) + 2;
+                            (p->iv.nitems > 0) + 2 + (p->prec_asy == PREC_DF ? 2 : 0);
         if (!(p->opts.directions & CJT_FWD)) info->kernels_fwd = 0;
         if (!(p->opts.directions & CJT_INV)) info->kernels_inv = 0;
     }

@@ -264,10 +264,47 @@ __global__ void k_asy_pack_inv_s(int64_t Ng, int64_t L, int nq, const R *__restr
     buf[(int64_t)p * L + idx] = o;
 }
 
-// double-float packs (CJT_DFLOAT): the input as double-floats (xdf), tables as double-floats
-__global__ void k_to_dfs(int64_t n, const double *__restrict__ x, dfs *__restrict__ xdf) {
+// ---------------------------------------------------------------------------
+// CJT_DFLOAT input: x as double-floats scaled by 2^-e, e the binary exponent of max |x|,
+// so that any input within the FP64 range keeps the double-float relative precision.
+// k_absmax_exp writes one exponent per block (CJT_EXP_BLOCKS blocks); k_to_dfs_scaled
+// takes their maximum (order-independent, so deterministic), converts, and leaves e in
+// exps[CJT_EXP_BLOCKS] for the kernels that undo the scaling.
+// ---------------------------------------------------------------------------
+constexpr int EXP_NONE = -100000;   // all-zero input
+
+__global__ void __launch_bounds__(256) k_absmax_exp(int64_t n, const double *__restrict__ x, int *__restrict__ exps) {
+    __shared__ double red[8];
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(x[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        int e = EXP_NONE;
+        if (m > 0.0 && isfinite(m)) frexp(m, &e);
+        else if (!isfinite(m)) e = 0;   // inf / nan: no scaling, they propagate
+        exps[blockIdx.x] = e;
+    }
+}
+
+__global__ void k_to_dfs_scaled(int64_t n, const double *__restrict__ x, int *__restrict__ exps,
+                                dfs *__restrict__ xdf) {
+    __shared__ int se;
+    if (threadIdx.x < 32) {
+        int e = EXP_NONE;
+        for (int j = threadIdx.x; j < CJT_EXP_BLOCKS; j += 32) e = max(e, exps[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        if (threadIdx.x == 0) se = e == EXP_NONE ? 0 : e;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) exps[CJT_EXP_BLOCKS] = se;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) xdf[i] = df_from(x[i]);
+    if (i < n) xdf[i] = df_from(ldexp(x[i], -se));
 }
 
 __global__ void k_asy_pack_fwd_df(int64_t N, int64_t L, int nq, const dfs *__restrict__ Cs,
@@ -320,26 +357,26 @@ __global__ void __launch_bounds__(128) k_rec_fwd_stored_df(const RecItem *__rest
     if (w >= nitems) return;
     const RecItem it = items[w];
     const int len = it.b - it.a;
-    const dfs *e = E + it.eoff + lane;
+    const float2 *e = reinterpret_cast<const float2 *>(E + it.eoff) + lane;
     const dfs *cc = cdf + it.a;
+    // eight streaming loads in flight per lane, four independent accumulators
     dfs acc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[j] = df_make(0.f, 0.f);
     int k = 0;
-    for (; k + 4 <= len; k += 4) {
-        dfs v[4], cv[4];
+    for (; k + 8 <= len; k += 8) {
+        float2 v[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float2 t = __ldcs(reinterpret_cast<const float2 *>(e + (int64_t)(k + j) * 32));
-            v[j] = df_make(t.x, t.y);
-            cv[j] = cc[k + j];
-        }
+        for (int j = 0; j < 8; ++j) v[j] = __ldcs(e + (int64_t)(k + j) * 32);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j] = df_mac(acc[j], v[j], cv[j]);
+        for (int j = 0; j < 8; ++j) acc[j & 3] = df_mac(acc[j & 3], df_make(v[j].x, v[j].y), cc[k + j]);
     }
-    for (; k < len; ++k) acc[k & 3] = df_mac(acc[k & 3], e[(int64_t)k * 32], cc[k]);
+    for (; k < len; ++k) {
+        const float2 v = __ldcs(e + (int64_t)k * 32);
+        acc[k & 3] = df_mac(acc[k & 3], df_make(v.x, v.y), cc[k]);
+    }
     const dfs S = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
-    partials[it.out + lane] = lane < it.nrows ? df_to(S) : 0.0;
+    reinterpret_cast<dfs *>(partials)[it.out + lane] = lane < it.nrows ? S : df_make(0.f, 0.f);
 }
 
 __global__ void __launch_bounds__(128) k_rec_inv_stored_df(const RecItem *__restrict__ items, int64_t nitems,
@@ -352,15 +389,29 @@ __global__ void __launch_bounds__(128) k_rec_inv_stored_df(const RecItem *__rest
     const RecItem it = items[w];
     gs[wib][lane] = lane < it.nrows ? gdf[it.row0 + lane] : df_make(0.f, 0.f);
     __syncwarp();
-    const int len = it.b - it.a;
-    const dfs *e = E + it.eoff;
+    const int len = it.b - it.a, nr = it.nrows;
+    const float2 *e = reinterpret_cast<const float2 *>(E + it.eoff);
     double *out = partials + it.out;
     for (int k0 = 0; k0 < len; k0 += 32) {
         const int k = k0 + lane;
         if (k < len) {
-            dfs acc = df_make(0.f, 0.f);
-            for (int r = 0; r < it.nrows; ++r) acc = df_mac(acc, gs[wib][r], e[(int64_t)r * len + k]);
-            out[k] = df_to(acc);
+            // rows in groups of eight loads in flight, four independent accumulators
+            dfs acc[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] = df_make(0.f, 0.f);
+            int r = 0;
+            for (; r + 8 <= nr; r += 8) {
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = __ldcs(e + (int64_t)(r + j) * len + k);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[j & 3] = df_mac(acc[j & 3], gs[wib][r + j], df_make(v[j].x, v[j].y));
+            }
+            for (; r < nr; ++r) {
+                const float2 v = __ldcs(e + (int64_t)r * len + k);
+                acc[r & 3] = df_mac(acc[r & 3], gs[wib][r], df_make(v.x, v.y));
+            }
+            out[k] = df_to(df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3])));
         }
     }
 }
@@ -372,6 +423,66 @@ __device__ __forceinline__ double re_d(float2 v) { return (double)v.x; }
 __device__ __forceinline__ double im_d(float2 v) { return (double)v.y; }
 __device__ __forceinline__ double re_d(dfc v) { return df_to(dfc_re(v)); }
 __device__ __forceinline__ double im_d(dfc v) { return df_to(dfc_im(v)); }
+
+// ---------------------------------------------------------------------------
+// combine, forward, CJT_DFLOAT: the same sums in double-float arithmetic on the scaled
+// input (partials P: double-floats from the stored recurrence, or doubles from the
+// recurrence at execution, which ran on the unscaled input); one conversion to double
+// and the exact unscaling 2^e at the end
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ dfs scaled_partial(dfs v, int) { return v; }
+__device__ __forceinline__ dfs scaled_partial(double v, int e) { return df_from(ldexp(v, -e)); }
+
+template <typename P>
+__global__ void k_combine_fwd_df(int64_t N, int64_t L, int M, const int *__restrict__ rowk,
+                                 const double *__restrict__ scale, const dfs *__restrict__ u,
+                                 const dfs *__restrict__ v, const dfc *__restrict__ buf,
+                                 const int64_t *__restrict__ row_base, const int *__restrict__ row_nseg,
+                                 const P *__restrict__ partials, const int *__restrict__ exps,
+                                 double2 *__restrict__ ext) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > N) return;
+    const int e = exps[CJT_EXP_BLOCKS];
+    const int nseg = row_nseg[i];
+    const int64_t base = row_base[i];
+    // rows near x = +-1 have up to N / seg_len segments: eight loads in flight, four sums
+    dfs ya[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ya[j] = df_make(0.f, 0.f);
+    int s = 0;
+    for (; s + 8 <= nseg; s += 8) {
+        P pv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pv[j] = partials[base + (int64_t)(s + j) * 32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ya[j & 3] = df_add(ya[j & 3], scaled_partial(pv[j], e));
+    }
+    for (; s < nseg; ++s) ya[0] = df_add(ya[0], scaled_partial(partials[base + (int64_t)s * 32], e));
+    dfs y = df_add(df_add(ya[0], ya[1]), df_add(ya[2], ya[3]));
+    const int k = rowk[i];
+    if (k >= 0) {
+        const int64_t im = i == 0 ? 0 : L - i;
+        for (int m = 0; m < M; ++m) {
+            const int q = k * M + m, p = q >> 1;
+            const dfc Z = buf[(int64_t)p * L + i], W = buf[(int64_t)p * L + im];
+            dfs re, imv;
+            if ((q & 1) == 0) {
+                re = df_add(dfc_re(Z), dfc_re(W));
+                imv = df_sub(dfc_im(Z), dfc_im(W));
+            } else {
+                re = df_add(dfc_im(Z), dfc_im(W));
+                imv = df_sub(dfc_re(W), dfc_re(Z));
+            }
+            // u, v carry 1/2 and the item's unscaling (plan time)
+            y = df_add(y, df_mms(u[m * (N + 1) + i], re, v[m * (N + 1) + i], imv));
+        }
+    }
+    // the even extension for the FP64 DCT-I (its errors would reach the inverse of a round
+    // trip through 1/A_n), unscaled
+    const double yv = ldexp(df_to(y), e);
+    ext[i] = make_double2(yv, 0.0);
+    if (i >= 1 && i < N) ext[2 * N - i] = make_double2(yv, 0.0);
+}
 
 // ---------------------------------------------------------------------------
 // combine, forward: REC segment partials + asymptotic terms; writes the even
@@ -387,8 +498,18 @@ __global__ void k_combine_fwd(int64_t N, int64_t L, int M, const int *__restrict
     if (i > N) return;
     const int nseg = row_nseg[i];
     const int64_t base = row_base[i];
-    double y = 0.0;
-    for (int s = 0; s < nseg; ++s) y += partials[base + (int64_t)s * 32];
+    // rows near x = +-1 have up to N / seg_len segments: eight loads in flight, four sums
+    double ya[4] = {0.0, 0.0, 0.0, 0.0};
+    int s = 0;
+    for (; s + 8 <= nseg; s += 8) {
+        double pv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pv[j] = partials[base + (int64_t)(s + j) * 32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ya[j & 3] += pv[j];
+    }
+    for (; s < nseg; ++s) ya[0] += partials[base + (int64_t)s * 32];
+    double y = (ya[0] + ya[1]) + (ya[2] + ya[3]);
     const int k = rowk[i];
     if (k >= 0) {
         const int64_t im = i == 0 ? 0 : L - i;
@@ -430,18 +551,18 @@ __global__ void k_inv_front_pack(int64_t N, int64_t L, const double *__restrict_
     buf[k] = make_double2(k <= N ? c[k] : 0.0, 0.0);
 }
 
-__global__ void k_inv_g(int64_t Ng, const double2 *__restrict__ F, const double *__restrict__ w, double *__restrict__ g,
-                        dfs *__restrict__ gdf) {
+__global__ void k_inv_g(int64_t Ng, const double2 *__restrict__ F, const double *__restrict__ w, double *__restrict__ g) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i > Ng) return;
-    const double v = w[i] * F[i].x;
-    g[i] = v;
-    if (gdf) gdf[i] = df_from(v);
+    g[i] = w[i] * F[i].x;
 }
 
-// Sum of the recurrence partials of every item covering degree n (fixed order:
-// warp w takes items w, w+32, ...; four interleaved accumulators; the 32 warp
-// sums are added in warp order).  One block per 32 consecutive degrees.
+// Sum of the recurrence partials of every item covering degree n, in a fixed order:
+// warp w takes the items in runs of 32 (runs w, w + RED_WARPS, ...), loads the run's
+// item descriptors with one coalesced load and broadcasts them by shuffles, so that the
+// partial loads of a run are independent and many are in flight; four interleaved
+// accumulators; the warp sums are added in warp order.  One block per 32 consecutive
+// degrees.
 constexpr int RED_WARPS = 32;
 __global__ void __launch_bounds__(32 * RED_WARPS) k_inv_reduce(int64_t N, int seg_len,
                                                                const int64_t *__restrict__ seg_ptr,
@@ -455,16 +576,27 @@ __global__ void __launch_bounds__(32 * RED_WARPS) k_inv_reduce(int64_t N, int se
     const int64_t s = n0 / seg_len, off = n - s * seg_len;
     const int64_t q0 = seg_ptr[s], q1 = seg_ptr[s + 1];
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    int64_t q = q0 + w;
-    for (; q + 3 * RED_WARPS < q1; q += 4 * RED_WARPS) {
+    for (int64_t qb = q0 + 32 * (int64_t)w; qb < q1; qb += 32 * RED_WARPS) {
+        const int64_t qq = qb + lane;
+        const bool ok = qq < q1;
+        const int64_t so = ok ? seg_out[qq] : 0;
+        const int sb = ok ? seg_b[qq] : 0;
+        const int cnt = (int)min((int64_t)32, q1 - qb);
+        int j = 0;
+        for (; j + 8 <= cnt; j += 8) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t qq = q + j * RED_WARPS;
-            if (n < seg_b[qq]) acc[j] += partials[seg_out[qq] + off];
+            for (int t = 0; t < 8; ++t) {
+                const int64_t o = __shfl_sync(0xffffffffu, so, j + t);
+                const int b = __shfl_sync(0xffffffffu, sb, j + t);
+                if (n < b) acc[t & 3] += partials[o + off];
+            }
+        }
+        for (; j < cnt; ++j) {
+            const int64_t o = __shfl_sync(0xffffffffu, so, j);
+            const int b = __shfl_sync(0xffffffffu, sb, j);
+            if (n < b) acc[0] += partials[o + off];
         }
     }
-    for (int j = 0; q < q1; q += RED_WARPS, ++j)
-        if (n < seg_b[q]) acc[j & 3] += partials[seg_out[q] + off];
     red[w][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     __syncthreads();
     if (w == 0 && n <= N) {
@@ -474,14 +606,18 @@ __global__ void __launch_bounds__(32 * RED_WARPS) k_inv_reduce(int64_t N, int se
     }
 }
 
+// exps (CJT_DFLOAT only): the transposed blocks ran on g scaled by 2^-e, and so did the
+// recurrence when rec_scaled; both are unscaled here.
 template <typename V>
 __global__ void k_combine_inv(int64_t N, int64_t L, int M, int nblk, const int *__restrict__ box3,
                               const double *__restrict__ scale, const double *__restrict__ Cnm,
                               const V *__restrict__ buf, const double *__restrict__ yrec,
-                              const double *__restrict__ s_n, double *__restrict__ out) {
+                              const double *__restrict__ s_n, const int *__restrict__ exps, int rec_scaled,
+                              double *__restrict__ out) {
     const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (n > N) return;
-    double y = yrec[n];
+    const double ua = exps ? ldexp(1.0, exps[CJT_EXP_BLOCKS]) : 1.0;
+    double y = rec_scaled ? ua * yrec[n] : yrec[n];
     // degree n belongs to block k when j_k <= n < top_k (top_0 = N+1, top_k = j_{k-1})
     int k = -1;
     for (int kk = 0; kk < nblk; ++kk) {
@@ -493,7 +629,7 @@ __global__ void k_combine_inv(int64_t N, int64_t L, int M, int nblk, const int *
             const int q = k * M + m, p = q >> 1;
             const V Z = buf[(int64_t)p * L + n];
             const double R = (q & 1) ? im_d(Z) : re_d(Z);
-            y = fma(Cnm[m * (N + 1) + n] * scale[2 * q + 1], R, y);
+            y = fma(Cnm[m * (N + 1) + n] * (scale[2 * q + 1] * ua), R, y);
         }
     }
     out[n] = s_n[n] * y;
@@ -518,14 +654,16 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     GridWork &gw = p->fw;
     const bool fp32 = p->prec_asy == PREC_F32, dfm = p->prec_asy == PREC_DF;
-    const void *tw_asy = fp32 ? p->d_tw32 : dfm ? p->d_twdf : p->d_tw64;
     const int M = p->M;
     int rc;
     const int nq = gw.nblk * M;
     const int64_t L = p->Lf;
+    // double-float execution: the input scaled to max |c| < 1 and converted once
+    const bool dfx = dfm;
     dfs *cdf = (dfs *)ws.xdf;
-    if (dfm && (nq > 0 || gw.E_df)) {
-        k_to_dfs<<<blocks_for(N + 1, 256), 256, 0, st>>>(N + 1, in, cdf);
+    if (dfx) {
+        k_absmax_exp<<<CJT_EXP_BLOCKS, 256, 0, st>>>(N + 1, in, ws.exps);
+        k_to_dfs_scaled<<<blocks_for(N + 1, 256), 256, 0, st>>>(N + 1, in, ws.exps, cdf);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     // the asymptotic transforms run on a side stream, concurrently with the recurrence
@@ -549,7 +687,7 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     if (nq > 0) {
         StageTimer tm(p, sa, CJT_STAGE_FWD_FFT);
-        rc = cjt_dft_exec(p->dft_f, ws.fft_f, ws.work, ws.scratch, p->npair_f, tw_asy, p->Ltab, sa);
+        rc = cjt_dft_exec(p->dft_f, ws.fft_f, ws.work, ws.scratch, p->npair_f, p->twiddles(p->prec_asy), sa);
         if (rc) return rc;
     }
     // REC
@@ -573,10 +711,14 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     double2 *ext = (double2 *)ws.dct;
     {
     StageTimer tm(p, st, CJT_STAGE_FWD_COMBINE);
-    if (dfm)
-        k_combine_fwd<dfc><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const dfc *)ws.fft_f, gw.d_row_base, gw.d_row_nseg,
-            ws.part_f, ext);
+    if (dfx && gw.E_df)
+        k_combine_fwd_df<dfs><<<blocks_for(N + 1, 256), 256, 0, st>>>(
+            N, L, M, gw.d_rowk, gw.d_scale, (const dfs *)gw.d_u, (const dfs *)gw.d_v, (const dfc *)ws.fft_f,
+            gw.d_row_base, gw.d_row_nseg, (const dfs *)ws.part_f, ws.exps, ext);
+    else if (dfx)
+        k_combine_fwd_df<double><<<blocks_for(N + 1, 256), 256, 0, st>>>(
+            N, L, M, gw.d_rowk, gw.d_scale, (const dfs *)gw.d_u, (const dfs *)gw.d_v, (const dfc *)ws.fft_f,
+            gw.d_row_base, gw.d_row_nseg, ws.part_f, ws.exps, ext);
     else if (fp32)
         k_combine_fwd<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
             N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const float2 *)ws.fft_f, gw.d_row_base, gw.d_row_nseg,
@@ -588,7 +730,7 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     CJT_CUDA_TRY(cudaGetLastError());
     }
     StageTimer tm(p, st, CJT_STAGE_FWD_DCT);
-    rc = cjt_dft_exec(p->dft_dct, ws.dct, ws.work, ws.scratch, 1, p->d_tw64, p->Ltab, st);
+    rc = cjt_dft_exec(p->dft_dct, ws.dct, ws.work, ws.scratch, 1, p->twiddles(PREC_F64), st);
     if (rc) return rc;
     k_dct_finish<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, (const double2 *)ws.dct, out);
     CJT_CUDA_TRY(cudaGetLastError());
@@ -604,8 +746,7 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     GridWork &gw = p->iv;
     const bool fp32 = p->prec_asy == PREC_F32, dfm = p->prec_asy == PREC_DF;
-    const void *tw_asy = fp32 ? p->d_tw32 : dfm ? p->d_twdf : p->d_tw64;
-    dfs *gdf = dfm ? (dfs *)ws.xdf : nullptr;
+    dfs *gdf = (dfs *)ws.xdf;
     const int M = p->M;
     const int64_t Ng = 2 * N, L = p->Li;
     // front end: p_N on the 2N grid, times the Clenshaw--Curtis weights
@@ -614,13 +755,21 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     StageTimer tm(p, st, CJT_STAGE_INV_FRONT);
     k_inv_front_pack<<<blocks_for(L, 256), 256, 0, st>>>(N, L, in, (double2 *)ws.dct);
     CJT_CUDA_TRY(cudaGetLastError());
-    rc = cjt_dft_exec(p->dft_front, ws.dct, ws.work, ws.scratch, 1, p->d_tw64, p->Ltab, st);
+    rc = cjt_dft_exec(p->dft_front, ws.dct, ws.work, ws.scratch, 1, p->twiddles(PREC_F64), st);
     if (rc) return rc;
-    k_inv_g<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)ws.dct, p->d_w, ws.g, gdf);
+    k_inv_g<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)ws.dct, p->d_w, ws.g);
     CJT_CUDA_TRY(cudaGetLastError());
     }
-    // transposed asymptotic blocks, on a side stream concurrently with the recurrence
     const int nq = gw.nblk * M;
+    // double-float execution: g scaled to max |g| < 1 and converted once.  The front end
+    // stays in FP64: its errors reach c_jac_n through 1/A_n, which grows with n.
+    const bool dfx = dfm;
+    if (dfx) {
+        k_absmax_exp<<<CJT_EXP_BLOCKS, 256, 0, st>>>(Ng + 1, ws.g, ws.exps);
+        k_to_dfs_scaled<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng + 1, ws.g, ws.exps, gdf);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
+    // transposed asymptotic blocks, on a side stream concurrently with the recurrence
     const bool ovl = nq > 0 && p->side;
     cudaStream_t sa = ovl ? p->side : st;
     if (ovl) {
@@ -643,7 +792,7 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     if (nq > 0) {
         StageTimer tm(p, sa, CJT_STAGE_INV_FFT);
-        rc = cjt_dft_exec(p->dft_i, ws.fft_i, ws.work, ws.scratch, p->npair_i, tw_asy, p->Ltab, sa);
+        rc = cjt_dft_exec(p->dft_i, ws.fft_i, ws.work, ws.scratch, p->npair_i, p->twiddles(p->prec_asy), sa);
         if (rc) return rc;
     }
     // transposed recurrence and the fixed-order sums over the items of each degree
@@ -670,15 +819,18 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
     }
     StageTimer tm(p, st, CJT_STAGE_INV_COMBINE);
-    if (dfm)
-        k_combine_inv<dfc><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const dfc *)ws.fft_i, ws.y, p->d_s, out);
+    if (dfx)
+        k_combine_inv<dfc><<<blocks_for(N + 1, 256), 256, 0, st>>>(N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm,
+                                                                  (const dfc *)ws.fft_i, ws.y, p->d_s, ws.exps,
+                                                                  gw.E_df ? 1 : 0, out);
     else if (fp32)
-        k_combine_inv<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const float2 *)ws.fft_i, ws.y, p->d_s, out);
+        k_combine_inv<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(N, L, M, gw.nblk, gw.d_box, gw.d_scale,
+                                                                     p->d_Cnm, (const float2 *)ws.fft_i, ws.y, p->d_s,
+                                                                     nullptr, 0, out);
     else
-        k_combine_inv<double2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.nblk, gw.d_box, gw.d_scale, p->d_Cnm, (const double2 *)ws.fft_i, ws.y, p->d_s, out);
+        k_combine_inv<double2><<<blocks_for(N + 1, 256), 256, 0, st>>>(N, L, M, gw.nblk, gw.d_box, gw.d_scale,
+                                                                      p->d_Cnm, (const double2 *)ws.fft_i, ws.y,
+                                                                      p->d_s, nullptr, 0, out);
     CJT_CUDA_TRY(cudaGetLastError());
     return CJT_OK;
 }

@@ -10,14 +10,16 @@
 //     pass B: L1 rows of length L2 (contiguous), store X[k1 + L1 k2]
 // Sub-transforms are decimation-in-frequency radix-4 stages (one radix-2 stage
 // last when log2 is odd) on a padded [column][element] shared-memory tile,
-// with twiddles read from a plan-owned table omega_{Ltab}^j computed by
-// sincospi (exact argument reduction).
+// with twiddles read from plan-owned tables computed by sincospi (exact argument
+// reduction): omega_{Ltab}^j, and per-stage copies laid out so that a warp's loads
+// are contiguous (Twiddles::stw).
 //
 // Lengths that are not powers of two (N not a power of two) go through
 // Bluestein's chirp-z form on top of the power-of-two transform.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "cjt_df.cuh"
 #include "cjt_internal.cuh"
@@ -61,19 +63,25 @@ template <> __device__ __forceinline__ dfc cscale(dfc a, double s) { return dfc_
 constexpr int FFT_THREADS = 256;
 constexpr int SMEM_PAD = 1;
 
-// frequency k -> its position after the DIF stages (mixed-radix digit reversal)
+// frequency k -> its position after the DIF stages: the base-4 digits of k's low
+// 2*floor(logLs/2) bits in reverse order (bit reversal, then the two bits of each digit
+// swapped back), and for odd logLs the top (radix-2) bit of k at weight 1
 __device__ __forceinline__ int dif_revinv(int k, int logLs) {
-    int p = 0, lb = logLs;
-    while (lb >= 2) { int q = k & 3; k >>= 2; lb -= 2; p += q << lb; }
-    if (lb == 1) p += k;  // remaining digit (0/1) at weight 1
-    return p;
+    const int d2 = logLs & ~1;
+    if (d2 == 0) return k;
+    unsigned r = __brev((unsigned)k & ((1u << d2) - 1u)) >> (32 - d2);
+    r = ((r & 0x55555555u) << 1) | ((r >> 1) & 0x55555555u);
+    return (logLs & 1) ? (int)((r << 1) | ((unsigned)k >> d2)) : (int)r;
 }
 
+constexpr int FFT_U = 4;   // global loads (and twiddle loads) in flight per thread in the load/store phases
+
 template <typename R>
-__global__ void __launch_bounds__(FFT_THREADS)
+__global__ void __launch_bounds__(FFT_THREADS, 4)
 k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__restrict__ out, int logLs,
           int64_t ncols, int tile, int64_t in_es, int64_t in_cs, int64_t in_ts, int64_t out_ks, int64_t out_cs,
-          int64_t out_ts, const typename cplx<R>::t *__restrict__ tw, int logLtab, int post_log) {
+          int64_t out_ts, const typename cplx<R>::t *__restrict__ tw, int logLtab, int post_log,
+          const typename cplx<R>::t *__restrict__ stw) {
     using V = typename cplx<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *s = reinterpret_cast<V *>(smem_raw);
@@ -85,18 +93,36 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
     const V *src = in + t * in_ts + c0 * in_cs;
     V *dst = out + t * out_ts + c0 * out_cs;
 
-    // load (natural order); lanes run along the contiguous dimension
+    // load (natural order); lanes run along the contiguous dimension; FFT_U loads in flight
     const int total = ncl * Ls;
-    if (in_es == 1) {
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            int e = idx & (Ls - 1), c = idx >> logLs;
-            s[c * ld + e] = src[c * in_cs + e];
+    const bool pow2c = (ncl & (ncl - 1)) == 0;
+    const int lgc = __ffs(ncl) - 1;
+    for (int i0 = threadIdx.x; i0 < total; i0 += FFT_U * blockDim.x) {
+        V v[FFT_U];
+        int at[FFT_U];
+#pragma unroll
+        for (int u = 0; u < FFT_U; ++u) {
+            const int idx = i0 + u * blockDim.x;
+            at[u] = -1;
+            if (idx < total) {
+                int c, e;
+                int64_t g;
+                if (in_es == 1) {
+                    e = idx & (Ls - 1);
+                    c = idx >> logLs;
+                    g = c * in_cs + e;
+                } else {
+                    c = pow2c ? (idx & (ncl - 1)) : idx % ncl;
+                    e = pow2c ? (idx >> lgc) : idx / ncl;
+                    g = c * in_cs + (int64_t)e * in_es;
+                }
+                at[u] = c * ld + e;
+                v[u] = src[g];
+            }
         }
-    } else {
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            int c = idx % ncl, e = idx / ncl;
-            s[c * ld + e] = src[c * in_cs + (int64_t)e * in_es];
-        }
+#pragma unroll
+        for (int u = 0; u < FFT_U; ++u)
+            if (at[u] >= 0) s[at[u]] = v[u];
     }
     __syncthreads();
 
@@ -114,9 +140,16 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
             V t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = cmul_mi(csub(x1, x3));
             V y0 = cadd(t0, t2), y2 = csub(t0, t2), y1 = cadd(t1, t3), y3 = csub(t1, t3);
             if (n0 != 0) {
-                y1 = cmul(y1, tw[(int64_t)n0 << twstep_log]);
-                y2 = cmul(y2, tw[(int64_t)(2 * n0) << twstep_log]);
-                y3 = cmul(y3, tw[(int64_t)(3 * n0) << twstep_log]);
+                if (stw) {
+                    const V *w = stw + stw_base(lb) + n0;
+                    y1 = cmul(y1, w[0]);
+                    y2 = cmul(y2, w[h]);
+                    y3 = cmul(y3, w[2 * h]);
+                } else {
+                    y1 = cmul(y1, tw[(int64_t)n0 << twstep_log]);
+                    y2 = cmul(y2, tw[(int64_t)(2 * n0) << twstep_log]);
+                    y3 = cmul(y3, tw[(int64_t)(3 * n0) << twstep_log]);
+                }
             }
             b[0] = y0; b[h] = y1; b[2 * h] = y2; b[3 * h] = y3;
         }
@@ -135,26 +168,37 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
         __syncthreads();
     }
 
-    // store in natural frequency order, optional four-step twiddle omega_{2^post_log}^{c k}
-    if (out_ks == 1) {
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            int k = idx & (Ls - 1), c = idx >> logLs;
-            V v = s[c * ld + dif_revinv(k, logLs)];
-            if (post_log >= 0) {
-                int64_t ex = ((c0 + c) * (int64_t)k) & ((1LL << post_log) - 1);
-                v = cmul(v, tw[ex << (logLtab - post_log)]);
+    // store in natural frequency order, optional four-step twiddle omega_{2^post_log}^{c k};
+    // FFT_U twiddle loads in flight
+    for (int i0 = threadIdx.x; i0 < total; i0 += FFT_U * blockDim.x) {
+        V v[FFT_U], w[FFT_U];
+        int64_t at[FFT_U];
+#pragma unroll
+        for (int u = 0; u < FFT_U; ++u) {
+            const int idx = i0 + u * blockDim.x;
+            at[u] = -1;
+            if (idx < total) {
+                int c, k;
+                if (out_ks == 1) {
+                    k = idx & (Ls - 1);
+                    c = idx >> logLs;
+                    at[u] = c * out_cs + k;
+                } else {
+                    c = pow2c ? (idx & (ncl - 1)) : idx % ncl;
+                    k = pow2c ? (idx >> lgc) : idx / ncl;
+                    at[u] = c * out_cs + (int64_t)k * out_ks;
+                }
+                v[u] = s[c * ld + dif_revinv(k, logLs)];
+                if (post_log >= 0) {
+                    const int64_t ex = ((c0 + c) * (int64_t)k) & ((1LL << post_log) - 1);
+                    w[u] = tw[ex << (logLtab - post_log)];
+                }
             }
-            dst[c * out_cs + k] = v;
         }
-    } else {
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            int c = idx % ncl, k = idx / ncl;
-            V v = s[c * ld + dif_revinv(k, logLs)];
-            if (post_log >= 0) {
-                int64_t ex = ((c0 + c) * (int64_t)k) & ((1LL << post_log) - 1);
-                v = cmul(v, tw[ex << (logLtab - post_log)]);
-            }
-            dst[c * out_cs + (int64_t)k * out_ks] = v;
+#pragma unroll
+        for (int u = 0; u < FFT_U; ++u) {
+            if (at[u] < 0) continue;
+            dst[at[u]] = post_log >= 0 ? cmul(v[u], w[u]) : v[u];
         }
     }
 }
@@ -168,7 +212,7 @@ int ilog2(int64_t v) {
 template <typename R>
 int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batch, int64_t in_es, int64_t in_cs,
                int64_t in_ts, int64_t out_ks, int64_t out_cs, int64_t out_ts, const void *tw, int logLtab,
-               int post_log, cudaStream_t st) {
+               int post_log, const void *stw, cudaStream_t st) {
     using V = typename cplx<R>::t;
     const int Ls = 1 << logLs;
     // Columns per CTA: at most ~64 KB of shared memory, and few enough that the
@@ -180,7 +224,8 @@ int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batc
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 152;
     }
-    const int64_t budget_elems = (int64_t)(65536 / sizeof(V));
+    // double-float: half the tile, so that more CTAs (and warps) share an SM
+    const int64_t budget_elems = (int64_t)((std::is_same<R, dfloat>::value ? 32768 : 65536) / sizeof(V));
     int64_t tile64 = std::min<int64_t>(std::min<int64_t>(ncols, 64), std::max<int64_t>(1, budget_elems / Ls));
     tile64 = std::min<int64_t>(tile64, std::max<int64_t>(1, ncols * batch / (2 * sms)));
     const int tile = (int)std::max<int64_t>(1, tile64);
@@ -190,28 +235,31 @@ int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batc
     if (prc) return prc;
     dim3 grid((unsigned)((ncols + tile - 1) / tile), (unsigned)batch);
     k_fft_sub<R><<<grid, threads, smem, st>>>((const V *)in, (V *)out, logLs, ncols, tile, in_es, in_cs, in_ts,
-                                                    out_ks, out_cs, out_ts, (const V *)tw, logLtab, post_log);
+                                                    out_ks, out_cs, out_ts, (const V *)tw, logLtab, post_log,
+                                                    (const V *)stw);
     CJT_CUDA_TRY(cudaGetLastError());
     return CJT_OK;
 }
 
 template <typename R>
-int fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab, cudaStream_t st) {
+int fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &T, cudaStream_t st) {
+    const void *tw = T.tw, *stw = T.stw;
+    const int64_t Ltab = T.Ltab;
     if (L <= 1 || batch <= 0) return CJT_OK;
     const int logL = ilog2(L), logLtab = ilog2(Ltab);
     if ((1LL << logL) != L || L > Ltab) return CJT_EINVAL;
     if (logL <= 12) {
         // direct: each "column" is one whole transform
-        return launch_sub<R>(data, data, logL, batch, 1, 1, L, 0, 1, L, 0, tw, logLtab, -1, st);
+        return launch_sub<R>(data, data, logL, batch, 1, 1, L, 0, 1, L, 0, tw, logLtab, -1, stw, st);
     }
     if (logL > 24 || scratch == nullptr) return CJT_EUNSUPPORTED;
     const int log1 = (logL + 1) / 2, log2 = logL - log1;
     const int64_t L1 = 1LL << log1, L2 = 1LL << log2;
     // pass A: columns n2 (L2 of them), elements n1 at stride L2
-    int rc = launch_sub<R>(data, scratch, log1, L2, batch, L2, 1, L, L2, 1, L, tw, logLtab, logL, st);
+    int rc = launch_sub<R>(data, scratch, log1, L2, batch, L2, 1, L, L2, 1, L, tw, logLtab, logL, stw, st);
     if (rc) return rc;
     // pass B: rows k1 (L1 of them), elements n2 contiguous, output X[k1 + L1 k2]
-    return launch_sub<R>(scratch, data, log2, L1, batch, 1, L2, L, L1, 1, L, tw, logLtab, -1, st);
+    return launch_sub<R>(scratch, data, log2, L1, batch, 1, L2, L, L1, 1, L, tw, logLtab, -1, stw, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -280,19 +328,18 @@ __global__ void k_to_dfc(int64_t n, const double2 *__restrict__ a, dfc *__restri
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <typename R>
-int dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const void *tw, int64_t Ltab,
-             cudaStream_t st) {
+int dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const Twiddles &tw, cudaStream_t st) {
     using V = typename cplx<R>::t;
     if (batch <= 0 || d.L <= 1) return CJT_OK;
-    if (!d.P) return fft_pow2<R>(data, scratch, d.L, batch, tw, Ltab, st);
+    if (!d.P) return fft_pow2<R>(data, scratch, d.L, batch, tw, st);
     dim3 g(nblk(d.P, 256), (unsigned)batch);
     k_blue_pre<V><<<g, 256, 0, st>>>(d.L, d.S, d.P, (const V *)data, (const V *)d.chirp, (V *)work);
     CJT_CUDA_TRY(cudaGetLastError());
-    int rc = fft_pow2<R>(work, scratch, d.P, batch, tw, Ltab, st);
+    int rc = fft_pow2<R>(work, scratch, d.P, batch, tw, st);
     if (rc) return rc;
     k_blue_mid<V><<<g, 256, 0, st>>>(d.P, (const V *)d.bhat, (V *)work);
     CJT_CUDA_TRY(cudaGetLastError());
-    rc = fft_pow2<R>(work, scratch, d.P, batch, tw, Ltab, st);
+    rc = fft_pow2<R>(work, scratch, d.P, batch, tw, st);
     if (rc) return rc;
     dim3 g2(nblk(d.K, 256), (unsigned)batch);
     k_blue_post<V><<<g2, 256, 0, st>>>(d.L, d.K, d.P, (const V *)work, (const V *)d.chirp, (V *)data,
@@ -328,7 +375,10 @@ int cjt_dft_setup(Dft &d, const void *tw64, int64_t Ltab, cudaStream_t st) {
     k_blue_chirp<<<nblk(nw, 256), 256, 0, st>>>(d.L, nw, w64, nullptr);
     k_blue_b<<<nblk(d.P, 256), 256, 0, st>>>(d.S, d.K, d.P, w64, b64);
     CJT_CUDA_TRY(cudaGetLastError());
-    int rc = fft_pow2<double>(b64, scr, d.P, 1, tw64, Ltab, st);
+    Twiddles t64;
+    t64.tw = tw64;
+    t64.Ltab = Ltab;
+    int rc = fft_pow2<double>(b64, scr, d.P, 1, t64, st);
     if (rc) return rc;
     if (d.prec == PREC_F32) {
         k_to_f32<<<nblk(nw, 256), 256, 0, st>>>(nw, w64, (float2 *)d.chirp);
@@ -347,18 +397,17 @@ int cjt_dft_setup(Dft &d, const void *tw64, int64_t Ltab, cudaStream_t st) {
     return CJT_OK;
 }
 
-int cjt_dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const void *tw, int64_t Ltab,
+int cjt_dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const Twiddles &tw,
                  cudaStream_t st) {
-    if (d.prec == PREC_F32) return dft_exec<float>(d, data, work, scratch, batch, tw, Ltab, st);
-    if (d.prec == PREC_DF) return dft_exec<dfloat>(d, data, work, scratch, batch, tw, Ltab, st);
-    return dft_exec<double>(d, data, work, scratch, batch, tw, Ltab, st);
+    if (d.prec == PREC_F32) return dft_exec<float>(d, data, work, scratch, batch, tw, st);
+    if (d.prec == PREC_DF) return dft_exec<dfloat>(d, data, work, scratch, batch, tw, st);
+    return dft_exec<double>(d, data, work, scratch, batch, tw, st);
 }
 
-int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab, int prec,
-                 cudaStream_t st) {
-    if (prec == PREC_F32) return fft_pow2<float>(data, scratch, L, batch, tw, Ltab, st);
-    if (prec == PREC_DF) return fft_pow2<dfloat>(data, scratch, L, batch, tw, Ltab, st);
-    return fft_pow2<double>(data, scratch, L, batch, tw, Ltab, st);
+int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &tw, int prec, cudaStream_t st) {
+    if (prec == PREC_F32) return fft_pow2<float>(data, scratch, L, batch, tw, st);
+    if (prec == PREC_DF) return fft_pow2<dfloat>(data, scratch, L, batch, tw, st);
+    return fft_pow2<double>(data, scratch, L, batch, tw, st);
 }
 
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch) { return L > 4096 ? L * batch : 0; }

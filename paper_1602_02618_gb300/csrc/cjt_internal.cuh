@@ -89,6 +89,7 @@ struct GridWork {
     // doubles, or double-floats (dfs, same 8 bytes) when E_df
     double *d_E = nullptr;
     bool E_df = false;
+    bool uv_df = false;           // forward grid: u, v held as double-floats (CJT_DFLOAT)
     int64_t nE = 0;
     // diagonals u_m, v_m on this grid
     double *d_u = nullptr, *d_v = nullptr;
@@ -108,6 +109,17 @@ struct GridWork {
 // chirp-z form: X_k = w_k sum_n (x_n w_n) conj(w_{k-n}), w_m = exp(-i pi m^2 / L), as a cyclic
 // convolution of power-of-two length P >= S + K - 1.
 enum { PREC_F64 = 0, PREC_F32 = 1, PREC_DF = 2 };   // element type of a transform
+
+// Twiddle tables of one precision: tw[k] = omega_{Ltab}^k (k < Ltab) and, when stw is set,
+// the stage tables of the shared-memory radix-4 stages: for block length Lb = 2^lb
+// (lb = 2..min(12, log2 Ltab)), stw[stw_base(lb) + r*(Lb/4) + n0] = omega_{Lb}^{(r+1) n0},
+// r = 0..2, contiguous in n0 so that a warp's twiddle loads are coalesced.
+struct Twiddles {
+    const void *tw = nullptr;
+    int64_t Ltab = 0;
+    const void *stw = nullptr;
+};
+__host__ __device__ inline int64_t stw_base(int lb) { return 3 * ((1LL << (lb - 2)) - 1); }
 inline int64_t prec_cbytes(int prec) { return prec == PREC_F32 ? 8 : 16; }   // bytes of one complex
 struct Dft {
     int64_t L = 0, S = 0, K = 0, P = 0;
@@ -123,9 +135,13 @@ struct Dft {
 struct Workspace {
     void *fft_f = nullptr, *fft_i = nullptr, *scratch = nullptr, *work = nullptr;
     double *dct = nullptr, *y = nullptr, *g = nullptr, *part_f = nullptr, *part_i = nullptr;
-    void *xdf = nullptr;   // CJT_DFLOAT: the input c (forward) or g (inverse) as double-floats
+    void *xdf = nullptr;   // CJT_DFLOAT: the input c (forward) or g (inverse) as double-floats,
+                           // scaled by an exact power of two 2^-e so that max |x| < 1
+    int *exps = nullptr;   // CJT_DFLOAT: per-block exponents of max |x|, then e at [CJT_EXP_BLOCKS]
 };
-enum { WS_FFT_F, WS_FFT_I, WS_SCRATCH, WS_WORK, WS_DCT, WS_Y, WS_G, WS_PART_F, WS_PART_I, WS_XDF, WS_COUNT };
+enum { WS_FFT_F, WS_FFT_I, WS_SCRATCH, WS_WORK, WS_DCT, WS_Y, WS_G, WS_PART_F, WS_PART_I, WS_XDF, WS_EXPS,
+       WS_COUNT };
+constexpr int CJT_EXP_BLOCKS = 128;
 
 struct cjt_plan_s {
     int64_t N = 0;
@@ -150,6 +166,14 @@ struct cjt_plan_s {
     void *d_tw64 = nullptr;       // double2[Ltab]
     void *d_tw32 = nullptr;       // float2[Ltab]
     void *d_twdf = nullptr;       // dfc[Ltab]
+    void *d_stw64 = nullptr, *d_stw32 = nullptr, *d_stwdf = nullptr;   // stage tables (Twiddles)
+    Twiddles twiddles(int prec) const {
+        Twiddles t;
+        t.Ltab = Ltab;
+        t.tw = prec == PREC_F32 ? d_tw32 : prec == PREC_DF ? d_twdf : d_tw64;
+        t.stw = prec == PREC_F32 ? d_stw32 : prec == PREC_DF ? d_stwdf : d_stw64;
+        return t;
+    }
     int prec_asy = PREC_F64;      // element type of the asymptotic transforms
     int npair_f = 0, npair_i = 0; // complex transforms of ASY item pairs
     Dft dft_f, dft_dct, dft_front, dft_i, dft_cc;
@@ -283,15 +307,14 @@ __host__ __device__ inline double cjt_hahn_h(int l, double a) {
 // ---------------------------------------------------------------------------
 // launchers implemented in the .cu files
 // ---------------------------------------------------------------------------
-int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const void *tw, int64_t Ltab,
-                 int prec, cudaStream_t st);
+int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &tw, int prec, cudaStream_t st);
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch);
 int cjt_fft_prime();
 // Bluestein length (0 when L is a power of two)
 int64_t cjt_dft_padded(int64_t L, int64_t S, int64_t K);
 // chirp and bhat for a Bluestein transform (in d.prec); tw64 must cover P
 int cjt_dft_setup(Dft &d, const void *tw64, int64_t Ltab, cudaStream_t st);
-int cjt_dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const void *tw, int64_t Ltab,
+int cjt_dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const Twiddles &tw,
                  cudaStream_t st);
 int64_t cjt_dft_work_bytes(const Dft &d, int64_t batch);
 int64_t cjt_dft_scratch_bytes(const Dft &d, int64_t batch);

@@ -98,7 +98,10 @@ extern "C" int cjt_cheb_coeffs_noalloc(int64_t N, const double *values_dev, doub
     k_na_twiddles<<<blocks_for(L, 256), 256, 0, st>>>(L, tw);
     k_na_pack<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, values_dev, buf);
     CJT_CUDA_TRY(cudaGetLastError());
-    rc = cjt_fft_pow2(buf, scratch, L, 1, tw, L, PREC_F64, st);
+    Twiddles T;
+    T.tw = tw;
+    T.Ltab = L;
+    rc = cjt_fft_pow2(buf, scratch, L, 1, T, PREC_F64, st);
     if (rc) return rc;
     k_na_finish<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, buf, c_cheb_dev);
     CJT_CUDA_TRY(cudaGetLastError());

@@ -411,8 +411,40 @@ __global__ void k_twiddles(int64_t L, double2 *tw64, float2 *tw32, dfc *twdf) {
     if (twdf) twdf[k] = dfc_make(df_from(c), df_from(s));
 }
 
-// stored recurrence values, doubles -> double-floats in place (same 8 bytes per entry)
-__global__ void k_E_to_df(int64_t n, double *E) {
+// CJT_DFLOAT, forward grid: u_m(theta_i) and v_m(theta_i) times 1/2 and the unscaling of
+// item (k(i), m), k(i) the deepest box of row i, as double-floats in place (0 outside the
+// boxes).  u_m and v_m alone grow beyond the float range near the ends of the wider boxes
+// for large m; the products are bounded by the partition tolerance's envelope.
+__global__ void k_fwd_uv_to_df(int64_t Ng, int M, const int *__restrict__ rowk, const double *__restrict__ scale,
+                               double *__restrict__ u, double *__restrict__ v) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int m = blockIdx.y;
+    if (i > Ng) return;
+    const int k = rowk[i];
+    const int64_t at = (int64_t)m * (Ng + 1) + i;
+    const double sc = k >= 0 ? 0.5 * scale[2 * (k * M + m) + 1] : 0.0;
+    const double uv = u[at] * sc, vv = v[at] * sc;
+    reinterpret_cast<dfs *>(u)[at] = df_from(uv);
+    reinterpret_cast<dfs *>(v)[at] = df_from(vv);
+}
+
+// stage twiddle tables (Twiddles::stw) from omega_{Ltab}^k, in each precision in use
+__global__ void k_stage_twiddles(int lmax, int logLtab, const double2 *__restrict__ tw64, double2 *stw64,
+                                 float2 *stw32, dfc *stwdf) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= stw_base(lmax + 1)) return;
+    int lb = 2;
+    while (stw_base(lb + 1) <= t) ++lb;
+    const int64_t h = 1LL << (lb - 2), rel = t - stw_base(lb);
+    const int64_t r = rel / h, n0 = rel - r * h;
+    const double2 w = tw64[((r + 1) * n0) << (logLtab - lb)];
+    if (stw64) stw64[t] = w;
+    if (stw32) stw32[t] = make_float2((float)w.x, (float)w.y);
+    if (stwdf) stwdf[t] = dfc_make(df_from(w.x), df_from(w.y));
+}
+
+// doubles -> double-floats in place (same 8 bytes per entry): stored recurrence values
+__global__ void k_to_df_inplace(int64_t n, double *E) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double v = E[i];
@@ -605,6 +637,13 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
     }
     k_rowk<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, gw.nblk, gw.d_box, gw.d_rowk);
     CJT_CUDA_TRY(cudaGetLastError());
+    if (!inverse && gw.nblk > 0 && p->opts.precision == CJT_DFLOAT) {
+        // the double-float combine reads u, v already multiplied by the unscaling of the row's item
+        dim3 g(blocks_for(Ng + 1, 256), M);
+        k_fwd_uv_to_df<<<g, 256, 0, st>>>(Ng, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v);
+        CJT_CUDA_TRY(cudaGetLastError());
+        gw.uv_df = true;
+    }
 
     tr.mark(inverse ? "inv: u,v tables, scales" : "fwd: u,v tables, scales");
     // ---- recurrence work: J(i) per row, chunks of <= 32 rows, degree segments
@@ -732,7 +771,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
                                                                    gw.d_E, inverse ? 1 : 0);
         CJT_CUDA_TRY(cudaGetLastError());
         if (p->opts.precision == CJT_DFLOAT) {
-            k_E_to_df<<<blocks_for(gw.nE, 256), 256, 0, st>>>(gw.nE, gw.d_E);
+            k_to_df_inplace<<<blocks_for(gw.nE, 256), 256, 0, st>>>(gw.nE, gw.d_E);
             CJT_CUDA_TRY(cudaGetLastError());
             gw.E_df = true;
         }
@@ -825,6 +864,21 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     k_twiddles<<<blocks_for(p->Ltab, 256), 256, 0, st>>>(p->Ltab, (double2 *)p->d_tw64, (float2 *)p->d_tw32,
                                                          (dfc *)p->d_twdf);
     CJT_CUDA_TRY(cudaGetLastError());
+    {
+        int logLtab = 0;
+        while ((1LL << logLtab) < p->Ltab) ++logLtab;
+        const int lmax = std::min(12, logLtab);
+        if (lmax >= 2) {
+            const int64_t n = stw_base(lmax + 1);
+            TRY(dalloc(p, (double2 **)&p->d_stw64, n));
+            if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_stw32, n));
+            if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_stwdf, n));   // dfc: 16 bytes
+            k_stage_twiddles<<<blocks_for(n, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)p->d_tw64,
+                                                                 (double2 *)p->d_stw64, (float2 *)p->d_stw32,
+                                                                 (dfc *)p->d_stwdf);
+            CJT_CUDA_TRY(cudaGetLastError());
+        }
+    }
     int64_t work = 0, scratch = 0;
     for (auto &u : used) {
         Dft &d = *u.first;
@@ -857,6 +911,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         p->ws_size[WS_PART_F] = (int64_t)sizeof(double) * (fwd ? std::max<int64_t>(p->fw.npartials, 1) : 0);
         p->ws_size[WS_PART_I] = (int64_t)sizeof(double) * (inv ? std::max<int64_t>(p->iv.npartials, 1) : 0);
         p->ws_size[WS_XDF] = pa == PREC_DF ? (int64_t)sizeof(dfs) * (inv ? 2 * N + 1 : N + 1) : 0;
+        p->ws_size[WS_EXPS] = pa == PREC_DF ? (int64_t)sizeof(int) * (CJT_EXP_BLOCKS + 1) : 0;
         int64_t off = 0;
         for (int k = 0; k < WS_COUNT; ++k) {
             p->ws_off[k] = off;
@@ -897,7 +952,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         CJT_CUDA_TRY(cudaGetLastError());
         cudaFreeAsync(T, st);
         cudaFreeAsync(start, st);
-        TRY(cjt_dft_exec(p->dft_cc, ws.dct, ws.work, ws.scratch, 1, p->d_tw64, p->Ltab, st));
+        TRY(cjt_dft_exec(p->dft_cc, ws.dct, ws.work, ws.scratch, 1, p->twiddles(PREC_F64), st));
         k_cc_weights<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)ws.dct, p->d_w);
         k_inv_norm<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, a, b, p->d_s);
         CJT_CUDA_TRY(cudaGetLastError());
@@ -929,5 +984,6 @@ Workspace cjt_carve(const cjt_plan_s *p, void *base) {
     w.part_f = (double *)at(WS_PART_F);
     w.part_i = (double *)at(WS_PART_I);
     w.xdf = at(WS_XDF);
+    w.exps = (int *)at(WS_EXPS);
     return w;
 }

@@ -149,3 +149,36 @@ def test_dfloat_in_a_batch_equals_alone(cjt):
         fn(p, xa, alone, arena)
         torch.cuda.synchronize()
         assert np.array_equal(alone.cpu().numpy(), o[off:off + c.size])
+
+
+@pytest.mark.parametrize("store", [0, 1])
+@pytest.mark.parametrize("s", [2.0 ** -600, 2.0 ** 600, 1e-200, 3.7e150])
+def test_dfloat_input_scale(cjt, orc, s, store):
+    """The double-float form scales its input by an exact power of two (from max |c|) before
+    converting it, so inputs anywhere in the FP64 range keep their relative accuracy, and a
+    power-of-two scaling of the input scales the result exactly."""
+    N, a, b = 4096, 0.3, -0.2
+    c = inputs.decaying_coefficients(N, 1.0, 17)
+    plan = cjt.Plan(N, a, b, precision=cjt.CJT_DFLOAT, M=13, rec_store=store)
+    for d, ref in ((cjt.CJT_FWD, orc.forward(c, a, b)), (cjt.CJT_INV, orc.inverse(c, a, b))):
+        y1 = run(cjt, plan, c, d)
+        ys = run(cjt, plan, c * s, d)
+        assert np.max(np.abs(ys / s - ref)) <= TOL * l1(c)
+        if s == 2.0 ** round(np.log2(s)):
+            assert np.array_equal(ys, y1 * s)
+
+
+def test_dfloat_at_2_20(cjt, orc):
+    """N = 2^20 (the size of the large mixed-precision workload): the double-float form
+    stays within the FP64 bound of the FP64 GPU form, and of the sampled oracle values."""
+    N = 1 << 20
+    a, b = inputs.jacobi_parameters(inputs.BASE_SEED + 4020)
+    c = inputs.decaying_coefficients(N, 1.0, inputs.BASE_SEED + 40)
+    pd = cjt.Plan(N, a, b, precision=cjt.CJT_DFLOAT, M=16, seg_len=1024, rec_store=1)
+    p64 = cjt.Plan(N, a, b, M=16, seg_len=1024)
+    for d in (cjt.CJT_FWD, cjt.CJT_INV):
+        assert np.max(np.abs(run(cjt, pd, c, d) - run(cjt, p64, c, d))) <= TOL * l1(c)
+    j = inputs.rng(8).integers(0, N + 1, 64)
+    fwd = run(cjt, pd, c, cjt.CJT_FWD)
+    assert np.max(np.abs(orc.cheb_series(fwd, j, N) - orc.jacobi_series(c, a, b, j, N))) <= TOL * l1(c)
+    assert np.max(np.abs(run(cjt, pd, fwd, cjt.CJT_INV) - c)) <= TOL * l1(c)
