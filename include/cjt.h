@@ -52,7 +52,7 @@ extern "C" {
 /* error codes */
 #define CJT_OK 0
 #define CJT_EINVAL (-1)      /* null pointer, N < 0, bad option value               */
-#define CJT_EDOMAIN (-2)     /* alpha or beta outside [-1/2, 1/2] (Sec. 2.1)         */
+#define CJT_EDOMAIN (-2)     /* alpha or beta outside [-1/2, 3/2] (Sec. 1.2, 2.1)     */
 #define CJT_ENOMEM (-3)      /* device or host allocation failed                     */
 #define CJT_ECUDA (-4)       /* a CUDA runtime call failed (see cjt_last_cuda_error) */
 #define CJT_ETIMEOUT (-5)    /* a bounded device-side wait gave up                   */
@@ -115,6 +115,8 @@ typedef struct {
     int64_t kernels_fwd, kernels_inv;   /* kernel launches of one execution              */
     int64_t workspace_bytes;            /* execution workspace one execution needs       */
     int64_t rec_store_bytes;            /* stored recurrence values (rec_store = 1)      */
+    int shift_alpha, shift_beta;        /* 0 or 1: alpha - shift_alpha and beta - shift_beta
+                                           lie in [-1/2, 1/2]                              */
 } cjt_plan_info;
 
 /* Stages reported by cjt_get_profile (forward 0-4, inverse 5-9). */
@@ -145,7 +147,14 @@ int cjt_plan_opts_default(cjt_plan_opts *opts);
  * indices are read back to size the launches).
  *   out    : receives the plan handle (NULL on failure)
  *   N      : degree, N >= 0 (N = 0 is the identity map); N <= 2^22
- *   alpha, beta : Jacobi parameters in [-1/2, 1/2] (else CJT_EDOMAIN)
+ *   alpha, beta : Jacobi parameters in [-1/2, 3/2] (else CJT_EDOMAIN).  The method itself
+ *            works on [-1/2, 1/2]^2 (Sec. 2.1); a parameter in (1/2, 3/2] is reached from
+ *            alpha - 1 (beta - 1) in the square by the two-term relation between Jacobi
+ *            polynomials whose parameters differ by one (Sec. 1.2): the coefficients are
+ *            converted in O(N) before the forward transform (a bidiagonal solve on the
+ *            input) and after the inverse transform (a bidiagonal product on the output).
+ *            Parameters below -1/2 would need the solve on the inverse transform's output,
+ *            which sums its errors over all higher degrees, so they are not offered.
  *   opts   : NULL for defaults
  * Errors: CJT_EINVAL, CJT_EDOMAIN, CJT_ENOMEM, CJT_ECUDA, CJT_EUNSUPPORTED.
  */
@@ -172,6 +181,21 @@ int cjt_forward(cjt_plan_t plan, const double *c_jac_dev, double *c_cheb_dev, vo
  * Errors: CJT_EINVAL (null), CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA.
  */
 int cjt_inverse(cjt_plan_t plan, const double *c_cheb_dev, double *c_jac_dev, void *stream);
+
+/*
+ * Jacobi-to-Jacobi conversion (Sec. 5: composing the forward and the inverse transform
+ * converts between Jacobi bases of different parameters):
+ *   c_out = P_N^{(gamma,delta)}^{-1} P_N^{(alpha,beta)} c_in,
+ * the coefficients, in the basis of plan `to` (parameters gamma, delta), of the
+ * polynomial of degree <= N whose coefficients in the basis of plan `from` (alpha, beta)
+ * are c_in.  Runs the forward transform of `from` into c_out, then the inverse transform
+ * of `to` in place on c_out, on `stream`.  c_in and c_out are device arrays of N+1
+ * doubles and may alias.  Both plans must own their workspace.
+ * Errors: CJT_EINVAL (null, plans of different N, shared-workspace plans),
+ * CJT_EDIRECTION (`from` without CJT_FWD or `to` without CJT_INV), and those of
+ * cjt_forward / cjt_inverse.
+ */
+int cjt_jacobi_to_jacobi(cjt_plan_t from, cjt_plan_t to, const double *c_in_dev, double *c_out_dev, void *stream);
 
 /*
  * Forward / inverse transform with a caller-supplied workspace: workspace_dev is

@@ -169,3 +169,10 @@ def inverse(c_cheb, alpha: float, beta: float, nthreads: int = 0) -> np.ndarray:
     out = np.empty_like(c)
     _check(_load().orc_inverse(c.size - 1, alpha, beta, _p(c), _p(out), nthreads), "inverse")
     return out
+
+
+def jacobi_to_jacobi(c, alpha: float, beta: float, gamma: float, delta: float, nthreads: int = 0) -> np.ndarray:
+    """Coefficients in P^{(gamma,delta)} of sum_n c_n P_n^{(alpha,beta)}: the forward transform
+    of (alpha, beta) followed by the inverse transform of (gamma, delta) (Sec. 5, composition
+    of the two transforms)."""
+    return inverse(forward(c, alpha, beta, nthreads), gamma, delta, nthreads)

@@ -29,7 +29,7 @@ def candidates(N: int, max_store_bytes: float):
     for M in CANDIDATES_M:
         for seg in CANDIDATES_SEG:
             out.append({"M": M, "seg_len": seg, "rec_store": 0})
-    for M in (5, 7, 10, 13):
+    for M in (5, 7, 10, 13, 16):
         for seg in CANDIDATES_SEG:
             out.append({"M": M, "seg_len": seg, "rec_store": 1})
         out.append({"M": M, "seg_len": 1024, "rec_store": 1, "ratio": 0.05})

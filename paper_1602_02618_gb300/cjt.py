@@ -47,7 +47,7 @@ class cjt_plan_info(ctypes.Structure):
                 ("nfft_inv", ctypes.c_int64), ("rec_items_fwd", ctypes.c_int64), ("rec_items_inv", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("plan_ms", ctypes.c_double), ("kernels_fwd", ctypes.c_int64),
                 ("kernels_inv", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("rec_store_bytes", ctypes.c_int64)]
+                ("rec_store_bytes", ctypes.c_int64), ("shift_alpha", ctypes.c_int), ("shift_beta", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -57,7 +57,7 @@ EXPORTED = ["cjt_plan_opts_default", "cjt_plan", "cjt_destroy", "cjt_get_info", 
             "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_strerror", "cjt_last_cuda_error",
             "cjt_version", "cjt_set_profiling", "cjt_get_profile", "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc",
             "cjt_forward_ws", "cjt_inverse_ws", "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info",
-            "cjt_batch_destroy"]
+            "cjt_batch_destroy", "cjt_jacobi_to_jacobi"]
 
 NOALLOC_MAX_N = 65536
 
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
         lib.cjt_cheb_coeffs_noalloc.argtypes = [i64, vp, vp, vp]
         lib.cjt_forward_ws.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.cjt_inverse_ws.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
+        lib.cjt_jacobi_to_jacobi.argtypes = [vp, vp, vp, vp, vp]
         lib.cjt_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int8),
                                          ctypes.POINTER(i64), vp, vp, i]
         lib.cjt_batch_launch.argtypes = [vp, vp]
@@ -117,7 +118,7 @@ def load(path: str = LIB_PATH):
         for name in ("cjt_plan_opts_default", "cjt_plan", "cjt_get_info", "cjt_forward", "cjt_inverse",
                      "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_set_profiling", "cjt_get_profile",
                      "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc", "cjt_forward_ws", "cjt_inverse_ws",
-                     "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info"):
+                     "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info", "cjt_jacobi_to_jacobi"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -245,6 +246,18 @@ def cjt_execute_batched(plans, dirs, offsets, x_dev, out_dev, stream=None):
     _check(load().cjt_execute_batched(count, arr, d, off, _dev_ptr(x_dev, total), _dev_ptr(out_dev, total),
                                       _stream_handle(stream)), "cjt_execute_batched")
     return out_dev
+
+
+def cjt_jacobi_to_jacobi(plan_from: Plan, plan_to: Plan, c_in, c_out=None, stream=None):
+    """Coefficients in the Jacobi basis of plan_to of the expansion c_in in the basis of
+    plan_from (forward of plan_from, then inverse of plan_to, on the device)."""
+    import torch
+    n = plan_from.N + 1
+    if c_out is None:
+        c_out = torch.empty(n, dtype=torch.float64, device=c_in.device)
+    _check(load().cjt_jacobi_to_jacobi(plan_from.handle, plan_to.handle, _dev_ptr(c_in, n), _dev_ptr(c_out, n),
+                                       _stream_handle(stream)), "cjt_jacobi_to_jacobi")
+    return c_out
 
 
 def cjt_forward_ws(plan: Plan, c_jac, c_cheb, workspace, stream=None):

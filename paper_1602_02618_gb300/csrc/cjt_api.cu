@@ -91,7 +91,7 @@ const char *cjt_strerror(int code) {
     switch (code) {
         case CJT_OK: return "success";
         case CJT_EINVAL: return "invalid argument";
-        case CJT_EDOMAIN: return "alpha or beta outside [-1/2, 1/2]";
+        case CJT_EDOMAIN: return "alpha or beta outside [-1/2, 3/2]";
         case CJT_ENOMEM: return "out of memory";
         case CJT_ECUDA: return "CUDA runtime error";
         case CJT_ETIMEOUT: return "device-side wait timed out";
@@ -120,7 +120,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     *out = nullptr;
     if (N < 0) return CJT_EINVAL;
     if (N > (1LL << 22)) return CJT_EUNSUPPORTED;
-    if (!(alpha >= -0.5 && alpha <= 0.5) || !(beta >= -0.5 && beta <= 0.5)) return CJT_EDOMAIN;
+    if (!(alpha >= -0.5 && alpha <= 1.5) || !(beta >= -0.5 && beta <= 1.5)) return CJT_EDOMAIN;
     cjt_plan_opts o;
     cjt_plan_opts_default(&o);
     if (opts) {
@@ -146,8 +146,15 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     cjt_plan_s *p = new (std::nothrow) cjt_plan_s();
     if (!p) return CJT_ENOMEM;
     p->N = N;
-    p->alpha = alpha;
-    p->beta = beta;
+    // one unit step down into the square [-1/2, 1/2]^2 for a parameter in (1/2, 3/2]
+    // (Sec. 1.2; alpha - 1 is exact there)
+    auto shift_of = [](double v) { return v > 0.5 ? 1 : 0; };
+    p->alpha_user = alpha;
+    p->beta_user = beta;
+    p->shift_a = shift_of(alpha);
+    p->shift_b = shift_of(beta);
+    p->alpha = alpha - p->shift_a;
+    p->beta = beta - p->shift_b;
     p->opts = o;
     p->seg_len = o.seg_len;
     cudaStream_t st = (cudaStream_t)stream;
@@ -185,8 +192,10 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
     if (!p || !info) return CJT_EINVAL;
     memset(info, 0, sizeof(*info));
     info->N = p->N;
-    info->alpha = p->alpha;
-    info->beta = p->beta;
+    info->alpha = p->alpha_user;
+    info->beta = p->beta_user;
+    info->shift_alpha = p->shift_a;
+    info->shift_beta = p->shift_b;
     info->M = p->M;
     info->precision = p->opts.precision;
     info->directions = p->opts.directions;
@@ -215,6 +224,8 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
                             (p->prec_asy == PREC_DF ? 2 : 0);   // input scaling to double-float
         info->kernels_inv = 1 + dft_launches(p->dft_front) + 1 + (nqi > 0 ? 1 + dft_launches(p->dft_i) : 0) +
                             (p->iv.nitems > 0) + 2 + (p->prec_asy == PREC_DF ? 2 : 0);
+        info->kernels_fwd += cjt_conv_kernels(p);
+        info->kernels_inv += cjt_conv_kernels(p);
         if (!(p->opts.directions & CJT_FWD)) info->kernels_fwd = 0;
         if (!(p->opts.directions & CJT_INV)) info->kernels_inv = 0;
     }
@@ -259,7 +270,8 @@ static int run_one(cjt_plan_t p, int direction, const double *in, double *out, c
     cudaStream_t st = (cudaStream_t)stream;
     int rc = cjt_internal_begin_use(p, st);
     if (rc) return rc;
-    rc = direction == CJT_FWD ? cjt_exec_forward(p, ws, in, out, st) : cjt_exec_inverse(p, ws, in, out, st);
+    rc = direction == CJT_FWD ? cjt_exec_forward_shifted(p, ws, in, out, st)
+                              : cjt_exec_inverse_shifted(p, ws, in, out, st);
     if (rc) return rc;
     return cjt_internal_end_use(p, st);
 }
@@ -272,6 +284,14 @@ int cjt_forward(cjt_plan_t p, const double *in, double *out, void *stream) {
 int cjt_inverse(cjt_plan_t p, const double *in, double *out, void *stream) {
     if (p && p->shared_ws && p->N > 0) return CJT_EINVAL;
     return p ? run_one(p, CJT_INV, in, out, p->ws, stream) : CJT_EINVAL;
+}
+
+int cjt_jacobi_to_jacobi(cjt_plan_t from, cjt_plan_t to, const double *in, double *out, void *stream) {
+    if (!from || !to || !in || !out || from->N != to->N) return CJT_EINVAL;
+    if (!(from->opts.directions & CJT_FWD) || !(to->opts.directions & CJT_INV)) return CJT_EDIRECTION;
+    int rc = cjt_forward(from, in, out, stream);
+    if (rc) return rc;
+    return cjt_inverse(to, out, out, stream);
 }
 
 int cjt_forward_ws(cjt_plan_t p, const double *in, double *out, void *ws, size_t bytes, void *stream) {
@@ -294,8 +314,8 @@ int cjt_execute_host(cjt_plan_t p, int direction, const double *in_host, double 
     if (rc) return rc;
     const size_t bytes = sizeof(double) * (size_t)(p->N + 1);
     CJT_CUDA_TRY(cudaMemcpyAsync(p->d_in, in_host, bytes, cudaMemcpyHostToDevice, st));
-    rc = direction == CJT_FWD ? cjt_exec_forward(p, p->ws, p->d_in, p->d_out, st)
-                              : cjt_exec_inverse(p, p->ws, p->d_in, p->d_out, st);
+    rc = direction == CJT_FWD ? cjt_exec_forward_shifted(p, p->ws, p->d_in, p->d_out, st)
+                              : cjt_exec_inverse_shifted(p, p->ws, p->d_in, p->d_out, st);
     if (rc) return rc;
     CJT_CUDA_TRY(cudaMemcpyAsync(out_host, p->d_out, bytes, cudaMemcpyDeviceToHost, st));
     rc = cjt_internal_end_use(p, st);

@@ -94,8 +94,9 @@ int issue(int count, const cjt_plan_t *plans, const int8_t *dir, const int64_t *
         for (int t : a.order[l]) {
             cjt_plan_s *p = plans[t];
             const Workspace ws = p->shared_ws ? cjt_carve(p, arenas[l]) : p->ws;
-            int rc = dir[t] == CJT_FWD ? cjt_exec_forward(p, ws, in + offsets[t], out + offsets[t], L.streams[l])
-                                       : cjt_exec_inverse(p, ws, in + offsets[t], out + offsets[t], L.streams[l]);
+            int rc = dir[t] == CJT_FWD
+                         ? cjt_exec_forward_shifted(p, ws, in + offsets[t], out + offsets[t], L.streams[l])
+                         : cjt_exec_inverse_shifted(p, ws, in + offsets[t], out + offsets[t], L.streams[l]);
             if (rc) return rc;
         }
         CJT_CUDA_TRY(cudaEventRecord(L.join[l], L.streams[l]));

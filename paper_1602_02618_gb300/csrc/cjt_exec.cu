@@ -558,11 +558,11 @@ __global__ void k_inv_g(int64_t Ng, const double2 *__restrict__ F, const double 
 }
 
 // Sum of the recurrence partials of every item covering degree n, in a fixed order:
-// warp w takes the items in runs of 32 (runs w, w + RED_WARPS, ...), loads the run's
-// item descriptors with one coalesced load and broadcasts them by shuffles, so that the
-// partial loads of a run are independent and many are in flight; four interleaved
-// accumulators; the warp sums are added in warp order.  One block per 32 consecutive
-// degrees.
+// warp w takes items w, w + RED_WARPS, w + 2 RED_WARPS, ... (round robin, so that short
+// segments spread over all warps), 32 of them at a time: lane l loads the descriptor of
+// the l-th, the warp broadcasts them by shuffles, and eight partial loads are in flight;
+// four interleaved accumulators; the warp sums are added in warp order.  One block per
+// 32 consecutive degrees.
 constexpr int RED_WARPS = 32;
 __global__ void __launch_bounds__(32 * RED_WARPS) k_inv_reduce(int64_t N, int seg_len,
                                                                const int64_t *__restrict__ seg_ptr,
@@ -576,12 +576,13 @@ __global__ void __launch_bounds__(32 * RED_WARPS) k_inv_reduce(int64_t N, int se
     const int64_t s = n0 / seg_len, off = n - s * seg_len;
     const int64_t q0 = seg_ptr[s], q1 = seg_ptr[s + 1];
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t qb = q0 + 32 * (int64_t)w; qb < q1; qb += 32 * RED_WARPS) {
-        const int64_t qq = qb + lane;
-        const bool ok = qq < q1;
+    const int64_t kmax = q1 - q0 > w ? (q1 - q0 - w + RED_WARPS - 1) / RED_WARPS : 0;   // this warp's items
+    for (int64_t kb = 0; kb < kmax; kb += 32) {
+        const int64_t qq = q0 + w + (int64_t)RED_WARPS * (kb + lane);
+        const bool ok = kb + lane < kmax;
         const int64_t so = ok ? seg_out[qq] : 0;
         const int sb = ok ? seg_b[qq] : 0;
-        const int cnt = (int)min((int64_t)32, q1 - qb);
+        const int cnt = (int)min((int64_t)32, kmax - kb);
         int j = 0;
         for (; j + 8 <= cnt; j += 8) {
 #pragma unroll

@@ -138,14 +138,19 @@ struct Workspace {
     void *xdf = nullptr;   // CJT_DFLOAT: the input c (forward) or g (inverse) as double-floats,
                            // scaled by an exact power of two 2^-e so that max |x| < 1
     int *exps = nullptr;   // CJT_DFLOAT: per-block exponents of max |x|, then e at [CJT_EXP_BLOCKS]
+    double *conv = nullptr;// parameter shifts: two coefficient buffers of N+1 and the scan's chunk maps
 };
+constexpr int CJT_CONV_CHUNK = 1024;   // degrees per chunk of the bidiagonal solve's scan
+__host__ __device__ inline int64_t cjt_conv_chunks(int64_t N) { return (N + 1 + CJT_CONV_CHUNK - 1) / CJT_CONV_CHUNK; }
 enum { WS_FFT_F, WS_FFT_I, WS_SCRATCH, WS_WORK, WS_DCT, WS_Y, WS_G, WS_PART_F, WS_PART_I, WS_XDF, WS_EXPS,
-       WS_COUNT };
+       WS_CONV, WS_COUNT };
 constexpr int CJT_EXP_BLOCKS = 128;
 
 struct cjt_plan_s {
     int64_t N = 0;
-    double alpha = 0, beta = 0;
+    double alpha = 0, beta = 0;          // the parameters the method runs on, in [-1/2, 1/2]^2
+    double alpha_user = 0, beta_user = 0;// the caller's: alpha + shift_a, beta + shift_b
+    int shift_a = 0, shift_b = 0;        // integer shifts (-1, 0, +1), Sec. 1.2
     cjt_plan_opts opts{};
     int M = 7;
     int64_t n_M = 0;
@@ -323,3 +328,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st);
 Workspace cjt_carve(const cjt_plan_s *p, void *base);
 int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st);
 int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st);
+// the transform entry points with the integer parameter shifts applied (Sec. 1.2)
+int cjt_exec_forward_shifted(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st);
+int cjt_exec_inverse_shifted(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st);
+int cjt_conv_kernels(const cjt_plan_s *p);   // launches the conversions add to one execution

@@ -318,7 +318,11 @@ __device__ __forceinline__ void mom_coeffs(double ab, double amb, int64_t k, dou
     *c0 = -(ab - (double)k + 2.0) * inv;
 }
 
-__global__ void k_mom_transfer(int64_t Ng, double a, double b, int64_t nchunk, double4 *T) {
+struct Mat2 {   // 2x2 transfer matrix [[x0, x1], [y0, y1]] of one chunk
+    double x0, x1, y0, y1;
+};
+
+__global__ void k_mom_transfer(int64_t Ng, double a, double b, int64_t nchunk, Mat2 *T) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= nchunk) return;
     const double ab = a + b, amb = a - b;
@@ -331,16 +335,16 @@ __global__ void k_mom_transfer(int64_t Ng, double a, double b, int64_t nchunk, d
         x0 = y0; y0 = nx;
         x1 = y1; y1 = ny;
     }
-    T[c] = make_double4(x0, x1, y0, y1);   // [[x0, x1], [y0, y1]]
+    T[c] = Mat2{x0, x1, y0, y1};
 }
 
-__global__ void k_mom_carry(int64_t nchunk, double mu0, double mu1, const double4 *T, double2 *start) {
+__global__ void k_mom_carry(int64_t nchunk, double mu0, double mu1, const Mat2 *T, double2 *start) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     double u = mu0, v = mu1;
     for (int64_t c = 0; c < nchunk; ++c) {
         start[c] = make_double2(u, v);
-        const double4 m = T[c];
-        const double nu = fma(m.x, u, m.y * v), nv = fma(m.z, u, m.w * v);
+        const Mat2 m = T[c];
+        const double nu = fma(m.x0, u, m.x1 * v), nv = fma(m.y0, u, m.y1 * v);
         u = nu;
         v = nv;
     }
@@ -912,6 +916,8 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         p->ws_size[WS_PART_I] = (int64_t)sizeof(double) * (inv ? std::max<int64_t>(p->iv.npartials, 1) : 0);
         p->ws_size[WS_XDF] = pa == PREC_DF ? (int64_t)sizeof(dfs) * (inv ? 2 * N + 1 : N + 1) : 0;
         p->ws_size[WS_EXPS] = pa == PREC_DF ? (int64_t)sizeof(int) * (CJT_EXP_BLOCKS + 1) : 0;
+        p->ws_size[WS_CONV] = (p->shift_a || p->shift_b)
+                                  ? (int64_t)sizeof(double) * (2 * (N + 1) + 3 * cjt_conv_chunks(N)) : 0;
         int64_t off = 0;
         for (int k = 0; k < WS_COUNT; ++k) {
             p->ws_off[k] = off;
@@ -942,9 +948,9 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         // modified moments mu_0..mu_Ng (Sec. 3.1, mu_1 with the sign of the weight's mean)
         const double mu1 = (b - a) / (a + b + 2.0) * mu0;
         const int64_t nchunk = std::max<int64_t>(1, (Ng - 1 + kMomChunk - 1) / kMomChunk);
-        double4 *T = nullptr;
+        Mat2 *T = nullptr;
         double2 *start = nullptr;
-        CJT_CUDA_TRY(cudaMallocAsync((void **)&T, sizeof(double4) * nchunk, st));
+        CJT_CUDA_TRY(cudaMallocAsync((void **)&T, sizeof(Mat2) * nchunk, st));
         CJT_CUDA_TRY(cudaMallocAsync((void **)&start, sizeof(double2) * nchunk, st));
         k_mom_transfer<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, T);
         k_mom_carry<<<1, 1, 0, st>>>(nchunk, mu0, mu1, T, start);
@@ -985,5 +991,6 @@ Workspace cjt_carve(const cjt_plan_s *p, void *base) {
     w.part_i = (double *)at(WS_PART_I);
     w.xdf = at(WS_XDF);
     w.exps = (int *)at(WS_EXPS);
+    w.conv = (double *)at(WS_CONV);
     return w;
 }

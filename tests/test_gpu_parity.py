@@ -177,7 +177,7 @@ def test_execute_host_matches_device(cjt):
 
 def test_error_codes(cjt):
     with pytest.raises(cjt.CJTError) as e:
-        cjt.Plan(64, 0.6, 0.0)
+        cjt.Plan(64, 1.6, 0.0)
     assert e.value.code == cjt.CJT_EDOMAIN
     with pytest.raises(cjt.CJTError) as e:
         cjt.Plan(-1, 0.0, 0.0)

@@ -369,3 +369,95 @@ def test_planted_dropped_B_term_is_caught(tmp_path):
     lib.orc_jacobi_values(8, 0.1, -0.3, 1, 3, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     exact = float(_eval_poly(ex.jacobi_monomial(5, 0.1, -0.3), Fraction(1, 2)))
     assert abs(out[5] - exact) > 1e-6
+
+
+def two_term_raise(a_coef, alpha, beta, which):
+    """Coefficients in P^{(alpha+1,beta)} (which='alpha') or P^{(alpha,beta+1)} (which='beta') of
+    sum_n a_n P_n^{(alpha,beta)}, in exact rationals, from the two-term connection relations
+    P_n^{(a,b)} = [(n+a+b+1) P_n^{(a,b+1)} + (n+a) P_{n-1}^{(a,b+1)}] / (2n+a+b+1) and
+    P_n^{(a,b)} = [(n+a+b+1) P_n^{(a+1,b)} - (n+b) P_{n-1}^{(a+1,b)}] / (2n+a+b+1)
+    (DLMF 18.9.5 and 18.9.6)."""
+    A, B = Fraction(alpha), Fraction(beta)
+    a = [Fraction(float(x)) for x in a_coef]
+    N = len(a) - 1
+    other = A if which == "beta" else B
+    sign = 1 if which == "beta" else -1
+    out = []
+    for n in range(N + 1):
+        v = a[n] * ((n + A + B + 1) / (2 * n + A + B + 1) if n > 0 else 1)   # P_0 = 1 in every basis
+        if n < N:
+            v += sign * a[n + 1] * (n + 1 + other) / (2 * n + A + B + 3)
+        out.append(v)
+    return np.array([float(v) for v in out])
+
+
+@pytest.mark.parametrize("alpha,beta,which", [(0.2, -0.5, "beta"), (-0.5, 0.3, "alpha"), (0.0, -0.5, "beta"),
+                                              (-0.5, -0.5, "alpha")])
+def test_jacobi_to_jacobi_two_term_connection(orc, alpha, beta, which):
+    """Jacobi-to-Jacobi conversion (forward then inverse, Sec. 5) against the two-term
+    connection of a unit parameter raise, an independent closed form."""
+    N = 200
+    c = inputs.decaying_coefficients(N, 1.0, seed=31)
+    g, d = (alpha + 1, beta) if which == "alpha" else (alpha, beta + 1)
+    got = orc.jacobi_to_jacobi(c, alpha, beta, g, d)
+    want = two_term_raise(c, alpha, beta, which)
+    assert np.max(np.abs(got - want)) <= 1e-14 * l1(c)
+
+
+def test_jacobi_to_jacobi_identity(orc):
+    c = inputs.decaying_coefficients(300, 1.0, seed=32)
+    assert np.max(np.abs(orc.jacobi_to_jacobi(c, 0.3, -0.1, 0.3, -0.1) - c)) <= 1e-14 * l1(c)
+
+
+# Parameters outside [-1/2, 1/2]^2, reached from the square by one integer shift (Sec. 1.2):
+# the oracle evaluates the definitions directly.  Its modified-moment recurrence loses
+# accuracy for alpha or beta above about 2, so the pinned domain is (-1, 3/2]^2.
+SHIFTED = [(1.5, 0.25), (-0.8, 0.4), (1.2, -0.9), (0.3, 1.5), (1.4, 1.1), (-0.95, -0.7)]
+
+
+@pytest.mark.parametrize("alpha,beta", SHIFTED)
+@pytest.mark.parametrize("N", [2, 7, 12])
+def test_forward_exact_rational_shifted_parameters(orc, alpha, beta, N):
+    c = inputs.decaying_coefficients(N, 1.0, seed=inputs.BASE_SEED + 5 * N)
+    exact = np.array([float(v) for v in ex.forward_exact(c, alpha, beta)])
+    assert np.max(np.abs(orc.forward(c, alpha, beta) - exact)) <= 1e-15 * l1(c)
+
+
+@pytest.mark.parametrize("alpha,beta", SHIFTED)
+def test_inverse_exact_rational_shifted_parameters(orc, alpha, beta):
+    N = 10
+    c = inputs.decaying_coefficients(N, 1.0, seed=23)
+    exact = np.array([float(v) for v in ex.inverse_exact(c, alpha, beta)])
+    assert np.max(np.abs(orc.inverse(c, alpha, beta) - exact)) <= 1e-14 * l1(c)
+
+
+def moment_closed_form(k, alpha, beta):
+    """mu_k = int T_k (1-x)^a (1+x)^b dx as a terminating sum: with T_k(x) the hypergeometric
+    polynomial 2F1(-k, k; 1/2; (1-x)/2) and Beta integrals term by term,
+    mu_k = mu_0 3F2(-k, k, a+1; 1/2, a+b+2; 1), mu_0 = 2^(a+b+1) G(a+1) G(b+1) / G(a+b+2)
+    (60 digits)."""
+    mpmath.mp.dps = 60
+    a, b = mpmath.mpf(alpha), mpmath.mpf(beta)
+    mu0 = 2 ** (a + b + 1) * mpmath.gamma(a + 1) * mpmath.gamma(b + 1) / mpmath.gamma(a + b + 2)
+    s, t = mpmath.mpf(0), mpmath.mpf(1)
+    for j in range(k + 1):
+        s += t
+        t *= (j - k) * (k + j) * (a + 1 + j) / ((mpmath.mpf(0.5) + j) * (j + 1) * (a + b + 2 + j))
+    return float(mu0 * s)
+
+
+@pytest.mark.parametrize("alpha,beta", SHIFTED + [(0.1, -0.3), (-0.5, -0.5)])
+def test_moments_closed_form(orc, alpha, beta):
+    K = 40
+    mu = orc.moments(K, alpha, beta)
+    for k in (0, 1, 2, 5, 12, 40):
+        ref = moment_closed_form(k, alpha, beta)
+        assert abs(mu[k] - ref) <= 1e-15 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("alpha,beta", SHIFTED)
+def test_round_trip_shifted_parameters(orc, alpha, beta):
+    N = 400
+    c = inputs.decaying_coefficients(N, 1.0, seed=24)
+    back = orc.inverse(orc.forward(c, alpha, beta), alpha, beta)
+    assert np.max(np.abs(back - c)) <= 1e-13 * l1(c)
