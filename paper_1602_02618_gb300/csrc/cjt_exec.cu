@@ -166,20 +166,26 @@ __global__ void __launch_bounds__(32 * RI_WARPS) k_rec_inv(const RecItem *__rest
 // ---------------------------------------------------------------------------
 // REC with stored values (rec_store): one fused multiply-add per entry
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_rec_fwd_stored(const RecItem *__restrict__ items, int64_t nitems,
-                                                       const double *__restrict__ c, const double *__restrict__ E,
-                                                       double *__restrict__ partials) {
-    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= nitems) return;
-    const RecItem it = items[w];
+// One CTA of SW warps per item: warp w takes a quarter of the item's degrees (eight
+// streaming loads in flight per lane), and the four partial sums are added in warp order.
+// Splitting the long items (rows near x = +-1) over four warps keeps the SMs busy to the
+// end of the launch.
+constexpr int SW = 4;
+__global__ void __launch_bounds__(32 * SW) k_rec_fwd_stored(const RecItem *__restrict__ items, int64_t nitems,
+                                                            const double *__restrict__ c, const double *__restrict__ E,
+                                                            double *__restrict__ partials) {
+    __shared__ double red[SW][32];
+    if ((int64_t)blockIdx.x >= nitems) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const RecItem it = items[blockIdx.x];
     const int len = it.b - it.a;
+    const int per = ((len + SW - 1) / SW + 7) & ~7;
+    const int k0 = min(len, w * per), k1 = min(len, k0 + per);
     const double *e = E + it.eoff + lane;
     const double *cc = c + it.a;
-    // eight independent streaming loads and accumulators per lane keep enough bytes in flight
     double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    int k = 0;
-    for (; k + 8 <= len; k += 8) {
+    int k = k0;
+    for (; k + 8 <= k1; k += 8) {
         double v[8], cv[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -189,29 +195,34 @@ __global__ void __launch_bounds__(128) k_rec_fwd_stored(const RecItem *__restric
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[j] = fma(v[j], cv[j], acc[j]);
     }
-    for (; k < len; ++k) acc[k & 7] = fma(__ldcs(e + (int64_t)k * 32), __ldg(cc + k), acc[k & 7]);
-    const double S = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-    partials[it.out + lane] = lane < it.nrows ? S : 0.0;
+    for (; k < k1; ++k) acc[0] = fma(__ldcs(e + (int64_t)k * 32), __ldg(cc + k), acc[0]);
+    red[w][lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    __syncthreads();
+    if (w == 0) {
+        const double S = (red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane]);
+        partials[it.out + lane] = lane < it.nrows ? S : 0.0;
+    }
 }
 
-__global__ void __launch_bounds__(128) k_rec_inv_stored(const RecItem *__restrict__ items, int64_t nitems,
-                                                       const double *__restrict__ g, const double *__restrict__ E,
-                                                       double *__restrict__ partials) {
-    __shared__ double gs[4][32];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * 4 + wib;
-    if (w >= nitems) return;
-    const RecItem it = items[w];
-    gs[wib][lane] = lane < it.nrows ? g[it.row0 + lane] : 0.0;
-    __syncwarp();
+// One CTA of SW warps per item: warp w takes the item's degree columns w*32 + lane,
+// (w + SW)*32 + lane, ...; each column sums its 32 rows in order.
+__global__ void __launch_bounds__(32 * SW) k_rec_inv_stored(const RecItem *__restrict__ items, int64_t nitems,
+                                                            const double *__restrict__ g, const double *__restrict__ E,
+                                                            double *__restrict__ partials) {
+    __shared__ double gs[32];
+    if ((int64_t)blockIdx.x >= nitems) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const RecItem it = items[blockIdx.x];
+    if (w == 0) gs[lane] = lane < it.nrows ? g[it.row0 + lane] : 0.0;
+    __syncthreads();
     const int len = it.b - it.a;
     const double *e = E + it.eoff;
     double *out = partials + it.out;
-    for (int k0 = 0; k0 < len; k0 += 32) {
+    for (int k0 = w * 32; k0 < len; k0 += 32 * SW) {
         const int k = k0 + lane;
         if (k < len) {
             double acc = 0.0;
-            for (int r = 0; r < it.nrows; ++r) acc = fma(gs[wib][r], __ldg(e + (int64_t)r * len + k), acc);
+            for (int r = 0; r < it.nrows; ++r) acc = fma(gs[r], __ldg(e + (int64_t)r * len + k), acc);
             out[k] = acc;
         }
     }
@@ -349,53 +360,60 @@ __global__ void k_asy_pack_inv_df(int64_t Ng, int64_t L, int nq, const dfs *__re
 // REC with stored double-float values: one double-float multiply-add per entry,
 // renormalised at every step (an unnormalised low part would let its own rounding
 // errors grow with the segment length)
-__global__ void __launch_bounds__(128) k_rec_fwd_stored_df(const RecItem *__restrict__ items, int64_t nitems,
-                                                          const dfs *__restrict__ cdf, const dfs *__restrict__ E,
-                                                          double *__restrict__ partials) {
-    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= nitems) return;
-    const RecItem it = items[w];
+// as k_rec_fwd_stored, in double-float arithmetic
+__global__ void __launch_bounds__(32 * SW) k_rec_fwd_stored_df(const RecItem *__restrict__ items, int64_t nitems,
+                                                               const dfs *__restrict__ cdf, const dfs *__restrict__ E,
+                                                               double *__restrict__ partials) {
+    __shared__ dfs red[SW][32];
+    if ((int64_t)blockIdx.x >= nitems) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const RecItem it = items[blockIdx.x];
     const int len = it.b - it.a;
+    const int per = ((len + SW - 1) / SW + 7) & ~7;
+    const int k0 = min(len, w * per), k1 = min(len, k0 + per);
     const float2 *e = reinterpret_cast<const float2 *>(E + it.eoff) + lane;
     const dfs *cc = cdf + it.a;
     // eight streaming loads in flight per lane, four independent accumulators
     dfs acc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[j] = df_make(0.f, 0.f);
-    int k = 0;
-    for (; k + 8 <= len; k += 8) {
+    int k = k0;
+    for (; k + 8 <= k1; k += 8) {
         float2 v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = __ldcs(e + (int64_t)(k + j) * 32);
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[j & 3] = df_mac(acc[j & 3], df_make(v[j].x, v[j].y), cc[k + j]);
     }
-    for (; k < len; ++k) {
+    for (; k < k1; ++k) {
         const float2 v = __ldcs(e + (int64_t)k * 32);
-        acc[k & 3] = df_mac(acc[k & 3], df_make(v.x, v.y), cc[k]);
+        acc[0] = df_mac(acc[0], df_make(v.x, v.y), cc[k]);
     }
-    const dfs S = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
-    reinterpret_cast<dfs *>(partials)[it.out + lane] = lane < it.nrows ? S : df_make(0.f, 0.f);
+    red[w][lane] = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
+    __syncthreads();
+    if (w == 0) {
+        const dfs S = df_add(df_add(red[0][lane], red[1][lane]), df_add(red[2][lane], red[3][lane]));
+        reinterpret_cast<dfs *>(partials)[it.out + lane] = lane < it.nrows ? S : df_make(0.f, 0.f);
+    }
 }
 
-__global__ void __launch_bounds__(128) k_rec_inv_stored_df(const RecItem *__restrict__ items, int64_t nitems,
-                                                          const dfs *__restrict__ gdf, const dfs *__restrict__ E,
-                                                          double *__restrict__ partials) {
-    __shared__ dfs gs[4][32];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * 4 + wib;
-    if (w >= nitems) return;
-    const RecItem it = items[w];
-    gs[wib][lane] = lane < it.nrows ? gdf[it.row0 + lane] : df_make(0.f, 0.f);
-    __syncwarp();
+// as k_rec_inv_stored, in double-float arithmetic (rows in groups of eight loads in flight,
+// four independent accumulators per column)
+__global__ void __launch_bounds__(32 * SW) k_rec_inv_stored_df(const RecItem *__restrict__ items, int64_t nitems,
+                                                               const dfs *__restrict__ gdf, const dfs *__restrict__ E,
+                                                               double *__restrict__ partials) {
+    __shared__ dfs gs[32];
+    if ((int64_t)blockIdx.x >= nitems) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const RecItem it = items[blockIdx.x];
+    if (w == 0) gs[lane] = lane < it.nrows ? gdf[it.row0 + lane] : df_make(0.f, 0.f);
+    __syncthreads();
     const int len = it.b - it.a, nr = it.nrows;
     const float2 *e = reinterpret_cast<const float2 *>(E + it.eoff);
     double *out = partials + it.out;
-    for (int k0 = 0; k0 < len; k0 += 32) {
+    for (int k0 = w * 32; k0 < len; k0 += 32 * SW) {
         const int k = k0 + lane;
         if (k < len) {
-            // rows in groups of eight loads in flight, four independent accumulators
             dfs acc[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[j] = df_make(0.f, 0.f);
@@ -405,11 +423,11 @@ __global__ void __launch_bounds__(128) k_rec_inv_stored_df(const RecItem *__rest
 #pragma unroll
                 for (int j = 0; j < 8; ++j) v[j] = __ldcs(e + (int64_t)(r + j) * len + k);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[j & 3] = df_mac(acc[j & 3], gs[wib][r + j], df_make(v[j].x, v[j].y));
+                for (int j = 0; j < 8; ++j) acc[j & 3] = df_mac(acc[j & 3], gs[r + j], df_make(v[j].x, v[j].y));
             }
             for (; r < nr; ++r) {
                 const float2 v = __ldcs(e + (int64_t)r * len + k);
-                acc[r & 3] = df_mac(acc[r & 3], gs[wib][r], df_make(v.x, v.y));
+                acc[0] = df_mac(acc[0], gs[r], df_make(v.x, v.y));
             }
             out[k] = df_to(df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3])));
         }
@@ -695,10 +713,10 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     if (gw.nitems > 0) {
         StageTimer tm(p, st, CJT_STAGE_FWD_REC);
         if (gw.d_E && gw.E_df)
-            k_rec_fwd_stored_df<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, cdf,
+            k_rec_fwd_stored_df<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, cdf,
                                                                                 (const dfs *)gw.d_E, ws.part_f);
         else if (gw.d_E)
-            k_rec_fwd_stored<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, in, gw.d_E,
+            k_rec_fwd_stored<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, in, gw.d_E,
                                                                              ws.part_f);
         else
             k_rec_fwd<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, gw.Ng, p->rt, in,
@@ -801,10 +819,10 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         StageTimer tm(p, st, CJT_STAGE_INV_REC);
         if (gw.nitems > 0) {
             if (gw.d_E && gw.E_df)
-                k_rec_inv_stored_df<<<blocks_for(gw.nitems, 4), 128, 0, st>>>(gw.d_items, gw.nitems, gdf,
+                k_rec_inv_stored_df<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, gdf,
                                                                                (const dfs *)gw.d_E, ws.part_i);
             else if (gw.d_E)
-                k_rec_inv_stored<<<blocks_for(gw.nitems, 4), 128, 0, st>>>(gw.d_items, gw.nitems, ws.g, gw.d_E,
+                k_rec_inv_stored<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, ws.g, gw.d_E,
                                                                             ws.part_i);
             else
                 k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt,

@@ -215,8 +215,8 @@ int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batc
                int post_log, const void *stw, cudaStream_t st) {
     using V = typename cplx<R>::t;
     const int Ls = 1 << logLs;
-    // Columns per CTA: at most ~64 KB of shared memory, and few enough that the
-    // launch spreads over every SM (>= 2 CTAs per SM when there is enough work).
+    // Columns per CTA: at most ~64 KB of shared memory (32 KB double-float), and few
+    // enough that the launch spreads over every SM.
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -227,8 +227,11 @@ int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batc
     // double-float: half the tile, so that more CTAs (and warps) share an SM
     const int64_t budget_elems = (int64_t)((std::is_same<R, dfloat>::value ? 32768 : 65536) / sizeof(V));
     int64_t tile64 = std::min<int64_t>(std::min<int64_t>(ncols, 64), std::max<int64_t>(1, budget_elems / Ls));
-    tile64 = std::min<int64_t>(tile64, std::max<int64_t>(1, ncols * batch / (2 * sms)));
-    const int tile = (int)std::max<int64_t>(1, tile64);
+    // at least four CTAs per SM when there is enough work (fewer, larger CTAs leave a
+    // partly empty last wave), and a power of two (shift/mask indexing)
+    tile64 = std::min<int64_t>(tile64, std::max<int64_t>(1, ncols * batch / (4 * sms)));
+    int tile = 1;
+    while ((int64_t)tile * 2 <= tile64) tile *= 2;
     size_t smem = (size_t)tile * (Ls + SMEM_PAD) * sizeof(V);
     const int threads = (int)std::min<int64_t>(FFT_THREADS, std::max<int64_t>(32, ((int64_t)tile * Ls / 4 + 31) / 32 * 32));
     int prc = cjt_fft_prime();
