@@ -50,6 +50,18 @@ __device__ __forceinline__ dfs df_add(dfs a, dfs b) {
 __device__ __forceinline__ dfs df_neg(dfs a) { return df_make(-a.h, -a.l); }
 __device__ __forceinline__ dfs df_sub(dfs a, dfs b) { return df_add(a, df_neg(b)); }
 
+// a + b without the final renormalisation: (s, e) with s + e = a + b up to the rounding
+// of a.l + b.l, e possibly above ulp(s)/2.  For intermediate sums that feed another
+// addition straight away (which renormalises); its error bound is the same multiple of
+// 2^-48 (|a| + |b|).
+__device__ __forceinline__ dfs df_add_nr(dfs a, dfs b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    return df_make(s, e);
+}
+
 // a * b
 __device__ __forceinline__ dfs df_mul(dfs a, dfs b) {
     const float p = __fmul_rn(a.h, b.h);
@@ -86,6 +98,10 @@ __device__ __forceinline__ dfs dfc_im(dfc a) { return df_make(a.ih, a.il); }
 __device__ __forceinline__ dfc dfc_zero() { dfc r; r.rh = r.rl = r.ih = r.il = 0.0f; return r; }
 __device__ __forceinline__ dfc dfc_add(dfc a, dfc b) { return dfc_make(df_add(dfc_re(a), dfc_re(b)), df_add(dfc_im(a), dfc_im(b))); }
 __device__ __forceinline__ dfc dfc_sub(dfc a, dfc b) { return dfc_make(df_sub(dfc_re(a), dfc_re(b)), df_sub(dfc_im(a), dfc_im(b))); }
+__device__ __forceinline__ dfc dfc_add_nr(dfc a, dfc b) { return dfc_make(df_add_nr(dfc_re(a), dfc_re(b)), df_add_nr(dfc_im(a), dfc_im(b))); }
+__device__ __forceinline__ dfc dfc_sub_nr(dfc a, dfc b) {
+    return dfc_make(df_add_nr(dfc_re(a), df_neg(dfc_re(b))), df_add_nr(dfc_im(a), df_neg(dfc_im(b))));
+}
 // a * w
 __device__ __forceinline__ dfc dfc_mul(dfc a, dfc w) {
     const dfs ar = dfc_re(a), ai = dfc_im(a), wr = dfc_re(w), wi = dfc_im(w);

@@ -52,7 +52,12 @@ template <typename V> __device__ __forceinline__ V cscale(V a, double s) {
     a.y = a.y * (decltype(a.y))s;
     return a;
 }
+// sums inside a butterfly that feed another sum at once (double-float: not renormalised)
+template <typename V> __device__ __forceinline__ V cadd_t(V a, V b) { return cadd(a, b); }
+template <typename V> __device__ __forceinline__ V csub_t(V a, V b) { return csub(a, b); }
 template <> __device__ __forceinline__ dfc cadd(dfc a, dfc b) { return dfc_add(a, b); }
+template <> __device__ __forceinline__ dfc cadd_t(dfc a, dfc b) { return dfc_add_nr(a, b); }
+template <> __device__ __forceinline__ dfc csub_t(dfc a, dfc b) { return dfc_sub_nr(a, b); }
 template <> __device__ __forceinline__ dfc csub(dfc a, dfc b) { return dfc_sub(a, b); }
 template <> __device__ __forceinline__ dfc cmul(dfc a, dfc b) { return dfc_mul(a, b); }
 template <> __device__ __forceinline__ dfc cmul_mi(dfc a) { return dfc_mul_mi(a); }
@@ -133,11 +138,11 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
         const int Lb = 1 << lb, h = Lb >> 2;
         const int twstep_log = logLtab - lb;  // omega_{Lb}^j = tw[j << (logLtab - lb)]
         for (int idx = threadIdx.x; idx < ncl * nb4; idx += blockDim.x) {
-            int c = idx / nb4, j = idx - c * nb4;
+            const int c = idx >> (logLs - 2), j = idx & (nb4 - 1);   // nb4 = Ls/4
             int blk = j >> (lb - 2), n0 = j & (h - 1);
             V *b = s + c * ld + blk * Lb + n0;
             V x0 = b[0], x1 = b[h], x2 = b[2 * h], x3 = b[3 * h];
-            V t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = cmul_mi(csub(x1, x3));
+            V t0 = cadd_t(x0, x2), t1 = csub_t(x0, x2), t2 = cadd_t(x1, x3), t3 = cmul_mi(csub_t(x1, x3));
             V y0 = cadd(t0, t2), y2 = csub(t0, t2), y1 = cadd(t1, t3), y3 = csub(t1, t3);
             if (n0 != 0) {
                 if (stw) {
@@ -159,7 +164,7 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
     if (lb == 1) {
         const int nb2 = Ls >> 1;
         for (int idx = threadIdx.x; idx < ncl * nb2; idx += blockDim.x) {
-            int c = idx / nb2, j = idx - c * nb2;
+            const int c = idx >> (logLs - 1), j = idx & (nb2 - 1);   // nb2 = Ls/2
             V *b = s + c * ld + 2 * j;
             V x0 = b[0], x1 = b[1];
             b[0] = cadd(x0, x1);
