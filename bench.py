@@ -193,12 +193,24 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
     else:
         items = inputs.batch_workload(args.batch_count)
         precision = precision_code(cjt, args.precision)
+    # plan options of the batch: M by size unless given; stored recurrence values for
+    # items with N <= store_max (the stored matrices of 4096 plans must fit beside them)
+    bopt = {}
+    for kv in filter(None, args.batch_options.split(",")):
+        k, v = kv.split("=")
+        bopt[k.strip()] = float(v) if k.strip() == "ratio" else int(v)
+    store_max = bopt.pop("store_max", 0 if big else 8192)
     t0 = time.perf_counter()
     plans = []
     for N, a, b, d, c in items:
-        M = 16 if big else (13 if N >= 16384 else 10)
-        plans.append(cjt.Plan(N, a, b, M=M, seg_len=256 if not big else 1024, precision=precision,
-                              directions=cjt.CJT_FWD if d == 1 else cjt.CJT_INV, shared_workspace=True))
+        # the batch's N are mostly not powers of two: Bluestein transforms cost 3-5x a
+        # power-of-two transform, so fewer asymptotic blocks (ratio 0.05) win
+        opts = {"M": 16, "seg_len": 1024} if big else {"M": 10, "seg_len": 256, "ratio": 0.05}
+        opts.update(bopt)
+        if N <= store_max:
+            opts["rec_store"] = 1
+        plans.append(cjt.Plan(N, a, b, precision=precision, directions=cjt.CJT_FWD if d == 1 else cjt.CJT_INV,
+                              shared_workspace=True, **opts))
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
     dirs = [1 if d == 1 else 2 for _, _, _, d, _ in items]
@@ -318,6 +330,8 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
                         "each, random forward/inverse, c_n=g_n/(n+1); %s; one captured CUDA graph per step"
                         % (len(items), PREC_NAMES[args.precision])),
                        "coefficients_per_step": coeffs, "lanes": args.lanes,
+                       "plan_options": args.batch_options or ("M=16, seg_len=1024" if big else
+                                                               "M=10, seg_len=256, ratio=0.05, rec_store for N <= 8192"),
                        "l2": "inputs (%.0f MB) exceed L2; flushed between steps" % (coeffs * 8 / 1e6)},
             "error": ({"vs_fp64_gpu_max_abs_over_l1": max(err64) if err64 else None,
                        "vs_oracle_sampled_values_max_abs_over_l1": max(errs) if errs else None,
@@ -392,6 +406,8 @@ def main():
     ap.add_argument("--planners", type=int, default=4)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--lanes", type=int, default=16)
+    ap.add_argument("--batch-options", default="",
+                    help="batched plans, overriding the defaults, e.g. M=7,ratio=0.02,store_max=4096")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
