@@ -3,16 +3,22 @@
 // forward (Eq. "CJT"):
 //   REC  k_rec_fwd      y_i^REC = sum_{n < J(i)} c_n P_n(x_i): Clenshaw--Smith for
 //                       pi/4 < theta_i < 3pi/4, Reinsch-modified (x0 = +-1) otherwise
-//                       (Sec. 4.2), one warp per (32 rows x degree segment)
-//   ASY  k_asy_pack_fwd a_{k,m}[n] = C_{n,m} c_n on degrees n >= j_k, two (k,m) per complex vector
+//                       (Sec. 4.2), one warp per (32 rows x degree segment);
+//                       k_rec_fwd_stored(_df): the same sums from the plan's stored values
+//   ASY  k_asy_pack_fwd_s / _df   a_{k,m}[n] = C_{n,m} c_n on degrees n >= j_k (pre-scaled
+//                       tables), two (k,m) per complex vector
 //        FFT            DCT-I and DST-I sums at theta_i (Eq. "PNASY")
-//   sum  k_combine_fwd  y_i = REC partials + sum_m u_m Re F - v_m Im F on the deepest box of row i
+//   sum  k_combine_fwd(_df)  y_i = REC partials + sum_m u_m Re F - v_m Im F on the deepest
+//                       box of row i
 //   DCT  FFT + k_dct_finish   c_cheb = T_N^{-1} y (inverse scaled DCT-I)
 // inverse (Eq. "CJTT"):
 //   front  FFT of [c_cheb; 0] -> p_N on the 2N grid, g = w o p_N (Clenshaw--Curtis weights)
-//   ASY^T  k_asy_pack_inv + FFT: Re sum_i (u_m + i v_m) g_i e^{-i n theta_i} per (k,m) box
-//   REC^T  k_rec_inv     forward recurrence g_i P_n(x_i) (Reinsch-modified near +-1), column sums
+//   ASY^T  k_asy_pack_inv_s / _df + FFT: Re sum_i (u_m + i v_m) g_i e^{-i n theta_i} per (k,m) box
+//   REC^T  k_rec_inv / k_rec_inv_stored(_df): g_i P_n(x_i) summed over each item's rows,
+//          then k_inv_reduce over the items of each degree
 //   sum    k_combine_inv y_n = REC^T + sum_m C_{n,m} ASY^T, c_jac_n = y_n / A_n
+// The double-float form (CJT_DFLOAT) scales its input by an exact power of two first
+// (k_absmax_exp, k_to_dfs_scaled) and undoes the scaling in the combines.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -373,17 +379,27 @@ __global__ void __launch_bounds__(32 * SW) k_rec_fwd_stored_df(const RecItem *__
     const int k0 = min(len, w * per), k1 = min(len, k0 + per);
     const float2 *e = reinterpret_cast<const float2 *>(E + it.eoff) + lane;
     const dfs *cc = cdf + it.a;
-    // eight streaming loads in flight per lane, four independent accumulators
+    // eight streaming loads per lane, the next eight issued before the current ones are
+    // used (software pipelining: the arithmetic is long enough to hide a load otherwise),
+    // four independent accumulators
     dfs acc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[j] = df_make(0.f, 0.f);
     int k = k0;
-    for (; k + 8 <= k1; k += 8) {
+    if (k + 8 <= k1) {
         float2 v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = __ldcs(e + (int64_t)(k + j) * 32);
+        for (; k + 8 <= k1; k += 8) {
+            float2 vn[8];
+            const bool more = k + 16 <= k1;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j & 3] = df_mac(acc[j & 3], df_make(v[j].x, v[j].y), cc[k + j]);
+            for (int j = 0; j < 8; ++j) vn[j] = more ? __ldcs(e + (int64_t)(k + 8 + j) * 32) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j & 3] = df_mac(acc[j & 3], df_make(v[j].x, v[j].y), cc[k + j]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = vn[j];
+        }
     }
     for (; k < k1; ++k) {
         const float2 v = __ldcs(e + (int64_t)k * 32);
@@ -418,12 +434,21 @@ __global__ void __launch_bounds__(32 * SW) k_rec_inv_stored_df(const RecItem *__
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[j] = df_make(0.f, 0.f);
             int r = 0;
-            for (; r + 8 <= nr; r += 8) {
+            if (r + 8 <= nr) {   // as in the forward kernel: the next eight rows load during this eight's arithmetic
                 float2 v[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) v[j] = __ldcs(e + (int64_t)(r + j) * len + k);
+                for (; r + 8 <= nr; r += 8) {
+                    float2 vn[8];
+                    const bool more = r + 16 <= nr;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[j & 3] = df_mac(acc[j & 3], gs[r + j], df_make(v[j].x, v[j].y));
+                    for (int j = 0; j < 8; ++j)
+                        vn[j] = more ? __ldcs(e + (int64_t)(r + 8 + j) * len + k) : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[j & 3] = df_mac(acc[j & 3], gs[r + j], df_make(v[j].x, v[j].y));
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = vn[j];
+                }
             }
             for (; r < nr; ++r) {
                 const float2 v = __ldcs(e + (int64_t)r * len + k);

@@ -89,7 +89,7 @@ struct GridWork {
     // doubles, or double-floats (dfs, same 8 bytes) when E_df
     double *d_E = nullptr;
     bool E_df = false;
-    bool uv_df = false;           // forward grid: u, v held as double-floats (CJT_DFLOAT)
+    bool uv_df = false;           // forward grid: u, v held as double-floats, premultiplied (CJT_DFLOAT)
     int64_t nE = 0;
     // diagonals u_m, v_m on this grid
     double *d_u = nullptr, *d_v = nullptr;

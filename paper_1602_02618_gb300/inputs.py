@@ -95,3 +95,15 @@ def mixed_large_workload(count: int = 64, N: int = 1 << 20, seed: int = BASE_SEE
         a, b = r.uniform(-0.45, 0.45, 2)
         out.append((N, float(a), float(b), 1 if t % 2 == 0 else -1, decaying_coefficients(N, 1.0, seed + 6000 + t)))
     return out
+
+
+def irregular_coefficients(N: int, seed: int = BASE_SEED) -> np.ndarray:
+    """c_n ~ U(0,1): coefficients of an irregular function (the paper's Fig. 3, left)."""
+    return rng(seed).uniform(0.0, 1.0, N + 1)
+
+
+def continuous_coefficients(N: int, seed: int = BASE_SEED) -> np.ndarray:
+    """c_n ~ U(-1,1) / (n+1)^2: coefficients of a continuous function (the paper's Fig. 3,
+    right; (n+1) so that c_0 is finite)."""
+    n = np.arange(N + 1, dtype=np.float64)
+    return rng(seed).uniform(-1.0, 1.0, N + 1) / (n + 1.0) ** 2
