@@ -68,6 +68,12 @@ template <> __device__ __forceinline__ dfc cscale(dfc a, double s) { return dfc_
 constexpr int FFT_THREADS = 256;
 constexpr int SMEM_PAD = 1;
 
+// Shared-memory position of element e of a column: the low three bits are XORed with a
+// fold of the higher bits.  A bijection on [0, Ls) that spreads the accesses that would
+// otherwise share banks (16-byte elements, eight per 128-byte row): the digit-reversed
+// read-out and the last radix-4 / radix-2 stages.
+__device__ __forceinline__ int swz(int e) { return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9)) & 7); }
+
 // frequency k -> its position after the DIF stages: the base-4 digits of k's low
 // 2*floor(logLs/2) bits in reverse order (bit reversal, then the two bits of each digit
 // swapped back), and for odd logLs the top (radix-2) bit of k at weight 1
@@ -121,7 +127,7 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
                     e = pow2c ? (idx >> lgc) : idx / ncl;
                     g = c * in_cs + (int64_t)e * in_es;
                 }
-                at[u] = c * ld + e;
+                at[u] = c * ld + swz(e);
                 v[u] = src[g];
             }
         }
@@ -140,8 +146,10 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
         for (int idx = threadIdx.x; idx < ncl * nb4; idx += blockDim.x) {
             const int c = idx >> (logLs - 2), j = idx & (nb4 - 1);   // nb4 = Ls/4
             int blk = j >> (lb - 2), n0 = j & (h - 1);
-            V *b = s + c * ld + blk * Lb + n0;
-            V x0 = b[0], x1 = b[h], x2 = b[2 * h], x3 = b[3 * h];
+            V *col = s + c * ld;
+            const int e0 = blk * Lb + n0;
+            const int i0 = swz(e0), i1 = swz(e0 + h), i2 = swz(e0 + 2 * h), i3 = swz(e0 + 3 * h);
+            V x0 = col[i0], x1 = col[i1], x2 = col[i2], x3 = col[i3];
             V t0 = cadd_t(x0, x2), t1 = csub_t(x0, x2), t2 = cadd_t(x1, x3), t3 = cmul_mi(csub_t(x1, x3));
             V y0 = cadd(t0, t2), y2 = csub(t0, t2), y1 = cadd(t1, t3), y3 = csub(t1, t3);
             if (n0 != 0) {
@@ -156,7 +164,7 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
                     y3 = cmul(y3, tw[(int64_t)(3 * n0) << twstep_log]);
                 }
             }
-            b[0] = y0; b[h] = y1; b[2 * h] = y2; b[3 * h] = y3;
+            col[i0] = y0; col[i1] = y1; col[i2] = y2; col[i3] = y3;
         }
         __syncthreads();
         lb -= 2;
@@ -165,10 +173,11 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
         const int nb2 = Ls >> 1;
         for (int idx = threadIdx.x; idx < ncl * nb2; idx += blockDim.x) {
             const int c = idx >> (logLs - 1), j = idx & (nb2 - 1);   // nb2 = Ls/2
-            V *b = s + c * ld + 2 * j;
-            V x0 = b[0], x1 = b[1];
-            b[0] = cadd(x0, x1);
-            b[1] = csub(x0, x1);
+            V *col = s + c * ld;
+            const int i0 = swz(2 * j), i1 = swz(2 * j + 1);
+            V x0 = col[i0], x1 = col[i1];
+            col[i0] = cadd(x0, x1);
+            col[i1] = csub(x0, x1);
         }
         __syncthreads();
     }
@@ -193,7 +202,7 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
                     k = pow2c ? (idx >> lgc) : idx / ncl;
                     at[u] = c * out_cs + (int64_t)k * out_ks;
                 }
-                v[u] = s[c * ld + dif_revinv(k, logLs)];
+                v[u] = s[c * ld + swz(dif_revinv(k, logLs))];
                 if (post_log >= 0) {
                     const int64_t ex = ((c0 + c) * (int64_t)k) & ((1LL << post_log) - 1);
                     w[u] = tw[ex << (logLtab - post_log)];
