@@ -210,6 +210,95 @@ __global__ void k_rec_states(int64_t nrows, const int *srow, int64_t Ng, int seg
     }
 }
 
+// Long rows (many segments): the states at the segment starts by a chunked scan.  The
+// recurrence is linear in its two-term state, so segment k maps the state at degree kS to
+// the state at degree (k+1)S by a 2x2 matrix: k_rec_seg_maps runs the same recurrence as
+// k_rec_states over segment k from the two unit states (its columns), one thread per
+// (row, segment); k_rec_seg_carry then applies the matrices in order, one thread per row.
+// The chain of S-step segments runs in parallel instead of one N-step chain per row.
+__device__ __forceinline__ void rec_row_setup(int row, int mode, int64_t Ng, const RecTables &t, double &x,
+                                              double &delta, const double *&Ce, const double *&rf) {
+    x = 0.0;
+    delta = 0.0;
+    Ce = rf = nullptr;
+    if (mode == REC_PLAIN) {
+        x = cospi((double)row / (double)Ng);
+    } else {
+        const bool plus = (mode == REC_REINSCH_P1);
+        if (plus) {
+            const double sv = sinpi((double)row / (2.0 * (double)Ng));
+            delta = -2.0 * sv * sv;
+        } else {
+            const double sv = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
+            delta = 2.0 * sv * sv;
+        }
+        Ce = plus ? t.Ce_p : t.Ce_m;
+        rf = plus ? t.rf_p : t.rf_m;
+    }
+}
+
+// lsrow: {row, mode, state_base, lane, nseg} per long row; loff[q] = first map of row q
+// (prefix sum of nseg - 1); maps[(loff[q] + k) * 4] = the two columns of segment k's map
+__global__ void k_rec_seg_maps(int64_t nlong, int64_t nmaps, const int *__restrict__ lsrow,
+                               const int64_t *__restrict__ loff, int64_t Ng, int seg_len, RecTables t,
+                               double *__restrict__ maps) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= nmaps) return;
+    int64_t lo = 0, hi = nlong - 1;   // the row q with loff[q] <= g < loff[q + 1]
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (loff[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const int64_t q = lo, k = g - loff[q];
+    const int *r = lsrow + 5 * q;
+    const int row = r[0], mode = r[1];
+    double x, delta;
+    const double *Ce, *rf;
+    rec_row_setup(row, mode, Ng, t, x, delta, Ce, rf);
+    const int64_t n0 = k * seg_len;
+    // columns: state (1, 0) and (0, 1) at degree n0
+    double p0 = 1.0, q0 = 0.0, p1 = 0.0, q1 = 1.0;
+    if (mode == REC_PLAIN) {
+#pragma unroll 4
+        for (int kk = 0; kk < seg_len; ++kk) {
+            const int64_t n = n0 + kk;
+            const double an = fma(__ldg(t.A + n), x, __ldg(t.B + n)), cn = __ldg(t.C + n);
+            const double pn0 = fma(an, p0, -cn * q0), pn1 = fma(an, p1, -cn * q1);
+            q0 = p0; p0 = pn0;
+            q1 = p1; p1 = pn1;
+        }
+    } else {
+#pragma unroll 4
+        for (int kk = 0; kk < seg_len; ++kk) {
+            const int64_t n = n0 + kk;
+            const double ad = __ldg(t.A + n) * delta, ce = __ldg(Ce + n), f = __ldg(rf + n);
+            const double e0 = fma(ad, p0, ce * q0), e1 = fma(ad, p1, ce * q1);
+            p0 = fma(p0, f, e0); q0 = e0;
+            p1 = fma(p1, f, e1); q1 = e1;
+        }
+    }
+    double *m = maps + g * 4;
+    m[0] = p0; m[1] = q0; m[2] = p1; m[3] = q1;
+}
+
+__global__ void k_rec_seg_carry(int64_t nlong, const int *__restrict__ lsrow, const int64_t *__restrict__ loff,
+                                const double *__restrict__ maps, double *__restrict__ states) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nlong) return;
+    const int *r = lsrow + 5 * q;
+    const int base = r[2], lane = r[3], nseg = r[4];
+    double a = 1.0, b = 0.0;   // (p, second state) at degree 0
+    for (int k = 0; k < nseg - 1; ++k) {
+        const double *m = maps + (loff[q] + k) * 4;
+        const double na = fma(a, m[0], b * m[2]), nb = fma(a, m[1], b * m[3]);
+        a = na;
+        b = nb;
+        double *st = states + ((int64_t)(base + k) * 32 + lane) * 2;
+        st[0] = a;
+        st[1] = b;
+    }
+}
+
 // --------------------------------------------------------------------------
 // pre-scaled transform inputs (the scale of each item is an exact power of two)
 // --------------------------------------------------------------------------
@@ -762,11 +851,49 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
     TRY(dalloc(p, &gw.d_states, std::max<int64_t>(nstate * 64, 1)));
     CJT_CUDA_TRY(cudaMemsetAsync(gw.d_states, 0, sizeof(double) * std::max<int64_t>(nstate * 64, 1), st));
     if (gw.nsrow > 0) {
-        TRY(dalloc(p, &gw.d_srow, (int64_t)srow.size()));
-        CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_srow, srow.data(), sizeof(int) * srow.size(), cudaMemcpyHostToDevice, st));
-        // one row per thread; 32-thread blocks spread the long chains over the SMs
-        k_rec_states<<<blocks_for(gw.nsrow, 32), 32, 0, st>>>(gw.nsrow, gw.d_srow, Ng, S, p->rt, gw.d_states);
-        CJT_CUDA_TRY(cudaGetLastError());
+        // rows with up to kShortSegs segments: one sequential chain per row (k_rec_states);
+        // longer rows: the chunked scan (k_rec_seg_maps, k_rec_seg_carry)
+        constexpr int kShortSegs = 16;
+        std::vector<int> shortrow, longrow;
+        std::vector<int64_t> loff;
+        int64_t nmaps = 0;
+        for (int64_t q = 0; q < gw.nsrow; ++q) {
+            const int *v = srow.data() + 6 * q;
+            if (v[5] <= kShortSegs) {
+                shortrow.insert(shortrow.end(), v, v + 6);
+            } else {
+                const int w[5] = {v[0], v[2], v[3], v[4], v[5]};
+                longrow.insert(longrow.end(), w, w + 5);
+                loff.push_back(nmaps);
+                nmaps += v[5] - 1;
+            }
+        }
+        const int64_t nshort = (int64_t)shortrow.size() / 6, nlong = (int64_t)longrow.size() / 5;
+        if (nshort > 0) {
+            TRY(dalloc(p, &gw.d_srow, (int64_t)shortrow.size()));
+            CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_srow, shortrow.data(), sizeof(int) * shortrow.size(),
+                                         cudaMemcpyHostToDevice, st));
+            // one row per thread; 32-thread blocks spread the chains over the SMs
+            k_rec_states<<<blocks_for(nshort, 32), 32, 0, st>>>(nshort, gw.d_srow, Ng, S, p->rt, gw.d_states);
+            CJT_CUDA_TRY(cudaGetLastError());
+        }
+        if (nlong > 0) {
+            int *d_l = nullptr;
+            int64_t *d_off = nullptr;
+            double *d_maps = nullptr;
+            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_l, sizeof(int) * longrow.size(), st));
+            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_off, sizeof(int64_t) * loff.size(), st));
+            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_maps, sizeof(double) * 4 * nmaps, st));
+            CJT_CUDA_TRY(cudaMemcpyAsync(d_l, longrow.data(), sizeof(int) * longrow.size(), cudaMemcpyHostToDevice, st));
+            CJT_CUDA_TRY(cudaMemcpyAsync(d_off, loff.data(), sizeof(int64_t) * loff.size(), cudaMemcpyHostToDevice, st));
+            k_rec_seg_maps<<<blocks_for(nmaps, 128), 128, 0, st>>>(nlong, nmaps, d_l, d_off, Ng, S, p->rt, d_maps);
+            k_rec_seg_carry<<<blocks_for(nlong, 64), 64, 0, st>>>(nlong, d_l, d_off, d_maps, gw.d_states);
+            CJT_CUDA_TRY(cudaGetLastError());
+            CJT_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors above go out of scope
+            cudaFreeAsync(d_maps, st);
+            cudaFreeAsync(d_off, st);
+            cudaFreeAsync(d_l, st);
+        }
     }
     gw.nE = eoff;
     if (p->opts.rec_store && gw.nitems > 0) {
