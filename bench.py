@@ -180,9 +180,9 @@ def cpu_baseline_sample():
 
 
 def run_batched(args, torch, cjt, dev, world, rank, dist):
-    """configs[2]: one step = a batch of transforms (N log-uniform in [64, 65536], own
+    """--config batched: one step = a batch of transforms (N log-uniform in [64, 65536], own
     (alpha, beta), random direction) replayed as one captured CUDA graph.
-    configs[3] (--config mixed64): 64 transforms at N = 2^20 in the mixed form, checked
+    --config mixed64: 64 transforms at N = 2^20 in the mixed form, checked
     against the plain FP64 GPU form and against the oracle at sampled points."""
     from paper_1602_02618_gb300 import inputs
     big = args.config == "mixed64"
@@ -353,7 +353,7 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
 
 
 def run_serving(args, torch, cjt, rank):
-    """configs[4]: Poisson arrivals at swept rates, continuous batching, 40 GB budget."""
+    """--config serving: Poisson arrivals at swept rates, continuous batching, 40 GB budget."""
     from paper_1602_02618_gb300 import inputs, serve
     precision = precision_code(cjt, args.precision)
     rates = [float(r) for r in args.rates.split(",")]

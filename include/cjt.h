@@ -71,6 +71,14 @@ extern "C" {
                                 final DCT-I in double.  Meets the FP64 error bound
                                 1e-12 ||c||_1 of this library's tests.                  */
 
+/* asymptotic expansion of the plan (cjt_plan_opts.expansion) */
+#define CJT_EXPANSION_AUTO 0           /* the ultraspherical formula when alpha = beta in
+                                          (-1/2, 1/2), Hahn's formula otherwise            */
+#define CJT_EXPANSION_HAHN 1           /* Hahn's formula for general (alpha, beta)
+                                          (Eq. "Jacasy", Sec. 2.1)                        */
+#define CJT_EXPANSION_ULTRASPHERICAL 2 /* alpha = beta = lambda - 1/2 (App. B.1): one
+                                          cosine per term (requires alpha = beta)         */
+
 /* directions a plan is built for */
 #define CJT_FWD 1
 #define CJT_INV 2
@@ -95,6 +103,12 @@ typedef struct {
                          the same stabilised forward recurrences, and keeps it in device
                          memory (8 bytes per recurrence step, rec_store_bytes); executions
                          then apply it with one fused multiply-add per entry             */
+    int expansion;    /* CJT_EXPANSION_AUTO (default), _HAHN or _ULTRASPHERICAL.  Both
+                         formulas give the same transform (to rounding); the
+                         ultraspherical one evaluates one cosine per term in the
+                         diagonals u_m, v_m instead of m+1 (App. B.1).  With Hahn's
+                         formula, alpha or beta = +-1/2 collapses each term to one cosine
+                         (App. B.2-B.3) in either case.                                  */
 } cjt_plan_opts;
 
 /* Summary of a plan (for reports and tests). Sizes are per direction. */
@@ -117,6 +131,7 @@ typedef struct {
     int64_t rec_store_bytes;            /* stored recurrence values (rec_store = 1)      */
     int shift_alpha, shift_beta;        /* 0 or 1: alpha - shift_alpha and beta - shift_beta
                                            lie in [-1/2, 1/2]                              */
+    int expansion;                      /* CJT_EXPANSION_HAHN or _ULTRASPHERICAL (used)    */
 } cjt_plan_info;
 
 /* Stages reported by cjt_get_profile (forward 0-4, inverse 5-9). */
@@ -289,6 +304,25 @@ int cjt_microbench_fma(int kind, double *flops, void *stream);
  */
 #define CJT_NOALLOC_MAX_N 65536
 int cjt_cheb_coeffs_noalloc(int64_t N, const double *values_dev, double *c_cheb_dev, void *stream);
+
+/*
+ * The plan's asymptotic expansion on the host (no GPU; for tests and reports).  The
+ * expansion is the one cjt_plan picks for (alpha, beta) in [-1/2, 1/2]^2 and the
+ * CJT_EXPANSION_* option `expansion`.
+ *   cjt_asy_coefficient: *C = C_{n,m} (Eq. "Cnmab" for Hahn's formula, App. B.1 for the
+ *       ultraspherical one), as the plan computes it (Eq. "Cnmabasy"/"Cnmabrec").
+ *   cjt_asy_eval: at theta = pi i / Ng with 0 < i < Ng,
+ *       *value = sum_{m<M} C_{n,m} [u_m(theta) cos(n theta) + v_m(theta) sin(n theta)]
+ *       (Eq. "Jacasyuv"), the M-term approximation of P_n^{(alpha,beta)}(cos theta), and
+ *       *bound = 2 C_{n,M} g_M(theta), the bound on its remainder that the partition uses
+ *       (Sec. 2.2; App. B.1: 2 C^lambda_{n,M} / sin^{M+lambda} theta).
+ * Errors: CJT_EINVAL (null pointer, n < 0, m outside 0..20, M outside 1..20, Ng outside
+ * [2, 2^30], i outside (0, Ng), an ultraspherical request with alpha != beta),
+ * CJT_EDOMAIN (alpha or beta outside [-1/2, 1/2]).
+ */
+int cjt_asy_coefficient(double alpha, double beta, int expansion, int64_t n, int m, double *C);
+int cjt_asy_eval(double alpha, double beta, int expansion, int M, int64_t n, int64_t i, int64_t Ng, double *value,
+                 double *bound);
 
 /* Wait for `stream` and report any CUDA error raised by earlier work. */
 int cjt_sync(void *stream);

@@ -30,12 +30,16 @@ CJT_MIXED = 1
 CJT_DFLOAT = 2
 CJT_FWD = 1
 CJT_INV = 2
+CJT_EXPANSION_AUTO = 0
+CJT_EXPANSION_HAHN = 1
+CJT_EXPANSION_ULTRASPHERICAL = 2
 
 
 class cjt_plan_opts(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("eps", ctypes.c_double), ("precision", ctypes.c_int),
                 ("directions", ctypes.c_int), ("ratio", ctypes.c_double), ("seg_len", ctypes.c_int),
-                ("use_asy", ctypes.c_int), ("shared_workspace", ctypes.c_int), ("rec_store", ctypes.c_int)]
+                ("use_asy", ctypes.c_int), ("shared_workspace", ctypes.c_int), ("rec_store", ctypes.c_int),
+                ("expansion", ctypes.c_int)]
 
 
 class cjt_plan_info(ctypes.Structure):
@@ -47,7 +51,8 @@ class cjt_plan_info(ctypes.Structure):
                 ("nfft_inv", ctypes.c_int64), ("rec_items_fwd", ctypes.c_int64), ("rec_items_inv", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("plan_ms", ctypes.c_double), ("kernels_fwd", ctypes.c_int64),
                 ("kernels_inv", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("rec_store_bytes", ctypes.c_int64), ("shift_alpha", ctypes.c_int), ("shift_beta", ctypes.c_int)]
+                ("rec_store_bytes", ctypes.c_int64), ("shift_alpha", ctypes.c_int), ("shift_beta", ctypes.c_int),
+                ("expansion", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -57,7 +62,7 @@ EXPORTED = ["cjt_plan_opts_default", "cjt_plan", "cjt_destroy", "cjt_get_info", 
             "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_strerror", "cjt_last_cuda_error",
             "cjt_version", "cjt_set_profiling", "cjt_get_profile", "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc",
             "cjt_forward_ws", "cjt_inverse_ws", "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info",
-            "cjt_batch_destroy", "cjt_jacobi_to_jacobi"]
+            "cjt_batch_destroy", "cjt_jacobi_to_jacobi", "cjt_asy_coefficient", "cjt_asy_eval"]
 
 NOALLOC_MAX_N = 65536
 
@@ -105,6 +110,8 @@ def load(path: str = LIB_PATH):
         lib.cjt_forward_ws.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.cjt_inverse_ws.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.cjt_jacobi_to_jacobi.argtypes = [vp, vp, vp, vp, vp]
+        lib.cjt_asy_coefficient.argtypes = [d, d, i, i64, i, ctypes.POINTER(d)]
+        lib.cjt_asy_eval.argtypes = [d, d, i, i, i64, i64, i64, ctypes.POINTER(d), ctypes.POINTER(d)]
         lib.cjt_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int8),
                                          ctypes.POINTER(i64), vp, vp, i]
         lib.cjt_batch_launch.argtypes = [vp, vp]
@@ -118,7 +125,8 @@ def load(path: str = LIB_PATH):
         for name in ("cjt_plan_opts_default", "cjt_plan", "cjt_get_info", "cjt_forward", "cjt_inverse",
                      "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_set_profiling", "cjt_get_profile",
                      "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc", "cjt_forward_ws", "cjt_inverse_ws",
-                     "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info", "cjt_jacobi_to_jacobi"):
+                     "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info", "cjt_jacobi_to_jacobi",
+                     "cjt_asy_coefficient", "cjt_asy_eval"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -158,10 +166,11 @@ class Plan:
 
     def __init__(self, N: int, alpha: float, beta: float, M: int = 0, eps: float = 0.0, precision: int = CJT_FP64,
                  directions: int = 0, ratio: float = 0.0, seg_len: int = 0, use_asy: int = 0,
-                 shared_workspace: bool = False, rec_store: int = 0, stream=None):
+                 shared_workspace: bool = False, rec_store: int = 0, expansion: int = CJT_EXPANSION_AUTO,
+                 stream=None):
         lib = load()
         o = cjt_plan_opts(M, eps, precision, directions, ratio, seg_len, use_asy, 1 if shared_workspace else 0,
-                          int(rec_store))
+                          int(rec_store), int(expansion))
         h = ctypes.c_void_p()
         _check(lib.cjt_plan(ctypes.byref(h), int(N), float(alpha), float(beta), ctypes.byref(o),
                             _stream_handle(stream)), "cjt_plan")
@@ -333,6 +342,23 @@ def microbench_fma(kind=True, stream=None) -> float:
     _check(load().cjt_microbench_fma(int(kind), ctypes.byref(v), _stream_handle(stream)),
            "cjt_microbench_fma")
     return v.value
+
+
+def asy_coefficient(alpha: float, beta: float, n: int, m: int, expansion: int = CJT_EXPANSION_AUTO) -> float:
+    """C_{n,m} of the expansion a plan for (alpha, beta) uses (host only, no GPU)."""
+    C = ctypes.c_double()
+    _check(load().cjt_asy_coefficient(float(alpha), float(beta), int(expansion), int(n), int(m), ctypes.byref(C)),
+           "cjt_asy_coefficient")
+    return C.value
+
+
+def asy_eval(alpha: float, beta: float, M: int, n: int, i: int, Ng: int, expansion: int = CJT_EXPANSION_AUTO):
+    """(value, bound): the plan's M-term expansion of P_n(cos(pi i / Ng)) and the bound on
+    its remainder that the partition uses (host only, no GPU)."""
+    v, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().cjt_asy_eval(float(alpha), float(beta), int(expansion), int(M), int(n), int(i), int(Ng),
+                               ctypes.byref(v), ctypes.byref(b)), "cjt_asy_eval")
+    return v.value, b.value
 
 
 def version() -> str:

@@ -133,6 +133,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
         if (opts->use_asy) o.use_asy = opts->use_asy;
         o.shared_workspace = opts->shared_workspace;
         o.rec_store = opts->rec_store;
+        o.expansion = opts->expansion;
     }
     if (o.M < 1 || o.M > 20) return CJT_EINVAL;
     if (!(o.eps > 0.0 && o.eps < 1.0)) return CJT_EINVAL;
@@ -140,6 +141,8 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     if (o.directions < 1 || o.directions > 3) return CJT_EINVAL;
     if (!(o.ratio == 0.0 || (o.ratio > 0.0 && o.ratio < 1.0))) return CJT_EINVAL;
     if (o.rec_store != 0 && o.rec_store != 1) return CJT_EINVAL;
+    if (o.expansion < CJT_EXPANSION_AUTO || o.expansion > CJT_EXPANSION_ULTRASPHERICAL) return CJT_EINVAL;
+    if (o.expansion == CJT_EXPANSION_ULTRASPHERICAL && alpha != beta) return CJT_EINVAL;
     if (o.seg_len < 32 || o.seg_len > (1 << 20) || (o.seg_len % 32) != 0) return CJT_EINVAL;
     if (N > (1LL << 21) && !is_pow2(N)) return CJT_EUNSUPPORTED;   // Bluestein lengths stay <= 2^24
 
@@ -196,6 +199,7 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
     info->beta = p->beta_user;
     info->shift_alpha = p->shift_a;
     info->shift_beta = p->shift_b;
+    info->expansion = p->expansion_used;
     info->M = p->M;
     info->precision = p->opts.precision;
     info->directions = p->opts.directions;
@@ -229,6 +233,48 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
         if (!(p->opts.directions & CJT_FWD)) info->kernels_fwd = 0;
         if (!(p->opts.directions & CJT_INV)) info->kernels_inv = 0;
     }
+    return CJT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the plan's asymptotic expansion on the host
+// ---------------------------------------------------------------------------
+namespace {
+int asy_host(double alpha, double beta, int expansion, AsyExp *e) {
+    if (!(alpha >= -0.5 && alpha <= 0.5) || !(beta >= -0.5 && beta <= 0.5)) return CJT_EDOMAIN;
+    if (expansion < CJT_EXPANSION_AUTO || expansion > CJT_EXPANSION_ULTRASPHERICAL) return CJT_EINVAL;
+    const bool corner = std::fabs(alpha) == 0.5 && std::fabs(beta) == 0.5;
+    return cjt_asy_make(alpha, beta, corner && alpha != beta ? CJT_EXPANSION_HAHN : expansion, e);
+}
+}  // namespace
+
+int cjt_asy_coefficient(double alpha, double beta, int expansion, int64_t n, int m, double *C) {
+    if (!C || n < 0 || m < 0 || m > 20) return CJT_EINVAL;
+    AsyExp e;
+    int rc = asy_host(alpha, beta, expansion, &e);
+    if (rc) return rc;
+    *C = cjt_asy_C(e, n, m);
+    return CJT_OK;
+}
+
+int cjt_asy_eval(double alpha, double beta, int expansion, int M, int64_t n, int64_t i, int64_t Ng, double *value,
+                 double *bound) {
+    if (!value || !bound || M < 1 || M > 20 || n < 0 || Ng < 2 || Ng > (1LL << 30) || i <= 0 || i >= Ng)
+        return CJT_EINVAL;
+    AsyExp e;
+    int rc = asy_host(alpha, beta, expansion, &e);
+    if (rc) return rc;
+    // cos(n theta), sin(n theta) with the argument reduced exactly: n i mod 2 Ng
+    const int64_t r = ((n % (2 * Ng)) * i) % (2 * Ng);
+    const double cn = cjt_host_cospi((double)r / (double)Ng), sn = cjt_host_sinpi((double)r / (double)Ng);
+    double s = 0.0;
+    for (int m = 0; m < M; ++m) {
+        double u, v;
+        cjt_asy_uv(e, m, i, Ng, &u, &v);
+        s += cjt_asy_C(e, n, m) * (u * cn + v * sn);
+    }
+    *value = s;
+    *bound = 2.0 * cjt_asy_C(e, n, M) * cjt_asy_env(e, M, i, Ng);
     return CJT_OK;
 }
 

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include <string>
 #include <vector>
 
@@ -156,6 +158,7 @@ struct cjt_plan_s {
     int64_t n_M = 0;
     double ratio = 0.5;
     bool corner = false;          // (alpha, beta) at a corner of the square: Hahn's series terminates
+    int expansion_used = CJT_EXPANSION_HAHN;   // the asymptotic formula of the plan
     int seg_len = 2048;
 
     RecTables rt{};
@@ -307,6 +310,176 @@ __host__ __device__ inline double cjt_hahn_h(int l, double a) {
     double r = 1.0;
     for (int k = 0; k < l; ++k) r *= (0.5 + a + k) * (0.5 - a + k) / (k + 1.0);
     return r;
+}
+
+// ---------------------------------------------------------------------------
+// The asymptotic expansion a plan uses.  Each term m has the DCT-I / DST-I form
+//   C_{n,m} [u_m(theta) cos(n theta) + v_m(theta) sin(n theta)]          (Eq. "Jacasyuv")
+// from cos(n theta - phi) = cos(n theta) cos(phi) + sin(n theta) sin(phi).
+//  * Hahn's formula for general (alpha, beta) (Eq. "Jacasy"): term m sums the m+1
+//    cosines h_l(a) h_{m-l}(b) cos(n theta - phi_{m,l}) / (sin^{l+a+1/2}(theta/2)
+//    cos^{m-l+b+1/2}(theta/2)), phi_{m,l} = (a+l+1/2) pi/2 - (a+b+m+1) theta/2.  Since
+//    h_l(+-1/2) = 0 for l >= 1, the sum keeps only l = 0 when a = +-1/2 and only l = m
+//    when b = +-1/2 (App. B.2-B.3): those terms are skipped, not evaluated.
+//  * The ultraspherical formula for alpha = beta = lambda - 1/2 (App. B.1): term m is the
+//    single cosine C^lambda_{n,m} cos(n theta - (m+lambda)(pi/2 - theta)) /
+//    sin^{m+lambda}(theta); for lambda in (0, 1) the remainder after M terms is below
+//    twice the first neglected term.
+// ---------------------------------------------------------------------------
+struct AsyExp {
+    int ultra = 0;            // 1: ultraspherical formula; 0: Hahn's formula
+    double a = 0, b = 0;      // Jacobi parameters (a = b when ultra)
+    double lam = 0;           // lambda = a + 1/2 (ultra)
+    double ha[21] = {0}, hb[21] = {0};   // h_l(a), h_l(b), l = 0..20
+};
+
+// C^lambda_{n,0} = 2^lambda Gamma(n+lambda+1/2) / (sqrt(pi) Gamma(n+lambda+1)).  With
+// x = n + lambda >= 9, the Stirling series (Sec. 4.1) gives the gamma ratio as
+// e^{1/2} (x+1)^{-1/2} exp(x log1p(-1/(2(x+1)))) S(x+1/2) / S(x+1); below, the downward
+// recurrence C^lambda_{n-1,0} = C^lambda_{n,0} (n+lambda) / (n+lambda-1/2).  Then
+// C^lambda_{n,m} = C^lambda_{n,m-1} (lambda+m-1)(m-lambda) / (2m(n+lambda+m))  (App. B.1).
+__host__ __device__ inline double cjt_ultra_C0_asy(double x) {
+    return 1.6487212707001281468 / sqrt(x + 1.0) * exp(x * log1p(-0.5 / (x + 1.0))) *
+           cjt_stirling_S(x + 0.5) / cjt_stirling_S(x + 1.0);
+}
+__host__ __device__ inline double cjt_ultra_C(int64_t n, int m, double lam) {
+    const int64_t n0 = (int64_t)ceil(9.0 - lam);
+    double C;
+    if (n >= n0) {
+        C = cjt_ultra_C0_asy((double)n + lam);
+    } else {
+        C = cjt_ultra_C0_asy((double)n0 + lam);
+        for (int64_t k = n0; k > n; --k) C = C * ((double)k + lam) / ((double)k + lam - 0.5);
+    }
+    C *= exp2(lam) * 0.56418958354775628695;   // 2^lambda / sqrt(pi)
+    for (int k = 1; k <= m; ++k) C = C * ((lam + k - 1.0) * (k - lam)) / (2.0 * k * ((double)n + lam + k));
+    return C;
+}
+
+// sin(pi x) and cos(pi x): the device's sinpi/cospi; on the host, sin and cos after an exact
+// reduction of x to [0, 1/2] (x mod 2, then 1 - r and 1/2 - r, exact by Sterbenz's lemma),
+// so that the values keep their relative accuracy near the zeros.
+inline double cjt_host_sinpi(double x) {
+    double r = std::fmod(std::fabs(x), 2.0), sg = x < 0 ? -1.0 : 1.0;
+    if (r >= 1.0) { r -= 1.0; sg = -sg; }
+    if (r > 0.5) r = 1.0 - r;
+    return sg * std::sin(3.14159265358979323846 * r);
+}
+inline double cjt_host_cospi(double x) {
+    double r = std::fmod(std::fabs(x), 2.0), sg = 1.0;
+    if (r >= 1.0) { r -= 1.0; sg = -1.0; }
+    if (r <= 0.25) return sg * std::cos(3.14159265358979323846 * r);
+    if (r <= 0.75) return sg * std::sin(3.14159265358979323846 * (0.5 - r));
+    return -sg * std::cos(3.14159265358979323846 * (1.0 - r));
+}
+__host__ __device__ inline void cjt_sincospi_(double x, double *s, double *c) {
+#ifdef __CUDA_ARCH__
+    sincospi(x, s, c);
+#else
+    *s = cjt_host_sinpi(x);
+    *c = cjt_host_cospi(x);
+#endif
+}
+__host__ __device__ inline double cjt_sinpi_(double x) {
+#ifdef __CUDA_ARCH__
+    return sinpi(x);
+#else
+    return cjt_host_sinpi(x);
+#endif
+}
+__host__ __device__ inline double cjt_cospi_(double x) {
+#ifdef __CUDA_ARCH__
+    return cospi(x);
+#else
+    return cjt_host_cospi(x);
+#endif
+}
+
+// C_{n,m} of the plan's expansion
+__host__ __device__ inline double cjt_asy_C(const AsyExp &e, int64_t n, int m) {
+    return e.ultra ? cjt_ultra_C(n, m, e.lam) : cjt_hahn_C(n, m, e.a, e.b);
+}
+
+// Envelope of |term m| / C_{n,m} at theta = pi i / Ng, 0 < i < Ng: Hahn's g_m (Sec. 2.2),
+// or 1/sin^{m+lambda}(theta) (App. B.1)
+__host__ __device__ inline double cjt_asy_env(const AsyExp &e, int m, int64_t i, int64_t Ng) {
+    if (e.ultra) return exp(-(m + e.lam) * log(cjt_sinpi_((double)i / (double)Ng)));
+    const double half = (double)i / (2.0 * (double)Ng);
+    const double ls = log(cjt_sinpi_(half)), lc = log(cjt_cospi_(half));
+    double s = 0.0;
+    for (int l = 0; l <= m; ++l) {
+        const double coef = e.ha[l] * e.hb[m - l];
+        if (coef == 0.0) continue;
+        s += coef * exp(-(l + e.a + 0.5) * ls - (m - l + e.b + 0.5) * lc);
+    }
+    return s;
+}
+
+// u_m and v_m at theta = pi i / Ng, 0 < i < Ng
+__host__ __device__ inline void cjt_asy_uv(const AsyExp &e, int m, int64_t i, int64_t Ng, double *u, double *v) {
+    if (e.ultra) {
+        const double x = (double)i / (double)Ng;
+        const double mag = exp(-(m + e.lam) * log(cjt_sinpi_(x)));
+        double s, c;
+        cjt_sincospi_((m + e.lam) * (0.5 - x), &s, &c);   // phi / pi = (m+lambda)(1/2 - theta/pi)
+        *u = mag * c;
+        *v = mag * s;
+        return;
+    }
+    const double half = (double)i / (2.0 * (double)Ng);
+    const double ls = log(cjt_sinpi_(half)), lc = log(cjt_cospi_(half));
+    double su = 0.0, sv = 0.0;
+    for (int l = 0; l <= m; ++l) {
+        const double coef = e.ha[l] * e.hb[m - l];
+        if (coef == 0.0) continue;
+        const double mag = coef * exp(-(l + e.a + 0.5) * ls - (m - l + e.b + 0.5) * lc);
+        // phi_{m,l} / pi = (a + l + 1/2)/2 - (a + b + m + 1) theta / (2 pi)
+        const double ph = 0.5 * (e.a + l + 0.5) - (e.a + e.b + m + 1.0) * half;
+        double s, c;
+        cjt_sincospi_(ph, &s, &c);
+        su = fma(mag, c, su);
+        sv = fma(mag, s, sv);
+    }
+    *u = su;
+    *v = sv;
+}
+
+// The expansion for (a, b) in [-1/2, 1/2]^2 and the plan option (CJT_EXPANSION_*):
+// ultraspherical when requested or by default when a = b with lambda in (0, 1).
+// Returns CJT_EINVAL for an ultraspherical request with a != b.
+inline int cjt_asy_make(double a, double b, int option, AsyExp *e) {
+    *e = AsyExp{};
+    e->a = a;
+    e->b = b;
+    for (int l = 0; l <= 20; ++l) { e->ha[l] = cjt_hahn_h(l, a); e->hb[l] = cjt_hahn_h(l, b); }
+    if (option == CJT_EXPANSION_ULTRASPHERICAL && a != b) return CJT_EINVAL;
+    const bool interior = a > -0.5 && a < 0.5;
+    if (option != CJT_EXPANSION_HAHN && a == b && interior) {
+        e->ultra = 1;
+        e->lam = a + 0.5;
+    }
+    return CJT_OK;
+}
+
+// n_M (Sec. 2.2; App. B.1 for the ultraspherical formula): the degree above which the
+// M-term remainder bound at theta = pi/2 is below eps
+inline int64_t cjt_asy_nM(const AsyExp &e, int M, double eps) {
+    double v;
+    if (e.ultra) {
+        double poch = 1.0, fact = 1.0;   // (lambda)_M (1-lambda)_M and M!
+        for (int k = 0; k < M; ++k) { poch *= (e.lam + k) * (1.0 - e.lam + k); fact *= k + 1.0; }
+        if (!(poch > 0)) return 0;
+        v = std::pow(eps * 1.77245385090551602730 * std::ldexp(fact, M) / (std::exp2(e.lam + 1.0) * poch),
+                     -1.0 / (M + 0.5));
+    } else {
+        // g_M(pi/2) = sum_l h_l(a) h_{M-l}(b) 2^{(M+a+b+1)/2}
+        double gh = 0.0;
+        for (int l = 0; l <= M; ++l) gh += e.ha[l] * e.hb[M - l];
+        gh *= std::pow(2.0, 0.5 * (M + e.a + e.b + 1.0));
+        if (!(gh > 0)) return 0;
+        v = std::pow(eps * std::ldexp(1.0, 2 * M - 1) * 1.77245385090551602730 / gh, -1.0 / (M + 0.5));
+    }
+    return (int64_t)std::floor(v);
 }
 
 // ---------------------------------------------------------------------------

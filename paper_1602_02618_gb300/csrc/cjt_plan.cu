@@ -16,12 +16,6 @@
 
 namespace {
 
-constexpr double kSqrtPi = 1.77245385090551602730;
-
-struct HahnH {
-    double ha[21];  // h_l(alpha)
-    double hb[21];  // h_l(beta)
-};
 
 // --------------------------------------------------------------------------
 // 1c: recurrence coefficients (Sec. 1.2) and Reinsch ratios at x0 = +-1 (Sec. 4.2)
@@ -70,59 +64,36 @@ __global__ void k_rec_tables(int64_t nmax, double a, double b, RecTables t) {
 }
 
 // --------------------------------------------------------------------------
-// Hahn coefficients C_{n,m} (Eq. "Cnmab", computed by Eq. "Cnmabasy"/"Cnmabrec")
+// Coefficients C_{n,m} of the plan's expansion: Hahn's (Eq. "Cnmab", computed by
+// Eq. "Cnmabasy"/"Cnmabrec") or the ultraspherical C^lambda_{n,m} (App. B.1)
 // --------------------------------------------------------------------------
-__global__ void k_hahn_C(int64_t N, int Mp1, double a, double b, double *Cnm) {
+__global__ void k_hahn_C(int64_t N, int Mp1, AsyExp e, double *Cnm) {
     int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int m = blockIdx.y;
     if (n > N || m >= Mp1) return;
-    Cnm[m * (N + 1) + n] = cjt_hahn_C(n, m, a, b);
+    Cnm[m * (N + 1) + n] = cjt_asy_C(e, n, m);
 }
 
 // --------------------------------------------------------------------------
-// diagonals u_m(theta_i), v_m(theta_i) (Eq. "Jacasyuv") on the grid theta_i = pi i / Ng
+// diagonals u_m(theta_i), v_m(theta_i) (Eq. "Jacasyuv"; App. B.1) on the grid
+// theta_i = pi i / Ng
 // --------------------------------------------------------------------------
-__global__ void k_hahn_uv(int64_t Ng, int M, double a, double b, HahnH h, double *u, double *v) {
+__global__ void k_hahn_uv(int64_t Ng, int M, AsyExp e, double *u, double *v) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i > Ng) return;
-    if (i == 0 || i == Ng) {
-        for (int m = 0; m < M; ++m) { u[m * (Ng + 1) + i] = 0.0; v[m * (Ng + 1) + i] = 0.0; }
-        return;
-    }
-    const double half = (double)i / (2.0 * (double)Ng);   // theta/(2 pi)... theta/2 = pi * half
-    const double ls = log(sinpi(half)), lc = log(cospi(half));
     for (int m = 0; m < M; ++m) {
         double su = 0.0, sv = 0.0;
-        for (int l = 0; l <= m; ++l) {
-            const double coef = h.ha[l] * h.hb[m - l];
-            if (coef == 0.0) continue;
-            const double mag = coef * exp(-(l + a + 0.5) * ls - (m - l + b + 0.5) * lc);
-            // theta_{m,l}/pi = (a + l + 1/2)/2 - (a + b + m + 1) theta / (2 pi)
-            const double ph = 0.5 * (a + l + 0.5) - (a + b + m + 1.0) * half;
-            double s, c;
-            sincospi(ph, &s, &c);
-            su = fma(mag, c, su);
-            sv = fma(mag, s, sv);
-        }
+        if (i != 0 && i != Ng) cjt_asy_uv(e, m, i, Ng, &su, &sv);
         u[m * (Ng + 1) + i] = su;
         v[m * (Ng + 1) + i] = sv;
     }
 }
 
-// envelope g_M(theta_i) of |f_M| (Sec. 2.2); +inf at the end points
-__global__ void k_envelope(int64_t Ng, int M, double a, double b, HahnH h, double *g) {
+// envelope of the remainder term M (Sec. 2.2; App. B.1); +inf at the end points
+__global__ void k_envelope(int64_t Ng, int M, AsyExp e, double *g) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i > Ng) return;
-    if (i == 0 || i == Ng) { g[i] = INFINITY; return; }
-    const double half = (double)i / (2.0 * (double)Ng);
-    const double ls = log(sinpi(half)), lc = log(cospi(half));
-    double s = 0.0;
-    for (int l = 0; l <= M; ++l) {
-        const double coef = h.ha[l] * h.hb[M - l];
-        if (coef == 0.0) continue;
-        s += coef * exp(-(l + a + 0.5) * ls - (M - l + b + 0.5) * lc);
-    }
-    g[i] = s;
+    g[i] = (i == 0 || i == Ng) ? INFINITY : cjt_asy_env(e, M, i, Ng);
 }
 
 __global__ void k_box_init(int nk, int *box) {
@@ -585,9 +556,8 @@ template <typename T> int dalloc(cjt_plan_s *p, T **ptr, int64_t count) {
 // ------------------------------------------------------------------------
 // partition of one grid (Sec. 2.2) and the recurrence work that remains
 // ------------------------------------------------------------------------
-int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const HahnH &h, cudaStream_t st) {
+int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyExp &h, cudaStream_t st) {
     PlanTrace tr(st);
-    const double a = p->alpha, b = p->beta;
     const int M = p->M;
     gw.Ng = Ng;
     gw.Jcap = p->N + 1;
@@ -613,7 +583,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
             int64_t j = (int64_t)std::floor(pw * (double)Ng);
             if (j <= p->n_M || j < 2) break;
             js.push_back(j);
-            thr.push_back(p->opts.eps / (2.0 * cjt_hahn_C(j, M, a, b)));
+            thr.push_back(p->opts.eps / (2.0 * cjt_asy_C(h, j, M)));
         }
         if (!js.empty()) {
             double *d_g = nullptr, *d_thr = nullptr;
@@ -621,7 +591,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
             CJT_CUDA_TRY(cudaMallocAsync((void **)&d_g, sizeof(double) * (Ng + 1), st));
             CJT_CUDA_TRY(cudaMallocAsync((void **)&d_thr, sizeof(double) * thr.size(), st));
             CJT_CUDA_TRY(cudaMallocAsync((void **)&d_b2, sizeof(int) * 2 * thr.size(), st));
-            k_envelope<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, M, a, b, h, d_g);
+            k_envelope<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, M, h, d_g);
             CJT_CUDA_TRY(cudaMemcpyAsync(d_thr, thr.data(), sizeof(double) * thr.size(), cudaMemcpyHostToDevice, st));
             k_box_init<<<1, 64, 0, st>>>((int)thr.size(), d_b2);
             unsigned nb = std::min<unsigned>(blocks_for(Ng, 256), 152 * 8);
@@ -659,7 +629,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
         CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_box, box3.data(), sizeof(int) * box3.size(), cudaMemcpyHostToDevice, st));
         TRY(dalloc(p, &gw.d_u, (int64_t)M * (Ng + 1)));
         TRY(dalloc(p, &gw.d_v, (int64_t)M * (Ng + 1)));
-        k_hahn_uv<<<blocks_for(Ng + 1, 128), 128, 0, st>>>(Ng, M, a, b, h, gw.d_u, gw.d_v);
+        k_hahn_uv<<<blocks_for(Ng + 1, 128), 128, 0, st>>>(Ng, M, h, gw.d_u, gw.d_v);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     if (gw.nblk > 0) {
@@ -672,17 +642,9 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const Hahn
             for (int m = 0; m < M; ++m) {
                 double mag;
                 if (!inverse) {
-                    mag = cjt_hahn_C(gw.jk[k], m, a, b);
+                    mag = cjt_asy_C(h, gw.jk[k], m);
                 } else {
-                    auto gm = [&](int64_t i) {
-                        const double half = (double)i / (2.0 * (double)Ng);
-                        const double ls = std::log(std::sin(M_PI * half)), lc = std::log(std::cos(M_PI * half));
-                        double s = 0.0;
-                        for (int l = 0; l <= m; ++l)
-                            s += h.ha[l] * h.hb[m - l] * std::exp(-(l + a + 0.5) * ls - (m - l + b + 0.5) * lc);
-                        return s;
-                    };
-                    mag = std::max(gm(gw.i1[k]), gm(gw.i2[k]));
+                    mag = std::max(cjt_asy_env(h, m, gw.i1[k], Ng), cjt_asy_env(h, m, gw.i2[k], Ng));
                 }
                 int e = 0;
                 if (mag > 0 && std::isfinite(mag)) std::frexp(mag, &e);
@@ -923,20 +885,12 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     p->M = p->corner ? 1 : p->opts.M;
     const int M = p->M;
 
-    HahnH h;
-    for (int l = 0; l <= 20; ++l) { h.ha[l] = cjt_hahn_h(l, a); h.hb[l] = cjt_hahn_h(l, b); }
-    // n_M from the envelope at pi/2 (Sec. 2.2): g_M(pi/2) = sum_l h_l(a) h_{M-l}(b) 2^{(M+a+b+1)/2}
-    {
-        double gh = 0.0;
-        for (int l = 0; l <= M; ++l) gh += h.ha[l] * h.hb[M - l];
-        gh *= std::pow(2.0, 0.5 * (M + a + b + 1.0));
-        if (gh > 0) {
-            double v = std::pow(p->opts.eps * std::ldexp(1.0, 2 * M - 1) * kSqrtPi / gh, -1.0 / (M + 0.5));
-            p->n_M = (int64_t)std::floor(v);
-        } else {
-            p->n_M = 0;
-        }
-    }
+    // the expansion (Hahn's formula, or the ultraspherical one for alpha = beta, App. B.1)
+    // and n_M from its remainder bound at pi/2 (Sec. 2.2)
+    AsyExp h;
+    TRY(cjt_asy_make(a, b, p->corner ? CJT_EXPANSION_HAHN : p->opts.expansion, &h));
+    p->expansion_used = h.ultra ? CJT_EXPANSION_ULTRASPHERICAL : CJT_EXPANSION_HAHN;
+    p->n_M = cjt_asy_nM(h, M, p->opts.eps);
 
     // 1c: recurrence tables for degrees 0..N+1
     p->Jcap = N + 1;
@@ -949,11 +903,11 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     k_rec_tables<<<blocks_for(nt, 256), 256, 0, st>>>(nt - 1, a, b, p->rt);
     CJT_CUDA_TRY(cudaGetLastError());
 
-    // Hahn coefficients for m = 0..M (row M is the partition's remainder term)
+    // coefficients C_{n,m} for m = 0..M (row M is the partition's remainder term)
     TRY(dalloc(p, &p->d_Cnm, (int64_t)(M + 1) * (N + 1)));
     {
         dim3 g(blocks_for(N + 1, 256), M + 1);
-        k_hahn_C<<<g, 256, 0, st>>>(N, M + 1, a, b, p->d_Cnm);
+        k_hahn_C<<<g, 256, 0, st>>>(N, M + 1, h, p->d_Cnm);
         CJT_CUDA_TRY(cudaGetLastError());
     }
 
