@@ -59,9 +59,11 @@ def measured_hbm_gbs():
         return 6800.0, "fallback HBM bandwidth 6.8 TB/s"
 
 
-def workload_desc(precision):
-    return ("forward+inverse CJT singly, %s, N in {2^12,2^14,2^16,2^18}, alpha,beta~U[-0.45,0.45] per transform, "
-            "c_n=g_n/(n+1)^1.5, g~N(0,1)" % PREC_NAMES[precision])
+def workload_desc(precision, params=""):
+    ab = ("(alpha,beta)=(%s) for every transform" % params) if params else \
+        "alpha,beta~U[-0.45,0.45] per transform"
+    return ("forward+inverse CJT singly, %s, N in {2^12,2^14,2^16,2^18}, %s, "
+            "c_n=g_n/(n+1)^1.5, g~N(0,1)" % (PREC_NAMES[precision], ab))
 
 
 class ClockSampler:
@@ -406,6 +408,10 @@ def main():
     ap.add_argument("--planners", type=int, default=4)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--lanes", type=int, default=16)
+    ap.add_argument("--params", default="",
+                    help="fixed (alpha, beta) for every transform of the single workload, e.g. 0,0 (Legendre)")
+    ap.add_argument("--expansion", choices=["auto", "hahn", "ultra"], default="auto",
+                    help="asymptotic formula of the plans (ultra: App. B.1, needs alpha = beta)")
     ap.add_argument("--batch-options", default="",
                     help="batched plans, overriding the defaults, e.g. M=7,ratio=0.02,store_max=4096")
     args = ap.parse_args()
@@ -443,6 +449,11 @@ def main():
     items = workload()
     if args.only_logn:
         items = [it for it in items if it[0] == (1 << args.only_logn)]
+    if args.params:
+        pa, pb = (float(v) for v in args.params.split(","))
+        items = [(N, pa, pb, c) for N, _, _, c in items]
+    expansion = {"auto": cjt.CJT_EXPANSION_AUTO, "hahn": cjt.CJT_EXPANSION_HAHN,
+                 "ultra": cjt.CJT_EXPANSION_ULTRASPHERICAL}[args.expansion]
     fixed = {}
     for kv in filter(None, args.fixed_options.split(",")):
         k, v = kv.split("=")
@@ -450,6 +461,8 @@ def main():
     plans, xs, ys, zs, chosen = [], [], [], [], []
     for N, a, b, c in items:
         opts = dict(fixed) if (fixed or args.no_autotune) else autotune.best_options(N, a, b, precision)
+        if expansion != cjt.CJT_EXPANSION_AUTO:
+            opts["expansion"] = expansion
         plans.append(cjt.Plan(N, a, b, precision=precision, **opts))
         chosen.append(opts)
         xs.append(torch.from_numpy(c).to(dev))
@@ -615,9 +628,12 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision],
             "data": "synthetic",
-            "config": {"workload": workload_desc(args.precision), "N": [1 << k for k in LOGNS],
+            "config": {"workload": workload_desc(args.precision, args.params), "N": [it[0] for it in items],
                        "options": chosen, "l2": "flushed between steps (512 MiB write, outside timed events)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "plan_ms": [round(inf["plan_ms"], 2) for inf in infos],
+                       "expansion": [inf["expansion"] for inf in infos],
+                       "parity_fold": [inf["parity_fold"] for inf in infos]},
             "error": {"round_trip_max_abs_over_l1": err},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
             "roofline": roof,

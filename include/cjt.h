@@ -102,7 +102,9 @@ typedef struct {
                          1: the plan evaluates the recurrence part of the matrix once, with
                          the same stabilised forward recurrences, and keeps it in device
                          memory (8 bytes per recurrence step, rec_store_bytes); executions
-                         then apply it with one fused multiply-add per entry             */
+                         then apply it with one fused multiply-add per entry.  With
+                         alpha = beta the rows i > Ng/2 are not stored but folded
+                         (parity_fold of cjt_plan_info)                                  */
     int expansion;    /* CJT_EXPANSION_AUTO (default), _HAHN or _ULTRASPHERICAL.  Both
                          formulas give the same transform (to rounding); the
                          ultraspherical one evaluates one cosine per term in the
@@ -119,8 +121,9 @@ typedef struct {
     int64_t n_M;             /* Sec. 2.2, from the envelope g_M(pi/2)                  */
     double ratio;            /* alpha_N actually used                                   */
     int nblk_fwd, nblk_inv;  /* asymptotic blocks (grid N, grid 2N)                     */
-    int64_t rec_steps_fwd;   /* sum_i J(i): recurrence steps of one forward transform  */
-    int64_t rec_steps_inv;   /* sum_i min(J(i), N+1) on the 2N grid                     */
+    int64_t rec_steps_fwd;   /* sum_i J(i): recurrence steps of one forward transform
+                                (with the parity fold: over the rows i <= N/2 only)     */
+    int64_t rec_steps_inv;   /* sum_i min(J(i), N+1) on the 2N grid (likewise)          */
     int64_t fft_len_fwd, fft_len_inv;   /* transform lengths used by the ASY blocks     */
     int64_t nfft_fwd, nfft_inv;         /* complex transforms per execution             */
     int64_t rec_items_fwd, rec_items_inv;
@@ -132,6 +135,10 @@ typedef struct {
     int shift_alpha, shift_beta;        /* 0 or 1: alpha - shift_alpha and beta - shift_beta
                                            lie in [-1/2, 1/2]                              */
     int expansion;                      /* CJT_EXPANSION_HAHN or _ULTRASPHERICAL (used)    */
+    int parity_fold;                    /* 1 when alpha = beta with rec_store: the stored
+                                           recurrence covers the rows i <= Ng/2 and yields
+                                           rows Ng - i by P_n(-x) = (-1)^n P_n(x)
+                                           (DLMF 18.6.1), half the values and the work    */
 } cjt_plan_info;
 
 /* Stages reported by cjt_get_profile (forward 0-4, inverse 5-9). */

@@ -52,7 +52,7 @@ class cjt_plan_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("plan_ms", ctypes.c_double), ("kernels_fwd", ctypes.c_int64),
                 ("kernels_inv", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("rec_store_bytes", ctypes.c_int64), ("shift_alpha", ctypes.c_int), ("shift_beta", ctypes.c_int),
-                ("expansion", ctypes.c_int)]
+                ("expansion", ctypes.c_int), ("parity_fold", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -200,6 +200,7 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
     info->shift_alpha = p->shift_a;
     info->shift_beta = p->shift_b;
     info->expansion = p->expansion_used;
+    info->parity_fold = (p->fw.fold || p->iv.fold) ? 1 : 0;
     info->M = p->M;
     info->precision = p->opts.precision;
     info->directions = p->opts.directions;

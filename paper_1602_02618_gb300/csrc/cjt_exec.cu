@@ -176,11 +176,15 @@ __global__ void __launch_bounds__(32 * RI_WARPS) k_rec_inv(const RecItem *__rest
 // streaming loads in flight per lane), and the four partial sums are added in warp order.
 // Splitting the long items (rows near x = +-1) over four warps keeps the SMs busy to the
 // end of the launch.
+// The sums over even and odd degrees are kept apart (accumulator j takes the degrees
+// a + k + j, a and k even, so its parity is that of j): their sum is the row's partial,
+// and under the parity fold their difference is the mirrored row's, since
+// P_n(-x) = (-1)^n P_n(x) when alpha = beta.
 constexpr int SW = 4;
 __global__ void __launch_bounds__(32 * SW) k_rec_fwd_stored(const RecItem *__restrict__ items, int64_t nitems,
                                                             const double *__restrict__ c, const double *__restrict__ E,
                                                             double *__restrict__ partials) {
-    __shared__ double red[SW][32];
+    __shared__ double red_e[SW][32], red_o[SW][32];
     if ((int64_t)blockIdx.x >= nitems) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RecItem it = items[blockIdx.x];
@@ -201,34 +205,47 @@ __global__ void __launch_bounds__(32 * SW) k_rec_fwd_stored(const RecItem *__res
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[j] = fma(v[j], cv[j], acc[j]);
     }
-    for (; k < k1; ++k) acc[0] = fma(__ldcs(e + (int64_t)k * 32), __ldg(cc + k), acc[0]);
-    red[w][lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    for (; k < k1; ++k) acc[k & 1] = fma(__ldcs(e + (int64_t)k * 32), __ldg(cc + k), acc[k & 1]);
+    red_e[w][lane] = (acc[0] + acc[2]) + (acc[4] + acc[6]);
+    red_o[w][lane] = (acc[1] + acc[3]) + (acc[5] + acc[7]);
     __syncthreads();
     if (w == 0) {
-        const double S = (red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane]);
-        partials[it.out + lane] = lane < it.nrows ? S : 0.0;
+        const double Se = (red_e[0][lane] + red_e[1][lane]) + (red_e[2][lane] + red_e[3][lane]);
+        const double So = (red_o[0][lane] + red_o[1][lane]) + (red_o[2][lane] + red_o[3][lane]);
+        const bool act = lane < it.nrows;
+        partials[it.out + lane] = act ? Se + So : 0.0;
+        if (it.mirror) partials[it.out2 + lane] = act ? Se - So : 0.0;
     }
 }
 
 // One CTA of SW warps per item: warp w takes the item's degree columns w*32 + lane,
-// (w + SW)*32 + lane, ...; each column sums its 32 rows in order.
+// (w + SW)*32 + lane, ...; each column sums its 32 rows in order.  Under the parity fold
+// row r also stands for row Ng - row0 - r: degree n gets P_n(x_r) (g_r + (-1)^n g_mirror),
+// and column k = k0 + lane (k0 and a multiples of 32) has the parity of its lane.
 __global__ void __launch_bounds__(32 * SW) k_rec_inv_stored(const RecItem *__restrict__ items, int64_t nitems,
-                                                            const double *__restrict__ g, const double *__restrict__ E,
-                                                            double *__restrict__ partials) {
-    __shared__ double gs[32];
+                                                            int64_t Ng, const double *__restrict__ g,
+                                                            const double *__restrict__ E, double *__restrict__ partials) {
+    __shared__ double gs[2][32];   // [0]: even degrees, [1]: odd degrees
     if ((int64_t)blockIdx.x >= nitems) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RecItem it = items[blockIdx.x];
-    if (w == 0) gs[lane] = lane < it.nrows ? g[it.row0 + lane] : 0.0;
+    if (w == 0) {
+        const bool act = lane < it.nrows;
+        const double gr = act ? g[it.row0 + lane] : 0.0;
+        const double gm = act && it.mirror ? g[Ng - it.row0 - lane] : 0.0;
+        gs[0][lane] = gr + gm;
+        gs[1][lane] = gr - gm;
+    }
     __syncthreads();
     const int len = it.b - it.a;
     const double *e = E + it.eoff;
+    const double *gl = gs[lane & 1];
     double *out = partials + it.out;
     for (int k0 = w * 32; k0 < len; k0 += 32 * SW) {
         const int k = k0 + lane;
         if (k < len) {
             double acc = 0.0;
-            for (int r = 0; r < it.nrows; ++r) acc = fma(gs[r], __ldg(e + (int64_t)r * len + k), acc);
+            for (int r = 0; r < it.nrows; ++r) acc = fma(gl[r], __ldg(e + (int64_t)r * len + k), acc);
             out[k] = acc;
         }
     }
@@ -370,7 +387,7 @@ __global__ void k_asy_pack_inv_df(int64_t Ng, int64_t L, int nq, const dfs *__re
 __global__ void __launch_bounds__(32 * SW) k_rec_fwd_stored_df(const RecItem *__restrict__ items, int64_t nitems,
                                                                const dfs *__restrict__ cdf, const dfs *__restrict__ E,
                                                                double *__restrict__ partials) {
-    __shared__ dfs red[SW][32];
+    __shared__ dfs red_e[SW][32], red_o[SW][32];
     if ((int64_t)blockIdx.x >= nitems) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RecItem it = items[blockIdx.x];
@@ -403,27 +420,40 @@ __global__ void __launch_bounds__(32 * SW) k_rec_fwd_stored_df(const RecItem *__
     }
     for (; k < k1; ++k) {
         const float2 v = __ldcs(e + (int64_t)k * 32);
-        acc[0] = df_mac(acc[0], df_make(v.x, v.y), cc[k]);
+        acc[k & 1] = df_mac(acc[k & 1], df_make(v.x, v.y), cc[k]);
     }
-    red[w][lane] = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
+    // accumulators 0, 2 hold the even degrees, 1, 3 the odd ones (as in k_rec_fwd_stored)
+    red_e[w][lane] = df_add(acc[0], acc[2]);
+    red_o[w][lane] = df_add(acc[1], acc[3]);
     __syncthreads();
     if (w == 0) {
-        const dfs S = df_add(df_add(red[0][lane], red[1][lane]), df_add(red[2][lane], red[3][lane]));
-        reinterpret_cast<dfs *>(partials)[it.out + lane] = lane < it.nrows ? S : df_make(0.f, 0.f);
+        const dfs Se = df_add(df_add(red_e[0][lane], red_e[1][lane]), df_add(red_e[2][lane], red_e[3][lane]));
+        const dfs So = df_add(df_add(red_o[0][lane], red_o[1][lane]), df_add(red_o[2][lane], red_o[3][lane]));
+        const bool act = lane < it.nrows;
+        reinterpret_cast<dfs *>(partials)[it.out + lane] = act ? df_add(Se, So) : df_make(0.f, 0.f);
+        if (it.mirror) reinterpret_cast<dfs *>(partials)[it.out2 + lane] = act ? df_sub(Se, So) : df_make(0.f, 0.f);
     }
 }
 
 // as k_rec_inv_stored, in double-float arithmetic (rows in groups of eight loads in flight,
 // four independent accumulators per column)
 __global__ void __launch_bounds__(32 * SW) k_rec_inv_stored_df(const RecItem *__restrict__ items, int64_t nitems,
-                                                               const dfs *__restrict__ gdf, const dfs *__restrict__ E,
+                                                               int64_t Ng, const dfs *__restrict__ gdf,
+                                                               const dfs *__restrict__ E,
                                                                double *__restrict__ partials) {
-    __shared__ dfs gs[32];
+    __shared__ dfs gsb[2][32];   // parity fold as in k_rec_inv_stored: [0] even, [1] odd degrees
     if ((int64_t)blockIdx.x >= nitems) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RecItem it = items[blockIdx.x];
-    if (w == 0) gs[lane] = lane < it.nrows ? gdf[it.row0 + lane] : df_make(0.f, 0.f);
+    if (w == 0) {
+        const bool act = lane < it.nrows;
+        const dfs gr = act ? gdf[it.row0 + lane] : df_make(0.f, 0.f);
+        const dfs gm = act && it.mirror ? gdf[Ng - it.row0 - lane] : df_make(0.f, 0.f);
+        gsb[0][lane] = it.mirror ? df_add(gr, gm) : gr;
+        gsb[1][lane] = it.mirror ? df_sub(gr, gm) : gr;
+    }
     __syncthreads();
+    const dfs *gs = gsb[lane & 1];
     const int len = it.b - it.a, nr = it.nrows;
     const float2 *e = reinterpret_cast<const float2 *>(E + it.eoff);
     double *out = partials + it.out;
@@ -844,10 +874,10 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         StageTimer tm(p, st, CJT_STAGE_INV_REC);
         if (gw.nitems > 0) {
             if (gw.d_E && gw.E_df)
-                k_rec_inv_stored_df<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, gdf,
+                k_rec_inv_stored_df<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, Ng, gdf,
                                                                                (const dfs *)gw.d_E, ws.part_i);
             else if (gw.d_E)
-                k_rec_inv_stored<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, ws.g, gw.d_E,
+                k_rec_inv_stored<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, Ng, ws.g, gw.d_E,
                                                                             ws.part_i);
             else
                 k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt,

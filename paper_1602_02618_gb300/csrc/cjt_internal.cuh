@@ -51,8 +51,11 @@ struct RecItem {
     int a, b;    // degree segment [a, b)
     int mode;    // REC_PLAIN / REC_REINSCH_P1 / REC_REINSCH_M1
     int state;   // state block index (32 lanes x 2 doubles), -1 when a == 0
+    int mirror;  // 1: parity fold (alpha = beta): lane r also stands for row Ng - row0 - r
+    int pad_;
     int64_t out; // forward: partial index base (32 values); inverse: base of b-a values
     int64_t eoff;// stored recurrence values of this item (rec_store): 32 x (b-a) doubles
+    int64_t out2;// forward, mirror: partial index base of the mirrored rows
 };
 
 // Recurrence tables for one direction (degrees 0..Jcap).
@@ -92,6 +95,10 @@ struct GridWork {
     double *d_E = nullptr;
     bool E_df = false;
     bool uv_df = false;           // forward grid: u, v held as double-floats, premultiplied (CJT_DFLOAT)
+    // parity fold (alpha = beta with rec_store): P_n(-x) = (-1)^n P_n(x), so the recurrence
+    // items cover the rows i <= Ng/2 and each also yields row Ng - i; the boxes are
+    // symmetric about the middle row
+    bool fold = false;
     int64_t nE = 0;
     // diagonals u_m, v_m on this grid
     double *d_u = nullptr, *d_v = nullptr;

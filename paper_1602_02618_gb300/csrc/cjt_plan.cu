@@ -615,6 +615,20 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
             if (gw.jk[k] < gw.Jcap) { jk.push_back(gw.jk[k]); i1.push_back(gw.i1[k]); i2.push_back(gw.i2[k]); }
         gw.jk.swap(jk); gw.i1.swap(i1); gw.i2.swap(i2);
     }
+    // parity fold (alpha = beta, stored recurrence values): the boxes are made symmetric
+    // about the middle row by intersecting each with its mirror image (a subset of the box,
+    // so the remainder bound still holds on it); an empty box drops it and the deeper ones
+    gw.fold = p->alpha == p->beta && p->opts.rec_store != 0;
+    if (gw.fold) {
+        size_t k = 0;
+        for (; k < gw.jk.size(); ++k) {
+            const int64_t lo = std::max(gw.i1[k], Ng - gw.i2[k]), hi = Ng - lo;
+            if (hi < lo) break;
+            gw.i1[k] = lo;
+            gw.i2[k] = hi;
+        }
+        gw.jk.resize(k); gw.i1.resize(k); gw.i2.resize(k);
+    }
     gw.nblk = (int)gw.jk.size();
     tr.mark(inverse ? "inv: partition" : "fwd: partition");
 
@@ -714,17 +728,21 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
         if (4 * i >= 3 * Ng) return REC_REINSCH_M1;
         return REC_PLAIN;
     };
-    struct Chunk { int64_t row0; int nrows; int64_t J; int mode; };
+    struct Chunk { int64_t row0; int nrows; int64_t J; int mode; int mirror; };
     std::vector<Chunk> chunks;
-    for (int64_t i = 0; i <= Ng;) {
+    // with the parity fold, chunks of the rows 2i < Ng stand also for their mirror rows
+    // Ng - i (same J by the symmetric boxes); the middle row (Ng even) is a chunk of its own
+    const int64_t ilast = gw.fold ? (Ng - 1) / 2 : Ng;
+    for (int64_t i = 0; i <= ilast;) {
         int64_t J = J_of(i);
         int md = mode_of(i);
-        Chunk c{i, 1, J, md};
+        Chunk c{i, 1, J, md, gw.fold ? 1 : 0};
         int64_t k = i + 1;
-        while (k <= Ng && c.nrows < 32 && J_of(k) == J && mode_of(k) == md) { ++c.nrows; ++k; }
+        while (k <= ilast && c.nrows < 32 && J_of(k) == J && mode_of(k) == md) { ++c.nrows; ++k; }
         chunks.push_back(c);
         i = k;
     }
+    if (gw.fold && Ng % 2 == 0) chunks.push_back(Chunk{Ng / 2, 1, J_of(Ng / 2), mode_of(Ng / 2), 0});
     gw.nchunks = (int64_t)chunks.size();
     std::vector<RecItem> items;
     std::vector<int> row_nseg(Ng + 1);
@@ -737,6 +755,10 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
         for (int r = 0; r < ch.nrows; ++r) {
             row_nseg[ch.row0 + r] = nseg;
             row_base[ch.row0 + r] = out_f + r;
+            if (ch.mirror) {   // the mirrored rows' partials follow the chunk's own
+                row_nseg[Ng - ch.row0 - r] = nseg;
+                row_base[Ng - ch.row0 - r] = out_f + (int64_t)nseg * 32 + r;
+            }
         }
         steps += ch.J * ch.nrows;
         int state_base = (int)nstate;
@@ -748,10 +770,14 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
             it.b = (int)std::min<int64_t>((int64_t)(s + 1) * S, ch.J);
             it.mode = ch.mode;
             it.state = s == 0 ? -1 : state_base + s - 1;
+            it.mirror = ch.mirror;
+            it.pad_ = 0;
+            it.out2 = -1;
             it.eoff = eoff;
             eoff += 32 * (int64_t)(it.b - it.a);
             if (!inverse) {
                 it.out = out_f + (int64_t)s * 32;
+                if (ch.mirror) it.out2 = it.out + (int64_t)nseg * 32;
             } else {
                 it.out = out_i;
                 out_i += it.b - it.a;
@@ -766,7 +792,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
             }
             nstate += nseg - 1;
         }
-        out_f += (int64_t)nseg * 32;
+        out_f += (int64_t)nseg * 32 * (ch.mirror ? 2 : 1);
     }
     gw.rec_steps = steps;
     gw.nstate = nstate;

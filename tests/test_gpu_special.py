@@ -140,3 +140,62 @@ def test_expansion_option_errors(cjt):
     for a in (0.5, -0.5):
         info = cjt.Plan(256, a, a, expansion=cjt.CJT_EXPANSION_ULTRASPHERICAL).info()
         assert info["M"] == 1
+
+
+# ---------------------------------------------------------------------------
+# parity fold: alpha = beta with stored recurrence values (P_n(-x) = (-1)^n P_n(x))
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("a", [0.0, 0.3, -0.45, 0.5, -0.5])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 7, 64, 1023, 1024, 4096])
+def test_parity_fold_matches_oracle(cjt, orc, N, a, prec):
+    c = inputs.decaying_coefficients(N, 1.0, inputs.BASE_SEED + 29 * N)
+    plan = cjt.Plan(N, a, a, rec_store=1, precision=prec)
+    assert plan.info()["parity_fold"] == 1
+    check(cjt, orc, plan, c, a, a)
+
+
+@pytest.mark.parametrize("opts", [dict(use_asy=-1), dict(seg_len=32), dict(M=13, ratio=0.05, seg_len=256),
+                                  dict(expansion=1), dict(M=3), dict(precision=2, use_asy=-1, seg_len=64),
+                                  dict(precision=1)])
+def test_parity_fold_options(cjt, orc, opts):
+    N, a = 3001 if opts.get("seg_len") == 32 else 4096, -0.2
+    c = inputs.decaying_coefficients(N, 1.5, 777)
+    plan = cjt.Plan(N, a, a, rec_store=1, **opts)
+    assert plan.info()["parity_fold"] == 1
+    if opts.get("precision") == 1:   # mixed form: its stated bounds (forward 1e-9, inverse 1e-5)
+        assert np.max(np.abs(run(cjt, plan, c, cjt.CJT_FWD) - orc.forward(c, a, a))) <= 1e-9 * l1(c)
+        assert np.max(np.abs(run(cjt, plan, c, cjt.CJT_INV) - orc.inverse(c, a, a))) <= 1e-5 * l1(c)
+    else:
+        check(cjt, orc, plan, c, a, a)
+
+
+def test_parity_fold_halves_the_stored_values(cjt):
+    """The folded plan stores (and runs) about half the recurrence of the same plan without
+    the fold (alpha = beta + 1e-9: the same partition to within a row or two)."""
+    N, a = 1 << 14, 0.25
+    pf = cjt.Plan(N, a, a, rec_store=1, M=10, expansion=cjt.CJT_EXPANSION_HAHN)
+    pn = cjt.Plan(N, a, a + 1e-9, rec_store=1, M=10)
+    fi, ni = pf.info(), pn.info()
+    assert fi["parity_fold"] == 1 and ni["parity_fold"] == 0
+    for key in ("rec_store_bytes", "rec_steps_fwd", "rec_steps_inv"):
+        assert 0.45 * ni[key] <= fi[key] <= 0.55 * ni[key], (key, fi[key], ni[key])
+    assert cjt.Plan(64, a, a).info()["parity_fold"] == 0   # only with stored values
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_parity_fold_full_size(cjt, orc, prec):
+    """Legendre (alpha = beta = 0) at N = 2^18: the folded plan against the unfolded one (the
+    recurrence at execution), sampled oracle values and the round trip."""
+    N, a = 1 << 18, 0.0
+    c = inputs.decaying_coefficients(N, 1.5, inputs.BASE_SEED + 88)
+    pf = cjt.Plan(N, a, a, M=13, rec_store=1, seg_len=1024, precision=prec)
+    p0 = cjt.Plan(N, a, a, M=13, seg_len=1024)
+    assert pf.info()["parity_fold"] == 1 and p0.info()["parity_fold"] == 0
+    ff = run(cjt, pf, c, cjt.CJT_FWD)
+    assert np.max(np.abs(ff - run(cjt, p0, c, cjt.CJT_FWD))) <= TOL * l1(c)
+    fi = run(cjt, pf, c, cjt.CJT_INV)
+    assert np.max(np.abs(fi - run(cjt, p0, c, cjt.CJT_INV))) <= TOL * l1(c)
+    j = np.unique(np.concatenate([np.arange(0, 20), N - np.arange(0, 20), inputs.rng(10).integers(0, N + 1, 100)]))
+    assert np.max(np.abs(orc.cheb_series(ff, j, N) - orc.jacobi_series(c, a, a, j, N))) <= TOL * l1(c)
+    assert np.max(np.abs(run(cjt, pf, ff, cjt.CJT_INV) - c)) <= TOL * l1(c)
