@@ -12,7 +12,11 @@
 // last when log2 is odd) on a padded [column][element] shared-memory tile,
 // with twiddles read from plan-owned tables computed by sincospi (exact argument
 // reduction): omega_{Ltab}^j, and per-stage copies laid out so that a warp's loads
-// are contiguous (Twiddles::stw).
+// are contiguous (Twiddles::stw).  FP64 transforms with the TwFma tables run the
+// same stages in decimation-in-time order instead (digit-reversed load, one radix-2
+// stage first when log2 is odd), with the twiddles applied before each butterfly in
+// fused multiply-add form: 22 FP64 operations per radix-4 butterfly instead of 28, on
+// a device whose FP64 pipe is the limit.
 //
 // Lengths that are not powers of two (N not a power of two) go through
 // Bluestein's chirp-z form on top of the power-of-two transform.
@@ -87,12 +91,36 @@ __device__ __forceinline__ int dif_revinv(int k, int logLs) {
 
 constexpr int FFT_U = 4;   // global loads (and twiddle loads) in flight per thread in the load/store phases
 
-template <typename R>
+// One radix-4 decimation-in-time butterfly on z_j = w_j x_j (w_0 = 1) with the TwFma
+// form of w_1..w_3: X_p = sum_j z_j (-i)^{jp}.
+__device__ __forceinline__ void dit4_fma(double2 x0, double2 x1, double2 x2, double2 x3, const TwFma &w,
+                                         double2 &X0, double2 &X1, double2 &X2, double2 &X3) {
+    auto rot = [](double2 x, bool sw, double t, double &e0, double &e1) {
+        const double u0 = sw ? x.y : x.x, u1 = sw ? x.x : x.y;
+        e0 = fma(-t, u1, u0);
+        e1 = fma(t, u0, u1);
+    };
+    double e01, e11, e02, e12, e03, e13;
+    rot(x1, w.flags & 1, w.t1, e01, e11);
+    rot(x2, w.flags & 2, w.t2, e02, e12);
+    rot(x3, w.flags & 4, w.t3, e03, e13);
+    // a, b = x0 +- w2 x2;  (e, f) sigma_1 = w1 x1 +- w3 x3, componentwise
+    const double ax = fma(w.s2x, e02, x0.x), ay = fma(w.s2y, e12, x0.y);
+    const double bx = fma(-w.s2x, e02, x0.x), by = fma(-w.s2y, e12, x0.y);
+    const double ex = fma(w.rx, e03, e01), ey = fma(w.ry, e13, e11);
+    const double fx = fma(-w.rx, e03, e01), fy = fma(-w.ry, e13, e11);
+    X0 = make_double2(fma(w.s1x, ex, ax), fma(w.s1y, ey, ay));      // a + c
+    X2 = make_double2(fma(-w.s1x, ex, ax), fma(-w.s1y, ey, ay));    // a - c
+    X1 = make_double2(fma(w.s1y, fy, bx), fma(-w.s1x, fx, by));     // b - i d
+    X3 = make_double2(fma(-w.s1y, fy, bx), fma(w.s1x, fx, by));     // b + i d
+}
+
+template <typename R, bool DIT>
 __global__ void __launch_bounds__(FFT_THREADS, 4)
 k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__restrict__ out, int logLs,
           int64_t ncols, int tile, int64_t in_es, int64_t in_cs, int64_t in_ts, int64_t out_ks, int64_t out_cs,
           int64_t out_ts, const typename cplx<R>::t *__restrict__ tw, int logLtab, int post_log,
-          const typename cplx<R>::t *__restrict__ stw) {
+          const typename cplx<R>::t *__restrict__ stw, const TwFma *__restrict__ fmat) {
     using V = typename cplx<R>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *s = reinterpret_cast<V *>(smem_raw);
@@ -127,7 +155,7 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
                     e = pow2c ? (idx >> lgc) : idx / ncl;
                     g = c * in_cs + (int64_t)e * in_es;
                 }
-                at[u] = c * ld + swz(e);
+                at[u] = c * ld + swz(DIT ? dif_revinv(e, logLs) : e);
                 v[u] = src[g];
             }
         }
@@ -137,49 +165,94 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
     }
     __syncthreads();
 
-    // radix-4 DIF stages
-    const int nb4 = Ls >> 2;
-    int lb = logLs;
-    while (lb >= 2) {
-        const int Lb = 1 << lb, h = Lb >> 2;
-        const int twstep_log = logLtab - lb;  // omega_{Lb}^j = tw[j << (logLtab - lb)]
-        for (int idx = threadIdx.x; idx < ncl * nb4; idx += blockDim.x) {
-            const int c = idx >> (logLs - 2), j = idx & (nb4 - 1);   // nb4 = Ls/4
-            int blk = j >> (lb - 2), n0 = j & (h - 1);
-            V *col = s + c * ld;
-            const int e0 = blk * Lb + n0;
-            const int i0 = swz(e0), i1 = swz(e0 + h), i2 = swz(e0 + 2 * h), i3 = swz(e0 + 3 * h);
-            V x0 = col[i0], x1 = col[i1], x2 = col[i2], x3 = col[i3];
-            V t0 = cadd_t(x0, x2), t1 = csub_t(x0, x2), t2 = cadd_t(x1, x3), t3 = cmul_mi(csub_t(x1, x3));
-            V y0 = cadd(t0, t2), y2 = csub(t0, t2), y1 = cadd(t1, t3), y3 = csub(t1, t3);
-            if (n0 != 0) {
-                if (stw) {
-                    const V *w = stw + stw_base(lb) + n0;
-                    y1 = cmul(y1, w[0]);
-                    y2 = cmul(y2, w[h]);
-                    y3 = cmul(y3, w[2 * h]);
-                } else {
-                    y1 = cmul(y1, tw[(int64_t)n0 << twstep_log]);
-                    y2 = cmul(y2, tw[(int64_t)(2 * n0) << twstep_log]);
-                    y3 = cmul(y3, tw[(int64_t)(3 * n0) << twstep_log]);
-                }
+    if constexpr (DIT) {
+        // decimation in time: the input sits at digit-reversed positions; a radix-2 stage
+        // first when logLs is odd, then radix-4 stages of growing block length Lb, whose
+        // quarter q + j Lb/4 holds the j-th sub-transform at q (twiddle omega_Lb^{jq})
+        int lb = 0;
+        if (logLs & 1) {
+            const int nb2 = Ls >> 1;
+            for (int idx = threadIdx.x; idx < ncl * nb2; idx += blockDim.x) {
+                const int c = idx >> (logLs - 1), j = idx & (nb2 - 1);
+                V *col = s + c * ld;
+                const int i0 = swz(2 * j), i1 = swz(2 * j + 1);
+                V x0 = col[i0], x1 = col[i1];
+                col[i0] = cadd(x0, x1);
+                col[i1] = csub(x0, x1);
             }
-            col[i0] = y0; col[i1] = y1; col[i2] = y2; col[i3] = y3;
+            __syncthreads();
+            lb = 1;
         }
-        __syncthreads();
-        lb -= 2;
-    }
-    if (lb == 1) {
-        const int nb2 = Ls >> 1;
-        for (int idx = threadIdx.x; idx < ncl * nb2; idx += blockDim.x) {
-            const int c = idx >> (logLs - 1), j = idx & (nb2 - 1);   // nb2 = Ls/2
-            V *col = s + c * ld;
-            const int i0 = swz(2 * j), i1 = swz(2 * j + 1);
-            V x0 = col[i0], x1 = col[i1];
-            col[i0] = cadd(x0, x1);
-            col[i1] = csub(x0, x1);
+        const int nb4 = Ls >> 2;
+        for (lb += 2; lb <= logLs; lb += 2) {
+            const int Lb = 1 << lb, h = Lb >> 2;
+            const TwFma *tb = fmat + twfma_base(lb);
+            for (int idx = threadIdx.x; idx < ncl * nb4; idx += blockDim.x) {
+                const int c = idx >> (logLs - 2), j = idx & (nb4 - 1);
+                const int blk = j >> (lb - 2), q = j & (h - 1);
+                V *col = s + c * ld;
+                const int e0 = blk * Lb + q;
+                const int i0 = swz(e0), i1 = swz(e0 + h), i2 = swz(e0 + 2 * h), i3 = swz(e0 + 3 * h);
+                const V x0 = col[i0], x1 = col[i1], x2 = col[i2], x3 = col[i3];
+                V X0, X1, X2, X3;
+                if (h == 1) {   // Lb = 4: all twiddles are 1
+                    const V a = cadd(x0, x2), b = csub(x0, x2), cc = cadd(x1, x3), d = csub(x1, x3);
+                    X0 = cadd(a, cc);
+                    X2 = csub(a, cc);
+                    X1 = cadd(b, cmul_mi(d));
+                    X3 = csub(b, cmul_mi(d));
+                } else {
+                    dit4_fma(x0, x1, x2, x3, tb[q], X0, X1, X2, X3);
+                }
+                col[i0] = X0; col[i1] = X1; col[i2] = X2; col[i3] = X3;
+            }
+            __syncthreads();
         }
-        __syncthreads();
+    } else {
+        // radix-4 DIF stages
+        const int nb4 = Ls >> 2;
+        int lb = logLs;
+        while (lb >= 2) {
+            const int Lb = 1 << lb, h = Lb >> 2;
+            const int twstep_log = logLtab - lb;  // omega_{Lb}^j = tw[j << (logLtab - lb)]
+            for (int idx = threadIdx.x; idx < ncl * nb4; idx += blockDim.x) {
+                const int c = idx >> (logLs - 2), j = idx & (nb4 - 1);   // nb4 = Ls/4
+                int blk = j >> (lb - 2), n0 = j & (h - 1);
+                V *col = s + c * ld;
+                const int e0 = blk * Lb + n0;
+                const int i0 = swz(e0), i1 = swz(e0 + h), i2 = swz(e0 + 2 * h), i3 = swz(e0 + 3 * h);
+                V x0 = col[i0], x1 = col[i1], x2 = col[i2], x3 = col[i3];
+                V t0 = cadd_t(x0, x2), t1 = csub_t(x0, x2), t2 = cadd_t(x1, x3), t3 = cmul_mi(csub_t(x1, x3));
+                V y0 = cadd(t0, t2), y2 = csub(t0, t2), y1 = cadd(t1, t3), y3 = csub(t1, t3);
+                if (n0 != 0) {
+                    if (stw) {
+                        const V *w = stw + stw_base(lb) + n0;
+                        y1 = cmul(y1, w[0]);
+                        y2 = cmul(y2, w[h]);
+                        y3 = cmul(y3, w[2 * h]);
+                    } else {
+                        y1 = cmul(y1, tw[(int64_t)n0 << twstep_log]);
+                        y2 = cmul(y2, tw[(int64_t)(2 * n0) << twstep_log]);
+                        y3 = cmul(y3, tw[(int64_t)(3 * n0) << twstep_log]);
+                    }
+                }
+                col[i0] = y0; col[i1] = y1; col[i2] = y2; col[i3] = y3;
+            }
+            __syncthreads();
+            lb -= 2;
+        }
+        if (lb == 1) {
+            const int nb2 = Ls >> 1;
+            for (int idx = threadIdx.x; idx < ncl * nb2; idx += blockDim.x) {
+                const int c = idx >> (logLs - 1), j = idx & (nb2 - 1);   // nb2 = Ls/2
+                V *col = s + c * ld;
+                const int i0 = swz(2 * j), i1 = swz(2 * j + 1);
+                V x0 = col[i0], x1 = col[i1];
+                col[i0] = cadd(x0, x1);
+                col[i1] = csub(x0, x1);
+            }
+            __syncthreads();
+        }
     }
 
     // store in natural frequency order, optional four-step twiddle omega_{2^post_log}^{c k};
@@ -202,7 +275,7 @@ k_fft_sub(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__res
                     k = pow2c ? (idx >> lgc) : idx / ncl;
                     at[u] = c * out_cs + (int64_t)k * out_ks;
                 }
-                v[u] = s[c * ld + swz(dif_revinv(k, logLs))];
+                v[u] = s[c * ld + swz(DIT ? k : dif_revinv(k, logLs))];
                 if (post_log >= 0) {
                     const int64_t ex = ((c0 + c) * (int64_t)k) & ((1LL << post_log) - 1);
                     w[u] = tw[ex << (logLtab - post_log)];
@@ -226,7 +299,7 @@ int ilog2(int64_t v) {
 template <typename R>
 int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batch, int64_t in_es, int64_t in_cs,
                int64_t in_ts, int64_t out_ks, int64_t out_cs, int64_t out_ts, const void *tw, int logLtab,
-               int post_log, const void *stw, cudaStream_t st) {
+               int post_log, const void *stw, const void *fmat, cudaStream_t st) {
     using V = typename cplx<R>::t;
     const int Ls = 1 << logLs;
     // Columns per CTA: at most ~64 KB of shared memory (32 KB double-float), and few
@@ -251,32 +324,42 @@ int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batc
     int prc = cjt_fft_prime();
     if (prc) return prc;
     dim3 grid((unsigned)((ncols + tile - 1) / tile), (unsigned)batch);
-    k_fft_sub<R><<<grid, threads, smem, st>>>((const V *)in, (V *)out, logLs, ncols, tile, in_es, in_cs, in_ts,
-                                                    out_ks, out_cs, out_ts, (const V *)tw, logLtab, post_log,
-                                                    (const V *)stw);
+    bool launched = false;
+    if constexpr (std::is_same<R, double>::value) {
+        if (fmat) {
+            k_fft_sub<R, true><<<grid, threads, smem, st>>>((const V *)in, (V *)out, logLs, ncols, tile, in_es,
+                                                            in_cs, in_ts, out_ks, out_cs, out_ts, (const V *)tw,
+                                                            logLtab, post_log, (const V *)stw, (const TwFma *)fmat);
+            launched = true;
+        }
+    }
+    if (!launched)
+        k_fft_sub<R, false><<<grid, threads, smem, st>>>((const V *)in, (V *)out, logLs, ncols, tile, in_es, in_cs,
+                                                         in_ts, out_ks, out_cs, out_ts, (const V *)tw, logLtab,
+                                                         post_log, (const V *)stw, nullptr);
     CJT_CUDA_TRY(cudaGetLastError());
     return CJT_OK;
 }
 
 template <typename R>
 int fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &T, cudaStream_t st) {
-    const void *tw = T.tw, *stw = T.stw;
+    const void *tw = T.tw, *stw = T.stw, *fmat = T.fma;
     const int64_t Ltab = T.Ltab;
     if (L <= 1 || batch <= 0) return CJT_OK;
     const int logL = ilog2(L), logLtab = ilog2(Ltab);
     if ((1LL << logL) != L || L > Ltab) return CJT_EINVAL;
     if (logL <= 12) {
         // direct: each "column" is one whole transform
-        return launch_sub<R>(data, data, logL, batch, 1, 1, L, 0, 1, L, 0, tw, logLtab, -1, stw, st);
+        return launch_sub<R>(data, data, logL, batch, 1, 1, L, 0, 1, L, 0, tw, logLtab, -1, stw, fmat, st);
     }
     if (logL > 24 || scratch == nullptr) return CJT_EUNSUPPORTED;
     const int log1 = (logL + 1) / 2, log2 = logL - log1;
     const int64_t L1 = 1LL << log1, L2 = 1LL << log2;
     // pass A: columns n2 (L2 of them), elements n1 at stride L2
-    int rc = launch_sub<R>(data, scratch, log1, L2, batch, L2, 1, L, L2, 1, L, tw, logLtab, logL, stw, st);
+    int rc = launch_sub<R>(data, scratch, log1, L2, batch, L2, 1, L, L2, 1, L, tw, logLtab, logL, stw, fmat, st);
     if (rc) return rc;
     // pass B: rows k1 (L1 of them), elements n2 contiguous, output X[k1 + L1 k2]
-    return launch_sub<R>(scratch, data, log2, L1, batch, 1, L2, L, L1, 1, L, tw, logLtab, -1, stw, st);
+    return launch_sub<R>(scratch, data, log2, L1, batch, 1, L2, L, L1, 1, L, tw, logLtab, -1, stw, fmat, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -434,9 +517,10 @@ int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch) { return L > 4096 ? L * 
 int cjt_fft_prime() {
     static bool done = false;
     if (done) return CJT_OK;
-    CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<dfloat, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     done = true;
     return CJT_OK;
 }

@@ -127,8 +127,27 @@ struct Twiddles {
     const void *tw = nullptr;
     int64_t Ltab = 0;
     const void *stw = nullptr;
+    const void *fma = nullptr;   // FP64 only: TwFma tables of the decimation-in-time stages
 };
 __host__ __device__ inline int64_t stw_base(int lb) { return 3 * ((1LL << (lb - 2)) - 1); }
+
+// Radix-4 decimation-in-time twiddles in fused multiply-add form (FP64 transforms).  For a
+// stage of block length Lb = 2^lb and q < Lb/4, each w_j = omega_Lb^{jq} (j = 1, 2, 3) is
+// written as sigma (1 + i t) when |Re w| >= |Im w| (sigma = Re w, t = Im w / Re w), else
+// as sigma (t + i) (sigma = Im w, t = Re w / Im w): |t| <= 1 and |sigma| >= 1/sqrt(2).
+// Then w x = (sx e0, sy e1) with e0 = u0 - t u1, e1 = u1 + t u0, where (u0, u1) is x or,
+// in the second form, x with its parts swapped, and (sx, sy) = (sigma, sigma) or
+// (-sigma, sigma).  Factoring sigma_1 out of w1 x1 +- w3 x3 leaves 22 multiply-adds per
+// butterfly instead of 28 operations (Goedecker's FMA radix-4 butterfly).
+struct __align__(16) TwFma {
+    double t1, t2, t3;    // t of w1, w2, w3
+    double s1x, s1y;      // (sx, sy) of w1
+    double s2x, s2y;      // (sx, sy) of w2
+    double rx, ry;        // (sx, sy) of w3 divided by those of w1
+    int flags;            // bit j-1: w_j in the sigma (t + i) form
+    int pad_;
+};
+__host__ __device__ inline int64_t twfma_base(int lb) { return (1LL << (lb - 2)) - 1; }
 inline int64_t prec_cbytes(int prec) { return prec == PREC_F32 ? 8 : 16; }   // bytes of one complex
 struct Dft {
     int64_t L = 0, S = 0, K = 0, P = 0;
@@ -182,11 +201,13 @@ struct cjt_plan_s {
     void *d_tw32 = nullptr;       // float2[Ltab]
     void *d_twdf = nullptr;       // dfc[Ltab]
     void *d_stw64 = nullptr, *d_stw32 = nullptr, *d_stwdf = nullptr;   // stage tables (Twiddles)
+    void *d_twfma = nullptr;      // TwFma tables (FP64 decimation-in-time stages)
     Twiddles twiddles(int prec) const {
         Twiddles t;
         t.Ltab = Ltab;
         t.tw = prec == PREC_F32 ? d_tw32 : prec == PREC_DF ? d_twdf : d_tw64;
         t.stw = prec == PREC_F32 ? d_stw32 : prec == PREC_DF ? d_stwdf : d_stw64;
+        t.fma = prec == PREC_F64 ? d_twfma : nullptr;
         return t;
     }
     int prec_asy = PREC_F64;      // element type of the asymptotic transforms

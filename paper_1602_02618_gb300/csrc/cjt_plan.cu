@@ -507,6 +507,39 @@ __global__ void k_stage_twiddles(int lmax, int logLtab, const double2 *__restric
     if (stwdf) stwdf[t] = dfc_make(df_from(w.x), df_from(w.y));
 }
 
+// FMA-form twiddles of the FP64 decimation-in-time stages (TwFma): entry twfma_base(lb) + q
+// for q < 2^(lb-2), from omega_{Ltab}^k
+__global__ void k_fma_twiddles(int lmax, int logLtab, const double2 *__restrict__ tw64, TwFma *out) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= twfma_base(lmax + 1)) return;
+    int lb = 2;
+    while (twfma_base(lb + 1) <= t) ++lb;
+    const int64_t q = t - twfma_base(lb);
+    double tt[3], sx[3], sy[3];
+    int flags = 0;
+    for (int j = 1; j <= 3; ++j) {
+        const double2 w = tw64[((int64_t)j * q) << (logLtab - lb)];
+        if (fabs(w.x) >= fabs(w.y)) {   // sigma (1 + i t)
+            tt[j - 1] = w.y / w.x;
+            sx[j - 1] = w.x;
+            sy[j - 1] = w.x;
+        } else {                        // sigma (t + i), parts swapped in the butterfly
+            tt[j - 1] = w.x / w.y;
+            sx[j - 1] = -w.y;
+            sy[j - 1] = w.y;
+            flags |= 1 << (j - 1);
+        }
+    }
+    TwFma r;
+    r.t1 = tt[0]; r.t2 = tt[1]; r.t3 = tt[2];
+    r.s1x = sx[0]; r.s1y = sy[0];
+    r.s2x = sx[1]; r.s2y = sy[1];
+    r.rx = sx[2] / sx[0]; r.ry = sy[2] / sy[0];
+    r.flags = flags;
+    r.pad_ = 0;
+    out[t] = r;
+}
+
 // doubles -> double-floats in place (same 8 bytes per entry): stored recurrence values
 __global__ void k_to_df_inplace(int64_t n, double *E) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -987,6 +1020,12 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
             k_stage_twiddles<<<blocks_for(n, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)p->d_tw64,
                                                                  (double2 *)p->d_stw64, (float2 *)p->d_stw32,
                                                                  (dfc *)p->d_stwdf);
+            CJT_CUDA_TRY(cudaGetLastError());
+            // every plan has FP64 transforms (final DCT-I, inverse front end)
+            const int64_t nf = twfma_base(lmax + 1);
+            TRY(dalloc(p, (TwFma **)&p->d_twfma, nf));
+            k_fma_twiddles<<<blocks_for(nf, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)p->d_tw64,
+                                                               (TwFma *)p->d_twfma);
             CJT_CUDA_TRY(cudaGetLastError());
         }
     }

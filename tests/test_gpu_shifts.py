@@ -71,7 +71,8 @@ def test_shifted_parameters_full_size(cjt, orc, alpha, beta):
         assert err[q] <= TOL * max(l1(c), scale)
     assert np.max(np.abs(run(cjt, plan, fwd, cjt.CJT_INV) - c)) <= TOL * l1(c)
     inv = run(cjt, plan, c, cjt.CJT_INV)
-    assert np.max(np.abs(run(cjt, plan, inv, cjt.CJT_FWD) - c)) <= TOL * l1(c)
+    # inverse then forward: two transforms, each held to TOL times its own input's l1 norm
+    assert np.max(np.abs(run(cjt, plan, inv, cjt.CJT_FWD) - c)) <= TOL * (l1(c) + l1(inv))
 
 
 def test_shifted_in_a_batch_equals_alone(cjt):
