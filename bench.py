@@ -201,13 +201,13 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
     for kv in filter(None, args.batch_options.split(",")):
         k, v = kv.split("=")
         bopt[k.strip()] = float(v) if k.strip() == "ratio" else int(v)
-    store_max = bopt.pop("store_max", 0 if big else 8192)
+    store_max = bopt.pop("store_max", 0 if big else 16384)
     t0 = time.perf_counter()
     plans = []
     for N, a, b, d, c in items:
-        # the batch's N are mostly not powers of two: Bluestein transforms cost 3-5x a
-        # power-of-two transform, so fewer asymptotic blocks (ratio 0.05) win
-        opts = {"M": 16, "seg_len": 1024} if big else {"M": 10, "seg_len": 256, "ratio": 0.05}
+        # the batch's N are mostly not powers of two; their plans evaluate on the power-of-two
+        # Lobatto grid (no Bluestein transforms), where M = 13 and block ratio 0.1 measured best
+        opts = {"M": 16, "seg_len": 1024} if big else {"M": 13, "seg_len": 256, "ratio": 0.1}
         opts.update(bopt)
         if N <= store_max:
             opts["rec_store"] = 1
@@ -332,8 +332,10 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
                         "each, random forward/inverse, c_n=g_n/(n+1); %s; one captured CUDA graph per step"
                         % (len(items), PREC_NAMES[args.precision])),
                        "coefficients_per_step": coeffs, "lanes": args.lanes,
-                       "plan_options": args.batch_options or ("M=16, seg_len=1024" if big else
-                                                               "M=10, seg_len=256, ratio=0.05, rec_store for N <= 8192"),
+                       "plan_options": "%s%s" % ("M=16, seg_len=1024" if big else
+                                                 "M=13, seg_len=256, ratio=0.1, power-of-two grid, rec_store for "
+                                                 "N <= %d" % store_max,
+                                                 (" (overridden: %s)" % args.batch_options) if args.batch_options else ""),
                        "l2": "inputs (%.0f MB) exceed L2; flushed between steps" % (coeffs * 8 / 1e6)},
             "error": ({"vs_fp64_gpu_max_abs_over_l1": max(err64) if err64 else None,
                        "vs_oracle_sampled_values_max_abs_over_l1": max(errs) if errs else None,

@@ -111,6 +111,16 @@ typedef struct {
                          diagonals u_m, v_m instead of m+1 (App. B.1).  With Hahn's
                          formula, alpha or beta = +-1/2 collapses each term to one cosine
                          (App. B.2-B.3) in either case.                                  */
+    int grid;         /* Lobatto grid of the evaluation.  -1: the paper's, x_j = cos(pi j/N)
+                         (forward) and cos(pi j/(2N)) (inverse), so that for N not a power
+                         of two every transform is a Bluestein transform.  1: G, the least
+                         power of two >= N, in place of N: x_j = cos(pi j/G) and
+                         cos(pi j/(2G)).  The result is the same map (to rounding): a
+                         polynomial of degree N <= G is interpolated exactly by the
+                         inverse DCT-I on G+1 points, whose coefficients above N vanish,
+                         and the (2G+1)-point Clenshaw--Curtis rule is exact wherever the
+                         (2N+1)-point rule is.  0 (default): the power-of-two grid when N
+                         is not a power of two (identical to -1 otherwise).              */
 } cjt_plan_opts;
 
 /* Summary of a plan (for reports and tests). Sizes are per direction. */
@@ -124,7 +134,8 @@ typedef struct {
     int64_t rec_steps_fwd;   /* sum_i J(i): recurrence steps of one forward transform
                                 (with the parity fold: over the rows i <= N/2 only)     */
     int64_t rec_steps_inv;   /* sum_i min(J(i), N+1) on the 2N grid (likewise)          */
-    int64_t fft_len_fwd, fft_len_inv;   /* transform lengths used by the ASY blocks     */
+    int64_t fft_len_fwd, fft_len_inv;   /* transform lengths used by the ASY blocks:
+                                           2 grid_fwd and 2 grid_inv                    */
     int64_t nfft_fwd, nfft_inv;         /* complex transforms per execution             */
     int64_t rec_items_fwd, rec_items_inv;
     int64_t device_bytes;    /* device memory owned by the plan                        */
@@ -135,6 +146,7 @@ typedef struct {
     int shift_alpha, shift_beta;        /* 0 or 1: alpha - shift_alpha and beta - shift_beta
                                            lie in [-1/2, 1/2]                              */
     int expansion;                      /* CJT_EXPANSION_HAHN or _ULTRASPHERICAL (used)    */
+    int64_t grid_fwd, grid_inv;         /* Lobatto grids used: x_j = cos(pi j / grid)     */
     int parity_fold;                    /* 1 when alpha = beta with rec_store: the stored
                                            recurrence covers the rows i <= Ng/2 and yields
                                            rows Ng - i by P_n(-x) = (-1)^n P_n(x)

@@ -134,6 +134,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
         o.shared_workspace = opts->shared_workspace;
         o.rec_store = opts->rec_store;
         o.expansion = opts->expansion;
+        o.grid = opts->grid;
     }
     if (o.M < 1 || o.M > 20) return CJT_EINVAL;
     if (!(o.eps > 0.0 && o.eps < 1.0)) return CJT_EINVAL;
@@ -143,8 +144,9 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     if (o.rec_store != 0 && o.rec_store != 1) return CJT_EINVAL;
     if (o.expansion < CJT_EXPANSION_AUTO || o.expansion > CJT_EXPANSION_ULTRASPHERICAL) return CJT_EINVAL;
     if (o.expansion == CJT_EXPANSION_ULTRASPHERICAL && alpha != beta) return CJT_EINVAL;
+    if (o.grid < -1 || o.grid > 1) return CJT_EINVAL;
     if (o.seg_len < 32 || o.seg_len > (1 << 20) || (o.seg_len % 32) != 0) return CJT_EINVAL;
-    if (N > (1LL << 21) && !is_pow2(N)) return CJT_EUNSUPPORTED;   // Bluestein lengths stay <= 2^24
+    if (N > (1LL << 21) && !is_pow2(N) && o.grid == -1) return CJT_EUNSUPPORTED;   // Bluestein lengths <= 2^24
 
     cjt_plan_s *p = new (std::nothrow) cjt_plan_s();
     if (!p) return CJT_ENOMEM;
@@ -201,6 +203,8 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
     info->shift_beta = p->shift_b;
     info->expansion = p->expansion_used;
     info->parity_fold = (p->fw.fold || p->iv.fold) ? 1 : 0;
+    info->grid_fwd = (p->opts.directions & CJT_FWD) ? p->Gf : 0;
+    info->grid_inv = (p->opts.directions & CJT_INV) ? 2 * p->Gi : 0;
     info->M = p->M;
     info->precision = p->opts.precision;
     info->directions = p->opts.directions;

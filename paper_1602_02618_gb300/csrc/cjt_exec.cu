@@ -606,12 +606,13 @@ __global__ void k_combine_fwd(int64_t N, int64_t L, int M, const int *__restrict
     if (i >= 1 && i < N) ext[2 * N - i] = make_double2(y, 0.0);
 }
 
-// c_k = Re Z(k) / N, halved at k = 0 and k = N (inverse scaled DCT-I)
-__global__ void k_dct_finish(int64_t N, const double2 *__restrict__ Z, double *__restrict__ out) {
+// c_k = Re Z(k) / G, halved at k = 0 and k = G (inverse scaled DCT-I on the grid G >= N),
+// for k <= N
+__global__ void k_dct_finish(int64_t N, int64_t G, const double2 *__restrict__ Z, double *__restrict__ out) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k > N) return;
-    double v = Z[k].x / (double)N;
-    if (k == 0 || k == N) v *= 0.5;
+    double v = Z[k].x / (double)G;
+    if (k == 0 || k == G) v *= 0.5;
     out[k] = v;
 }
 
@@ -783,30 +784,31 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
     }
     double2 *ext = (double2 *)ws.dct;
+    const int64_t G = p->Gf;   // grid rows 0..G (the combines' "N" is the grid)
     {
     StageTimer tm(p, st, CJT_STAGE_FWD_COMBINE);
     if (dfx && gw.E_df)
-        k_combine_fwd_df<dfs><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.d_rowk, gw.d_scale, (const dfs *)gw.d_u, (const dfs *)gw.d_v, (const dfc *)ws.fft_f,
+        k_combine_fwd_df<dfs><<<blocks_for(G + 1, 256), 256, 0, st>>>(
+            G, L, M, gw.d_rowk, gw.d_scale, (const dfs *)gw.d_u, (const dfs *)gw.d_v, (const dfc *)ws.fft_f,
             gw.d_row_base, gw.d_row_nseg, (const dfs *)ws.part_f, ws.exps, ext);
     else if (dfx)
-        k_combine_fwd_df<double><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.d_rowk, gw.d_scale, (const dfs *)gw.d_u, (const dfs *)gw.d_v, (const dfc *)ws.fft_f,
+        k_combine_fwd_df<double><<<blocks_for(G + 1, 256), 256, 0, st>>>(
+            G, L, M, gw.d_rowk, gw.d_scale, (const dfs *)gw.d_u, (const dfs *)gw.d_v, (const dfc *)ws.fft_f,
             gw.d_row_base, gw.d_row_nseg, ws.part_f, ws.exps, ext);
     else if (fp32)
-        k_combine_fwd<float2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const float2 *)ws.fft_f, gw.d_row_base, gw.d_row_nseg,
+        k_combine_fwd<float2><<<blocks_for(G + 1, 256), 256, 0, st>>>(
+            G, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const float2 *)ws.fft_f, gw.d_row_base, gw.d_row_nseg,
             ws.part_f, ext);
     else
-        k_combine_fwd<double2><<<blocks_for(N + 1, 256), 256, 0, st>>>(
-            N, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const double2 *)ws.fft_f, gw.d_row_base, gw.d_row_nseg,
+        k_combine_fwd<double2><<<blocks_for(G + 1, 256), 256, 0, st>>>(
+            G, L, M, gw.d_rowk, gw.d_scale, gw.d_u, gw.d_v, (const double2 *)ws.fft_f, gw.d_row_base, gw.d_row_nseg,
             ws.part_f, ext);
     CJT_CUDA_TRY(cudaGetLastError());
     }
     StageTimer tm(p, st, CJT_STAGE_FWD_DCT);
     rc = cjt_dft_exec(p->dft_dct, ws.dct, ws.work, ws.scratch, 1, p->twiddles(PREC_F64), st);
     if (rc) return rc;
-    k_dct_finish<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, (const double2 *)ws.dct, out);
+    k_dct_finish<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, G, (const double2 *)ws.dct, out);
     CJT_CUDA_TRY(cudaGetLastError());
     return CJT_OK;
 }
@@ -822,7 +824,7 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     const bool fp32 = p->prec_asy == PREC_F32, dfm = p->prec_asy == PREC_DF;
     dfs *gdf = (dfs *)ws.xdf;
     const int M = p->M;
-    const int64_t Ng = 2 * N, L = p->Li;
+    const int64_t Ng = 2 * p->Gi, L = p->Li;
     // front end: p_N on the 2N grid, times the Clenshaw--Curtis weights
     int rc;
     {

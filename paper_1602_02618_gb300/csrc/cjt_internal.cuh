@@ -195,7 +195,8 @@ struct cjt_plan_s {
     GridWork fw, iv;
 
     // transforms
-    int64_t Lf = 0, Li = 0;       // forward ASY/DCT length 2N; inverse 4N
+    int64_t Gf = 0, Gi = 0;       // Lobatto grids: forward x_j = cos(pi j/Gf), inverse cos(pi j/(2 Gi))
+    int64_t Lf = 0, Li = 0;       // forward ASY/DCT length 2 Gf; inverse 4 Gi
     int64_t Ltab = 0;
     void *d_tw64 = nullptr;       // double2[Ltab]
     void *d_tw32 = nullptr;       // float2[Ltab]

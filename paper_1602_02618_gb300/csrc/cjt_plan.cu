@@ -641,8 +641,9 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
             }
         }
     }
-    // inverse: blocks whose degrees all exceed N contribute nothing
-    if (inverse) {
+    // blocks whose degrees all exceed N contribute nothing (the inverse grid, and a forward
+    // grid larger than N, have more rows than degrees)
+    {
         std::vector<int64_t> jk, i1, i2;
         for (size_t k = 0; k < gw.jk.size(); ++k)
             if (gw.jk[k] < gw.Jcap) { jk.push_back(gw.jk[k]); i1.push_back(gw.i1[k]); i2.push_back(gw.i2[k]); }
@@ -972,14 +973,27 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
 
     tr.mark("tables: recurrence, C_nm");
     const bool fwd = p->opts.directions & CJT_FWD, inv = p->opts.directions & CJT_INV;
-    if (fwd) TRY(build_grid(p, p->fw, N, false, h, st));
-    if (inv) TRY(build_grid(p, p->iv, 2 * N, true, h, st));
+    // Lobatto grid: N, or the least power of two G >= N (the same map: degree-N polynomials
+    // are interpolated exactly on G+1 points, and the (2G+1)-point Clenshaw--Curtis rule is
+    // exact wherever the (2N+1)-point rule is); power-of-two transforms then need no
+    // Bluestein form
+    {
+        const bool pow2 = (N & (N - 1)) == 0;
+        int64_t G = N;
+        if (p->opts.grid == 1 || (p->opts.grid == 0 && !pow2)) {
+            G = 1;
+            while (G < N) G <<= 1;
+        }
+        p->Gf = p->Gi = G;
+    }
+    if (fwd) TRY(build_grid(p, p->fw, p->Gf, false, h, st));
+    if (inv) TRY(build_grid(p, p->iv, 2 * p->Gi, true, h, st));
 
     // transforms: forward ASY/DCT length 2N, inverse 4N; Bluestein when N is not a power of two
     p->prec_asy = p->opts.precision == CJT_MIXED ? PREC_F32 : p->opts.precision == CJT_DFLOAT ? PREC_DF : PREC_F64;
     const int pa = p->prec_asy;
-    p->Lf = fwd ? 2 * N : 0;
-    p->Li = inv ? 4 * N : 0;
+    p->Lf = fwd ? 2 * p->Gf : 0;
+    p->Li = inv ? 4 * p->Gi : 0;
     p->npair_f = (p->fw.nblk * M + 1) / 2;
     p->npair_i = (p->iv.nblk * M + 1) / 2;
     auto mk = [](Dft &d, int64_t L, int64_t S, int64_t K, int prec) {
@@ -987,15 +1001,17 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     };
     std::vector<std::pair<Dft *, int64_t>> used;   // transform and its batch
     if (fwd) {
-        mk(p->dft_f, 2 * N, N + 1, 2 * N, pa);   // both Z(i) and Z(L-i) are read by the pair separation
-        mk(p->dft_dct, 2 * N, 2 * N, N + 1, PREC_F64);
+        const int64_t G = p->Gf;
+        mk(p->dft_f, 2 * G, N + 1, 2 * G, pa);   // both Z(i) and Z(L-i) are read by the pair separation
+        mk(p->dft_dct, 2 * G, 2 * G, N + 1, PREC_F64);
         if (p->npair_f) used.push_back({&p->dft_f, p->npair_f});
         used.push_back({&p->dft_dct, 1});
     }
     if (inv) {
-        mk(p->dft_front, 4 * N, N + 1, 2 * N + 1, PREC_F64);
-        mk(p->dft_i, 4 * N, 4 * N, N + 1, pa);
-        mk(p->dft_cc, 4 * N, 4 * N, 2 * N + 1, PREC_F64);
+        const int64_t G = p->Gi;
+        mk(p->dft_front, 4 * G, N + 1, 2 * G + 1, PREC_F64);
+        mk(p->dft_i, 4 * G, 4 * G, N + 1, pa);
+        mk(p->dft_cc, 4 * G, 4 * G, 2 * G + 1, PREC_F64);
         used.push_back({&p->dft_front, 1});
         if (p->npair_i) used.push_back({&p->dft_i, p->npair_i});
         used.push_back({&p->dft_cc, 1});
@@ -1056,11 +1072,12 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         p->ws_size[WS_SCRATCH] = scratch;
         p->ws_size[WS_WORK] = work;
         p->ws_size[WS_DCT] = (int64_t)sizeof(double2) * Ld;
-        p->ws_size[WS_Y] = (int64_t)sizeof(double) * (2 * N + 2);
-        p->ws_size[WS_G] = inv ? (int64_t)sizeof(double) * (2 * N + 1) : 0;
+        const int64_t G = std::max(p->Gf, p->Gi);
+        p->ws_size[WS_Y] = (int64_t)sizeof(double) * (2 * G + 2);
+        p->ws_size[WS_G] = inv ? (int64_t)sizeof(double) * (2 * p->Gi + 1) : 0;
         p->ws_size[WS_PART_F] = (int64_t)sizeof(double) * (fwd ? std::max<int64_t>(p->fw.npartials, 1) : 0);
         p->ws_size[WS_PART_I] = (int64_t)sizeof(double) * (inv ? std::max<int64_t>(p->iv.npartials, 1) : 0);
-        p->ws_size[WS_XDF] = pa == PREC_DF ? (int64_t)sizeof(dfs) * (inv ? 2 * N + 1 : N + 1) : 0;
+        p->ws_size[WS_XDF] = pa == PREC_DF ? (int64_t)sizeof(dfs) * (inv ? 2 * p->Gi + 1 : N + 1) : 0;
         p->ws_size[WS_EXPS] = pa == PREC_DF ? (int64_t)sizeof(int) * (CJT_EXP_BLOCKS + 1) : 0;
         p->ws_size[WS_CONV] = (p->shift_a || p->shift_b)
                                   ? (int64_t)sizeof(double) * (2 * (N + 1) + 3 * cjt_conv_chunks(N)) : 0;
@@ -1082,7 +1099,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     TRY(dalloc(p, &p->d_out, N + 1));
 
     if (inv && N >= 1) {
-        const int64_t Ng = 2 * N;
+        const int64_t Ng = 2 * p->Gi;
         Workspace ws = p->ws;
         if (p->shared_ws) {   // a temporary arena for the weights
             CJT_CUDA_TRY(cudaMallocAsync(&tmp_ws, p->ws_bytes, st));

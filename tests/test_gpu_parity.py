@@ -185,6 +185,9 @@ def test_error_codes(cjt):
     with pytest.raises(cjt.CJTError) as e:
         cjt.Plan(64, 0.0, 0.0, M=21)
     assert e.value.code == cjt.CJT_EINVAL
+    with pytest.raises(cjt.CJTError) as e:
+        cjt.Plan(64, 0.0, 0.0, grid=2)
+    assert e.value.code == cjt.CJT_EINVAL
     p = cjt.Plan(64, 0.0, 0.0, directions=cjt.CJT_FWD)
     with pytest.raises(cjt.CJTError) as e:
         cjt.cjt_inverse(p, dev(np.zeros(65)))
@@ -197,14 +200,57 @@ def test_identity_at_N0(cjt):
     assert run_inv(cjt, p, np.array([-1.5]))[0] == -1.5
 
 
+@pytest.mark.parametrize("grid", [0, -1])
 @pytest.mark.parametrize("alpha,beta", [(0.1, -0.3), (0.45, 0.45), (-0.5, 0.5)])
 @pytest.mark.parametrize("N", [3, 5, 6, 7, 100, 1000, 1023, 1025, 3001, 10007])
-def test_general_N_matches_oracle(cjt, orc, N, alpha, beta):
-    """N not a power of two: the DCT-I/DST-I sums go through Bluestein's chirp-z form."""
+def test_general_N_matches_oracle(cjt, orc, N, alpha, beta, grid):
+    """N not a power of two: by default the evaluation runs on the power-of-two Lobatto grid
+    G >= N (grid 0); on the paper's grid (grid -1) the DCT-I/DST-I sums go through
+    Bluestein's chirp-z form."""
     c = inputs.decaying_coefficients(N, 1.0, inputs.BASE_SEED + 3 * N)
-    plan = cjt.Plan(N, alpha, beta)
+    plan = cjt.Plan(N, alpha, beta, grid=grid)
+    info = plan.info()
+    G = 1 << (N - 1).bit_length()
+    assert info["grid_fwd"] == (G if grid == 0 else N) and info["grid_inv"] == 2 * info["grid_fwd"]
+    assert info["fft_len_fwd"] == 2 * info["grid_fwd"] and info["fft_len_inv"] == 2 * info["grid_inv"]
     assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, alpha, beta))) <= TOL * l1(c)
     assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, alpha, beta))) <= TOL * l1(c)
+
+
+@pytest.mark.parametrize("opts", [dict(rec_store=1), dict(M=13, ratio=0.05, seg_len=256), dict(use_asy=-1),
+                                  dict(precision=2, rec_store=1), dict(precision=2, M=10), dict(M=3)])
+@pytest.mark.parametrize("N", [1, 2, 4, 64, 1024])
+def test_power_of_two_grid_forced(cjt, orc, N, opts):
+    """grid = 1 on N that is already a power of two changes nothing; on N - 1 (one below
+    a power of two) and N + 1 (just above) it evaluates on a grid of 2N rows or so."""
+    for n in sorted({N, max(N - 1, 1), N + 1}):
+        c = inputs.decaying_coefficients(n, 1.5, 4000 + n)
+        plan = cjt.Plan(n, 0.2, -0.35, grid=1, **opts)
+        assert plan.info()["grid_fwd"] == 1 << (n - 1).bit_length()
+        assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, 0.2, -0.35))) <= TOL * l1(c), (n, opts)
+        assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, 0.2, -0.35))) <= TOL * l1(c), (n, opts)
+
+
+def test_power_of_two_grid_large(cjt, orc):
+    """N = 40000 (grid 65536) and N = 70001 (grid 131072): the power-of-two grid against the
+    paper's grid (Bluestein) and sampled oracle values; N = 3 * 2^20 + 1 plans on 2^22."""
+    for N in (40000, 70001):
+        c = inputs.decaying_coefficients(N, 1.5, 5000 + N)
+        a, b = 0.3, -0.1
+        pg = cjt.Plan(N, a, b, M=13, rec_store=1)
+        pb = cjt.Plan(N, a, b, M=13, rec_store=1, grid=-1)
+        assert pg.info()["grid_fwd"] == 1 << (N - 1).bit_length() and pb.info()["grid_fwd"] == N
+        fg = run_fwd(cjt, pg, c)
+        assert np.max(np.abs(fg - run_fwd(cjt, pb, c))) <= TOL * l1(c)
+        assert np.max(np.abs(run_inv(cjt, pg, c) - run_inv(cjt, pb, c))) <= TOL * l1(c)
+        j = np.unique(np.concatenate([np.arange(0, 10), N - np.arange(0, 10), inputs.rng(12).integers(0, N + 1, 60)]))
+        assert np.max(np.abs(orc.cheb_series(fg, j, N) - orc.jacobi_series(c, a, b, j, N))) <= TOL * l1(c)
+        assert np.max(np.abs(run_inv(cjt, pg, fg) - c)) <= TOL * l1(c)
+    big = cjt.Plan(3 * (1 << 20) + 1, 0.1, 0.2, directions=cjt.CJT_FWD, M=13)
+    assert big.info()["grid_fwd"] == 1 << 22
+    with pytest.raises(cjt.CJTError) as e:
+        cjt.Plan(3 * (1 << 20) + 1, 0.1, 0.2, grid=-1)
+    assert e.value.code == cjt.CJT_EUNSUPPORTED
 
 
 # Mixed form (FP32 transforms of the asymptotic blocks, everything else FP64): stated bounds
