@@ -43,9 +43,15 @@ int cjt_internal_side_stream(cudaStream_t *out) {
     if (dev < 0 || dev >= 64) return CJT_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(mu);
     if (pool[dev].empty()) {
+        // Highest priority: the side streams carry the asymptotic chain (pack, two FFT
+        // passes), the longer of the two concurrent chains.  At equal priority the CTA
+        // scheduler hands freed SMs to the recurrence kernel launched first, whose
+        // thousands of CTAs then hold the chain back until they are all dispatched.
+        int least = 0, greatest = 0;
+        CJT_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
         for (int k = 0; k < 32; ++k) {
             cudaStream_t s;
-            CJT_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            CJT_CUDA_TRY(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest));
             pool[dev].push_back(s);
         }
     }
