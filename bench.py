@@ -13,8 +13,10 @@ timed steps, outside the timed events.
 Prints one JSON line.  `--impl reference` times the CPU oracle instead
 (rank 0 only), on a bounded sample of the same workload.
 
-Multi-GPU: transforms are independent, so `--gpus N` under torchrun runs N
-replicas of the workload (weak scaling, no collective on the data path).
+Multi-GPU: transforms are independent, so `--gpus N` under torchrun gives each
+rank its own seeded shard of the same shape (rank 0: the one-GPU workload) with
+no collective on the data path; `value` is the coefficients of all ranks over
+the slowest rank's time (weak scaling).
 """
 from __future__ import annotations
 
@@ -36,9 +38,11 @@ LOGNS = (12, 14, 16, 18)
 FP64_PEAK_DERIVED = 152 * 2070e6 * 4.0   # 152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM (1.25 TFLOP/s nominal)
 
 
-def workload():
-    from paper_1602_02618_gb300 import inputs
-    return inputs.single_workload(Ns=tuple(1 << k for k in LOGNS))
+def workload(rank=0):
+    """Rank `rank`'s items (rank 0: the one-GPU workload; see multirank.rank_seed)."""
+    from paper_1602_02618_gb300 import inputs, multirank
+    return inputs.single_workload(Ns=tuple(1 << k for k in LOGNS),
+                                  seed=multirank.rank_seed(inputs.BASE_SEED, rank))
 
 
 PREC_NAMES = {"fp64": "FP64", "mixed": "mixed (FP32 ASY transforms)",
@@ -133,12 +137,14 @@ def run_reference(args):
     items = workload()
     coeffs = 2 * sum(N + 1 for N, _, _, _ in items)
     small = [it for it in items if it[0] <= (1 << 14)]
+    # every host core, whatever OMP_NUM_THREADS says (torchrun sets it to 1 for N > 1)
+    cores = os.cpu_count() or 1
     def step():
         t = {}
         for N, a, b, c in small:
             t0 = time.perf_counter()
-            f = orc.forward(c, a, b)
-            orc.inverse(f, a, b)
+            f = orc.forward(c, a, b, nthreads=cores)
+            orc.inverse(f, a, b, nthreads=cores)
             t[N] = time.perf_counter() - t0
         Nmax = max(t)
         return sum(t[N] if N in t else t[Nmax] * (N / Nmax) ** 2 for N, _, _, _ in items)
@@ -147,7 +153,6 @@ def run_reference(args):
     times = [step() for _ in range(args.steps)]
     total = float(np.sum(times))
     value = coeffs * len(times) / total
-    cores = os.cpu_count()
     sample = ("oracle forward+inverse (double-double, O(N^2)) run in full at N=2^12 and 2^14; N=2^16, 2^18 "
               "extrapolated as t(2^14)*(N/2^14)^2")
     print(json.dumps({
@@ -166,17 +171,18 @@ def cpu_baseline_sample():
     orc.build()
     items = workload()
     coeffs = 2 * sum(N + 1 for N, _, _, _ in items)
+    cores = os.cpu_count() or 1
     t = {}
     for N, a, b, c in items:
         if N > (1 << 14):
             continue
         t0 = time.perf_counter()
-        f = orc.forward(c, a, b)
-        orc.inverse(f, a, b)
+        f = orc.forward(c, a, b, nthreads=cores)
+        orc.inverse(f, a, b, nthreads=cores)
         t[N] = time.perf_counter() - t0
     Nmax = max(t)
     total = sum(t[N] if N in t else t[Nmax] * (N / Nmax) ** 2 for N, _, _, _ in items)
-    return {"value": coeffs / total, "unit": "coeffs/s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": coeffs / total, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
             "sample": "oracle forward+inverse (double-double) in full at N=2^12, 2^14; N=2^16, 2^18 extrapolated "
                       "as t(2^14)*(N/2^14)^2; total %.1f s measured" % sum(t.values())}
 
@@ -186,14 +192,15 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
     (alpha, beta), random direction) replayed as one captured CUDA graph.
     --config mixed64: 64 transforms at N = 2^20 in the mixed form, checked
     against the plain FP64 GPU form and against the oracle at sampled points."""
-    from paper_1602_02618_gb300 import inputs
+    from paper_1602_02618_gb300 import inputs, multirank
     big = args.config == "mixed64"
+    seed = multirank.rank_seed(inputs.BASE_SEED, rank)
     if big:
-        items = inputs.mixed_large_workload(64, 1 << 20)
+        items = inputs.mixed_large_workload(64, 1 << 20, seed=seed)
         # the FP32 form of the workload, or (--precision df) its double-float form
         precision = cjt.CJT_DFLOAT if args.precision == "df" else cjt.CJT_MIXED
     else:
-        items = inputs.batch_workload(args.batch_count)
+        items = inputs.batch_workload(args.batch_count, seed=seed)
         precision = precision_code(cjt, args.precision)
     # plan options of the batch: M by size unless given; stored recurrence values for
     # items with N <= store_max (the stored matrices of 4096 plans must fit beside them)
@@ -233,8 +240,7 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
     for _ in range(args.warmup):
         batch.launch()
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    multirank.barrier(dist)
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     sampler.start()
     time.sleep(0.3)
@@ -245,14 +251,12 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
         batch.launch()
         evs[k][1].record(stream)
     torch.cuda.synchronize()
+    multirank.barrier(dist)
     clocks = sampler.stop()
     step_ms = np.array([a.elapsed_time(b) for a, b in evs])
-    total_s = float(step_ms.sum()) / 1e3
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = coeffs * args.steps * world / total_s
+    total_s = multirank.max_over_ranks(float(step_ms.sum()) / 1e3, dist, dev)
+    coeffs_all = multirank.sum_over_ranks(coeffs, dist, dev)
+    value = multirank.job_rate(coeffs_all * args.steps, total_s)
     # accuracy against the oracle on the items it computes in well under a second
     from oracle import oracle as orc
     orc.build()
@@ -312,7 +316,7 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
         batch.launch()
         host_out.copy_(out, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = multirank.max_over_ranks(time.perf_counter() - t0, dist, dev)
     plan_bytes = sum(p.info()["device_bytes"] for p in plans)
     if rank == 0:
         print(json.dumps({
@@ -347,7 +351,8 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
                          "traffic": None,
                          "peak_source": "effective peak of the work mix: recurrence on the derived FP64 pipe "
                                         "peak, transforms at the %s" % asy_src},
-            "e2e": {"value": coeffs * ksteps * world / e2e_s, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs * 8,
+            "e2e": {"value": multirank.job_rate(coeffs_all * ksteps, e2e_s), "unit": "coeffs/s",
+                    "h2d_bytes_per_step": coeffs * 8,
                     "d2h_bytes_per_step": coeffs * 8},
             "gpu_launches": int(binfo["kernels"]) * args.steps,
             "setup": {"plan_s": plan_s, "graph_capture_s": graph_s, "plan_bytes": plan_bytes,
@@ -356,15 +361,17 @@ def run_batched(args, torch, cjt, dev, world, rank, dist):
         }))
 
 
-def run_serving(args, torch, cjt, rank):
-    """--config serving: Poisson arrivals at swept rates, continuous batching, 40 GB budget."""
-    from paper_1602_02618_gb300 import inputs, serve
+def run_serving(args, torch, cjt, dev, world, rank, dist):
+    """--config serving: Poisson arrivals at swept rates, continuous batching, 40 GB budget.
+    Under torchrun each rank serves its own request stream on its own GPU."""
+    from paper_1602_02618_gb300 import inputs, multirank, serve
     precision = precision_code(cjt, args.precision)
     rates = [float(r) for r in args.rates.split(",")]
     results = []
     for k, rate in enumerate(rates):
         reqs = [serve.Request(N, a, b, cjt.CJT_FWD if d == 1 else cjt.CJT_INV, c)
-                for N, a, b, d, c in inputs.serving_requests(args.requests, seed=inputs.BASE_SEED + 100 * k)]
+                for N, a, b, d, c in inputs.serving_requests(
+                    args.requests, seed=multirank.rank_seed(inputs.BASE_SEED, rank) + 100 * k)]
         sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
         sampler.start()
         server = serve.Server(slots=16, mem_budget=40e9, precision=precision, planners=args.planners)
@@ -376,10 +383,14 @@ def run_serving(args, torch, cjt, rank):
         st["clocks"] = sampler.stop()
         results.append(st)
         torch.cuda.empty_cache()
-    best = max(results, key=lambda r: r["coeffs_per_s"])
+    # every rank serves the same arrival rates: the job's throughput at a rate is the sum
+    # over ranks, and the line reports the best rate
+    job = [multirank.sum_over_ranks(r["coeffs_per_s"], dist, dev) for r in results]
+    kbest = int(np.argmax(job))
+    best, value = results[kbest], job[kbest]
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": best["coeffs_per_s"], "unit": "coeffs/s", "n_gpus": 1,
+            "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world,
             "steps": args.requests, "warmup": 0, "ms_per_step": best["mean_ms"],
             "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPES[args.precision],
@@ -424,9 +435,8 @@ def main():
         return
 
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1602_02618_gb300 import multirank
+    world, rank, local = multirank.env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -439,7 +449,10 @@ def main():
     from paper_1602_02618_gb300 import autotune, cjt
 
     if args.config == "serving":
-        run_serving(args, torch, cjt, rank)
+        run_serving(args, torch, cjt, dev, world, rank, dist)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
         return
     if args.config in ("batched", "mixed64"):
         run_batched(args, torch, cjt, dev, world, rank, dist)
@@ -448,7 +461,7 @@ def main():
             dist.destroy_process_group()
         return
     precision = precision_code(cjt, args.precision)
-    items = workload()
+    items = workload(rank)
     if args.only_logn:
         items = [it for it in items if it[0] == (1 << args.only_logn)]
     if args.params:
@@ -485,8 +498,7 @@ def main():
     for p in plans:
         p.set_profiling(True)
         p.profile()  # clear
-    if dist:
-        dist.barrier()
+    multirank.barrier(dist)
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
@@ -500,15 +512,12 @@ def main():
         torch.cuda.nvtx.range_pop()
         evs[k][1].record(stream)
     torch.cuda.synchronize()
+    multirank.barrier(dist)
     clocks = sampler.stop()
     step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
-    total_s = float(step_ms.sum()) / 1e3
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-        dist.barrier()
-    value = coeffs_per_step * args.steps * world / total_s
+    total_s = multirank.max_over_ranks(float(step_ms.sum()) / 1e3, dist, dev)
+    coeffs_all = multirank.sum_over_ranks(coeffs_per_step, dist, dev)
+    value = multirank.job_rate(coeffs_all * args.steps, total_s)
 
     # stage times measured live during the timed region
     prof = {}
@@ -624,16 +633,11 @@ def main():
     e2e_s = float("nan")
     if not args.no_e2e:
         e2e_step()
-        if dist:
-            dist.barrier()
+        multirank.barrier(dist)
         t0 = time.perf_counter()
         for _ in range(ksteps):
             e2e_step()
-        e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = multirank.max_over_ranks(time.perf_counter() - t0, dist, dev)
     bytes_io = 2 * sum(8 * (N + 1) for N, _, _, _ in items)
 
     if rank == 0:
@@ -647,7 +651,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload_desc(args.precision, args.params), "N": [it[0] for it in items],
                        "options": chosen, "l2": "flushed between steps (512 MiB write, outside timed events)",
-                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "parallelism": ("%d independent shards (one per rank, no collective on the data path)"
+                                       % world) if world > 1 else "single GPU",
                        "plan_ms": [round(inf["plan_ms"], 2) for inf in infos],
                        "expansion": [inf["expansion"] for inf in infos],
                        "parity_fold": [inf["parity_fold"] for inf in infos]},
@@ -655,7 +660,8 @@ def main():
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": (coeffs_per_step * ksteps * world / e2e_s) if e2e_s == e2e_s else None, "unit": "coeffs/s",
+            "e2e": {"value": multirank.job_rate(coeffs_all * ksteps, e2e_s) if e2e_s == e2e_s else None,
+                    "unit": "coeffs/s",
                     "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
             "gpu_launches": int(launches),
             "clocks": clocks,
