@@ -79,6 +79,12 @@ extern "C" {
 #define CJT_EXPANSION_ULTRASPHERICAL 2 /* alpha = beta = lambda - 1/2 (App. B.1): one
                                           cosine per term (requires alpha = beta)         */
 
+/* values of cjt_plan_opts.overlap */
+#define CJT_OVERLAP_AUTO 0
+#define CJT_OVERLAP_ASY_FIRST 1
+#define CJT_OVERLAP_EQUAL 2
+#define CJT_OVERLAP_REC_FIRST 3
+
 /* directions a plan is built for */
 #define CJT_FWD 1
 #define CJT_INV 2
@@ -121,6 +127,16 @@ typedef struct {
                          and the (2G+1)-point Clenshaw--Curtis rule is exact wherever the
                          (2N+1)-point rule is.  0 (default): the power-of-two grid when N
                          is not a power of two (identical to -1 otherwise).              */
+    int overlap;      /* scheduling of an execution's two concurrent chains, the
+                         asymptotic blocks (pack, transforms; Eq. "PNASY") and the
+                         recurrence (Sec. 4.2), which run on separate streams and join
+                         before the combine.  The result does not depend on it (bit for
+                         bit).  CJT_OVERLAP_ASY_FIRST: the asymptotic chain on a stream of
+                         the highest priority, so the CTA scheduler serves it first and
+                         the recurrence fills the SMs it leaves.  CJT_OVERLAP_EQUAL: both
+                         at normal priority.  CJT_OVERLAP_REC_FIRST: the recurrence on a
+                         stream of the highest priority.  CJT_OVERLAP_AUTO (0, default):
+                         the library's choice for the plan's precision.                   */
 } cjt_plan_opts;
 
 /* Summary of a plan (for reports and tests). Sizes are per direction. */
@@ -151,6 +167,7 @@ typedef struct {
                                            recurrence covers the rows i <= Ng/2 and yields
                                            rows Ng - i by P_n(-x) = (-1)^n P_n(x)
                                            (DLMF 18.6.1), half the values and the work    */
+    int overlap;                        /* CJT_OVERLAP_* used (AUTO resolved)              */
 } cjt_plan_info;
 
 /* Stages reported by cjt_get_profile (forward 0-4, inverse 5-9). */

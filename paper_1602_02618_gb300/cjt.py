@@ -33,13 +33,17 @@ CJT_INV = 2
 CJT_EXPANSION_AUTO = 0
 CJT_EXPANSION_HAHN = 1
 CJT_EXPANSION_ULTRASPHERICAL = 2
+CJT_OVERLAP_AUTO = 0
+CJT_OVERLAP_ASY_FIRST = 1
+CJT_OVERLAP_EQUAL = 2
+CJT_OVERLAP_REC_FIRST = 3
 
 
 class cjt_plan_opts(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("eps", ctypes.c_double), ("precision", ctypes.c_int),
                 ("directions", ctypes.c_int), ("ratio", ctypes.c_double), ("seg_len", ctypes.c_int),
                 ("use_asy", ctypes.c_int), ("shared_workspace", ctypes.c_int), ("rec_store", ctypes.c_int),
-                ("expansion", ctypes.c_int), ("grid", ctypes.c_int)]
+                ("expansion", ctypes.c_int), ("grid", ctypes.c_int), ("overlap", ctypes.c_int)]
 
 
 class cjt_plan_info(ctypes.Structure):
@@ -53,7 +57,7 @@ class cjt_plan_info(ctypes.Structure):
                 ("kernels_inv", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("rec_store_bytes", ctypes.c_int64), ("shift_alpha", ctypes.c_int), ("shift_beta", ctypes.c_int),
                 ("expansion", ctypes.c_int), ("grid_fwd", ctypes.c_int64), ("grid_inv", ctypes.c_int64),
-                ("parity_fold", ctypes.c_int)]
+                ("parity_fold", ctypes.c_int), ("overlap", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -168,10 +172,10 @@ class Plan:
     def __init__(self, N: int, alpha: float, beta: float, M: int = 0, eps: float = 0.0, precision: int = CJT_FP64,
                  directions: int = 0, ratio: float = 0.0, seg_len: int = 0, use_asy: int = 0,
                  shared_workspace: bool = False, rec_store: int = 0, expansion: int = CJT_EXPANSION_AUTO,
-                 grid: int = 0, stream=None):
+                 grid: int = 0, overlap: int = CJT_OVERLAP_AUTO, stream=None):
         lib = load()
         o = cjt_plan_opts(M, eps, precision, directions, ratio, seg_len, use_asy, 1 if shared_workspace else 0,
-                          int(rec_store), int(expansion), int(grid))
+                          int(rec_store), int(expansion), int(grid), int(overlap))
         h = ctypes.c_void_p()
         _check(lib.cjt_plan(ctypes.byref(h), int(N), float(alpha), float(beta), ctypes.byref(o),
                             _stream_handle(stream)), "cjt_plan")

@@ -34,28 +34,30 @@ int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st) {
     return CJT_OK;
 }
 
-int cjt_internal_side_stream(cudaStream_t *out) {
+int cjt_internal_side_stream(bool high, cudaStream_t *out) {
+    // Two pools per device: streams of the highest priority and of normal priority.  A
+    // chain on a high-priority stream is served first by the CTA scheduler: at equal
+    // priority it hands freed SMs to the kernel launched first, so a chain whose head
+    // kernel waits behind the thousands of CTAs of the other chain's kernel effectively
+    // runs after it.
     static std::mutex mu;
-    static std::vector<cudaStream_t> pool[64];
-    static unsigned next[64] = {0};
+    static std::vector<cudaStream_t> pool[2][64];
+    static unsigned next[2][64] = {{0}};
     int dev = 0;
     CJT_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return CJT_EUNSUPPORTED;
+    const int h = high ? 1 : 0;
     std::lock_guard<std::mutex> lk(mu);
-    if (pool[dev].empty()) {
-        // Highest priority: the side streams carry the asymptotic chain (pack, two FFT
-        // passes), the longer of the two concurrent chains.  At equal priority the CTA
-        // scheduler hands freed SMs to the recurrence kernel launched first, whose
-        // thousands of CTAs then hold the chain back until they are all dispatched.
+    if (pool[h][dev].empty()) {
         int least = 0, greatest = 0;
         CJT_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
         for (int k = 0; k < 32; ++k) {
             cudaStream_t s;
-            CJT_CUDA_TRY(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest));
-            pool[dev].push_back(s);
+            CJT_CUDA_TRY(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, high ? greatest : least));
+            pool[h][dev].push_back(s);
         }
     }
-    *out = pool[dev][next[dev]++ % pool[dev].size()];
+    *out = pool[h][dev][next[h][dev]++ % pool[h][dev].size()];
     return CJT_OK;
 }
 
@@ -79,6 +81,7 @@ void free_plan(cjt_plan_s *p) {
     if (p->done) cudaEventDestroy(p->done);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->ev_join_rec) cudaEventDestroy(p->ev_join_rec);
     delete p;
 }
 }  // namespace
@@ -141,6 +144,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
         o.rec_store = opts->rec_store;
         o.expansion = opts->expansion;
         o.grid = opts->grid;
+        o.overlap = opts->overlap;
     }
     if (o.M < 1 || o.M > 20) return CJT_EINVAL;
     if (!(o.eps > 0.0 && o.eps < 1.0)) return CJT_EINVAL;
@@ -151,6 +155,8 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     if (o.expansion < CJT_EXPANSION_AUTO || o.expansion > CJT_EXPANSION_ULTRASPHERICAL) return CJT_EINVAL;
     if (o.expansion == CJT_EXPANSION_ULTRASPHERICAL && alpha != beta) return CJT_EINVAL;
     if (o.grid < -1 || o.grid > 1) return CJT_EINVAL;
+    if (o.overlap < CJT_OVERLAP_AUTO || o.overlap > CJT_OVERLAP_REC_FIRST) return CJT_EINVAL;
+    if (o.overlap == CJT_OVERLAP_AUTO) o.overlap = CJT_OVERLAP_ASY_FIRST;
     if (o.seg_len < 32 || o.seg_len > (1 << 20) || (o.seg_len % 32) != 0) return CJT_EINVAL;
     if (N > (1LL << 21) && !is_pow2(N) && o.grid == -1) return CJT_EUNSUPPORTED;   // Bluestein lengths <= 2^24
 
@@ -209,6 +215,7 @@ int cjt_get_info(cjt_plan_t p, cjt_plan_info *info) {
     info->shift_beta = p->shift_b;
     info->expansion = p->expansion_used;
     info->parity_fold = (p->fw.fold || p->iv.fold) ? 1 : 0;
+    info->overlap = p->opts.overlap;
     info->grid_fwd = (p->opts.directions & CJT_FWD) ? p->Gf : 0;
     info->grid_inv = (p->opts.directions & CJT_INV) ? 2 * p->Gi : 0;
     info->M = p->M;

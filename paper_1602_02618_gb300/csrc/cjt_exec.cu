@@ -742,11 +742,14 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         CJT_CUDA_TRY(cudaGetLastError());
     }
     // the asymptotic transforms run on a side stream, concurrently with the recurrence
+    // (on the caller's stream, or on a second side stream with CJT_OVERLAP_REC_FIRST)
     const bool ovl = nq > 0 && p->side;
     cudaStream_t sa = ovl ? p->side : st;
+    cudaStream_t sr = (ovl && p->side_rec) ? p->side_rec : st;
     if (ovl) {
         CJT_CUDA_TRY(cudaEventRecord(p->ev_fork, st));
         CJT_CUDA_TRY(cudaStreamWaitEvent(sa, p->ev_fork, 0));
+        if (sr != st) CJT_CUDA_TRY(cudaStreamWaitEvent(sr, p->ev_fork, 0));
     }
     if (nq > 0) {
         dim3 gp(blocks_for(L, 256), p->npair_f);
@@ -767,21 +770,25 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     // REC
     if (gw.nitems > 0) {
-        StageTimer tm(p, st, CJT_STAGE_FWD_REC);
+        StageTimer tm(p, sr, CJT_STAGE_FWD_REC);
         if (gw.d_E && gw.E_df)
-            k_rec_fwd_stored_df<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, cdf,
+            k_rec_fwd_stored_df<<<(unsigned)gw.nitems, 32 * SW, 0, sr>>>(gw.d_items, gw.nitems, cdf,
                                                                                 (const dfs *)gw.d_E, ws.part_f);
         else if (gw.d_E)
-            k_rec_fwd_stored<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, in, gw.d_E,
+            k_rec_fwd_stored<<<(unsigned)gw.nitems, 32 * SW, 0, sr>>>(gw.d_items, gw.nitems, in, gw.d_E,
                                                                              ws.part_f);
         else
-            k_rec_fwd<<<blocks_for(gw.nitems * 32, 128), 128, 0, st>>>(gw.d_items, gw.nitems, gw.Ng, p->rt, in,
+            k_rec_fwd<<<blocks_for(gw.nitems * 32, 128), 128, 0, sr>>>(gw.d_items, gw.nitems, gw.Ng, p->rt, in,
                                                                       gw.d_states, ws.part_f);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     if (ovl) {
         CJT_CUDA_TRY(cudaEventRecord(p->ev_join, sa));
         CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
+        if (sr != st) {
+            CJT_CUDA_TRY(cudaEventRecord(p->ev_join_rec, sr));
+            CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join_rec, 0));
+        }
     }
     double2 *ext = (double2 *)ws.dct;
     const int64_t G = p->Gf;   // grid rows 0..G (the combines' "N" is the grid)
@@ -846,11 +853,14 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         CJT_CUDA_TRY(cudaGetLastError());
     }
     // transposed asymptotic blocks, on a side stream concurrently with the recurrence
+    // (on the caller's stream, or on a second side stream with CJT_OVERLAP_REC_FIRST)
     const bool ovl = nq > 0 && p->side;
     cudaStream_t sa = ovl ? p->side : st;
+    cudaStream_t sr = (ovl && p->side_rec) ? p->side_rec : st;
     if (ovl) {
         CJT_CUDA_TRY(cudaEventRecord(p->ev_fork, st));
         CJT_CUDA_TRY(cudaStreamWaitEvent(sa, p->ev_fork, 0));
+        if (sr != st) CJT_CUDA_TRY(cudaStreamWaitEvent(sr, p->ev_fork, 0));
     }
     if (nq > 0) {
         dim3 gp(blocks_for(L, 256), p->npair_i);
@@ -873,26 +883,30 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     // transposed recurrence and the fixed-order sums over the items of each degree
     {
-        StageTimer tm(p, st, CJT_STAGE_INV_REC);
+        StageTimer tm(p, sr, CJT_STAGE_INV_REC);
         if (gw.nitems > 0) {
             if (gw.d_E && gw.E_df)
-                k_rec_inv_stored_df<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, Ng, gdf,
+                k_rec_inv_stored_df<<<(unsigned)gw.nitems, 32 * SW, 0, sr>>>(gw.d_items, gw.nitems, Ng, gdf,
                                                                                (const dfs *)gw.d_E, ws.part_i);
             else if (gw.d_E)
-                k_rec_inv_stored<<<(unsigned)gw.nitems, 32 * SW, 0, st>>>(gw.d_items, gw.nitems, Ng, ws.g, gw.d_E,
+                k_rec_inv_stored<<<(unsigned)gw.nitems, 32 * SW, 0, sr>>>(gw.d_items, gw.nitems, Ng, ws.g, gw.d_E,
                                                                             ws.part_i);
             else
-                k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, st>>>(gw.d_items, gw.nitems, Ng, p->rt,
+                k_rec_inv<<<blocks_for(gw.nitems, RI_WARPS), 32 * RI_WARPS, 0, sr>>>(gw.d_items, gw.nitems, Ng, p->rt,
                                                                                      ws.g, gw.d_states, ws.part_i);
             CJT_CUDA_TRY(cudaGetLastError());
         }
-        k_inv_reduce<<<blocks_for(N + 1, 32), 32 * RED_WARPS, 0, st>>>(N, p->seg_len, gw.d_seg_ptr, gw.d_seg_out,
+        k_inv_reduce<<<blocks_for(N + 1, 32), 32 * RED_WARPS, 0, sr>>>(N, p->seg_len, gw.d_seg_ptr, gw.d_seg_out,
                                                                          gw.d_seg_b, ws.part_i, ws.y);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     if (ovl) {
         CJT_CUDA_TRY(cudaEventRecord(p->ev_join, sa));
         CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
+        if (sr != st) {
+            CJT_CUDA_TRY(cudaEventRecord(p->ev_join_rec, sr));
+            CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join_rec, 0));
+        }
     }
     StageTimer tm(p, st, CJT_STAGE_INV_COMBINE);
     if (dfx)

@@ -38,7 +38,9 @@ void cjt_internal_set_cuda_error(cudaError_t e, const char *what);
 struct cjt_plan_s;
 int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st);
 int cjt_internal_end_use(cjt_plan_s *p, cudaStream_t st);
-int cjt_internal_side_stream(cudaStream_t *out);   // round-robin pool of non-blocking streams per device
+// round-robin pools of non-blocking streams per device, of the highest (high) or the
+// normal priority
+int cjt_internal_side_stream(bool high, cudaStream_t *out);
 
 // ---------------------------------------------------------------------------
 // recurrence work items
@@ -224,10 +226,12 @@ struct cjt_plan_s {
     double *d_s = nullptr;        // inverse: 1/A_n (N+1)
     double *d_in = nullptr, *d_out = nullptr;  // staging for cjt_execute_host
 
-    // overlap of the asymptotic transforms with the recurrence: a side stream from the
-    // device pool and a fork/join event pair
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // overlap of the asymptotic transforms with the recurrence (option overlap): the
+    // asymptotic chain on a side stream from a device pool, the recurrence on the caller's
+    // stream or (CJT_OVERLAP_REC_FIRST) on a high-priority side stream; a fork event and
+    // one join event per side stream
+    cudaStream_t side = nullptr, side_rec = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_rec = nullptr;
 
     // concurrency guard
     cudaStream_t last_stream = nullptr;

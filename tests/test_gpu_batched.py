@@ -92,6 +92,27 @@ def test_batch_graph_equals_alone_and_replays(cjt, orc):
     batch.close()
 
 
+@pytest.mark.parametrize("overlap", [2, 3])
+def test_batch_graph_overlap_modes(cjt, overlap):
+    """A captured batch of plans whose recurrence runs on its own side stream (or whose
+    chains share one priority) replays to the items' results alone, bit for bit."""
+    items = mixed_items(count=12, seed=inputs.BASE_SEED + 950)
+    ref = run_alone(cjt, items)
+    plans = [cjt.Plan(N, a, b, precision=prec, shared_workspace=True, overlap=overlap)
+             for N, a, b, d, prec, _ in items]
+    offs, x = pack(items)
+    out = torch.full_like(x, float("nan"))
+    batch = cjt.Batch(plans, [it[3] for it in items], offs, x, out, nstreams=4)
+    for rep in range(2):
+        out.fill_(float("nan"))
+        batch.launch()
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        for (N, *_), off, r in zip(items, offs, ref):
+            assert np.array_equal(o[off:off + N + 1], r), (rep, N)
+    batch.close()
+
+
 def test_workspace_entry_points(cjt):
     N, a, b = 5000, 0.2, -0.1
     c = inputs.decaying_coefficients(N, 1.0, 17)

@@ -283,3 +283,32 @@ def test_stored_recurrence_values(cjt, orc, N):
     assert info["rec_store_bytes"] >= 8 * (info["rec_steps_fwd"] + info["rec_steps_inv"]) > 0
     assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, a, b))) <= TOL * l1(c)
     assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, a, b))) <= TOL * l1(c)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("overlap", [1, 2, 3])
+@pytest.mark.parametrize("store", [0, 1])
+def test_overlap_modes_are_bit_identical(cjt, orc, precision, overlap, store):
+    """The option `overlap` only schedules the two concurrent chains of an execution:
+    every mode gives the default plan's result bit for bit, on repeated executions, and
+    the forward and inverse stay within the form's bound against the oracle."""
+    N, a, b = 1 << 14, 0.1, -0.3
+    c = inputs.decaying_coefficients(N, 1.0, inputs.BASE_SEED + 77)
+    ref_plan = cjt.Plan(N, a, b, precision=precision, rec_store=store)
+    plan = cjt.Plan(N, a, b, precision=precision, rec_store=store, overlap=overlap)
+    assert ref_plan.info()["overlap"] == cjt.CJT_OVERLAP_ASY_FIRST
+    assert plan.info()["overlap"] == overlap and plan.info()["nblk_fwd"] > 0 and plan.info()["nblk_inv"] > 0
+    want_f, want_i = run_fwd(cjt, ref_plan, c), run_inv(cjt, ref_plan, c)
+    for _ in range(2):
+        assert np.array_equal(run_fwd(cjt, plan, c), want_f)
+        assert np.array_equal(run_inv(cjt, plan, c), want_i)
+    tol_f, tol_i = (1e-9, 1e-5) if precision == 1 else (TOL, TOL)
+    assert np.max(np.abs(want_f - orc.forward(c, a, b))) <= tol_f * l1(c)
+    assert np.max(np.abs(want_i - orc.inverse(c, a, b))) <= tol_i * l1(c)
+
+
+def test_overlap_option_checked(cjt):
+    for bad in (-1, 4):
+        with pytest.raises(cjt.CJTError) as e:
+            cjt.Plan(64, 0.1, -0.3, overlap=bad)
+        assert e.value.code == cjt.CJT_EINVAL
