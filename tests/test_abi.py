@@ -45,3 +45,31 @@ def test_host_only_calls(lib):
 def test_binding_names_match_header():
     from paper_1602_02618_gb300 import cjt
     assert sorted(cjt.EXPORTED) == declared_functions()
+
+
+def header_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/cjt.h, in order."""
+    text = open(os.path.join(ROOT, "include", "cjt.h")).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    m = re.search(r"typedef\s+struct\s*\{([^}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, names = re.match(r"(\w+)\s+(.*)", decl).groups()
+        fields += [(n.strip(), ctype) for n in names.split(",")]
+    return fields
+
+
+@pytest.mark.parametrize("name", ["cjt_plan_opts", "cjt_plan_info"])
+def test_binding_structs_match_header(name):
+    """The ctypes structures of the binding list the header's fields in the header's order,
+    with the same C types, so that options and plan summaries cross the ABI intact."""
+    import ctypes as ct
+    from paper_1602_02618_gb300 import cjt
+    ctypes_of = {"int": ct.c_int, "double": ct.c_double, "int64_t": ct.c_int64}
+    want = [(n, ctypes_of[t]) for n, t in header_struct_fields(name)]
+    got = list(getattr(cjt, name)._fields_)
+    assert got == want
