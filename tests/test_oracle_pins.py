@@ -7,8 +7,10 @@ connection coefficients), endpoint values (Eq. "Pnendpts"), the symmetry
 relation (Eq. "Pnsym"), library quadrature (Gauss--Jacobi from SciPy) for the
 modified moments and the orthonormalisation constants (Eq. "Anab"),
 mpmath Gamma functions, and a dense linear solve for the inverse map
-(Eq. "iCJT").  A planted-mistake test shows that the moment pin catches the
-mu_1 sign as printed in Sec. 3.1.
+(Eq. "iCJT").  Planted-mistake tests build copies of the oracle with one
+plausible slip each (the mu_1 sign as printed in Sec. 3.1, a dropped B_n, the
+missing halving of c_N, a Clenshaw--Curtis end factor, a wrong normalisation
+constant) and show that a pin rejects every one.
 """
 import ctypes
 import os
@@ -369,6 +371,57 @@ def test_planted_dropped_B_term_is_caught(tmp_path):
     lib.orc_jacobi_values(8, 0.1, -0.3, 1, 3, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     exact = float(_eval_poly(ex.jacobi_monomial(5, 0.1, -0.3), Fraction(1, 2)))
     assert abs(out[5] - exact) > 1e-6
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_planted_missing_last_halving_is_caught(tmp_path):
+    """T_N^{-1} halves c_N as well as c_0 (aliasing of T_N on N+1 Lobatto points); a copy
+    that halves c_0 only fails the exact-rational pin of the forward map."""
+    lib = _build_mutant(tmp_path, "if (k == 0 || k == N) s = dd_mul_d(s, 0.5);\n        c[k] = s.hi + s.lo;",
+                        "if (k == 0) s = dd_mul_d(s, 0.5);\n        c[k] = s.hi + s.lo;")
+    lib.orc_forward.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, _dp, _dp, ctypes.c_int]
+    N, a, b = 5, 0.1, -0.3
+    c = inputs.decaying_coefficients(N, 1.0, seed=inputs.BASE_SEED + N)
+    got = np.empty(N + 1)
+    lib.orc_forward(N, a, b, c.ctypes.data_as(_dp), got.ctypes.data_as(_dp), 1)
+    exact = np.array([float(v) for v in ex.forward_exact(c, a, b)])
+    assert np.max(np.abs(got - exact)) > 1e-3 * np.abs(exact).max()
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_planted_cc_weight_end_factor_is_caught(tmp_path):
+    """The Clenshaw--Curtis weights carry eps_i = 1/2 at both ends; a copy without it at
+    i = Ng fails the exactness pin w^T T_k = mu_k."""
+    lib = _build_mutant(tmp_path, "if (i == 0 || i == Ng) s = dd_mul_d(s, 0.5);\n        w[i] = s;",
+                        "if (i == 0) s = dd_mul_d(s, 0.5);\n        w[i] = s;")
+    lib.orc_cc_weights.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int]
+    lib.orc_moments.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, _dp]
+    Ng = 32
+    w, mu = np.empty(Ng + 1), np.empty(Ng + 1)
+    lib.orc_cc_weights(Ng, 0.1, -0.3, w.ctypes.data_as(_dp), 1)
+    lib.orc_moments(Ng, 0.1, -0.3, mu.ctypes.data_as(_dp))
+    i = np.arange(Ng + 1)
+    err = max(abs(np.dot(w, np.cos(np.pi * ((i * k) % (2 * Ng)) / Ng)) - mu[k]) for k in range(Ng + 1))
+    assert err > 1e-3 * mu[0]
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_planted_norm_constant_slip_is_caught(tmp_path):
+    """A_1 = mu_0 (a+1)(b+1)/(a+b+3) (Eq. "Anab"); a copy with a+b+2 in the denominator
+    fails the Gamma-function pin from n = 1 on."""
+    lib = _build_mutant(tmp_path, "dd_add(ab, dd_d(3.0)));", "dd_add(ab, dd_d(2.0)));")
+    lib.orc_norm_consts.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, _dp]
+    N, a, b = 50, 0.1, -0.3
+    A = np.empty(N + 1)
+    lib.orc_norm_consts(N, a, b, A.ctypes.data_as(_dp))
+    am, bm = mpmath.mpf(a), mpmath.mpf(b)
+    n = 10
+    ref = (2 ** (am + bm + 1) * mpmath.gamma(n + am + 1) * mpmath.gamma(n + bm + 1)
+           / ((2 * n + am + bm + 1) * mpmath.gamma(n + am + bm + 1) * mpmath.factorial(n)))
+    assert abs(A[n] / float(ref) - 1) > 1e-3
 
 
 def two_term_raise(a_coef, alpha, beta, which):
