@@ -125,6 +125,35 @@ class ClockSampler:
                 "power_w_median": float(np.median(power)) if power else None}
 
 
+def _oracle_step_seconds(orc, items, forward, inverse, nthreads):
+    """Seconds of one step of the workload on the CPU: forward then inverse run in full for
+    the items with N <= 2^14; the larger items extrapolated by the exact O(N^2) cost of the
+    definitions, t(2^14) (N / 2^14)^2.  Returns (step seconds, seconds measured)."""
+    t = {}
+    for N, a, b, c in items:
+        if N > (1 << 14):
+            continue
+        t0 = time.perf_counter()
+        f = forward(c, a, b, nthreads=nthreads)
+        inverse(f, a, b, nthreads=nthreads)
+        t[N] = time.perf_counter() - t0
+    Nmax = max(t)
+    return sum(t[N] if N in t else t[Nmax] * (N / Nmax) ** 2 for N, _, _, _ in items), sum(t.values())
+
+
+SAMPLE = ("forward+inverse run in full at N=2^12 and 2^14; N=2^16, 2^18 extrapolated as "
+          "t(2^14)*(N/2^14)^2")
+
+
+def fp64_naive_baseline(orc, items, coeffs, cores):
+    """The plain-double O(N^2) forward and inverse (orc_forward_f64, orc_inverse_f64) on all
+    host cores and on one core, same sample as the oracle."""
+    all_s, _ = _oracle_step_seconds(orc, items, orc.forward_f64, orc.inverse_f64, cores)
+    one_s, _ = _oracle_step_seconds(orc, items, orc.forward_f64, orc.inverse_f64, 1)
+    return {"value_all_cores": coeffs / all_s, "value_1_core": coeffs / one_s, "unit": "coeffs/s",
+            "cores": cores, "sample": "plain-double O(N^2) " + SAMPLE}
+
+
 def run_reference(args):
     """The CPU oracle on the host cores: each step runs the oracle's forward and inverse
     transform on the N = 2^12 and N = 2^14 items of the workload (full transforms) and
@@ -136,55 +165,40 @@ def run_reference(args):
     orc.build()
     items = workload()
     coeffs = 2 * sum(N + 1 for N, _, _, _ in items)
-    small = [it for it in items if it[0] <= (1 << 14)]
     # every host core, whatever OMP_NUM_THREADS says (torchrun sets it to 1 for N > 1)
     cores = os.cpu_count() or 1
     def step():
-        t = {}
-        for N, a, b, c in small:
-            t0 = time.perf_counter()
-            f = orc.forward(c, a, b, nthreads=cores)
-            orc.inverse(f, a, b, nthreads=cores)
-            t[N] = time.perf_counter() - t0
-        Nmax = max(t)
-        return sum(t[N] if N in t else t[Nmax] * (N / Nmax) ** 2 for N, _, _, _ in items)
+        return _oracle_step_seconds(orc, items, orc.forward, orc.inverse, cores)[0]
     for _ in range(args.warmup):
         step()
     times = [step() for _ in range(args.steps)]
     total = float(np.sum(times))
     value = coeffs * len(times) / total
-    sample = ("oracle forward+inverse (double-double, O(N^2)) run in full at N=2^12 and 2^14; N=2^16, 2^18 "
-              "extrapolated as t(2^14)*(N/2^14)^2")
+    sample = "oracle (double-double, O(N^2)) " + SAMPLE
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (double-double)",
         "data": "synthetic", "config": {"workload": workload_desc("fp64")},
-        "cpu_baseline": {"value": value, "unit": "coeffs/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "coeffs/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "fp64_naive": fp64_naive_baseline(orc, items, coeffs, cores)},
         "e2e": {"value": value, "unit": "coeffs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
 def cpu_baseline_sample():
-    """The oracle as it stands, timed once on the host cores (same sample as --impl reference)."""
+    """The oracle as it stands (double-double), timed once on the host cores (same sample as
+    --impl reference), and beside it the plain-double O(N^2) baseline on all cores and on
+    one core."""
     from oracle import oracle as orc
     orc.build()
     items = workload()
     coeffs = 2 * sum(N + 1 for N, _, _, _ in items)
     cores = os.cpu_count() or 1
-    t = {}
-    for N, a, b, c in items:
-        if N > (1 << 14):
-            continue
-        t0 = time.perf_counter()
-        f = orc.forward(c, a, b, nthreads=cores)
-        orc.inverse(f, a, b, nthreads=cores)
-        t[N] = time.perf_counter() - t0
-    Nmax = max(t)
-    total = sum(t[N] if N in t else t[Nmax] * (N / Nmax) ** 2 for N, _, _, _ in items)
+    total, measured = _oracle_step_seconds(orc, items, orc.forward, orc.inverse, cores)
     return {"value": coeffs / total, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
-            "sample": "oracle forward+inverse (double-double) in full at N=2^12, 2^14; N=2^16, 2^18 extrapolated "
-                      "as t(2^14)*(N/2^14)^2; total %.1f s measured" % sum(t.values())}
+            "sample": "oracle (double-double) %s; total %.1f s measured" % (SAMPLE, measured),
+            "fp64_naive": fp64_naive_baseline(orc, items, coeffs, cores)}
 
 
 def run_batched(args, torch, cjt, dev, world, rank, dist):

@@ -28,7 +28,7 @@
  * The file must be compiled with -ffp-contract=off (no implicit fma contraction
  * inside the error-free transformations).
  *
- * A second, plain-double forward path (orc_forward_f64) exists only as the
+ * Second, plain-double paths (orc_forward_f64, orc_inverse_f64) exist only as the
  * timed "naive O(N^2) CPU" baseline; parity uses the double-double routines.
  *
  * All entry points return 0 on success and a negative value on bad arguments.
@@ -541,5 +541,83 @@ int orc_inverse(int64_t N, double a, double b, const double *c_cheb, double *c_j
     }
     free(An); free(part); free(g); free(w);
     rec_table_free(&t);
+    return 0;
+}
+
+/* Plain-double inverse (the definition of orc_inverse in plain double arithmetic and
+ * libm cosines): moments by the recurrence of Sec. 3.1, Clenshaw--Curtis weights by
+ * the direct cosine sum, g_i = w_i p_N(x_i) on the 2N grid, the inner products
+ * sum_i g_i P_n(x_i) by the three-term recurrence and 1/A_n (Eq. "Anab").  The naive
+ * O(N^2) CPU reference timed beside the forward one. */
+int orc_inverse_f64(int64_t N, double a, double b, const double *c_cheb, double *c_jac, int nthreads) {
+    if (N < 0) return -1;
+    if (N == 0) { c_jac[0] = c_cheb[0]; return 0; }
+    int nt = nthreads_default(nthreads);
+    const int64_t Ng = 2 * N;
+    const double ab = a + b;
+    double *mu = (double *)malloc(sizeof(double) * (size_t)(Ng + 1));
+    double *tab = (double *)malloc(sizeof(double) * (size_t)(2 * Ng));
+    double *g = (double *)malloc(sizeof(double) * (size_t)(Ng + 1));
+    double *A = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    double *B = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    double *C = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    double *An = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    double *part = (double *)calloc((size_t)nt * (size_t)(N + 1), sizeof(double));
+    mu[0] = mu0_double(a, b);
+    mu[1] = (b - a) / (ab + 2.0) * mu[0];
+    for (int64_t k = 1; k < Ng; ++k)
+        mu[k + 1] = -(2.0 * (a - b) * mu[k] + (ab + 2.0 - (double)k) * mu[k - 1]) / (ab + (double)k + 2.0);
+    for (int64_t m = 0; m < 2 * Ng; ++m) tab[m] = cos(M_PI * (double)m / (double)Ng);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int64_t i = 0; i <= Ng; ++i) {
+        /* weight w_i (Eq. "CCweights") and p_N(x_i) = sum_k c_k T_k(x_i); k = N <= Ng - 1 */
+        double s = 0.0, v = c_cheb[0];
+        int64_t m = 0;
+        for (int64_t k = 1; k < Ng; ++k) {
+            m += i;
+            if (m >= 2 * Ng) m -= 2 * Ng;
+            s += mu[k] * tab[m];
+            if (k <= N) v += c_cheb[k] * tab[m];
+        }
+        double w = (2.0 * s + mu[0] + ((i & 1) ? -mu[Ng] : mu[Ng])) / (double)Ng;
+        if (i == 0 || i == Ng) w *= 0.5;
+        g[i] = w * v;
+    }
+    for (int64_t n = 0; n <= N; ++n) {
+        dd x, yy, z;
+        rec_coeffs_dd(n, a, b, &x, &yy, &z);
+        A[n] = x.hi; B[n] = yy.hi; C[n] = z.hi;
+    }
+    An[0] = mu[0];
+    if (N >= 1) An[1] = mu[0] * (a + 1.0) * (b + 1.0) / (ab + 3.0);
+    for (int64_t n = 2; n <= N; ++n) {
+        const double nn = (double)n;
+        An[n] = An[n - 1] * (nn + a) * (nn + b) * (ab + 2.0 * nn - 1.0) / ((ab + 2.0 * nn + 1.0) * (ab + nn) * nn);
+    }
+#pragma omp parallel num_threads(nt)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *acc = part + (size_t)tid * (size_t)(N + 1);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i <= Ng; ++i) {
+            const double x = tab[i];
+            double pm = 0.0, p = g[i];
+            acc[0] += p;
+            for (int64_t n = 0; n < N; ++n) {
+                double pn = (A[n] * x + B[n]) * p - C[n] * pm;
+                pm = p; p = pn;
+                acc[n + 1] += p;
+            }
+        }
+    }
+    for (int64_t n = 0; n <= N; ++n) {
+        double s = 0.0;
+        for (int q = 0; q < nt; ++q) s += part[(size_t)q * (size_t)(N + 1) + (size_t)n];
+        c_jac[n] = s / An[n];
+    }
+    free(mu); free(tab); free(g); free(A); free(B); free(C); free(An); free(part);
     return 0;
 }

@@ -62,9 +62,10 @@ def _load():
             lib.orc_cc_weights.argtypes = [i64, d, d, _dp, i]
             lib.orc_norm_consts.argtypes = [i64, d, d, _dp]
             lib.orc_inverse.argtypes = [i64, d, d, _dp, _dp, i]
+            lib.orc_inverse_f64.argtypes = [i64, d, d, _dp, _dp, i]
             for name in ("orc_jacobi_values", "orc_jacobi_series", "orc_cheb_series", "orc_forward",
                          "orc_forward_values", "orc_forward_f64", "orc_moments", "orc_cc_weights",
-                         "orc_norm_consts", "orc_inverse"):
+                         "orc_norm_consts", "orc_inverse", "orc_inverse_f64"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -168,6 +169,14 @@ def inverse(c_cheb, alpha: float, beta: float, nthreads: int = 0) -> np.ndarray:
     c = np.ascontiguousarray(c_cheb, dtype=np.float64)
     out = np.empty_like(c)
     _check(_load().orc_inverse(c.size - 1, alpha, beta, _p(c), _p(out), nthreads), "inverse")
+    return out
+
+
+def inverse_f64(c_cheb, alpha: float, beta: float, nthreads: int = 0) -> np.ndarray:
+    """Plain-double O(N^2) inverse transform (the timed naive baseline)."""
+    c = np.ascontiguousarray(c_cheb, dtype=np.float64)
+    out = np.empty_like(c)
+    _check(_load().orc_inverse_f64(c.size - 1, alpha, beta, _p(c), _p(out), nthreads), "inverse_f64")
     return out
 
 

@@ -304,6 +304,18 @@ def test_inverse_matches_exact_rational(orc, alpha, beta):
     assert np.max(np.abs(got - exact)) <= 1e-14 * l1(c)
 
 
+@pytest.mark.parametrize("alpha,beta", [(0.1, -0.3), (0.45, 0.45), (-0.5, 0.5)])
+def test_plain_double_baselines(orc, alpha, beta):
+    """The timed plain-double forward and inverse compute the same maps as the double-double
+    oracle, within plain-double rounding: the three-term recurrence near x = +-1 loses about
+    n^2 eps, so the bound grows with N (measured 2e-14 at N = 257, 2.5e-12 at N = 4096)."""
+    for N, bound in ((1, 1e-15), (12, 1e-15), (257, 1e-13), (2048, 1e-11)):
+        c = inputs.decaying_coefficients(N, 1.0, seed=inputs.BASE_SEED + 3 * N)
+        assert np.max(np.abs(orc.forward_f64(c, alpha, beta) - orc.forward(c, alpha, beta))) <= bound * l1(c)
+        assert np.max(np.abs(orc.inverse_f64(c, alpha, beta) - orc.inverse(c, alpha, beta))) <= bound * l1(c)
+    assert orc.inverse_f64(np.array([2.5]), alpha, beta)[0] == 2.5
+
+
 @pytest.mark.parametrize("alpha,beta", [(0.1, -0.3), (0.45, 0.45)])
 def test_inverse_matches_dense_solve(orc, alpha, beta):
     """Route (i): solve P_N c_jac = T_N c_cheb with LAPACK (Eq. iCJT)."""
