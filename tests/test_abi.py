@@ -73,3 +73,27 @@ def test_binding_structs_match_header(name):
     want = [(n, ctypes_of[t]) for n, t in header_struct_fields(name)]
     got = list(getattr(cjt, name)._fields_)
     assert got == want
+
+
+def test_without_a_device_calls_fail_loudly():
+    """With no usable GPU the library reports errors instead of computing anything on the
+    host: argument errors first (before any device call), then CJT_ECUDA with the CUDA
+    runtime's message; no handle is returned and nothing crashes."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1602_02618_gb300 import cjt
+    lib = cjt.load()
+    h = ctypes.c_void_p()
+    o = cjt.default_opts()
+    assert lib.cjt_plan(ctypes.byref(h), 64, 0.9, 2.0, ctypes.byref(o), None) == cjt.CJT_EDOMAIN
+    assert lib.cjt_plan(ctypes.byref(h), -1, 0.1, -0.3, ctypes.byref(o), None) == cjt.CJT_EINVAL
+    assert lib.cjt_plan(None, 64, 0.1, -0.3, ctypes.byref(o), None) == cjt.CJT_EINVAL
+    assert lib.cjt_cheb_coeffs_noalloc(64, None, None, None) == cjt.CJT_EINVAL
+    assert lib.cjt_plan(ctypes.byref(h), 64, 0.1, -0.3, ctypes.byref(o), None) == cjt.CJT_ECUDA
+    assert h.value is None
+    assert lib.cjt_last_cuda_error()
+    with pytest.raises(cjt.CJTError) as e:
+        cjt.Plan(64, 0.1, -0.3, stream=0)      # the default stream, named without torch
+    assert e.value.code == cjt.CJT_ECUDA
+    assert lib.cjt_sync(None) == cjt.CJT_ECUDA
