@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <type_traits>
 
 #include "cjt_df.cuh"
@@ -303,13 +305,19 @@ int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batc
     using V = typename cplx<R>::t;
     const int Ls = 1 << logLs;
     // Columns per CTA: at most ~64 KB of shared memory (32 KB double-float), and few
-    // enough that the launch spreads over every SM.
-    static int sms = 0;
+    // enough that the launch spreads over every SM of the current device.
+    int prc = cjt_fft_prime();
+    if (prc) return prc;
+    static std::atomic<int> sms_of[64];
+    int dev = 0;
+    CJT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return CJT_EUNSUPPORTED;
+    int sms = sms_of[dev].load(std::memory_order_relaxed);
     if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
+        int v = 0;
+        CJT_CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+        sms = v > 0 ? v : 152;
+        sms_of[dev].store(sms, std::memory_order_relaxed);
     }
     // double-float: half the tile, so that more CTAs (and warps) share an SM
     const int64_t budget_elems = (int64_t)((std::is_same<R, dfloat>::value ? 32768 : 65536) / sizeof(V));
@@ -321,8 +329,6 @@ int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batc
     while ((int64_t)tile * 2 <= tile64) tile *= 2;
     size_t smem = (size_t)tile * (Ls + SMEM_PAD) * sizeof(V);
     const int threads = (int)std::min<int64_t>(FFT_THREADS, std::max<int64_t>(32, ((int64_t)tile * Ls / 4 + 31) / 32 * 32));
-    int prc = cjt_fft_prime();
-    if (prc) return prc;
     dim3 grid((unsigned)((ncols + tile - 1) / tile), (unsigned)batch);
     bool launched = false;
     if constexpr (std::is_same<R, double>::value) {
@@ -512,15 +518,20 @@ int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twid
 
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch) { return L > 4096 ? L * batch : 0; }
 
-// One-time function attributes, so that later launches (possibly under stream capture)
-// make no configuration calls.
+// Function attributes, set once per device (they belong to the device's context), so
+// that later launches (possibly under stream capture) make no configuration calls.
 int cjt_fft_prime() {
-    static bool done = false;
-    if (done) return CJT_OK;
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    CJT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return CJT_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return CJT_OK;
     CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     CJT_CUDA_TRY(cudaFuncSetAttribute(k_fft_sub<dfloat, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    done = true;
+    done[dev] = true;
     return CJT_OK;
 }
