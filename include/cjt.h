@@ -357,6 +357,24 @@ int cjt_cheb_coeffs_noalloc(int64_t N, const double *values_dev, double *c_cheb_
  * CJT_EDOMAIN (alpha or beta outside [-1/2, 1/2]).
  */
 int cjt_asy_coefficient(double alpha, double beta, int expansion, int64_t n, int m, double *C);
+
+/*
+ * The plan's recurrence-table entries for degree n on the host (no GPU; for tests and
+ * reports), computed by the same function as the plan kernel that fills the tables.
+ * out[0..CJT_REC_COEFFS-1] receives, in this order:
+ *   A_n, B_n, C_n   three-term recurrence P_{n+1} = (A_n x + B_n) P_n - C_n P_{n-1}
+ *                   (Sec. 1.2; n = 0: A_0 = (a+b+2)/2, B_0 = (a-b)/2, C_0 = 0);
+ *   r^f_n(+1), r^f_n(-1)   forward ratios P_{n+1}(x0)/P_n(x0) of the modified forward
+ *                   recurrence (Sec. 4.2);
+ *   r^b_n(+1), r^b_n(-1)   backward ratios of the modified Clenshaw--Smith algorithm
+ *                   (Lemma of Sec. 4.2; 0 at n = 0, where the ratio is infinite);
+ *   C_n / r^f_{n-1}(+1), C_n / r^f_{n-1}(-1)   (0 at n = 0);
+ *   C_n r^b_n(+1), C_n r^b_n(-1)               (0 at n = 0).
+ * Errors: CJT_EINVAL (null out, n < 0 or n > 2^40), CJT_EDOMAIN (alpha or beta outside
+ * [-1/2, 1/2]; plans for parameters above 1/2 use the tables of alpha - 1 or beta - 1).
+ */
+#define CJT_REC_COEFFS 11
+int cjt_rec_coefficients(double alpha, double beta, int64_t n, double *out);
 int cjt_asy_eval(double alpha, double beta, int expansion, int M, int64_t n, int64_t i, int64_t Ng, double *value,
                  double *bound);
 

@@ -67,7 +67,8 @@ EXPORTED = ["cjt_plan_opts_default", "cjt_plan", "cjt_destroy", "cjt_get_info", 
             "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_strerror", "cjt_last_cuda_error",
             "cjt_version", "cjt_set_profiling", "cjt_get_profile", "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc",
             "cjt_forward_ws", "cjt_inverse_ws", "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info",
-            "cjt_batch_destroy", "cjt_jacobi_to_jacobi", "cjt_asy_coefficient", "cjt_asy_eval"]
+            "cjt_batch_destroy", "cjt_jacobi_to_jacobi", "cjt_asy_coefficient", "cjt_asy_eval",
+            "cjt_rec_coefficients"]
 
 NOALLOC_MAX_N = 65536
 
@@ -117,6 +118,7 @@ def load(path: str = LIB_PATH):
         lib.cjt_jacobi_to_jacobi.argtypes = [vp, vp, vp, vp, vp]
         lib.cjt_asy_coefficient.argtypes = [d, d, i, i64, i, ctypes.POINTER(d)]
         lib.cjt_asy_eval.argtypes = [d, d, i, i, i64, i64, i64, ctypes.POINTER(d), ctypes.POINTER(d)]
+        lib.cjt_rec_coefficients.argtypes = [d, d, i64, ctypes.POINTER(d)]
         lib.cjt_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int8),
                                          ctypes.POINTER(i64), vp, vp, i]
         lib.cjt_batch_launch.argtypes = [vp, vp]
@@ -131,7 +133,7 @@ def load(path: str = LIB_PATH):
                      "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_set_profiling", "cjt_get_profile",
                      "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc", "cjt_forward_ws", "cjt_inverse_ws",
                      "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info", "cjt_jacobi_to_jacobi",
-                     "cjt_asy_coefficient", "cjt_asy_eval"):
+                     "cjt_asy_coefficient", "cjt_asy_eval", "cjt_rec_coefficients"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -364,6 +366,17 @@ def asy_eval(alpha: float, beta: float, M: int, n: int, i: int, Ng: int, expansi
     _check(load().cjt_asy_eval(float(alpha), float(beta), int(expansion), int(M), int(n), int(i), int(Ng),
                                ctypes.byref(v), ctypes.byref(b)), "cjt_asy_eval")
     return v.value, b.value
+
+
+REC_FIELDS = ("A", "B", "C", "rf_p", "rf_m", "rb_p", "rb_m", "Ce_p", "Ce_m", "Cr_p", "Cr_m")
+
+
+def rec_coefficients(alpha: float, beta: float, n: int) -> dict:
+    """The plan's recurrence-table entries for degree n (host only, no GPU): A_n, B_n, C_n,
+    the Reinsch ratios r^f_n(+-1), r^b_n(+-1), C_n / r^f_{n-1}(+-1) and C_n r^b_n(+-1)."""
+    out = (ctypes.c_double * len(REC_FIELDS))()
+    _check(load().cjt_rec_coefficients(float(alpha), float(beta), int(n), out), "cjt_rec_coefficients")
+    return dict(zip(REC_FIELDS, list(out)))
 
 
 def version() -> str:

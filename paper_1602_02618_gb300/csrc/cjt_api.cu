@@ -275,6 +275,15 @@ int cjt_asy_coefficient(double alpha, double beta, int expansion, int64_t n, int
     return CJT_OK;
 }
 
+int cjt_rec_coefficients(double alpha, double beta, int64_t n, double *out) {
+    if (!out || n < 0 || n > (1LL << 40)) return CJT_EINVAL;
+    if (!(alpha >= -0.5 && alpha <= 0.5) || !(beta >= -0.5 && beta <= 0.5)) return CJT_EDOMAIN;
+    const RecRow r = cjt_rec_row(n, alpha, beta);
+    const double v[CJT_REC_COEFFS] = {r.A, r.B, r.C, r.rf_p, r.rf_m, r.rb_p, r.rb_m, r.Ce_p, r.Ce_m, r.Cr_p, r.Cr_m};
+    for (int k = 0; k < CJT_REC_COEFFS; ++k) out[k] = v[k];
+    return CJT_OK;
+}
+
 int cjt_asy_eval(double alpha, double beta, int expansion, int M, int64_t n, int64_t i, int64_t Ng, double *value,
                  double *bound) {
     if (!value || !bound || M < 1 || M > 20 || n < 0 || Ng < 2 || Ng > (1LL << 30) || i <= 0 || i >= Ng)

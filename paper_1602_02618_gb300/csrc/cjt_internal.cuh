@@ -67,6 +67,58 @@ struct RecTables {
     double *Cr_m, *rbinv_m, *Ce_m, *rf_m;   // x0 = -1
 };
 
+// One degree's entries of the recurrence tables: the three-term coefficients (Sec. 1.2)
+// and the Reinsch quantities at x0 = +-1 (Sec. 4.2).  Used by the plan kernel that fills
+// RecTables and by the host entry point cjt_rec_coefficients.
+struct RecRow {
+    double A, B, C;
+    double rf_p, rf_m;         // forward ratios r^f_n(+-1) = pi_{n+1}(+-1)/pi_n(+-1)
+    double rb_p, rb_m;         // backward ratios r^b_n(+-1) (Lemma of Sec. 4.2); n >= 1
+    double Ce_p, Ce_m;         // e-form coefficient C_n / r^f_{n-1}(+-1)
+    double Cr_p, Cr_m;         // C_n r^b_n(+-1)
+    double rbinv_p, rbinv_m;   // 1 / r^b_n(+-1)
+};
+__host__ __device__ __forceinline__ RecRow cjt_rec_row(int64_t n, double a, double b) {
+    RecRow r;
+    const double nn = (double)n, ab = a + b;
+    double A, B, C;
+    if (n == 0) {
+        // from P_1 = (a-b)/2 + (a+b+2)/2 x (avoids 0/0 when a+b = 0 or -1)
+        A = 0.5 * (ab + 2.0);
+        B = 0.5 * (a - b);
+        C = 0.0;
+    } else {
+        const double t0 = 2.0 * nn + ab, t1 = t0 + 1.0, t2 = t0 + 2.0, s1 = nn + ab + 1.0;
+        A = t1 * t2 / (2.0 * (nn + 1.0) * s1);
+        B = (a - b) * ab * t1 / (2.0 * (nn + 1.0) * s1 * t0);
+        C = (nn + a) * (nn + b) * t2 / ((nn + 1.0) * s1 * t0);
+    }
+    r.A = A;
+    r.B = B;
+    r.C = C;
+    r.rf_p = (nn + a + 1.0) / (nn + 1.0);
+    r.rf_m = -(nn + b + 1.0) / (nn + 1.0);
+    if (n == 0) {
+        r.Ce_p = 0.0;
+        r.Ce_m = 0.0;
+    } else {
+        r.Ce_p = C * nn / (nn + a);
+        r.Ce_m = -C * nn / (nn + b);
+    }
+    // r^b_0 is infinite: its slots hold 0, which the kernels never read at n = 0
+    if (n == 0) {
+        r.rb_p = 0.0; r.Cr_p = 0.0; r.rbinv_p = 0.0;
+        r.rb_m = 0.0; r.Cr_m = 0.0; r.rbinv_m = 0.0;
+    } else {
+        const double common = (nn + 1.0) / nn * (ab + nn + 1.0) * (ab + 2.0 * nn) / (ab + 2.0 * nn + 2.0);
+        const double rbp = common / (nn + b);
+        const double rbm = -common / (nn + a);
+        r.rb_p = rbp; r.Cr_p = C * rbp; r.rbinv_p = 1.0 / rbp;
+        r.rb_m = rbm; r.Cr_m = C * rbm; r.rbinv_m = 1.0 / rbm;
+    }
+    return r;
+}
+
 // Partition and recurrence work of one grid (N points for forward, 2N for inverse).
 struct GridWork {
     int64_t Ng = 0;        // grid: points x_i = cos(pi i / Ng), i = 0..Ng

@@ -23,44 +23,16 @@ namespace {
 __global__ void k_rec_tables(int64_t nmax, double a, double b, RecTables t) {
     int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (n > nmax) return;
-    const double nn = (double)n, ab = a + b;
-    double A, B, C;
-    if (n == 0) {
-        // from P_1 = (a-b)/2 + (a+b+2)/2 x (avoids 0/0 when a+b = 0 or -1)
-        A = 0.5 * (ab + 2.0);
-        B = 0.5 * (a - b);
-        C = 0.0;
-    } else {
-        const double t0 = 2.0 * nn + ab, t1 = t0 + 1.0, t2 = t0 + 2.0, s1 = nn + ab + 1.0;
-        A = t1 * t2 / (2.0 * (nn + 1.0) * s1);
-        B = (a - b) * ab * t1 / (2.0 * (nn + 1.0) * s1 * t0);
-        C = (nn + a) * (nn + b) * t2 / ((nn + 1.0) * s1 * t0);
-    }
-    t.A[n] = A;
-    t.B[n] = B;
-    t.C[n] = C;
-    // forward ratios r^f_n(+-1) = pi_{n+1}(+-1)/pi_n(+-1)  (Sec. 4.2)
-    t.rf_p[n] = (nn + a + 1.0) / (nn + 1.0);
-    t.rf_m[n] = -(nn + b + 1.0) / (nn + 1.0);
-    // e-form coefficient Ce_n = C_n / r^f_{n-1}
-    if (n == 0) {
-        t.Ce_p[n] = 0.0;
-        t.Ce_m[n] = 0.0;
-    } else {
-        t.Ce_p[n] = C * nn / (nn + a);
-        t.Ce_m[n] = -C * nn / (nn + b);
-    }
-    // backward ratios r^b_n(+-1) (Lemma of Sec. 4.2); r^b_0 is infinite
-    if (n == 0) {
-        t.Cr_p[n] = 0.0; t.rbinv_p[n] = 0.0;
-        t.Cr_m[n] = 0.0; t.rbinv_m[n] = 0.0;
-    } else {
-        const double common = (nn + 1.0) / nn * (ab + nn + 1.0) * (ab + 2.0 * nn) / (ab + 2.0 * nn + 2.0);
-        const double rbp = common / (nn + b);
-        const double rbm = -common / (nn + a);
-        t.Cr_p[n] = C * rbp; t.rbinv_p[n] = 1.0 / rbp;
-        t.Cr_m[n] = C * rbm; t.rbinv_m[n] = 1.0 / rbm;
-    }
+    const RecRow r = cjt_rec_row(n, a, b);
+    t.A[n] = r.A;
+    t.B[n] = r.B;
+    t.C[n] = r.C;
+    t.rf_p[n] = r.rf_p;
+    t.rf_m[n] = r.rf_m;
+    t.Ce_p[n] = r.Ce_p;
+    t.Ce_m[n] = r.Ce_m;
+    t.Cr_p[n] = r.Cr_p; t.rbinv_p[n] = r.rbinv_p;
+    t.Cr_m[n] = r.Cr_m; t.rbinv_m[n] = r.rbinv_m;
 }
 
 // --------------------------------------------------------------------------
