@@ -312,3 +312,30 @@ def test_overlap_option_checked(cjt):
         with pytest.raises(cjt.CJTError) as e:
             cjt.Plan(64, 0.1, -0.3, overlap=bad)
         assert e.value.code == cjt.CJT_EINVAL
+
+
+@pytest.mark.parametrize("grid", [0, -1])
+def test_golden_fixtures_exact_values(cjt, grid):
+    """The CUDA path against the stored exact values at the paper's Fig. 1 parameters
+    (alpha, beta) = (1/8, 3/8), N = 12 (tests/golden, written from exact rationals), on the
+    power-of-two grid and on the paper's grid."""
+    import os
+    from fractions import Fraction
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    for name, run in (("forward_exact_N12_a1o8_b3o8.txt", run_fwd), ("inverse_exact_N12_a1o8_b3o8.txt", run_inv)):
+        meta, rows = {}, []
+        for line in open(os.path.join(here, name)):
+            line = line.strip()
+            if line.startswith("#"):
+                if ":" in line:
+                    k, v = line[1:].split(":", 1)
+                    meta[k.strip()] = v.strip()
+            elif line:
+                rows.append([Fraction(t) for t in line.split()])
+        a, b = float(Fraction(meta["alpha"])), float(Fraction(meta["beta"]))
+        c = np.array([float(r[0]) for r in rows])
+        exact = np.array([float(r[1]) for r in rows])
+        plan = cjt.Plan(len(c) - 1, a, b, grid=grid)
+        assert np.max(np.abs(run(cjt, plan, c) - exact)) <= TOL * l1(c), name
+        plan.close()
+

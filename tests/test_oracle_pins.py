@@ -152,6 +152,18 @@ def test_forward_golden_fixture(orc):
     assert all(a == r[1] for a, r in zip(again, rows))
 
 
+def test_inverse_golden_fixture(orc):
+    """Stored exact values of the inverse map (written by tests/golden/make_golden.py)."""
+    meta, rows = _read_golden("inverse_exact_N12_a1o8_b3o8.txt")
+    alpha, beta = float(Fraction(meta["alpha"])), float(Fraction(meta["beta"]))
+    c = np.array([float(r[0]) for r in rows])
+    exact = np.array([float(r[1]) for r in rows])
+    got = orc.inverse(c, alpha, beta)
+    assert np.max(np.abs(got - exact)) <= 1e-15 * l1(c)
+    again = ex.inverse_exact(c, alpha, beta)
+    assert all(a == r[1] for a, r in zip(again, rows))
+
+
 def test_forward_chebyshev_closed_form(orc):
     """alpha = beta = -1/2: P_n = ((1/2)_n / n!) T_n, so c_cheb_n = ((1/2)_n/n!) c_n."""
     N = 300
