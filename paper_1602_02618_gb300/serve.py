@@ -12,9 +12,12 @@ request runs from its arrival to its result being on the host.
 
 Every transform runs in the library's kernels through the C ABI
 (cjt_plan, cjt_forward_ws / cjt_inverse_ws); this module only schedules.
-Admission by memory: the device bytes of resident plans plus slot arenas and
-I/O buffers stay below `mem_budget`; plans not in use are evicted
-least-recently-used when a new one would exceed it.
+Admission by memory: before a planner builds a new plan, plans not in use are
+evicted least-recently-used until the resident plans, the slot arenas and I/O
+buffers and the new plan's estimate fit in `mem_budget`; while plans in use fill
+it, the planner waits for them to be released.  Slot arenas grow to the largest
+workspace their slot has served; they count against the budget but are not
+gated themselves (at most slots x the largest workspace).
 """
 from __future__ import annotations
 
