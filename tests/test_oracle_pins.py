@@ -246,6 +246,47 @@ def test_series_evaluators(orc):
     assert np.max(np.abs(back - hi)) < 1e-14 * l1(c)
 
 
+def test_double_double_series_accuracy(orc):
+    """The parity oracle evaluates sum_n c_n P_n(x_j) in double-double: hi + lo must agree
+    with a 50-digit evaluation far beyond double precision, near x = +-1 too, where a
+    plain-double recurrence loses about n^2 eps.  A slip in the error-free transformations
+    (a dropped low part) would leave every double-precision pin passing but fail here."""
+    mpmath.mp.dps = 50
+    N, a, b = 1500, 0.1, -0.3
+    c = inputs.decaying_coefficients(N, 1.0, seed=inputs.BASE_SEED + 55)
+    j = np.array([1, 2, 7, N // 2, N - 3, N - 1])
+    hi, lo = orc.jacobi_series(c, a, b, j, N, lo=True)
+    A_, B_ = mpmath.mpf(a), mpmath.mpf(b)
+    # the recurrence checked against mpmath's hypergeometric Jacobi polynomials first
+    x_chk = mpmath.cos(mpmath.pi * 7 / N)
+    for jj, x in zip(j, [mpmath.cos(mpmath.pi * int(q) / N) for q in j]):
+        pm, p, s, mag = mpmath.mpf(0), mpmath.mpf(1), mpmath.mpf(c[0]), abs(mpmath.mpf(c[0]))
+        for n in range(N):
+            nn = mpmath.mpf(n)
+            if n == 0:
+                An, Bn, Cn = (A_ + B_ + 2) / 2, (A_ - B_) / 2, mpmath.mpf(0)
+            else:
+                t0 = 2 * nn + A_ + B_
+                den = 2 * (nn + 1) * (nn + A_ + B_ + 1) * t0
+                An = (t0 + 1) * (t0 + 2) * t0 / den
+                Bn = (A_ * A_ - B_ * B_) * (t0 + 1) / den
+                Cn = 2 * (nn + A_) * (nn + B_) * (t0 + 2) / den
+            pm, p = p, (An * x + Bn) * p - Cn * pm
+            if jj == 7 and n + 1 in (2, 500, N):
+                assert abs(p - mpmath.jacobi(n + 1, A_, B_, x_chk)) < mpmath.mpf(10) ** -40 * (1 + abs(p))
+            s += mpmath.mpf(c[n + 1]) * p
+            mag += abs(mpmath.mpf(c[n + 1]) * p)
+        q = list(j).index(jj)
+        err = abs(mpmath.mpf(hi[q]) + mpmath.mpf(lo[q]) - s)
+        assert err <= mpmath.mpf(10) ** -27 * mag, (int(jj), float(err), float(mag))
+    # the Chebyshev side of the grid evaluation likewise
+    hc, lc = orc.cheb_series(c, j, N, lo=True)
+    for q, jj in enumerate(j):
+        th = mpmath.pi * int(jj) / N
+        s = mpmath.fsum(mpmath.mpf(c[k]) * mpmath.cos(k * th) for k in range(N + 1))
+        assert abs(mpmath.mpf(hc[q]) + mpmath.mpf(lc[q]) - s) <= mpmath.mpf(10) ** -27 * l1(c)
+
+
 # --------------------------------------------------------------------------
 # inverse transform and its ingredients
 # --------------------------------------------------------------------------
