@@ -32,8 +32,10 @@
  *    with its own workspace may be in use on one stream at a time: a call on a
  *    different stream while the plan's previous work is still running returns
  *    CJT_EBUSY.  A plan built with shared_workspace holds only read-only tables
- *    and may run on any number of streams at once, each execution with its own
- *    workspace.  Distinct plans are independent and may run concurrently.
+ *    and may run on any number of streams at once, from any number of host
+ *    threads, each execution with its own workspace: every execution takes its
+ *    own side stream and fork/join events from a per-device pool.  Distinct
+ *    plans are independent and may run concurrently.
  *  - Return values: 0 (CJT_OK) on success, a negative CJT_E* code otherwise;
  *    cjt_strerror() names it.  No C++ exception crosses this boundary.
  *  - The library never falls back to a CPU path: every step of a transform
@@ -277,9 +279,12 @@ int cjt_execute_host(cjt_plan_t plan, int direction, const double *in_host, doub
  * direction.  The items are spread, longest first, over a set of internal
  * streams that fork from and join back to `stream` through events, so the
  * call is ordered like any other work on `stream`.  Plans built with
- * shared_workspace borrow per-stream workspace arenas owned by the library
- * (grown on demand; the growing call must not be under stream capture).  A
- * plan may appear at most once per call; in_dev and out_dev must not overlap.
+ * shared_workspace borrow per-stream workspace arenas owned by the library,
+ * grown on demand by calls that are not under stream capture (a call under
+ * capture that would need a larger arena returns CJT_EBUSY).  An outgrown arena
+ * is kept, not freed, until the process exits, so that a graph captured from an
+ * earlier call stays valid.  A plan may appear at most once per call; in_dev
+ * and out_dev must not overlap.
  * Errors: CJT_EINVAL, CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA, CJT_ENOMEM.
  */
 int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, const int64_t *offsets,

@@ -34,31 +34,72 @@ int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st) {
     return CJT_OK;
 }
 
-int cjt_internal_side_stream(bool high, cudaStream_t *out) {
-    // Two pools per device: streams of the highest priority and of normal priority.  A
-    // chain on a high-priority stream is served first by the CTA scheduler: at equal
-    // priority it hands freed SMs to the kernel launched first, so a chain whose head
-    // kernel waits behind the thousands of CTAs of the other chain's kernel effectively
-    // runs after it.
-    static std::mutex mu;
-    static std::vector<cudaStream_t> pool[2][64];
-    static unsigned next[2][64] = {{0}};
+namespace {
+// Per device and overlap mode: every context ever made (kept until exit) and the free ones
+// in the order they were given back.  A chain on a stream of the highest priority is served
+// first by the CTA scheduler: at equal priority it hands freed SMs to the kernel launched
+// first, so a chain whose head kernel waits behind the thousands of CTAs of the other
+// chain's kernel effectively runs after it.
+constexpr int kOvPoolMin = 32;   // contexts made before any is reused
+std::mutex g_ov_mu;
+std::vector<OvCtx *> g_ov_all[64][4];
+std::vector<OvCtx *> g_ov_free[64][4];
+
+int make_ovctx(int dev, int mode, OvCtx **out) {
+    int least = 0, greatest = 0;
+    CJT_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    OvCtx *c = new (std::nothrow) OvCtx();
+    if (!c) return CJT_ENOMEM;
+    c->dev = dev;
+    c->mode = mode;
+    const int prio_side = mode == CJT_OVERLAP_ASY_FIRST ? greatest : least;
+    CJT_CUDA_TRY(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_side));
+    CJT_CUDA_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    CJT_CUDA_TRY(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
+    if (mode == CJT_OVERLAP_REC_FIRST) {
+        CJT_CUDA_TRY(cudaStreamCreateWithPriority(&c->side_rec, cudaStreamNonBlocking, greatest));
+        CJT_CUDA_TRY(cudaEventCreateWithFlags(&c->join_rec, cudaEventDisableTiming));
+    }
+    g_ov_all[dev][mode].push_back(c);
+    *out = c;
+    return CJT_OK;
+}
+
+// id of the stream capture `s` belongs to (0 when it is not being captured)
+unsigned long long capture_id(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    unsigned long long id = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, &id) != cudaSuccess) return ~0ULL;
+    return cs == cudaStreamCaptureStatusNone ? 0 : id;
+}
+}  // namespace
+
+int cjt_internal_ovctx_acquire(int overlap, cudaStream_t origin, OvCtx **out) {
     int dev = 0;
     CJT_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return CJT_EUNSUPPORTED;
-    const int h = high ? 1 : 0;
-    std::lock_guard<std::mutex> lk(mu);
-    if (pool[h][dev].empty()) {
-        int least = 0, greatest = 0;
-        CJT_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-        for (int k = 0; k < 32; ++k) {
-            cudaStream_t s;
-            CJT_CUDA_TRY(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, high ? greatest : least));
-            pool[h][dev].push_back(s);
+    if (dev < 0 || dev >= 64 || overlap < 1 || overlap > 3) return CJT_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_ov_mu);
+    auto &fr = g_ov_free[dev][overlap];
+    if ((int)g_ov_all[dev][overlap].size() >= kOvPoolMin) {
+        const unsigned long long mine = capture_id(origin);
+        for (size_t k = 0; k < fr.size(); ++k) {
+            OvCtx *c = fr[k];
+            const unsigned long long cs = capture_id(c->side);
+            const unsigned long long cr = c->side_rec ? capture_id(c->side_rec) : 0;
+            if ((cs == 0 || cs == mine) && (cr == 0 || cr == mine)) {
+                fr.erase(fr.begin() + (long)k);
+                *out = c;
+                return CJT_OK;
+            }
         }
     }
-    *out = pool[h][dev][next[h][dev]++ % pool[h][dev].size()];
-    return CJT_OK;
+    return make_ovctx(dev, overlap, out);
+}
+
+void cjt_internal_ovctx_release(OvCtx *c) {
+    if (!c) return;
+    std::lock_guard<std::mutex> lk(g_ov_mu);
+    g_ov_free[c->dev][c->mode].push_back(c);
 }
 
 int cjt_internal_end_use(cjt_plan_s *p, cudaStream_t st) {
@@ -79,9 +120,6 @@ void free_plan(cjt_plan_s *p) {
     for (void *v : p->allocs) cudaFree(v);
     p->allocs.clear();
     if (p->done) cudaEventDestroy(p->done);
-    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-    if (p->ev_join) cudaEventDestroy(p->ev_join);
-    if (p->ev_join_rec) cudaEventDestroy(p->ev_join_rec);
     delete p;
 }
 }  // namespace

@@ -16,6 +16,7 @@
 #include <numeric>
 #include <vector>
 
+#include "cjt_group.cuh"
 #include "cjt_internal.cuh"
 
 namespace {
@@ -127,11 +128,15 @@ int default_lanes() {
     return std::min(std::max(n, 1), 64);
 }
 
-// the library's lanes and growable arenas for cjt_execute_batched, per device
+// the library's lanes and growable arenas for cjt_execute_batched, per device.  An arena
+// that is outgrown is retired, not freed: a graph captured from an earlier call may still
+// hold its address, and a replay of that graph must not write into freed memory.  Retired
+// arenas stay allocated until the process exits.
 struct Context {
     Lanes lanes;
     std::vector<void *> arena;
     std::vector<int64_t> bytes;
+    std::vector<void *> retired;
 };
 std::mutex g_mu;
 Context g_ctx[64];
@@ -142,10 +147,21 @@ struct cjt_batch_s {
     Lanes lanes;
     std::vector<void *> arenas;
     int64_t arena_bytes = 0;
+    cjt_group_t group = nullptr;   // the grouped items (cjt_group.cu)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
 };
+
+namespace {
+// workspace of one wave of the grouped items: CJT_BATCH_ARENA_MB, default 4096 MiB (two
+// such arenas alternate between consecutive waves)
+int64_t group_arena_budget() {
+    const char *e = getenv("CJT_BATCH_ARENA_MB");
+    const long long mb = e ? atoll(e) : 4096;
+    return (int64_t)std::max(16LL, mb) << 20;
+}
+}  // namespace
 
 extern "C" {
 
@@ -177,7 +193,7 @@ int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, c
     for (int l = 0; l < nl; ++l) {
         if (a.need[l] > C.bytes[l]) {
             if (capturing) return CJT_EBUSY;   // arenas cannot grow under capture
-            if (C.arena[l]) CJT_CUDA_TRY(cudaFree(C.arena[l]));
+            if (C.arena[l]) C.retired.push_back(C.arena[l]);
             C.arena[l] = nullptr;
             C.bytes[l] = 0;
             cudaError_t e = cudaMalloc(&C.arena[l], a.need[l]);
@@ -206,35 +222,57 @@ int cjt_batch_create(cjt_batch_t *out, int count, const cjt_plan_t *plans, const
     if (rc) return rc;
     if (count == 0) return CJT_EINVAL;
     cjt_batch_s *b = new cjt_batch_s();
-    const int nl = std::min(nstreams > 0 ? std::min(nstreams, 64) : default_lanes(), count);
-    Assignment a = assign(count, plans, dir, nl);
     auto fail = [&](int code) {
         cjt_batch_destroy(b);
         return code;
     };
-    rc = make_lanes(b->lanes, nl);
+    // the grouped items, and the rest (one chain of launches per item on the lanes)
+    std::vector<int> grouped, rest;
+    const bool no_group = getenv("CJT_BATCH_NO_GROUP") != nullptr;
+    for (int t = 0; t < count; ++t)
+        (!no_group && cjt_group_eligible(plans[t], dir[t]) ? grouped : rest).push_back(t);
+    rc = cjt_group_create(&b->group, grouped, plans, dir, offsets, in_dev, out_dev, group_arena_budget());
     if (rc) return fail(rc);
-    b->arenas.assign(nl, nullptr);
-    for (int l = 0; l < nl; ++l) {
-        if (!a.need[l]) continue;
-        cudaError_t e = cudaMalloc(&b->arenas[l], a.need[l]);
-        if (e != cudaSuccess) {
-            cjt_internal_set_cuda_error(e, "cudaMalloc");
-            return fail(CJT_ENOMEM);
-        }
-        b->arena_bytes += a.need[l];
+    b->arena_bytes += cjt_group_arena_bytes(b->group);
+    b->kernels += cjt_group_kernels(b->group);
+    std::vector<cjt_plan_t> rp;
+    std::vector<int8_t> rd;
+    std::vector<int64_t> ro;
+    for (int t : rest) {
+        rp.push_back(plans[t]);
+        rd.push_back(dir[t]);
+        ro.push_back(offsets[t]);
     }
-    for (int t = 0; t < count; ++t) {
-        cjt_plan_info inf;
-        cjt_get_info(plans[t], &inf);
-        b->kernels += dir[t] == CJT_FWD ? inf.kernels_fwd : inf.kernels_inv;
+    const int nrest = (int)rest.size();
+    const int nl = nrest ? std::min(nstreams > 0 ? std::min(nstreams, 64) : default_lanes(), nrest) : 0;
+    Assignment a;
+    if (nrest) {
+        a = assign(nrest, rp.data(), rd.data(), nl);
+        rc = make_lanes(b->lanes, nl);
+        if (rc) return fail(rc);
+        b->arenas.assign(nl, nullptr);
+        for (int l = 0; l < nl; ++l) {
+            if (!a.need[l]) continue;
+            cudaError_t e = cudaMalloc(&b->arenas[l], a.need[l]);
+            if (e != cudaSuccess) {
+                cjt_internal_set_cuda_error(e, "cudaMalloc");
+                return fail(CJT_ENOMEM);
+            }
+            b->arena_bytes += a.need[l];
+        }
+        for (int t : rest) {
+            cjt_plan_info inf;
+            cjt_get_info(plans[t], &inf);
+            b->kernels += dir[t] == CJT_FWD ? inf.kernels_fwd : inf.kernels_inv;
+        }
     }
     // capture on a private stream: the graph has no tie to any stream once instantiated
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return fail(CJT_ECUDA);
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = issue(count, plans, dir, offsets, in_dev, out_dev, a, b->lanes, b->arenas, cs);
+        rc = cjt_group_issue(b->group, cs);
+        if (!rc && nrest) rc = issue(nrest, rp.data(), rd.data(), ro.data(), in_dev, out_dev, a, b->lanes, b->arenas, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
         if (!rc && e2 != cudaSuccess) {
             cjt_internal_set_cuda_error(e2, "cudaStreamEndCapture");
@@ -273,6 +311,7 @@ void cjt_batch_destroy(cjt_batch_t b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaDeviceSynchronize();
+    cjt_group_destroy(b->group);
     for (void *v : b->arenas)
         if (v) cudaFree(v);
     for (auto s : b->lanes.streams) cudaStreamDestroy(s);

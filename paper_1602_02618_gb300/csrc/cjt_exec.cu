@@ -26,72 +26,29 @@
 
 #include "cjt_df.cuh"
 #include "cjt_internal.cuh"
+#include "cjt_kern.cuh"
 
 namespace {
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------------------
-// REC, forward: one warp per item, lane = row
+// single-transform launches of the bodies in cjt_kern.cuh
 // ---------------------------------------------------------------------------
+using cjt_kern::SW;
+using cjt_kern::RED_WARPS;
+using cjt_kern::re_d;
+using cjt_kern::im_d;
+
 __global__ void __launch_bounds__(128) k_rec_fwd(const RecItem *__restrict__ items, int64_t nitems, int64_t Ng,
                                                 RecTables t, const double *__restrict__ c,
                                                 const double *__restrict__ states, double *__restrict__ partials) {
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
     if (w >= nitems) return;
     const RecItem it = items[w];
-    const int row = it.row0 + min(lane, it.nrows - 1);
-    double P1 = 1.0, P2 = 0.0;
-    if (it.state >= 0) {
-        const double2 sv = reinterpret_cast<const double2 *>(states)[(int64_t)it.state * 32 + lane];
-        P1 = sv.x;
-        P2 = sv.y;
-    }
-    double S;
-    if (it.mode == REC_PLAIN) {
-        const double x = cospi((double)row / (double)Ng);
-        double u1 = 0.0, u2 = 0.0;
-        for (int n = it.b - 1; n >= it.a; --n) {
-            const double w0 = fma(-__ldg(t.C + n + 1), u2, __ldg(c + n));
-            const double u0 = fma(fma(__ldg(t.A + n), x, __ldg(t.B + n)), u1, w0);
-            u2 = u1;
-            u1 = u0;
-        }
-        // segment sum = pi_a u_a - C_a pi_{a-1} u_{a+1}
-        S = fma(P1, u1, -__ldg(t.C + it.a) * P2 * u2);
-    } else {
-        const bool plus = it.mode == REC_REINSCH_P1;
-        double delta;
-        if (plus) {
-            const double s = sinpi((double)row / (2.0 * (double)Ng));
-            delta = -2.0 * s * s;
-        } else {
-            const double s = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
-            delta = 2.0 * s * s;
-        }
-        const double *Cr = plus ? t.Cr_p : t.Cr_m;
-        const double *rbinv = plus ? t.rbinv_p : t.rbinv_m;
-        const double *Ce = plus ? t.Ce_p : t.Ce_m;
-        double u = 0.0, e = 0.0, uprev = 0.0;
-        for (int n = it.b - 1; n >= it.a; --n) {
-            const double wn = fma(__ldg(Cr + n + 1), e, __ldg(c + n));
-            const double en = fma(__ldg(t.A + n) * delta, u, wn);
-            const double un = fma(u, __ldg(rbinv + n), en);
-            uprev = u;
-            u = un;
-            e = en;
-        }
-        // segment sum = pi_a e_a + C_a/r^f_{a-1} u_{a+1} e^f_a
-        S = fma(P1, e, __ldg(Ce + it.a) * uprev * P2);
-    }
-    partials[it.out + lane] = lane < it.nrows ? S : 0.0;
+    cjt_kern::rec_fwd_warp(it, threadIdx.x & 31, Ng, t, c, states, partials);
 }
 
-// ---------------------------------------------------------------------------
-// REC, inverse (transposed): one warp per item; lane = row; the degree sums
-// over the warp's rows go through a padded shared-memory tile.
-// ---------------------------------------------------------------------------
 constexpr int RI_WARPS = 4;
 __global__ void __launch_bounds__(32 * RI_WARPS) k_rec_inv(const RecItem *__restrict__ items, int64_t nitems,
                                                           int64_t Ng, RecTables t, const double *__restrict__ g,
@@ -100,202 +57,41 @@ __global__ void __launch_bounds__(32 * RI_WARPS) k_rec_inv(const RecItem *__rest
     __shared__ double tile[RI_WARPS][32][33];
     const int wib = threadIdx.x >> 5;
     const int64_t w = (int64_t)blockIdx.x * RI_WARPS + wib;
-    const int lane = threadIdx.x & 31;
     if (w >= nitems) return;
     const RecItem it = items[w];
-    const bool active = lane < it.nrows;
-    const int row = it.row0 + min(lane, it.nrows - 1);
-    const double gi = active ? g[row] : 0.0;
-    double P1 = gi, P2 = 0.0;
-    if (active && it.state >= 0) {
-        const double2 sv = reinterpret_cast<const double2 *>(states)[(int64_t)it.state * 32 + lane];
-        P1 = sv.x * gi;
-        P2 = sv.y * gi;
-    }
-    double(*tl)[33] = tile[wib];
-    double *out = partials + it.out - it.a;
-    if (it.mode == REC_PLAIN) {
-        const double x = cospi((double)row / (double)Ng);
-        double p = P1, pm = P2;
-        for (int n0 = it.a; n0 < it.b; n0 += 32) {
-            const int cnt = min(32, it.b - n0);
-            for (int r = 0; r < cnt; ++r) {
-                const int n = n0 + r;
-                tl[r][lane] = p;
-                const double pn = fma(fma(__ldg(t.A + n), x, __ldg(t.B + n)), p, -__ldg(t.C + n) * pm);
-                pm = p;
-                p = pn;
-            }
-            __syncwarp();
-            if (lane < cnt) {
-                double s = 0.0;
-#pragma unroll 8
-                for (int r = 0; r < 32; ++r) s += tl[lane][r];
-                out[n0 + lane] = s;
-            }
-            __syncwarp();
-        }
-    } else {
-        const bool plus = it.mode == REC_REINSCH_P1;
-        double delta;
-        if (plus) {
-            const double s = sinpi((double)row / (2.0 * (double)Ng));
-            delta = -2.0 * s * s;
-        } else {
-            const double s = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
-            delta = 2.0 * s * s;
-        }
-        const double *Ce = plus ? t.Ce_p : t.Ce_m;
-        const double *rf = plus ? t.rf_p : t.rf_m;
-        double p = P1, e = P2;
-        for (int n0 = it.a; n0 < it.b; n0 += 32) {
-            const int cnt = min(32, it.b - n0);
-            for (int r = 0; r < cnt; ++r) {
-                const int n = n0 + r;
-                tl[r][lane] = p;
-                const double en = fma(__ldg(t.A + n) * delta, p, __ldg(Ce + n) * e);
-                p = fma(p, __ldg(rf + n), en);
-                e = en;
-            }
-            __syncwarp();
-            if (lane < cnt) {
-                double s = 0.0;
-#pragma unroll 8
-                for (int r = 0; r < 32; ++r) s += tl[lane][r];
-                out[n0 + lane] = s;
-            }
-            __syncwarp();
-        }
-    }
+    cjt_kern::rec_inv_warp(it, threadIdx.x & 31, tile[wib], Ng, t, g, states, partials);
 }
 
-// ---------------------------------------------------------------------------
-// REC with stored values (rec_store): one fused multiply-add per entry
-// ---------------------------------------------------------------------------
-// One CTA of SW warps per item: warp w takes a quarter of the item's degrees (eight
-// streaming loads in flight per lane), and the four partial sums are added in warp order.
-// Splitting the long items (rows near x = +-1) over four warps keeps the SMs busy to the
-// end of the launch.
-// The sums over even and odd degrees are kept apart (accumulator j takes the degrees
-// a + k + j, a and k even, so its parity is that of j): their sum is the row's partial,
-// and under the parity fold their difference is the mirrored row's, since
-// P_n(-x) = (-1)^n P_n(x) when alpha = beta.
-constexpr int SW = 4;
 __global__ void __launch_bounds__(32 * SW) k_rec_fwd_stored(const RecItem *__restrict__ items, int64_t nitems,
                                                             const double *__restrict__ c, const double *__restrict__ E,
                                                             double *__restrict__ partials) {
-    __shared__ double red_e[SW][32], red_o[SW][32];
     if ((int64_t)blockIdx.x >= nitems) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RecItem it = items[blockIdx.x];
-    const int len = it.b - it.a;
-    const int per = ((len + SW - 1) / SW + 7) & ~7;
-    const int k0 = min(len, w * per), k1 = min(len, k0 + per);
-    const double *e = E + it.eoff + lane;
-    const double *cc = c + it.a;
-    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    int k = k0;
-    for (; k + 8 <= k1; k += 8) {
-        double v[8], cv[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            v[j] = __ldcs(e + (int64_t)(k + j) * 32);
-            cv[j] = __ldg(cc + k + j);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] = fma(v[j], cv[j], acc[j]);
-    }
-    for (; k < k1; ++k) acc[k & 1] = fma(__ldcs(e + (int64_t)k * 32), __ldg(cc + k), acc[k & 1]);
-    red_e[w][lane] = (acc[0] + acc[2]) + (acc[4] + acc[6]);
-    red_o[w][lane] = (acc[1] + acc[3]) + (acc[5] + acc[7]);
-    __syncthreads();
-    if (w == 0) {
-        const double Se = (red_e[0][lane] + red_e[1][lane]) + (red_e[2][lane] + red_e[3][lane]);
-        const double So = (red_o[0][lane] + red_o[1][lane]) + (red_o[2][lane] + red_o[3][lane]);
-        const bool act = lane < it.nrows;
-        partials[it.out + lane] = act ? Se + So : 0.0;
-        if (it.mirror) partials[it.out2 + lane] = act ? Se - So : 0.0;
-    }
+    cjt_kern::rec_fwd_stored_cta(it, c, E, partials);
 }
 
-// One CTA of SW warps per item: warp w takes the item's degree columns w*32 + lane,
-// (w + SW)*32 + lane, ...; each column sums its 32 rows in order.  Under the parity fold
-// row r also stands for row Ng - row0 - r: degree n gets P_n(x_r) (g_r + (-1)^n g_mirror),
-// and column k = k0 + lane (k0 and a multiples of 32) has the parity of its lane.
 __global__ void __launch_bounds__(32 * SW) k_rec_inv_stored(const RecItem *__restrict__ items, int64_t nitems,
                                                             int64_t Ng, const double *__restrict__ g,
                                                             const double *__restrict__ E, double *__restrict__ partials) {
-    __shared__ double gs[2][32];   // [0]: even degrees, [1]: odd degrees
     if ((int64_t)blockIdx.x >= nitems) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RecItem it = items[blockIdx.x];
-    if (w == 0) {
-        const bool act = lane < it.nrows;
-        const double gr = act ? g[it.row0 + lane] : 0.0;
-        const double gm = act && it.mirror ? g[Ng - it.row0 - lane] : 0.0;
-        gs[0][lane] = gr + gm;
-        gs[1][lane] = gr - gm;
-    }
-    __syncthreads();
-    const int len = it.b - it.a;
-    const double *e = E + it.eoff;
-    const double *gl = gs[lane & 1];
-    double *out = partials + it.out;
-    for (int k0 = w * 32; k0 < len; k0 += 32 * SW) {
-        const int k = k0 + lane;
-        if (k < len) {
-            double acc = 0.0;
-            for (int r = 0; r < it.nrows; ++r) acc = fma(gl[r], __ldg(e + (int64_t)r * len + k), acc);
-            out[k] = acc;
-        }
-    }
+    cjt_kern::rec_inv_stored_cta(it, Ng, g, E, partials);
 }
 
-// ---------------------------------------------------------------------------
-// ASY packs: pair p holds items q = 2p, 2p+1 (q = k*M + m) as the real and imaginary
-// parts of one complex transform input, from the pre-scaled tables; arithmetic in the
-// transform precision R.
-// ---------------------------------------------------------------------------
 template <typename V, typename R>
 __global__ void k_asy_pack_fwd_s(int64_t N, int64_t L, int nq, const R *__restrict__ Cs, const double *__restrict__ c,
                                  V *__restrict__ buf) {
     const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int p = blockIdx.y;
     if (n >= L) return;
-    V o;
-    o.x = 0;
-    o.y = 0;
-    if (n <= N) {
-        const R cn = (R)c[n];
-        const int q = 2 * p;
-        o.x = Cs[(int64_t)q * (N + 1) + n] * cn;
-        if (q + 1 < nq) o.y = Cs[(int64_t)(q + 1) * (N + 1) + n] * cn;
-    }
-    buf[(int64_t)p * L + n] = o;
+    cjt_kern::asy_pack_fwd_elem<V, R>(n, blockIdx.y, N, L, nq, Cs, c, buf);
 }
 
 template <typename V, typename R>
 __global__ void k_asy_pack_inv_s(int64_t Ng, int64_t L, int nq, const R *__restrict__ Us, const R *__restrict__ Vs,
                                  const double *__restrict__ g, V *__restrict__ buf) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int p = blockIdx.y;
     if (idx >= L) return;
-    // H(idx) = (z(idx) + conj z(L - idx)) / 2: the box rows lie in [1, Ng - 1]
-    const bool lo = idx <= Ng;
-    const int64_t i = lo ? idx : L - idx;
-    const R gi = (R)g[i];
-    const R sgn = lo ? (R)1 : (R)-1;
-    const int q = 2 * p;
-    const R h0r = Us[(int64_t)q * (Ng + 1) + i] * gi, h0i = sgn * Vs[(int64_t)q * (Ng + 1) + i] * gi;
-    R h1r = 0, h1i = 0;
-    if (q + 1 < nq) {
-        h1r = Us[(int64_t)(q + 1) * (Ng + 1) + i] * gi;
-        h1i = sgn * Vs[(int64_t)(q + 1) * (Ng + 1) + i] * gi;
-    }
-    V o;
-    o.x = h0r - h1i;
-    o.y = h0i + h1r;
-    buf[(int64_t)p * L + idx] = o;
+    cjt_kern::asy_pack_inv_elem<V, R>(idx, blockIdx.y, Ng, L, nq, Us, Vs, g, buf);
 }
 
 // ---------------------------------------------------------------------------
@@ -489,14 +285,6 @@ __global__ void __launch_bounds__(32 * SW) k_rec_inv_stored_df(const RecItem *__
     }
 }
 
-// transform output components as doubles
-__device__ __forceinline__ double re_d(double2 v) { return v.x; }
-__device__ __forceinline__ double im_d(double2 v) { return v.y; }
-__device__ __forceinline__ double re_d(float2 v) { return (double)v.x; }
-__device__ __forceinline__ double im_d(float2 v) { return (double)v.y; }
-__device__ __forceinline__ double re_d(dfc v) { return df_to(dfc_re(v)); }
-__device__ __forceinline__ double im_d(dfc v) { return df_to(dfc_im(v)); }
-
 // ---------------------------------------------------------------------------
 // combine, forward, CJT_DFLOAT: the same sums in double-float arithmetic on the scaled
 // input (partials P: double-floats from the stored recurrence, or doubles from the
@@ -557,10 +345,7 @@ __global__ void k_combine_fwd_df(int64_t N, int64_t L, int M, const int *__restr
     if (i >= 1 && i < N) ext[2 * N - i] = make_double2(yv, 0.0);
 }
 
-// ---------------------------------------------------------------------------
-// combine, forward: REC segment partials + asymptotic terms; writes the even
-// extension of y (length 2N) for the final DCT-I
-// ---------------------------------------------------------------------------
+
 template <typename V>
 __global__ void k_combine_fwd(int64_t N, int64_t L, int M, const int *__restrict__ rowk,
                               const double *__restrict__ scale, const double *__restrict__ u,
@@ -569,120 +354,38 @@ __global__ void k_combine_fwd(int64_t N, int64_t L, int M, const int *__restrict
                               const double *__restrict__ partials, double2 *__restrict__ ext) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i > N) return;
-    const int nseg = row_nseg[i];
-    const int64_t base = row_base[i];
-    // rows near x = +-1 have up to N / seg_len segments: eight loads in flight, four sums
-    double ya[4] = {0.0, 0.0, 0.0, 0.0};
-    int s = 0;
-    for (; s + 8 <= nseg; s += 8) {
-        double pv[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) pv[j] = partials[base + (int64_t)(s + j) * 32];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) ya[j & 3] += pv[j];
-    }
-    for (; s < nseg; ++s) ya[0] += partials[base + (int64_t)s * 32];
-    double y = (ya[0] + ya[1]) + (ya[2] + ya[3]);
-    const int k = rowk[i];
-    if (k >= 0) {
-        const int64_t im = i == 0 ? 0 : L - i;
-        for (int m = 0; m < M; ++m) {
-            const int q = k * M + m, p = q >> 1;
-            const V Z = buf[(int64_t)p * L + i], W = buf[(int64_t)p * L + im];
-            double re, imv;
-            if ((q & 1) == 0) {
-                re = 0.5 * (re_d(Z) + re_d(W));
-                imv = 0.5 * (im_d(Z) - im_d(W));
-            } else {
-                re = 0.5 * (im_d(Z) + im_d(W));
-                imv = 0.5 * (re_d(W) - re_d(Z));
-            }
-            const double us = scale[2 * q + 1];
-            y = fma(u[m * (N + 1) + i] * us, re, y);
-            y = fma(-v[m * (N + 1) + i] * us, imv, y);
-        }
-    }
-    ext[i] = make_double2(y, 0.0);
-    if (i >= 1 && i < N) ext[2 * N - i] = make_double2(y, 0.0);
+    cjt_kern::combine_fwd_elem<V>(i, N, L, M, rowk, scale, u, v, buf, row_base, row_nseg, partials, ext);
 }
 
-// c_k = Re Z(k) / G, halved at k = 0 and k = G (inverse scaled DCT-I on the grid G >= N),
-// for k <= N
+// c_k for k <= N from the transform of the grid G >= N
 __global__ void k_dct_finish(int64_t N, int64_t G, const double2 *__restrict__ Z, double *__restrict__ out) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k > N) return;
-    double v = Z[k].x / (double)G;
-    if (k == 0 || k == G) v *= 0.5;
-    out[k] = v;
+    cjt_kern::dct_finish_elem(k, G, Z, out);
 }
 
-// ---------------------------------------------------------------------------
-// inverse front end and transposed blocks
-// ---------------------------------------------------------------------------
 __global__ void k_inv_front_pack(int64_t N, int64_t L, const double *__restrict__ c, double2 *__restrict__ buf) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= L) return;
-    buf[k] = make_double2(k <= N ? c[k] : 0.0, 0.0);
+    cjt_kern::inv_front_pack_elem(k, N, c, buf);
 }
 
 __global__ void k_inv_g(int64_t Ng, const double2 *__restrict__ F, const double *__restrict__ w, double *__restrict__ g) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i > Ng) return;
-    g[i] = w[i] * F[i].x;
+    cjt_kern::inv_g_elem(i, F, w, g);
 }
 
-// Sum of the recurrence partials of every item covering degree n, in a fixed order:
-// warp w takes items w, w + RED_WARPS, w + 2 RED_WARPS, ... (round robin, so that short
-// segments spread over all warps), 32 of them at a time: lane l loads the descriptor of
-// the l-th, the warp broadcasts them by shuffles, and eight partial loads are in flight;
-// four interleaved accumulators; the warp sums are added in warp order.  One block per
-// 32 consecutive degrees.
-constexpr int RED_WARPS = 32;
+// one block per 32 consecutive degrees
 __global__ void __launch_bounds__(32 * RED_WARPS) k_inv_reduce(int64_t N, int seg_len,
                                                                const int64_t *__restrict__ seg_ptr,
                                                                const int64_t *__restrict__ seg_out,
                                                                const int *__restrict__ seg_b,
                                                                const double *__restrict__ partials,
                                                                double *__restrict__ y) {
-    __shared__ double red[RED_WARPS][33];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t n0 = (int64_t)blockIdx.x * 32, n = n0 + lane;
-    const int64_t s = n0 / seg_len, off = n - s * seg_len;
-    const int64_t q0 = seg_ptr[s], q1 = seg_ptr[s + 1];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const int64_t kmax = q1 - q0 > w ? (q1 - q0 - w + RED_WARPS - 1) / RED_WARPS : 0;   // this warp's items
-    for (int64_t kb = 0; kb < kmax; kb += 32) {
-        const int64_t qq = q0 + w + (int64_t)RED_WARPS * (kb + lane);
-        const bool ok = kb + lane < kmax;
-        const int64_t so = ok ? seg_out[qq] : 0;
-        const int sb = ok ? seg_b[qq] : 0;
-        const int cnt = (int)min((int64_t)32, kmax - kb);
-        int j = 0;
-        for (; j + 8 <= cnt; j += 8) {
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int64_t o = __shfl_sync(0xffffffffu, so, j + t);
-                const int b = __shfl_sync(0xffffffffu, sb, j + t);
-                if (n < b) acc[t & 3] += partials[o + off];
-            }
-        }
-        for (; j < cnt; ++j) {
-            const int64_t o = __shfl_sync(0xffffffffu, so, j);
-            const int b = __shfl_sync(0xffffffffu, sb, j);
-            if (n < b) acc[0] += partials[o + off];
-        }
-    }
-    red[w][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-    __syncthreads();
-    if (w == 0 && n <= N) {
-        double t = 0.0;
-        for (int k = 0; k < RED_WARPS; ++k) t += red[k][lane];
-        y[n] = t;
-    }
+    cjt_kern::inv_reduce_block(blockIdx.x, N, seg_len, seg_ptr, seg_out, seg_b, partials, y);
 }
 
-// exps (CJT_DFLOAT only): the transposed blocks ran on g scaled by 2^-e, and so did the
-// recurrence when rec_scaled; both are unscaled here.
 template <typename V>
 __global__ void k_combine_inv(int64_t N, int64_t L, int M, int nblk, const int *__restrict__ box3,
                               const double *__restrict__ scale, const double *__restrict__ Cnm,
@@ -691,29 +394,19 @@ __global__ void k_combine_inv(int64_t N, int64_t L, int M, int nblk, const int *
                               double *__restrict__ out) {
     const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (n > N) return;
-    const double ua = exps ? ldexp(1.0, exps[CJT_EXP_BLOCKS]) : 1.0;
-    double y = rec_scaled ? ua * yrec[n] : yrec[n];
-    // degree n belongs to block k when j_k <= n < top_k (top_0 = N+1, top_k = j_{k-1})
-    int k = -1;
-    for (int kk = 0; kk < nblk; ++kk) {
-        const int64_t top = kk == 0 ? N + 1 : box3[3 * (kk - 1)];
-        if (n >= box3[3 * kk] && n < top) k = kk;
-    }
-    if (k >= 0) {
-        for (int m = 0; m < M; ++m) {
-            const int q = k * M + m, p = q >> 1;
-            const V Z = buf[(int64_t)p * L + n];
-            const double R = (q & 1) ? im_d(Z) : re_d(Z);
-            y = fma(Cnm[m * (N + 1) + n] * (scale[2 * q + 1] * ua), R, y);
-        }
-    }
-    out[n] = s_n[n] * y;
+    cjt_kern::combine_inv_elem<V>(n, N, L, M, nblk, box3, scale, Cnm, buf, yrec, s_n, exps, rec_scaled, out);
 }
 
 __global__ void k_copy(int64_t n, const double *__restrict__ in, double *__restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = in[i];
 }
+
+// gives an execution's overlap context back to the pool on every return path
+struct OvGuard {
+    OvCtx *c;
+    ~OvGuard() { cjt_internal_ovctx_release(c); }
+};
 
 }  // namespace
 
@@ -743,13 +436,19 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     // the asymptotic transforms run on a side stream, concurrently with the recurrence
     // (on the caller's stream, or on a second side stream with CJT_OVERLAP_REC_FIRST)
-    const bool ovl = nq > 0 && p->side;
-    cudaStream_t sa = ovl ? p->side : st;
-    cudaStream_t sr = (ovl && p->side_rec) ? p->side_rec : st;
+    const bool ovl = nq > 0;
+    OvCtx *oc = nullptr;
     if (ovl) {
-        CJT_CUDA_TRY(cudaEventRecord(p->ev_fork, st));
-        CJT_CUDA_TRY(cudaStreamWaitEvent(sa, p->ev_fork, 0));
-        if (sr != st) CJT_CUDA_TRY(cudaStreamWaitEvent(sr, p->ev_fork, 0));
+        rc = cjt_internal_ovctx_acquire(p->opts.overlap, st, &oc);
+        if (rc) return rc;
+    }
+    OvGuard og{oc};
+    cudaStream_t sa = ovl ? oc->side : st;
+    cudaStream_t sr = (ovl && oc->side_rec) ? oc->side_rec : st;
+    if (ovl) {
+        CJT_CUDA_TRY(cudaEventRecord(oc->fork, st));
+        CJT_CUDA_TRY(cudaStreamWaitEvent(sa, oc->fork, 0));
+        if (sr != st) CJT_CUDA_TRY(cudaStreamWaitEvent(sr, oc->fork, 0));
     }
     if (nq > 0) {
         dim3 gp(blocks_for(L, 256), p->npair_f);
@@ -783,11 +482,11 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         CJT_CUDA_TRY(cudaGetLastError());
     }
     if (ovl) {
-        CJT_CUDA_TRY(cudaEventRecord(p->ev_join, sa));
-        CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
+        CJT_CUDA_TRY(cudaEventRecord(oc->join, sa));
+        CJT_CUDA_TRY(cudaStreamWaitEvent(st, oc->join, 0));
         if (sr != st) {
-            CJT_CUDA_TRY(cudaEventRecord(p->ev_join_rec, sr));
-            CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join_rec, 0));
+            CJT_CUDA_TRY(cudaEventRecord(oc->join_rec, sr));
+            CJT_CUDA_TRY(cudaStreamWaitEvent(st, oc->join_rec, 0));
         }
     }
     double2 *ext = (double2 *)ws.dct;
@@ -854,13 +553,19 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     // transposed asymptotic blocks, on a side stream concurrently with the recurrence
     // (on the caller's stream, or on a second side stream with CJT_OVERLAP_REC_FIRST)
-    const bool ovl = nq > 0 && p->side;
-    cudaStream_t sa = ovl ? p->side : st;
-    cudaStream_t sr = (ovl && p->side_rec) ? p->side_rec : st;
+    const bool ovl = nq > 0;
+    OvCtx *oc = nullptr;
     if (ovl) {
-        CJT_CUDA_TRY(cudaEventRecord(p->ev_fork, st));
-        CJT_CUDA_TRY(cudaStreamWaitEvent(sa, p->ev_fork, 0));
-        if (sr != st) CJT_CUDA_TRY(cudaStreamWaitEvent(sr, p->ev_fork, 0));
+        rc = cjt_internal_ovctx_acquire(p->opts.overlap, st, &oc);
+        if (rc) return rc;
+    }
+    OvGuard og{oc};
+    cudaStream_t sa = ovl ? oc->side : st;
+    cudaStream_t sr = (ovl && oc->side_rec) ? oc->side_rec : st;
+    if (ovl) {
+        CJT_CUDA_TRY(cudaEventRecord(oc->fork, st));
+        CJT_CUDA_TRY(cudaStreamWaitEvent(sa, oc->fork, 0));
+        if (sr != st) CJT_CUDA_TRY(cudaStreamWaitEvent(sr, oc->fork, 0));
     }
     if (nq > 0) {
         dim3 gp(blocks_for(L, 256), p->npair_i);
@@ -901,11 +606,11 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         CJT_CUDA_TRY(cudaGetLastError());
     }
     if (ovl) {
-        CJT_CUDA_TRY(cudaEventRecord(p->ev_join, sa));
-        CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
+        CJT_CUDA_TRY(cudaEventRecord(oc->join, sa));
+        CJT_CUDA_TRY(cudaStreamWaitEvent(st, oc->join, 0));
         if (sr != st) {
-            CJT_CUDA_TRY(cudaEventRecord(p->ev_join_rec, sr));
-            CJT_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join_rec, 0));
+            CJT_CUDA_TRY(cudaEventRecord(oc->join_rec, sr));
+            CJT_CUDA_TRY(cudaStreamWaitEvent(st, oc->join_rec, 0));
         }
     }
     StageTimer tm(p, st, CJT_STAGE_INV_COMBINE);

@@ -38,9 +38,20 @@ void cjt_internal_set_cuda_error(cudaError_t e, const char *what);
 struct cjt_plan_s;
 int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st);
 int cjt_internal_end_use(cjt_plan_s *p, cudaStream_t st);
-// round-robin pools of non-blocking streams per device, of the highest (high) or the
-// normal priority
-int cjt_internal_side_stream(bool high, cudaStream_t *out);
+// Side streams and events of one execution's two concurrent chains (the asymptotic blocks
+// and the recurrence, option overlap).  Each execution takes a context of its own from a
+// per-device pool for the time it enqueues its work and gives it back at once (cudaEvent
+// records and waits are resolved when they are enqueued), so executions on different host
+// threads never share a fork or join event.  The pool hands out its contexts in turn, so
+// consecutive executions on different streams put their asymptotic chains on different side
+// streams, and it skips a context whose stream still belongs to another open stream capture.
+struct OvCtx {
+    int dev = 0, mode = 0;
+    cudaStream_t side = nullptr, side_rec = nullptr;   // side_rec: CJT_OVERLAP_REC_FIRST only
+    cudaEvent_t fork = nullptr, join = nullptr, join_rec = nullptr;
+};
+int cjt_internal_ovctx_acquire(int overlap, cudaStream_t origin, OvCtx **out);
+void cjt_internal_ovctx_release(OvCtx *c);
 
 // ---------------------------------------------------------------------------
 // recurrence work items
@@ -277,13 +288,6 @@ struct cjt_plan_s {
     double *d_w = nullptr;        // inverse: Clenshaw--Curtis weights (2N+1)
     double *d_s = nullptr;        // inverse: 1/A_n (N+1)
     double *d_in = nullptr, *d_out = nullptr;  // staging for cjt_execute_host
-
-    // overlap of the asymptotic transforms with the recurrence (option overlap): the
-    // asymptotic chain on a side stream from a device pool, the recurrence on the caller's
-    // stream or (CJT_OVERLAP_REC_FIRST) on a high-priority side stream; a fork event and
-    // one join event per side stream
-    cudaStream_t side = nullptr, side_rec = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_rec = nullptr;
 
     // concurrency guard
     cudaStream_t last_stream = nullptr;

@@ -1101,15 +1101,6 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     if (tmp_ws) cudaFreeAsync(tmp_ws, st);
     tr.mark("buffers, inverse weights");
     CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
-    if (p->fw.nblk > 0 || p->iv.nblk > 0) {
-        TRY(cjt_internal_side_stream(p->opts.overlap == CJT_OVERLAP_ASY_FIRST, &p->side));
-        CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
-        CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
-        if (p->opts.overlap == CJT_OVERLAP_REC_FIRST) {
-            TRY(cjt_internal_side_stream(true, &p->side_rec));
-            CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join_rec, cudaEventDisableTiming));
-        }
-    }
     CJT_CUDA_TRY(cudaStreamSynchronize(st));
     return CJT_OK;
 }
