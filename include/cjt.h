@@ -222,6 +222,25 @@ void cjt_destroy(cjt_plan_t plan);
 int cjt_get_info(cjt_plan_t plan, cjt_plan_info *info);
 
 /*
+ * Stated error bound of the plan's transform in `direction`, per unit ||c_in||_1 of the
+ * input: max_k |c_k - c_k^exact| <= *bound * ||c_in||_1.
+ *   CJT_FP64, CJT_DFLOAT: 1e-12, the bound this library states and tests for its FP64
+ *       arithmetic (the paper bounds the inverse pessimistically, Sec. 3.3).
+ *   CJT_MIXED: 1e-12 plus a bound on what the FP32 transforms of the asymptotic blocks
+ *       add, derived at plan time from the componentwise error of an FP32 transform of
+ *       length L, eps_F = 2^-24 (3 log2 L + 8) times the sum of its inputs' moduli, carried
+ *       through the scaled items and the diagonals (Eq. "Jacasyuv"):
+ *         forward: 2 eps_F max_i sum_m (|u_m| + |v_m|)(theta_i) (C_{j_k,m} + paired item),
+ *         inverse: eps_F max_n (1/A_n) sum_m C_{n,m} sum_{i in box} w_i (|u_m| + |v_m|)(theta_i)
+ *                  (+ paired item),
+ *       with the boxes, j_k and C_{n,m} of the plan's partition (Sec. 2.2), the
+ *       Clenshaw--Curtis weights w_i (Eq. "CCweights") and 1/A_n (Eq. "Anab"): the growth
+ *       of 1/A_n with n is why the inverse's bound exceeds the forward's.
+ * Errors: CJT_EINVAL (null, bad direction), CJT_EDIRECTION.
+ */
+int cjt_error_bound(cjt_plan_t plan, int direction, double *bound);
+
+/*
  * Forward transform (Eq. "CJT"): c_cheb_dev[k], k = 0..N, from c_jac_dev[n].
  * Both are device arrays of N+1 doubles; they may alias.
  * Errors: CJT_EINVAL (null), CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA.
@@ -291,12 +310,20 @@ int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, c
                         const double *in_dev, double *out_dev, void *stream);
 
 /*
- * A captured batch: cjt_batch_create sizes private workspace arenas for the
- * items (nstreams concurrent lanes, 0 -> 16), captures the whole batched
- * execution of the given items and buffers into one CUDA graph and
- * instantiates it; cjt_batch_launch replays it on `stream` with a single graph
- * launch.  Plans and buffers must outlive the batch.  cjt_batch_info reports
- * the number of kernel nodes and the arena bytes.
+ * A captured batch: cjt_batch_create captures the whole batched execution of the
+ * given items and buffers into one CUDA graph and instantiates it; cjt_batch_launch
+ * replays it on `stream` with a single graph launch.  Plans and buffers must outlive
+ * the batch.  cjt_batch_info reports the kernel launches of one replay and the bytes
+ * of the batch's private workspace arenas.
+ *   Grouped execution (Sec. 4: one plan machinery over many coefficient sets): items
+ * in FP64 or the mixed form with power-of-two transform lengths and no parameter
+ * shift run stage by stage, one launch per stage over many items, and one batched
+ * FFT per (length, precision) class.  The items are taken by decreasing cost and
+ * packed into waves whose workspace fits CJT_BATCH_ARENA_MB MiB (environment,
+ * default 4096); consecutive waves alternate between two such arenas and two pairs
+ * of streams.  Every grouped item's result is bit-identical to the same plan run
+ * alone.  The other items (double-float form, shifted parameters, Bluestein
+ * lengths) run one chain of launches each over `nstreams` lanes (0 -> 16).
  */
 typedef struct cjt_batch_s *cjt_batch_t;
 int cjt_batch_create(cjt_batch_t *out, int count, const cjt_plan_t *plans, const int8_t *dir,
@@ -306,12 +333,44 @@ int cjt_batch_info(cjt_batch_t batch, int64_t *kernels, int64_t *arena_bytes);
 void cjt_batch_destroy(cjt_batch_t batch);
 
 /*
+ * End-to-end batched execution from host memory: copies in_host (the batch's whole input,
+ * offsets as given to cjt_batch_create) to the batch's device input buffer, replays the
+ * batch, copies its device output buffer to out_host and waits for `stream`.  Both host
+ * arrays hold max_t (offsets[t] + N_t + 1) doubles (pinned memory gives the fastest
+ * copies).  Errors: CJT_EINVAL (null), CJT_ECUDA.
+ */
+int cjt_batch_launch_host(cjt_batch_t batch, const double *in_host, double *out_host, void *stream);
+
+/*
+ * Batch profiling.  With cjt_batch_set_profiling(batch, 1), cjt_batch_launch issues the
+ * grouped items' kernels directly, one after another on one stream (the same kernels and
+ * results as a replay of its graph, without the overlap of its streams), with a CUDA event
+ * pair around every launch, and cjt_batch_get_profile waits for them and returns per stage
+ * kind s < n the summed milliseconds ms[s] and the launches counts[s] since the last call
+ * (either pointer may be NULL).  Items that run one chain each (see cjt_batch_create) run
+ * as in a replay and are not timed.
+ */
+#define CJT_BSTAGE_FFT_ASY 0      /* DCT-I/DST-I of the asymptotic blocks (Eq. "PNASY", "CJTT") */
+#define CJT_BSTAGE_FFT_DCT 1      /* final DCT-I and the inverse front end                       */
+#define CJT_BSTAGE_REC 2          /* recurrences at execution (Sec. 4.2)                         */
+#define CJT_BSTAGE_REC_STORED 3   /* stored recurrence values (rec_store)                        */
+#define CJT_BSTAGE_REDUCE 4       /* fixed-order sums over the transposed recurrence's items     */
+#define CJT_BSTAGE_PACK 5         /* C_{n,m} c_n and (u_m + i v_m) g packing                     */
+#define CJT_BSTAGE_COMBINE 6      /* accumulation of the asymptotic terms, 1/A_n                 */
+#define CJT_BSTAGE_OTHER 7        /* front-end packing, Clenshaw--Curtis weights, DCT scaling    */
+#define CJT_NBSTAGE 8
+int cjt_batch_set_profiling(cjt_batch_t batch, int on);
+int cjt_batch_get_profile(cjt_batch_t batch, double *ms, int64_t *counts, int n);
+
+/*
  * Stage profiling.  cjt_set_profiling(plan, 1) makes every later execution of
- * the plan record a CUDA event pair around each stage on the launching stream;
+ * the plan run its stages one after another on the launching stream (the
+ * asymptotic chain no longer overlaps the recurrence) and record a CUDA event
+ * pair around each stage, so that each pair times its stage alone;
  * cjt_get_profile waits for those events and returns, per stage s < n, the
  * summed milliseconds ms[s] and the number of timed launches counts[s]
- * (either pointer may be NULL), then clears the record.  Profiling adds one
- * event record per stage boundary and is off by default.
+ * (either pointer may be NULL), then clears the record.  Results are the same
+ * bit for bit.  Profiling is off by default.
  */
 int cjt_set_profiling(cjt_plan_t plan, int on);
 int cjt_get_profile(cjt_plan_t plan, double *ms, int64_t *counts, int n);

@@ -68,9 +68,12 @@ EXPORTED = ["cjt_plan_opts_default", "cjt_plan", "cjt_destroy", "cjt_get_info", 
             "cjt_version", "cjt_set_profiling", "cjt_get_profile", "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc",
             "cjt_forward_ws", "cjt_inverse_ws", "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info",
             "cjt_batch_destroy", "cjt_jacobi_to_jacobi", "cjt_asy_coefficient", "cjt_asy_eval",
-            "cjt_rec_coefficients"]
+            "cjt_rec_coefficients", "cjt_error_bound", "cjt_batch_launch_host", "cjt_batch_set_profiling",
+            "cjt_batch_get_profile"]
 
 NOALLOC_MAX_N = 65536
+
+BSTAGES = ["fft_asy", "fft_dct", "rec", "rec_stored", "reduce", "pack", "combine", "other"]
 
 STAGES = ["fwd_rec", "fwd_pack", "fwd_fft", "fwd_combine", "fwd_dct", "inv_front", "inv_pack", "inv_fft",
           "inv_rec", "inv_combine"]
@@ -125,6 +128,10 @@ def load(path: str = LIB_PATH):
         lib.cjt_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.cjt_batch_destroy.argtypes = [vp]
         lib.cjt_batch_destroy.restype = None
+        lib.cjt_batch_launch_host.argtypes = [vp, vp, vp, vp]
+        lib.cjt_batch_set_profiling.argtypes = [vp, i]
+        lib.cjt_batch_get_profile.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64), i]
+        lib.cjt_error_bound.argtypes = [vp, i, ctypes.POINTER(d)]
         lib.cjt_strerror.argtypes = [i]
         lib.cjt_strerror.restype = ctypes.c_char_p
         lib.cjt_last_cuda_error.restype = ctypes.c_char_p
@@ -133,7 +140,8 @@ def load(path: str = LIB_PATH):
                      "cjt_execute_host", "cjt_execute_batched", "cjt_sync", "cjt_set_profiling", "cjt_get_profile",
                      "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc", "cjt_forward_ws", "cjt_inverse_ws",
                      "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info", "cjt_jacobi_to_jacobi",
-                     "cjt_asy_coefficient", "cjt_asy_eval", "cjt_rec_coefficients"):
+                     "cjt_asy_coefficient", "cjt_asy_eval", "cjt_rec_coefficients", "cjt_error_bound",
+                     "cjt_batch_launch_host", "cjt_batch_set_profiling", "cjt_batch_get_profile"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -293,6 +301,13 @@ def cjt_inverse_ws(plan: Plan, c_cheb, c_jac, workspace, stream=None):
     return c_jac
 
 
+def error_bound(plan: Plan, direction: int) -> float:
+    """Stated error bound of the plan's transform in `direction`, per unit ||c_in||_1."""
+    v = ctypes.c_double()
+    _check(load().cjt_error_bound(plan.handle, int(direction), ctypes.byref(v)), "cjt_error_bound")
+    return v.value
+
+
 class Batch:
     """cjt_batch_t: a batched execution captured into one CUDA graph."""
 
@@ -310,6 +325,26 @@ class Batch:
 
     def launch(self, stream=None):
         _check(load().cjt_batch_launch(self._h, _stream_handle(stream)), "cjt_batch_launch")
+
+    def launch_host(self, x_host: np.ndarray, out_host: np.ndarray, stream=None):
+        """Host input -> device -> replay -> host output, synchronous (whole-batch arrays)."""
+        if x_host.dtype != np.float64 or out_host.dtype != np.float64 or x_host.size != out_host.size:
+            raise ValueError("float64 host arrays of equal size expected")
+        _check(load().cjt_batch_launch_host(self._h, ctypes.c_void_p(x_host.ctypes.data),
+                                            ctypes.c_void_p(out_host.ctypes.data), _stream_handle(stream)),
+               "cjt_batch_launch_host")
+        return out_host
+
+    def set_profiling(self, on: bool = True):
+        _check(load().cjt_batch_set_profiling(self._h, 1 if on else 0), "cjt_batch_set_profiling")
+
+    def profile(self):
+        """{stage kind: (total ms, launches)} of the profiled launches since the last call."""
+        n = len(BSTAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        _check(load().cjt_batch_get_profile(self._h, ms, cnt, n), "cjt_batch_get_profile")
+        return {BSTAGES[s]: (ms[s], cnt[s]) for s in range(n)}
 
     def info(self):
         k, b = ctypes.c_int64(), ctypes.c_int64()

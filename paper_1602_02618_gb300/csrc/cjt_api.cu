@@ -343,6 +343,15 @@ int cjt_asy_eval(double alpha, double beta, int expansion, int M, int64_t n, int
     return CJT_OK;
 }
 
+int cjt_error_bound(cjt_plan_t p, int direction, double *bound) {
+    if (!p || !bound) return CJT_EINVAL;
+    if (direction != CJT_FWD && direction != CJT_INV) return CJT_EINVAL;
+    if (!(p->opts.directions & direction)) return CJT_EDIRECTION;
+    const double fp64 = 1e-12;   // the FP64 form's stated bound (all forms' FP64 parts)
+    *bound = fp64 + (p->opts.precision == CJT_MIXED ? (direction == CJT_FWD ? p->err_mixed_fwd : p->err_mixed_inv) : 0.0);
+    return CJT_OK;
+}
+
 int cjt_set_profiling(cjt_plan_t p, int on) {
     if (!p) return CJT_EINVAL;
     p->prof = on != 0;

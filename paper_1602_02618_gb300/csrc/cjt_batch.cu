@@ -148,6 +148,15 @@ struct cjt_batch_s {
     std::vector<void *> arenas;
     int64_t arena_bytes = 0;
     cjt_group_t group = nullptr;   // the grouped items (cjt_group.cu)
+    // the items that run one chain each, for direct (profiled) launches
+    std::vector<cjt_plan_t> rp;
+    std::vector<int8_t> rd;
+    std::vector<int64_t> ro;
+    Assignment ra;
+    const double *in = nullptr;
+    double *out = nullptr;
+    int64_t total = 0;             // doubles of the input and of the output buffer
+    bool prof = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
@@ -235,17 +244,20 @@ int cjt_batch_create(cjt_batch_t *out, int count, const cjt_plan_t *plans, const
     if (rc) return fail(rc);
     b->arena_bytes += cjt_group_arena_bytes(b->group);
     b->kernels += cjt_group_kernels(b->group);
-    std::vector<cjt_plan_t> rp;
-    std::vector<int8_t> rd;
-    std::vector<int64_t> ro;
+    std::vector<cjt_plan_t> &rp = b->rp;
+    std::vector<int8_t> &rd = b->rd;
+    std::vector<int64_t> &ro = b->ro;
     for (int t : rest) {
         rp.push_back(plans[t]);
         rd.push_back(dir[t]);
         ro.push_back(offsets[t]);
     }
+    b->in = in_dev;
+    b->out = out_dev;
+    for (int t = 0; t < count; ++t) b->total = std::max(b->total, offsets[t] + plans[t]->N + 1);
     const int nrest = (int)rest.size();
     const int nl = nrest ? std::min(nstreams > 0 ? std::min(nstreams, 64) : default_lanes(), nrest) : 0;
-    Assignment a;
+    Assignment &a = b->ra;
     if (nrest) {
         a = assign(nrest, rp.data(), rd.data(), nl);
         rc = make_lanes(b->lanes, nl);
@@ -295,8 +307,44 @@ int cjt_batch_create(cjt_batch_t *out, int count, const cjt_plan_t *plans, const
 
 int cjt_batch_launch(cjt_batch_t b, void *stream) {
     if (!b || !b->exec) return CJT_EINVAL;
-    CJT_CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!b->prof) {
+        CJT_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+        return CJT_OK;
+    }
+    // profiled: the graph's launches issued directly, with events around the grouped ones
+    int rc = cjt_group_issue(b->group, st, true);
+    if (!rc && !b->rp.empty())
+        rc = issue((int)b->rp.size(), b->rp.data(), b->rd.data(), b->ro.data(), b->in, b->out, b->ra, b->lanes,
+                   b->arenas, st);
+    return rc;
+}
+
+int cjt_batch_launch_host(cjt_batch_t b, const double *in_host, double *out_host, void *stream) {
+    if (!b || !b->exec || !in_host || !out_host) return CJT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * (size_t)b->total;
+    CJT_CUDA_TRY(cudaMemcpyAsync((void *)b->in, in_host, bytes, cudaMemcpyHostToDevice, st));
+    int rc = cjt_batch_launch(b, stream);
+    if (rc) return rc;
+    CJT_CUDA_TRY(cudaMemcpyAsync(out_host, b->out, bytes, cudaMemcpyDeviceToHost, st));
+    CJT_CUDA_TRY(cudaStreamSynchronize(st));
     return CJT_OK;
+}
+
+int cjt_batch_set_profiling(cjt_batch_t b, int on) {
+    if (!b) return CJT_EINVAL;
+    b->prof = on != 0;
+    return CJT_OK;
+}
+
+int cjt_batch_get_profile(cjt_batch_t b, double *ms, int64_t *counts, int n) {
+    if (!b || n < 0) return CJT_EINVAL;
+    for (int s = 0; s < n; ++s) {
+        if (ms) ms[s] = 0.0;
+        if (counts) counts[s] = 0;
+    }
+    return cjt_group_profile(b->group, ms, counts, n);
 }
 
 int cjt_batch_info(cjt_batch_t b, int64_t *kernels, int64_t *arena_bytes) {

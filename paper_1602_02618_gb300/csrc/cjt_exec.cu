@@ -436,7 +436,7 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     // the asymptotic transforms run on a side stream, concurrently with the recurrence
     // (on the caller's stream, or on a second side stream with CJT_OVERLAP_REC_FIRST)
-    const bool ovl = nq > 0;
+    const bool ovl = nq > 0 && !p->prof;   // profiled: the two chains one after the other
     OvCtx *oc = nullptr;
     if (ovl) {
         rc = cjt_internal_ovctx_acquire(p->opts.overlap, st, &oc);
@@ -553,7 +553,7 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
     }
     // transposed asymptotic blocks, on a side stream concurrently with the recurrence
     // (on the caller's stream, or on a second side stream with CJT_OVERLAP_REC_FIRST)
-    const bool ovl = nq > 0;
+    const bool ovl = nq > 0 && !p->prof;   // profiled: the two chains one after the other
     OvCtx *oc = nullptr;
     if (ovl) {
         rc = cjt_internal_ovctx_acquire(p->opts.overlap, st, &oc);

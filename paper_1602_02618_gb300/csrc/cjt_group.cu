@@ -28,6 +28,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -219,6 +221,7 @@ enum { EV_FORK, EV_FRONT, EV_SIDE, EV_N };
 
 struct Step {
     int type = 0;
+    int cat = -1;                     // CJT_BSTAGE_* of the launch (profiling)
     int op = 0, prec = PREC_F64;      // ST_ELEM: Elem op and transform precision; ST_REC: REC_K_*
     size_t tab = 0;                   // ST_ELEM / ST_REDUCE: GTab offset; ST_REC: sel offset
     size_t pre = 0;                   // ST_REC: prefix offset
@@ -263,6 +266,10 @@ struct cjt_group_s {
     cudaEvent_t ev[2][EV_N] = {{nullptr}};
     cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
     int64_t kernels = 0;
+    // profiling: an event pair around every launch step of a direct (not captured) issue
+    struct Rec { int cat; cudaEvent_t a, b; };
+    std::vector<Rec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
 };
 
 bool cjt_group_eligible(const cjt_plan_s *p, int dir) {
@@ -299,6 +306,8 @@ template <int OP> void add_elem(cjt_group_s *g, std::vector<Step> &out, const st
     s.type = ST_ELEM;
     s.op = OP;
     s.prec = prec;
+    s.cat = (OP == OP_PACK_FWD || OP == OP_PACK_INV) ? CJT_BSTAGE_PACK
+            : (OP == OP_COMBINE_FWD || OP == OP_COMBINE_INV) ? CJT_BSTAGE_COMBINE : CJT_BSTAGE_OTHER;
     s.tab = push_table(g->tables, tab);
     s.grid = (int64_t)tab.size();
     out.push_back(s);
@@ -316,6 +325,7 @@ void add_rec(cjt_group_s *g, std::vector<Step> &out, const std::vector<int> &sel
     Step s;
     s.type = ST_REC;
     s.op = kind;
+    s.cat = (kind == REC_K_FWD_STORED || kind == REC_K_INV_STORED) ? CJT_BSTAGE_REC_STORED : CJT_BSTAGE_REC;
     s.tab = push_table(g->tables, s2);
     s.pre = push_table(g->tables, pre);
     s.nsel = (int)s2.size();
@@ -330,6 +340,7 @@ void add_reduce(cjt_group_s *g, std::vector<Step> &out, const std::vector<int> &
     if (tab.empty()) return;
     Step s;
     s.type = ST_REDUCE;
+    s.cat = CJT_BSTAGE_REDUCE;
     s.tab = push_table(g->tables, tab);
     s.grid = (int64_t)tab.size();
     out.push_back(s);
@@ -415,6 +426,30 @@ int run_step(cjt_group_s *g, const Step &s, int pair, cudaStream_t st) {
             return CJT_OK;
     }
     return CJT_EINVAL;
+}
+
+cudaEvent_t prof_event(cjt_group_s *g) {
+    if (!g->prof_pool.empty()) {
+        cudaEvent_t e = g->prof_pool.back();
+        g->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// run_step, with an event pair around a launch step when `prof`
+int run_step_p(cjt_group_s *g, const Step &s, int pair, cudaStream_t st, bool prof) {
+    if (!prof || s.cat < 0) return run_step(g, s, pair, st);
+    cudaEvent_t a = prof_event(g), b = prof_event(g);
+    if (!a || !b) return CJT_ECUDA;
+    CJT_CUDA_TRY(cudaEventRecord(a, st));
+    int rc = run_step(g, s, pair, st);
+    if (rc) return rc;
+    CJT_CUDA_TRY(cudaEventRecord(b, st));
+    g->prof_pending.push_back({s.cat, a, b});
+    return CJT_OK;
 }
 
 int64_t step_kernels(const Step &s) {
@@ -529,10 +564,11 @@ int64_t plan_wave(cjt_group_s *g, const std::vector<int> &items, const std::vect
             d.g = reinterpret_cast<double *>(base + off_g[k]);
         }
     }
-    auto ffts = [&](std::vector<Step> &out, const std::vector<Cls> &v, size_t scr) {
+    auto ffts = [&](std::vector<Step> &out, const std::vector<Cls> &v, size_t scr, int cat) {
         for (auto &c : v) {
             Step s;
             s.type = ST_FFT;
+            s.cat = cat;
             s.data = c.off;
             s.scratch = scr;
             s.L = c.L;
@@ -557,17 +593,17 @@ int64_t plan_wave(cjt_group_s *g, const std::vector<int> &items, const std::vect
     }
     // main: inverse front end
     add_elem<OP_FRONT_PACK>(g, wv.main_front, inv, PREC_F64);
-    ffts(wv.main_front, front, off_scr_main);
+    ffts(wv.main_front, front, off_scr_main, CJT_BSTAGE_FFT_DCT);
     add_elem<OP_INV_G>(g, wv.main_front, inv, PREC_F64);
     wv.main_front.push_back(ev_step(ST_RECORD, EV_FRONT));
     // side: forward ASY, then (after the front end) inverse ASY
     add_elem<OP_PACK_FWD>(g, wv.side, fwd64, PREC_F64);
     add_elem<OP_PACK_FWD>(g, wv.side, fwd32, PREC_F32);
-    ffts(wv.side, asy_f, off_scr_side);
+    ffts(wv.side, asy_f, off_scr_side, CJT_BSTAGE_FFT_ASY);
     if (!inv.empty()) wv.side.push_back(ev_step(ST_WAIT, EV_FRONT));
     add_elem<OP_PACK_INV>(g, wv.side, inv64, PREC_F64);
     add_elem<OP_PACK_INV>(g, wv.side, inv32, PREC_F32);
-    ffts(wv.side, asy_i, off_scr_side);
+    ffts(wv.side, asy_i, off_scr_side, CJT_BSTAGE_FFT_ASY);
     wv.side.push_back(ev_step(ST_RECORD, EV_SIDE));
     // main: recurrences and the reduction
     add_rec(g, wv.main_rec, fwd_sto, REC_K_FWD_STORED);
@@ -579,7 +615,7 @@ int64_t plan_wave(cjt_group_s *g, const std::vector<int> &items, const std::vect
     wv.main_post.push_back(ev_step(ST_WAIT, EV_SIDE));
     add_elem<OP_COMBINE_FWD>(g, wv.main_post, fwd64, PREC_F64);
     add_elem<OP_COMBINE_FWD>(g, wv.main_post, fwd32, PREC_F32);
-    ffts(wv.main_post, dct, off_scr_main);
+    ffts(wv.main_post, dct, off_scr_main, CJT_BSTAGE_FFT_DCT);
     add_elem<OP_DCT_FINISH>(g, wv.main_post, fwd, PREC_F64);
     add_elem<OP_COMBINE_INV>(g, wv.main_post, inv64, PREC_F64);
     add_elem<OP_COMBINE_INV>(g, wv.main_post, inv32, PREC_F32);
@@ -752,29 +788,50 @@ int cjt_group_create(cjt_group_t *out, const std::vector<int> &idx, const cjt_pl
     return CJT_OK;
 }
 
-int cjt_group_issue(cjt_group_t g, cudaStream_t origin) {
+// CJT_GROUP_TRACE=1: one line per launch step on stderr (stream, kind, op, length class,
+// sequences or work items, CTAs), in issue order, to read beside a profiler's launch list
+static void trace_step(const Step &s, int wave, const char *stream) {
+    static const bool on = getenv("CJT_GROUP_TRACE") != nullptr;
+    if (!on || s.type == ST_RECORD || s.type == ST_WAIT) return;
+    static const char *names[] = {"elem", "rec", "reduce", "fft"};
+    fprintf(stderr, "[cjt group] wave %d %s %s op=%d prec=%d L=%lld count=%lld grid=%lld total=%lld\n", wave, stream,
+            names[s.type], s.op, s.prec, (long long)s.L, (long long)s.count, (long long)s.grid, (long long)s.total);
+}
+
+int cjt_group_issue(cjt_group_t g, cudaStream_t origin, bool prof) {
     if (!g) return CJT_OK;
     CJT_CUDA_TRY(cudaEventRecord(g->fork, origin));
     bool used[2] = {false, false};
     for (auto &wv : g->waves) {
         const int a = wv.pair;
-        cudaStream_t m = g->main[a], s = g->side[a];
-        if (!used[a]) {
+        // profiled: every launch on one stream, so that each event pair times its launch alone
+        cudaStream_t m = prof ? g->main[0] : g->main[a], s = prof ? g->main[0] : g->side[a];
+        const int ua = prof ? 0 : a;
+        if (!used[ua]) {
             CJT_CUDA_TRY(cudaStreamWaitEvent(m, g->fork, 0));
-            used[a] = true;
+            used[ua] = true;
         }
         // the side stream starts with its wave
         CJT_CUDA_TRY(cudaEventRecord(g->ev[a][EV_FORK], m));
         CJT_CUDA_TRY(cudaStreamWaitEvent(s, g->ev[a][EV_FORK], 0));
         int rc;
-        for (auto &st : wv.main_front)
-            if ((rc = run_step(g, st, a, m))) return rc;
-        for (auto &st : wv.side)
-            if ((rc = run_step(g, st, a, s))) return rc;
-        for (auto &st : wv.main_rec)
-            if ((rc = run_step(g, st, a, m))) return rc;
-        for (auto &st : wv.main_post)
-            if ((rc = run_step(g, st, a, m))) return rc;
+        const int wi = (int)(&wv - g->waves.data());
+        for (auto &st : wv.main_front) {
+            trace_step(st, wi, "main");
+            if ((rc = run_step_p(g, st, a, m, prof))) return rc;
+        }
+        for (auto &st : wv.side) {
+            trace_step(st, wi, "side");
+            if ((rc = run_step_p(g, st, a, s, prof))) return rc;
+        }
+        for (auto &st : wv.main_rec) {
+            trace_step(st, wi, "main");
+            if ((rc = run_step_p(g, st, a, m, prof))) return rc;
+        }
+        for (auto &st : wv.main_post) {
+            trace_step(st, wi, "main");
+            if ((rc = run_step_p(g, st, a, m, prof))) return rc;
+        }
     }
     for (int a = 0; a < 2; ++a) {
         if (!used[a]) continue;
@@ -782,6 +839,28 @@ int cjt_group_issue(cjt_group_t g, cudaStream_t origin) {
         CJT_CUDA_TRY(cudaStreamWaitEvent(origin, g->join[a], 0));
     }
     return CJT_OK;
+}
+
+int cjt_group_profile(cjt_group_t g, double *ms, int64_t *counts, int n) {
+    if (!g) return CJT_OK;
+    int rc = CJT_OK;
+    for (auto &r : g->prof_pending) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) {
+            cjt_internal_set_cuda_error(e, "cudaEventElapsedTime");
+            rc = CJT_ECUDA;
+        }
+        if (r.cat < n) {
+            if (ms) ms[r.cat] += t;
+            if (counts) counts[r.cat] += 1;
+        }
+        g->prof_pool.push_back(r.a);
+        g->prof_pool.push_back(r.b);
+    }
+    g->prof_pending.clear();
+    return rc;
 }
 
 int64_t cjt_group_kernels(cjt_group_t g) { return g ? g->kernels : 0; }
@@ -801,5 +880,7 @@ void cjt_group_destroy(cjt_group_t g) {
             if (g->ev[a][k]) cudaEventDestroy(g->ev[a][k]);
     }
     if (g->fork) cudaEventDestroy(g->fork);
+    for (auto &r : g->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : g->prof_pool) cudaEventDestroy(e);
     delete g;
 }

@@ -296,6 +296,9 @@ struct cjt_plan_s {
 
     int64_t device_bytes = 0;
     double plan_ms = 0;
+    // CJT_MIXED: bound on the error the FP32 transforms add, per unit ||c_in||_1, for each
+    // direction (cjt_error_bound); 0 in the other forms
+    double err_mixed_fwd = 0, err_mixed_inv = 0;
     std::vector<void *> allocs;
 
     // stage profiling (CUDA events on the launching stream)

@@ -520,6 +520,98 @@ __global__ void k_to_df_inplace(int64_t n, double *E) {
     reinterpret_cast<dfs *>(E)[i] = df_from(v);
 }
 
+
+// --------------------------------------------------------------------------
+// Error bound of the mixed form (FP32 transforms).  A transform of length L in FP32
+// (unit roundoff u = 2^-24) computes each output within eps_F sum_n |z_n| of the exact
+// one: every radix-4 stage adds at most 5u times the sum of the moduli of the inputs that
+// feed an output (two levels of additions, the rounded twiddle and the fused complex
+// multiply), the radix-2 stage u, the four-step twiddle 3u, and the rounding of the
+// packed inputs to float 3u; the transform's unit-modulus weights carry earlier errors
+// without growth.  Conservatively eps_F = u (3 log2 L + 8).
+//   forward: row i of box k adds sum_m (u_m Re F_q - v_m Im F_q) / s_q, where the complex
+//   transform holds items q and q' (its pair partner) scaled by s_q, s_q', and
+//   sum_n |a_q[n]| <= s_q C_{j_k,m} ||c||_1 (C_{n,m} decreases in n).  The final inverse
+//   DCT-I maps max |dy| to at most 2 max |dy| in the coefficients:
+//     err_fwd = 2 eps_F max_i sum_m (|u_m| + |v_m|)(theta_i) (C_{j_k,m} + s_q'/s_q C_{j_k',m'}).
+//   inverse: degree n of block k adds C_{n,m} R_q(n) / s_q, with the transform's inputs of
+//   moduli <= s_q (|u_m| + |v_m|) |g_i| / 2 at rows i and Ng' - i of the box, |g_i| <=
+//   w_i ||c||_1 (|T_k| <= 1), and the result is scaled by 1/A_n:
+//     err_inv = eps_F max_n (1/A_n) sum_m C_{n,m} (U_q + s_q'/s_q U_q'),
+//     U_q = sum_{i in box k} |w_i| (|u_m| + |v_m|)(theta_i).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void atomic_max_pos(double *at, double v) {
+    // non-negative doubles order like their bit patterns as signed 64-bit integers
+    atomicMax(reinterpret_cast<long long *>(at), __double_as_longlong(v));
+}
+
+__global__ void k_err_fwd(int64_t N, int64_t Ng, int M, int nq, const int *__restrict__ rowk,
+                          const int *__restrict__ box3, const double *__restrict__ Cnm,
+                          const double *__restrict__ scale, const double *__restrict__ u,
+                          const double *__restrict__ v, double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > Ng) return;
+    const int k = rowk[i];
+    if (k < 0) return;
+    const int64_t j = box3[3 * k];
+    double s = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const int q = k * M + m, qp = q ^ 1;
+        double c = Cnm[m * (N + 1) + j];
+        if (qp < nq) {
+            const int kp = qp / M, mp = qp - kp * M;
+            c += scale[2 * qp] * scale[2 * q + 1] * Cnm[mp * (N + 1) + box3[3 * kp]];
+        }
+        s += (fabs(u[m * (Ng + 1) + i]) + fabs(v[m * (Ng + 1) + i])) * c;
+    }
+    atomic_max_pos(out, s);
+}
+
+// U_q for every item q, one block per q, summed in a fixed order
+__global__ void k_err_inv_U(int64_t Ng, int M, const int *__restrict__ box3, const double *__restrict__ w,
+                            const double *__restrict__ u, const double *__restrict__ v, double *__restrict__ U) {
+    __shared__ double red[256];
+    const int q = blockIdx.x, k = q / M, m = q - k * M;
+    const int64_t i1 = box3[3 * k + 1], i2 = box3[3 * k + 2];
+    double s = 0.0;
+    for (int64_t i = i1 + threadIdx.x; i <= i2; i += blockDim.x)
+        s += fabs(w[i]) * (fabs(u[m * (Ng + 1) + i]) + fabs(v[m * (Ng + 1) + i]));
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) U[q] = red[0];
+}
+
+__global__ void k_err_inv(int64_t N, int M, int nblk, int nq, const int *__restrict__ box3,
+                          const double *__restrict__ Cnm, const double *__restrict__ scale,
+                          const double *__restrict__ U, const double *__restrict__ s_n, double *__restrict__ out) {
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n > N) return;
+    int k = -1;
+    for (int kk = 0; kk < nblk; ++kk) {
+        const int64_t top = kk == 0 ? N + 1 : box3[3 * (kk - 1)];
+        if (n >= box3[3 * kk] && n < top) k = kk;
+    }
+    if (k < 0) return;
+    double s = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const int q = k * M + m, qp = q ^ 1;
+        double uq = U[q];
+        if (qp < nq) uq += scale[2 * qp] * scale[2 * q + 1] * U[qp];
+        s += Cnm[m * (N + 1) + n] * uq;
+    }
+    atomic_max_pos(out, s_n[n] * s);
+}
+
+inline double mixed_eps_fft(int64_t L) {
+    int lg = 0;
+    while ((1LL << lg) < L) ++lg;
+    return std::ldexp(1.0, -24) * (3.0 * lg + 8.0);
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // CJT_PLAN_TRACE=1: print the wall time of each planning step (synchronising after each)
@@ -1100,6 +1192,31 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     }
     if (tmp_ws) cudaFreeAsync(tmp_ws, st);
     tr.mark("buffers, inverse weights");
+    if (pa == PREC_F32 && (p->fw.nblk > 0 || p->iv.nblk > 0)) {
+        // bound on the FP32 transforms' error (see k_err_fwd): two maxima read back once
+        double *acc = nullptr, *U = nullptr;
+        const int nqi = p->iv.nblk * M;
+        CJT_CUDA_TRY(cudaMallocAsync((void **)&acc, 2 * sizeof(double), st));
+        CJT_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+        if (fwd && p->fw.nblk > 0)
+            k_err_fwd<<<blocks_for(p->Gf + 1, 256), 256, 0, st>>>(N, p->Gf, M, p->fw.nblk * M, p->fw.d_rowk,
+                                                                   p->fw.d_box, p->d_Cnm, p->fw.d_scale, p->fw.d_u,
+                                                                   p->fw.d_v, acc);
+        if (inv && nqi > 0) {
+            CJT_CUDA_TRY(cudaMallocAsync((void **)&U, nqi * sizeof(double), st));
+            k_err_inv_U<<<nqi, 256, 0, st>>>(2 * p->Gi, M, p->iv.d_box, p->d_w, p->iv.d_u, p->iv.d_v, U);
+            k_err_inv<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, M, p->iv.nblk, nqi, p->iv.d_box, p->d_Cnm,
+                                                               p->iv.d_scale, U, p->d_s, acc + 1);
+        }
+        CJT_CUDA_TRY(cudaGetLastError());
+        double h[2] = {0.0, 0.0};
+        CJT_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CJT_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFreeAsync(acc, st);
+        if (U) cudaFreeAsync(U, st);
+        p->err_mixed_fwd = fwd ? 2.0 * mixed_eps_fft(p->Lf) * h[0] : 0.0;
+        p->err_mixed_inv = inv ? mixed_eps_fft(p->Li) * h[1] : 0.0;
+    }
     CJT_CUDA_TRY(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
     CJT_CUDA_TRY(cudaStreamSynchronize(st));
     return CJT_OK;

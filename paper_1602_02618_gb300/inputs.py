@@ -28,11 +28,26 @@ def rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(int(seed)))
 
 
+def _power(x: np.ndarray, p: float) -> np.ndarray:
+    """x^p, bit-identical on every platform for the exponents the workloads use: integer and
+    half-integer p through products and the correctly rounded square root (a libm pow may
+    round differently on different machines), other p through numpy's power."""
+    if p == 0:
+        return np.ones_like(x)
+    k = int(np.floor(p))
+    if p == k or p - k == 0.5:
+        out = np.ones_like(x)
+        for _ in range(k):
+            out = out * x
+        return out * np.sqrt(x) if p != k else out
+    return x ** p
+
+
 def decaying_coefficients(N: int, p: float, seed: int = BASE_SEED) -> np.ndarray:
     """c_n = g_n/(n+1)^p for n = 0..N with g_n i.i.d. standard normal (float64)."""
     g = rng(seed).standard_normal(N + 1)
     n = np.arange(N + 1, dtype=np.float64)
-    return g / (n + 1.0) ** p
+    return g / _power(n + 1.0, p)
 
 
 def uniform_coefficients(N: int, seed: int = BASE_SEED) -> np.ndarray:
@@ -106,4 +121,4 @@ def continuous_coefficients(N: int, seed: int = BASE_SEED) -> np.ndarray:
     """c_n ~ U(-1,1) / (n+1)^2: coefficients of a continuous function (the paper's Fig. 3,
     right; (n+1) so that c_0 is finite)."""
     n = np.arange(N + 1, dtype=np.float64)
-    return rng(seed).uniform(-1.0, 1.0, N + 1) / (n + 1.0) ** 2
+    return rng(seed).uniform(-1.0, 1.0, N + 1) / _power(n + 1.0, 2)
