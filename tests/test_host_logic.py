@@ -31,7 +31,12 @@ def test_coefficient_recipes():
     N = 4096
     g = inputs.rng(inputs.BASE_SEED).standard_normal(N + 1)
     c = inputs.decaying_coefficients(N, 1.5, inputs.BASE_SEED)
-    assert np.array_equal(c, g / (np.arange(N + 1) + 1.0) ** 1.5)
+    n1 = np.arange(N + 1) + 1.0
+    # (n+1)^1.5 as a product with the correctly rounded square root: the same bits on every
+    # platform, and within an ulp or two of the power
+    assert np.array_equal(c, g / (n1 * np.sqrt(n1)))
+    assert np.max(np.abs(c - g / n1 ** 1.5) / np.abs(c)) < 1e-15
+    assert np.array_equal(inputs.decaying_coefficients(N, 1.0, 7), inputs.rng(7).standard_normal(N + 1) / n1)
     u = inputs.irregular_coefficients(N)
     assert u.min() >= 0.0 and u.max() < 1.0
     v = inputs.continuous_coefficients(N)
