@@ -140,15 +140,16 @@ def oracle_seconds_estimate(N, d):
 
 
 def batched_sample(items, budget_s=1.2):
-    """The batch's first items, in order, up to about `budget_s` of oracle time on 8 cores."""
+    """The batch's transforms, in order, that fit about `budget_s` of oracle time on 8 cores
+    (each item's estimate within what is left of the budget; the large items are skipped)."""
     out, t = [], 0.0
     for N, a, b, d, c in items:
         e = oracle_seconds_estimate(N, d)
-        if out and t + e > budget_s:
+        if t + e > budget_s:
             continue
         out.append((N, a, b, d, c))
         t += e
-        if t >= budget_s:
+        if budget_s - t < 0.01:
             break
     return out
 
@@ -179,8 +180,10 @@ def cpu_sample(config):
         return single_sample_items(), ("forward and inverse at N = 2^12 and 2^14 and forward at 2^16 of the "
                                       "single-transform workload, in full")
     items = batch_sample_items()
-    return items, ("the first %d transforms (N <= %d, %d coefficients) of the 4096-transform batch, in full"
-                   % (len(items), max(it[0] for it in items), sum(it[0] + 1 for it in items)))
+    return items, ("%d transforms (N from %d to %d, %d coefficients) of the 4096-transform batch, the first in "
+                   "order that fit the sample's time, in full"
+                   % (len(items), min(it[0] for it in items), max(it[0] for it in items),
+                      sum(it[0] + 1 for it in items)))
 
 
 def batch_sample_items():
@@ -318,10 +321,19 @@ def run_batched(ctx, big=False, steps=None):
         items = inputs.batch_workload(args.batch_count, seed=seed)
         precision = precision_code(cjt, args.precision)
     t0 = time.perf_counter()
-    plans = []
-    for N, a, b, d, c in items:
-        plans.append(cjt.Plan(N, a, b, precision=precision, directions=cjt.CJT_FWD if d == 1 else cjt.CJT_INV,
-                              shared_workspace=True, **batch_plan_options(N, big, precision, cjt)))
+    tune = None
+    if big or args.batch_fixed:
+        plans = []
+        for N, a, b, d, c in items:
+            plans.append(cjt.Plan(N, a, b, precision=precision, directions=cjt.CJT_FWD if d == 1 else cjt.CJT_INV,
+                                  shared_workspace=True, **batch_plan_options(N, big, precision, cjt)))
+    else:
+        from paper_1602_02618_gb300 import autotune
+        # the plans may take the budget, within the device memory free now less 30 GB for the
+        # arenas (about 9 GB), the I/O buffers and the runtime
+        free, _ = torch.cuda.mem_get_info(dev)
+        budget = min(args.batch_plan_gb * 1e9, free - 30e9)
+        plans, _, tune = autotune.build_batch_plans(items, precision, plan_budget_bytes=budget)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
     dirs = [1 if d == 1 else 2 for _, _, _, d, _ in items]
@@ -452,8 +464,12 @@ def run_batched(ctx, big=False, steps=None):
                      "CUDA graph per step" % ("double-float" if precision == cjt.CJT_DFLOAT else "FP32"))
         if big else BATCH_DESC % PREC_NAMES[args.precision],
         "coefficients_per_step": coeffs,
-        "plan_options": "M=16, seg_len=1024" if big else
-        "M=13, seg_len=256, ratio=0.1, power-of-two grid, rec_store for N <= 16384",
+        "plan_options": "M=16, seg_len=1024" if big else (
+            "M=13, seg_len=256, ratio=0.1, power-of-two grid, rec_store for N <= 16384" if args.batch_fixed else
+            {"autotuner": "autotune.build_batch_plans: per size class (M, ratio) by the modelled FP64-pipe work "
+                          "of candidate plans; stored recurrence values in increasing N while the plans fit %.0f GB"
+                          % ((tune["plan_budget_bytes"] if tune else 0) / 1e9), "classes": tune["classes"] if tune else None,
+             "stored_items": tune["stored_items"] if tune else None}),
         "l2": "inputs (%.0f MB) exceed L2; flushed between steps" % (coeffs * 8 / 1e6),
         "error": err, "roofline": roof,
         "e2e": {"value": multirank.job_rate(coeffs_all * ksteps, e2e_s), "unit": "coeffs/s",
@@ -776,6 +792,10 @@ def main():
     ap.add_argument("--planners", type=int, default=4)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--lanes", type=int, default=16)
+    ap.add_argument("--batch-plan-gb", type=float, default=230.0,
+                    help="device memory the batched workload's plans may take (autotuned options)")
+    ap.add_argument("--batch-fixed", action="store_true",
+                    help="batched workload with fixed options (M=13, ratio=0.1, stored values for N <= 16384)")
     ap.add_argument("--params", default="",
                     help="fixed (alpha, beta) for every transform of the single workload, e.g. 0,0 (Legendre)")
     ap.add_argument("--expansion", choices=["auto", "hahn", "ultra"], default="auto",

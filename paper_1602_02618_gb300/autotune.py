@@ -127,3 +127,117 @@ def best_options(N: int, alpha: float, beta: float, precision: int = 0, directio
                       "candidates": [{"options": o, "ms": t} for t, o in results]}
         _save(cache)
     return dict(best)
+
+
+# ---------------------------------------------------------------------------
+# Batches: options per size class under a device-memory budget
+# ---------------------------------------------------------------------------
+# Measured fractions of the FP64 pipe peak of the grouped stage kernels (grouped batch,
+# serialised launches on GB300): recurrence at execution, stored values, transforms.
+ETA_REC, ETA_STORED, ETA_FFT = 0.75, 0.85, 0.82
+BATCH_CANDIDATES = [{"M": M, "ratio": r} for M in (7, 10, 13, 16) for r in (0.0, 0.1, 0.05)]
+
+
+def _work_model(info, direction):
+    """Modelled FP64-pipe seconds-at-peak factors of one execution: (recurrence steps,
+    transform flop / ETA_FFT), from a plan's summary."""
+    import math
+    f = direction == 1
+    L = info["fft_len_fwd"] if f else info["fft_len_inv"]
+    nfft = info["nfft_fwd"] if f else info["nfft_inv"]
+    steps = info["rec_steps_fwd"] if f else info["rec_steps_inv"]
+    lg = max(math.log2(max(L, 2)), 1.0)
+    return float(steps), nfft * 5.0 * L * lg / ETA_FFT
+
+
+def batch_class_options(items, precision: int = 0, samples: int = 2, seed: int = 0):
+    """Per size class (floor log2 N) of a batch: the fastest candidate (M, block ratio) with
+    the recurrence at execution and with stored values, by the modelled FP64-pipe work of
+    `samples` planned items of the class (8 flop per recurrence step at ETA_REC, 2 flop per
+    stored value at ETA_STORED, the transforms at ETA_FFT), and the measured plan-table
+    bytes per coefficient of the first.  Returns {class: dict}."""
+    import math
+    import numpy as np
+    from . import cjt
+    classes = {}
+    for t, it in enumerate(items):
+        classes.setdefault(int(math.floor(math.log2(max(it[0], 1)))), []).append(t)
+    rng = np.random.default_rng(seed)
+    out = {}
+    for k, members in sorted(classes.items()):
+        pick = [members[i] for i in rng.choice(len(members), min(samples, len(members)), replace=False)]
+        res = []
+        for opts in BATCH_CANDIDATES:
+            t_rec = t_sto = tab = n1 = 0.0
+            ok = True
+            for t in pick:
+                N, a, b, d = items[t][:4]
+                try:
+                    p = cjt.Plan(N, a, b, precision=precision, directions=1 if d == 1 else 2,
+                                 shared_workspace=True, **opts)
+                except cjt.CJTError:
+                    ok = False
+                    break
+                inf = p.info()
+                p.close()
+                steps, fft = _work_model(inf, d)
+                t_rec += 8.0 * steps / ETA_REC + fft
+                t_sto += 2.0 * steps / ETA_STORED + fft
+                tab += inf["device_bytes"]
+                n1 += N + 1.0
+            if ok:
+                res.append((opts, t_rec / n1, t_sto / n1, tab / n1))
+        if res:
+            plain = min(res, key=lambda r: r[1])
+            store = min(res, key=lambda r: r[2])
+            out[k] = {"plain": dict(plain[0]), "store": dict(store[0]), "cost_plain": plain[1],
+                      "cost_store": store[2], "store_better": store[2] < plain[1],
+                      "table_bytes_per_coeff": max(plain[3], store[3]), "members": members}
+    return out
+
+
+def build_batch_plans(items, precision: int = 0, plan_budget_bytes: float = 200e9, samples: int = 2,
+                      seed: int = 0):
+    """Plans for every item of a batch (shared workspace, for the grouped executor), with the
+    options of batch_class_options.  Items are planned in increasing N.  An item of a class
+    whose stored-values option models faster gets stored recurrence values while the plans
+    built so far, its own stored values and the modelled tables of the items still to come
+    (1.25 x the sampled bytes per coefficient) fit plan_budget_bytes; every other item is
+    planned with the recurrence at execution.  The time saved per stored byte is the same for
+    every item (6 flop per 8 bytes), so the smaller items, which need fewer bytes per
+    coefficient, come first.  Returns (plans in item order, options, report)."""
+    import math
+    from . import cjt
+    cls = batch_class_options(items, precision, samples, seed)
+    order = sorted(range(len(items)), key=lambda t: items[t][0])
+    klass = [int(math.floor(math.log2(max(it[0], 1)))) for it in items]
+    remaining = sum(1.25 * cls[klass[t]]["table_bytes_per_coeff"] * (items[t][0] + 1.0) for t in order
+                    if klass[t] in cls)
+    used = 0.0
+    plans, opts = [None] * len(items), [None] * len(items)
+    stored = 0
+    for t in order:
+        N, a, b, d = items[t][:4]
+        c = cls.get(klass[t])
+        est = 1.25 * c["table_bytes_per_coeff"] * (N + 1.0) if c else 0.0
+        remaining -= est
+        o = None
+        p = None
+        if c and c["store_better"]:
+            o = dict(c["store"], seg_len=256 if N <= 16384 else 1024, rec_store=1)
+            p = cjt.Plan(N, a, b, precision=precision, directions=1 if d == 1 else 2, shared_workspace=True, **o)
+            if used + p.info()["device_bytes"] + remaining > plan_budget_bytes:
+                p.close()
+                p = None
+            else:
+                stored += 1
+        if p is None:
+            o = dict(c["plain"] if c else {}, seg_len=256 if N <= 16384 else 1024, rec_store=0)
+            p = cjt.Plan(N, a, b, precision=precision, directions=1 if d == 1 else 2, shared_workspace=True, **o)
+        used += p.info()["device_bytes"]
+        plans[t], opts[t] = p, o
+    report = {"classes": {str(k): {"plain": v["plain"], "store": v["store"], "store_better": v["store_better"],
+                                   "stored_items": sum(1 for t in v["members"] if opts[t]["rec_store"]),
+                                   "items": len(v["members"])} for k, v in cls.items()},
+              "plan_bytes": used, "plan_budget_bytes": plan_budget_bytes, "stored_items": stored}
+    return plans, opts, report

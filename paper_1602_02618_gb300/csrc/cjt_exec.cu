@@ -79,19 +79,23 @@ __global__ void __launch_bounds__(32 * SW) k_rec_inv_stored(const RecItem *__res
 }
 
 template <typename V, typename R>
-__global__ void k_asy_pack_fwd_s(int64_t N, int64_t L, int nq, const R *__restrict__ Cs, const double *__restrict__ c,
-                                 V *__restrict__ buf) {
+__global__ void k_asy_pack_fwd_s(int64_t N, int64_t L, int M, int nq, const int *__restrict__ box3,
+                                 const double *__restrict__ Cnm, const double *__restrict__ scale,
+                                 const double *__restrict__ c, V *__restrict__ buf) {
     const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (n >= L) return;
-    cjt_kern::asy_pack_fwd_elem<V, R>(n, blockIdx.y, N, L, nq, Cs, c, buf);
+    const cjt_kern::PairScale ps = cjt_kern::pair_scale(blockIdx.y, M, nq, scale);
+    cjt_kern::asy_pack_fwd_elem<V, R>(n, blockIdx.y, ps, N, L, box3, Cnm, c, buf);
 }
 
 template <typename V, typename R>
-__global__ void k_asy_pack_inv_s(int64_t Ng, int64_t L, int nq, const R *__restrict__ Us, const R *__restrict__ Vs,
-                                 const double *__restrict__ g, V *__restrict__ buf) {
+__global__ void k_asy_pack_inv_s(int64_t Ng, int64_t L, int M, int nq, const int *__restrict__ box3,
+                                 const double *__restrict__ u, const double *__restrict__ v,
+                                 const double *__restrict__ scale, const double *__restrict__ g, V *__restrict__ buf) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= L) return;
-    cjt_kern::asy_pack_inv_elem<V, R>(idx, blockIdx.y, Ng, L, nq, Us, Vs, g, buf);
+    const cjt_kern::PairScale ps = cjt_kern::pair_scale(blockIdx.y, M, nq, scale);
+    cjt_kern::asy_pack_inv_elem<V, R>(idx, blockIdx.y, ps, Ng, L, box3, u, v, g, buf);
 }
 
 // ---------------------------------------------------------------------------
@@ -456,9 +460,10 @@ int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         if (dfm)
             k_asy_pack_fwd_df<<<gp, 256, 0, sa>>>(N, L, nq, (const dfs *)gw.d_Cs, cdf, (dfc *)ws.fft_f);
         else if (fp32)
-            k_asy_pack_fwd_s<float2, float><<<gp, 256, 0, sa>>>(N, L, nq, (const float *)gw.d_Cs, in, (float2 *)ws.fft_f);
+            k_asy_pack_fwd_s<float2, float><<<gp, 256, 0, sa>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in,
+                                                               (float2 *)ws.fft_f);
         else
-            k_asy_pack_fwd_s<double2, double><<<gp, 256, 0, sa>>>(N, L, nq, (const double *)gw.d_Cs, in,
+            k_asy_pack_fwd_s<double2, double><<<gp, 256, 0, sa>>>(N, L, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, in,
                                                                  (double2 *)ws.fft_f);
         CJT_CUDA_TRY(cudaGetLastError());
     }
@@ -574,11 +579,11 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
             k_asy_pack_inv_df<<<gp, 256, 0, sa>>>(Ng, L, nq, (const dfs *)gw.d_Us, (const dfs *)gw.d_Vs, gdf,
                                                   (dfc *)ws.fft_i);
         else if (fp32)
-            k_asy_pack_inv_s<float2, float><<<gp, 256, 0, sa>>>(Ng, L, nq, (const float *)gw.d_Us,
-                                                                (const float *)gw.d_Vs, ws.g, (float2 *)ws.fft_i);
+            k_asy_pack_inv_s<float2, float><<<gp, 256, 0, sa>>>(Ng, L, M, nq, gw.d_box, gw.d_u, gw.d_v, gw.d_scale,
+                                                                ws.g, (float2 *)ws.fft_i);
         else
-            k_asy_pack_inv_s<double2, double><<<gp, 256, 0, sa>>>(Ng, L, nq, (const double *)gw.d_Us,
-                                                                  (const double *)gw.d_Vs, ws.g, (double2 *)ws.fft_i);
+            k_asy_pack_inv_s<double2, double><<<gp, 256, 0, sa>>>(Ng, L, M, nq, gw.d_box, gw.d_u, gw.d_v,
+                                                                  gw.d_scale, ws.g, (double2 *)ws.fft_i);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     if (nq > 0) {

@@ -57,7 +57,6 @@ struct __align__(16) GDesc {
     const int64_t *row_base;
     const int *row_nseg;
     const double *scale, *u, *v, *Cnm, *w, *s_n;
-    const void *Cs, *Us, *Vs;
     const int *box;
     const int64_t *seg_ptr, *seg_out;
     const int *seg_b;
@@ -83,49 +82,61 @@ constexpr int GE_CHUNK = 8 * GE_THREADS;   // elements per CTA of the elementwis
 enum { OP_PACK_FWD, OP_PACK_INV, OP_COMBINE_FWD, OP_DCT_FINISH, OP_FRONT_PACK, OP_INV_G, OP_COMBINE_INV, OP_NELEM };
 
 template <int OP> struct Elem;
+// packs: the pair's scales are formed once per thread and pair (PairCache)
+struct PairCache {
+    int p = -1;
+    cjt_kern::PairScale ps;
+    __device__ const cjt_kern::PairScale &of(int pp, const GDesc &d) {
+        if (pp != p) {
+            p = pp;
+            ps = cjt_kern::pair_scale(pp, d.M, d.nq, d.scale);
+        }
+        return ps;
+    }
+};
 template <> struct Elem<OP_FRONT_PACK> {
     static __host__ __device__ int64_t size(const GDesc &d) { return d.L; }   // 4G
-    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t k) {
+    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t k, PairCache &) {
         cjt_kern::inv_front_pack_elem(k, d.N, d.in, d.dct);
     }
 };
 template <> struct Elem<OP_INV_G> {
     static __host__ __device__ int64_t size(const GDesc &d) { return d.Ng + 1; }
-    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t i) {
+    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t i, PairCache &) {
         cjt_kern::inv_g_elem(i, d.dct, d.w, d.g);
     }
 };
 template <> struct Elem<OP_PACK_FWD> {
     static __host__ __device__ int64_t size(const GDesc &d) { return (int64_t)d.npair * d.L; }
-    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t idx) {
+    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t idx, PairCache &pc) {
         const int p = (int)(idx >> d.logL);
-        cjt_kern::asy_pack_fwd_elem<V, R>(idx & (d.L - 1), p, d.N, d.L, d.nq, (const R *)d.Cs, d.in, (V *)d.fft);
+        cjt_kern::asy_pack_fwd_elem<V, R>(idx & (d.L - 1), p, pc.of(p, d), d.N, d.L, d.box, d.Cnm, d.in, (V *)d.fft);
     }
 };
 template <> struct Elem<OP_PACK_INV> {
     static __host__ __device__ int64_t size(const GDesc &d) { return (int64_t)d.npair * d.L; }
-    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t idx) {
+    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t idx, PairCache &pc) {
         const int p = (int)(idx >> d.logL);
-        cjt_kern::asy_pack_inv_elem<V, R>(idx & (d.L - 1), p, d.Ng, d.L, d.nq, (const R *)d.Us, (const R *)d.Vs,
-                                          d.g, (V *)d.fft);
+        cjt_kern::asy_pack_inv_elem<V, R>(idx & (d.L - 1), p, pc.of(p, d), d.Ng, d.L, d.box, d.u, d.v, d.g,
+                                          (V *)d.fft);
     }
 };
 template <> struct Elem<OP_COMBINE_FWD> {
     static __host__ __device__ int64_t size(const GDesc &d) { return d.G + 1; }
-    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t i) {
+    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t i, PairCache &) {
         cjt_kern::combine_fwd_elem<V>(i, d.G, d.L, d.M, d.rowk, d.scale, d.u, d.v, (const V *)d.fft, d.row_base,
                                       d.row_nseg, d.part, d.dct);
     }
 };
 template <> struct Elem<OP_DCT_FINISH> {
     static __host__ __device__ int64_t size(const GDesc &d) { return d.N + 1; }
-    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t k) {
+    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t k, PairCache &) {
         cjt_kern::dct_finish_elem(k, d.G, d.dct, d.out);
     }
 };
 template <> struct Elem<OP_COMBINE_INV> {
     static __host__ __device__ int64_t size(const GDesc &d) { return d.N + 1; }
-    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t n) {
+    template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t n, PairCache &) {
         cjt_kern::combine_inv_elem<V>(n, d.N, d.L, d.M, d.nblk, d.box, d.scale, d.Cnm, (const V *)d.fft, d.y, d.s_n,
                                       nullptr, 0, d.out);
     }
@@ -144,7 +155,8 @@ __global__ void __launch_bounds__(GE_THREADS) k_g_elem(const GDesc *__restrict__
     __syncthreads();
     const int64_t n = Elem<OP>::size(sd);
     const int64_t i0 = (int64_t)e.blk * GE_CHUNK, i1 = min(n, i0 + GE_CHUNK);
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += GE_THREADS) Elem<OP>::template apply<V, R>(sd, i);
+    PairCache pc;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += GE_THREADS) Elem<OP>::template apply<V, R>(sd, i, pc);
 }
 
 // ---------------------------------------------------------------------------
@@ -651,9 +663,6 @@ GDesc make_desc(const cjt_plan_s *p, int dir, const double *in, double *out) {
     d.Cnm = p->d_Cnm;
     d.w = p->d_w;
     d.s_n = p->d_s;
-    d.Cs = gw.d_Cs;
-    d.Us = gw.d_Us;
-    d.Vs = gw.d_Vs;
     d.box = gw.d_box;
     d.seg_ptr = gw.d_seg_ptr;
     d.seg_out = gw.d_seg_out;

@@ -219,40 +219,74 @@ __device__ __forceinline__ void rec_inv_stored_cta(const RecItem &it, int64_t Ng
 
 // ---------------------------------------------------------------------------
 // ASY packs: pair p holds items q = 2p, 2p+1 (q = k*M + m) as the real and imaginary
-// parts of one complex transform input, from the pre-scaled tables; arithmetic in the
-// transform precision R.  Element n of pair p's input of length L.
+// parts of one complex transform input; arithmetic in the transform precision R.  Each
+// item is scaled by its exact power of two s_q = scale[2q] (so that the two items of a
+// transform have comparable magnitudes); the scaled factors are formed here from the
+// plan's C_{n,m} (forward) or u_m, v_m (inverse) tables, rounded to R, as
+//   forward  Cs_q[n] = s_q C_{n,m}          for n >= j_k (0 below)
+//   inverse  Us_q[i] = s_q u_m(theta_i)/2,  Vs_q[i] = s_q v_m(theta_i)/2  on box k's rows
 // ---------------------------------------------------------------------------
+// The two items of pair p: their (block, term) indices and scales, formed once per pair.
+struct PairScale {
+    int m0, m1;          // terms of items 2p and 2p+1 (m1 < 0: no second item)
+    int k0, k1;          // their blocks
+    double s0, s1;       // scale[2q] of each
+};
+__device__ __forceinline__ PairScale pair_scale(int p, int M, int nq, const double *__restrict__ scale) {
+    PairScale ps;
+    const int q = 2 * p;
+    ps.k0 = q / M;
+    ps.m0 = q - ps.k0 * M;
+    ps.s0 = scale[2 * q];
+    if (q + 1 < nq) {
+        ps.k1 = (q + 1) / M;
+        ps.m1 = q + 1 - ps.k1 * M;
+        ps.s1 = scale[2 * (q + 1)];
+    } else {
+        ps.k1 = 0;
+        ps.m1 = -1;
+        ps.s1 = 0.0;
+    }
+    return ps;
+}
+
 template <typename V, typename R>
-__device__ __forceinline__ void asy_pack_fwd_elem(int64_t n, int p, int64_t N, int64_t L, int nq,
-                                                  const R *__restrict__ Cs, const double *__restrict__ c,
-                                                  V *__restrict__ buf) {
+__device__ __forceinline__ void asy_pack_fwd_elem(int64_t n, int p, const PairScale &ps, int64_t N, int64_t L,
+                                                  const int *__restrict__ box3, const double *__restrict__ Cnm,
+                                                  const double *__restrict__ c, V *__restrict__ buf) {
     V o;
     o.x = 0;
     o.y = 0;
     if (n <= N) {
         const R cn = (R)c[n];
-        const int q = 2 * p;
-        o.x = Cs[(int64_t)q * (N + 1) + n] * cn;
-        if (q + 1 < nq) o.y = Cs[(int64_t)(q + 1) * (N + 1) + n] * cn;
+        o.x = (R)(n >= box3[3 * ps.k0] ? Cnm[ps.m0 * (N + 1) + n] * ps.s0 : 0.0) * cn;
+        if (ps.m1 >= 0) o.y = (R)(n >= box3[3 * ps.k1] ? Cnm[ps.m1 * (N + 1) + n] * ps.s1 : 0.0) * cn;
     }
     buf[(int64_t)p * L + n] = o;
 }
 
 template <typename V, typename R>
-__device__ __forceinline__ void asy_pack_inv_elem(int64_t idx, int p, int64_t Ng, int64_t L, int nq,
-                                                  const R *__restrict__ Us, const R *__restrict__ Vs,
-                                                  const double *__restrict__ g, V *__restrict__ buf) {
+__device__ __forceinline__ void asy_pack_inv_elem(int64_t idx, int p, const PairScale &ps, int64_t Ng, int64_t L,
+                                                  const int *__restrict__ box3, const double *__restrict__ u,
+                                                  const double *__restrict__ v, const double *__restrict__ g,
+                                                  V *__restrict__ buf) {
     // H(idx) = (z(idx) + conj z(L - idx)) / 2: the box rows lie in [1, Ng - 1]
     const bool lo = idx <= Ng;
     const int64_t i = lo ? idx : L - idx;
     const R gi = (R)g[i];
     const R sgn = lo ? (R)1 : (R)-1;
-    const int q = 2 * p;
-    const R h0r = Us[(int64_t)q * (Ng + 1) + i] * gi, h0i = sgn * Vs[(int64_t)q * (Ng + 1) + i] * gi;
+    const bool in0 = i >= box3[3 * ps.k0 + 1] && i <= box3[3 * ps.k0 + 2];
+    const double sc0 = 0.5 * ps.s0;
+    const R u0 = (R)(in0 ? sc0 * u[ps.m0 * (Ng + 1) + i] : 0.0), v0 = (R)(in0 ? sc0 * v[ps.m0 * (Ng + 1) + i] : 0.0);
+    const R h0r = u0 * gi, h0i = sgn * v0 * gi;
     R h1r = 0, h1i = 0;
-    if (q + 1 < nq) {
-        h1r = Us[(int64_t)(q + 1) * (Ng + 1) + i] * gi;
-        h1i = sgn * Vs[(int64_t)(q + 1) * (Ng + 1) + i] * gi;
+    if (ps.m1 >= 0) {
+        const bool in1 = i >= box3[3 * ps.k1 + 1] && i <= box3[3 * ps.k1 + 2];
+        const double sc1 = 0.5 * ps.s1;
+        const R u1 = (R)(in1 ? sc1 * u[ps.m1 * (Ng + 1) + i] : 0.0);
+        const R v1 = (R)(in1 ? sc1 * v[ps.m1 * (Ng + 1) + i] : 0.0);
+        h1r = u1 * gi;
+        h1i = sgn * v1 * gi;
     }
     V o;
     o.x = h0r - h1i;

@@ -767,19 +767,13 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
         TRY(dalloc(p, &gw.d_scale, (int64_t)sc.size()));
         CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_scale, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, st));
         const int nq = gw.nblk * M;
-        const bool f32 = p->opts.precision == CJT_MIXED, df = p->opts.precision == CJT_DFLOAT;
+        const bool df = p->opts.precision == CJT_DFLOAT;
         if (!inverse) {
             dim3 g(blocks_for(p->N + 1, 256), nq);
             if (df) {
                 TRY(dalloc(p, (double **)&gw.d_Cs, (int64_t)nq * (p->N + 1)));   // dfs: 8 bytes
                 k_scaled_C<dfs><<<g, 256, 0, st>>>(p->N, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, (dfs *)gw.d_Cs);
-            } else if (f32) {
-                TRY(dalloc(p, (float **)&gw.d_Cs, (int64_t)nq * (p->N + 1)));
-                k_scaled_C<float><<<g, 256, 0, st>>>(p->N, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, (float *)gw.d_Cs);
-            } else {
-                TRY(dalloc(p, (double **)&gw.d_Cs, (int64_t)nq * (p->N + 1)));
-                k_scaled_C<double><<<g, 256, 0, st>>>(p->N, M, nq, gw.d_box, p->d_Cnm, gw.d_scale, (double *)gw.d_Cs);
-            }
+            }   // FP64 and mixed forms: the packs scale C_{n,m} as they read it
         } else {
             dim3 g(blocks_for(Ng + 1, 256), nq);
             if (df) {
@@ -787,17 +781,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
                 TRY(dalloc(p, (double **)&gw.d_Vs, (int64_t)nq * (Ng + 1)));
                 k_scaled_uv<dfs><<<g, 256, 0, st>>>(Ng, M, nq, gw.d_box, gw.d_u, gw.d_v, gw.d_scale,
                                                     (dfs *)gw.d_Us, (dfs *)gw.d_Vs);
-            } else if (f32) {
-                TRY(dalloc(p, (float **)&gw.d_Us, (int64_t)nq * (Ng + 1)));
-                TRY(dalloc(p, (float **)&gw.d_Vs, (int64_t)nq * (Ng + 1)));
-                k_scaled_uv<float><<<g, 256, 0, st>>>(Ng, M, nq, gw.d_box, gw.d_u, gw.d_v, gw.d_scale,
-                                                      (float *)gw.d_Us, (float *)gw.d_Vs);
-            } else {
-                TRY(dalloc(p, (double **)&gw.d_Us, (int64_t)nq * (Ng + 1)));
-                TRY(dalloc(p, (double **)&gw.d_Vs, (int64_t)nq * (Ng + 1)));
-                k_scaled_uv<double><<<g, 256, 0, st>>>(Ng, M, nq, gw.d_box, gw.d_u, gw.d_v, gw.d_scale,
-                                                       (double *)gw.d_Us, (double *)gw.d_Vs);
-            }
+            }   // FP64 and mixed forms: the packs scale u_m, v_m as they read them
         }
         CJT_CUDA_TRY(cudaGetLastError());
         CJT_CUDA_TRY(cudaStreamSynchronize(st));
