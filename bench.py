@@ -789,7 +789,7 @@ def main():
     ap.add_argument("--config", choices=["all", "single", "batched", "mixed64", "serving"], default="all")
     ap.add_argument("--rates", default="50,200,800,3200")
     ap.add_argument("--requests", type=int, default=200)
-    ap.add_argument("--planners", type=int, default=4)
+    ap.add_argument("--planners", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--lanes", type=int, default=16)
     ap.add_argument("--batch-plan-gb", type=float, default=230.0,

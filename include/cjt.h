@@ -241,6 +241,19 @@ int cjt_get_info(cjt_plan_t plan, cjt_plan_info *info);
 int cjt_error_bound(cjt_plan_t plan, int direction, double *bound);
 
 /*
+ * The plan's partition (Sec. 2.2) on the grid of `direction` (x_i = cos(pi i / Ng), Ng the
+ * forward grid or twice the inverse one, grid_fwd / grid_inv of cjt_plan_info): block k
+ * (k = 1..nblk, outermost first) is the box of degrees [j_k, j_{k-1}) (j_0 = N+1) and rows
+ * [i_k^1, i_k^2], where the asymptotic formula's remainder bound 2 C_{j_k,M} g_M(theta_i) is
+ * below eps on every row; boxes[3(k-1) + 0..2] = j_k, i_k^1, i_k^2 (int64, cap blocks room).
+ * With alpha = beta and stored recurrence values the boxes are the ones after the parity
+ * fold (symmetric about the middle row).  *nblk receives the number of blocks.
+ * Errors: CJT_EINVAL (null pointer, cap < 0, bad direction, or more than cap blocks, with
+ * *nblk set), CJT_EDIRECTION.
+ */
+int cjt_get_partition(cjt_plan_t plan, int direction, int cap, int64_t *boxes, int *nblk);
+
+/*
  * Forward transform (Eq. "CJT"): c_cheb_dev[k], k = 0..N, from c_jac_dev[n].
  * Both are device arrays of N+1 doubles; they may alias.
  * Errors: CJT_EINVAL (null), CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA.

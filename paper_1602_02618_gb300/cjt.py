@@ -69,7 +69,7 @@ EXPORTED = ["cjt_plan_opts_default", "cjt_plan", "cjt_destroy", "cjt_get_info", 
             "cjt_forward_ws", "cjt_inverse_ws", "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info",
             "cjt_batch_destroy", "cjt_jacobi_to_jacobi", "cjt_asy_coefficient", "cjt_asy_eval",
             "cjt_rec_coefficients", "cjt_error_bound", "cjt_batch_launch_host", "cjt_batch_set_profiling",
-            "cjt_batch_get_profile"]
+            "cjt_batch_get_profile", "cjt_get_partition"]
 
 NOALLOC_MAX_N = 65536
 
@@ -132,6 +132,7 @@ def load(path: str = LIB_PATH):
         lib.cjt_batch_set_profiling.argtypes = [vp, i]
         lib.cjt_batch_get_profile.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64), i]
         lib.cjt_error_bound.argtypes = [vp, i, ctypes.POINTER(d)]
+        lib.cjt_get_partition.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
         lib.cjt_strerror.argtypes = [i]
         lib.cjt_strerror.restype = ctypes.c_char_p
         lib.cjt_last_cuda_error.restype = ctypes.c_char_p
@@ -141,7 +142,8 @@ def load(path: str = LIB_PATH):
                      "cjt_microbench_fma", "cjt_cheb_coeffs_noalloc", "cjt_forward_ws", "cjt_inverse_ws",
                      "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info", "cjt_jacobi_to_jacobi",
                      "cjt_asy_coefficient", "cjt_asy_eval", "cjt_rec_coefficients", "cjt_error_bound",
-                     "cjt_batch_launch_host", "cjt_batch_set_profiling", "cjt_batch_get_profile"):
+                     "cjt_batch_launch_host", "cjt_batch_set_profiling", "cjt_batch_get_profile",
+                     "cjt_get_partition"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -167,6 +169,11 @@ def _dev_ptr(t, n):
         raise TypeError("expected a contiguous float64 CUDA tensor")
     if t.numel() < n:
         raise ValueError("tensor has %d elements, need %d" % (t.numel(), n))
+    # the library launches on the current device, where its plans and arrays live
+    cur = torch.cuda.current_device()
+    if t.device.index != cur:
+        raise ValueError("tensor on cuda:%d while cuda:%d is current; call under torch.cuda.device(%d)"
+                         % (t.device.index, cur, t.device.index))
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -299,6 +306,16 @@ def cjt_inverse_ws(plan: Plan, c_cheb, c_jac, workspace, stream=None):
                                  ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
                                  _stream_handle(stream)), "cjt_inverse_ws")
     return c_jac
+
+
+def partition(plan: Plan, direction: int):
+    """The plan's blocks on the grid of `direction`: a list of (j_k, i_k^1, i_k^2), outermost
+    first (Sec. 2.2)."""
+    cap = 64
+    boxes = (ctypes.c_int64 * (3 * cap))()
+    n = ctypes.c_int()
+    _check(load().cjt_get_partition(plan.handle, int(direction), cap, boxes, ctypes.byref(n)), "cjt_get_partition")
+    return [(boxes[3 * k], boxes[3 * k + 1], boxes[3 * k + 2]) for k in range(n.value)]
 
 
 def error_bound(plan: Plan, direction: int) -> float:

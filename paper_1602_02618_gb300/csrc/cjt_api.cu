@@ -343,6 +343,21 @@ int cjt_asy_eval(double alpha, double beta, int expansion, int M, int64_t n, int
     return CJT_OK;
 }
 
+int cjt_get_partition(cjt_plan_t p, int direction, int cap, int64_t *boxes, int *nblk) {
+    if (!p || !nblk || cap < 0 || (cap > 0 && !boxes)) return CJT_EINVAL;
+    if (direction != CJT_FWD && direction != CJT_INV) return CJT_EINVAL;
+    if (!(p->opts.directions & direction)) return CJT_EDIRECTION;
+    const GridWork &gw = direction == CJT_FWD ? p->fw : p->iv;
+    *nblk = gw.nblk;
+    if (gw.nblk > cap) return CJT_EINVAL;
+    for (int k = 0; k < gw.nblk; ++k) {
+        boxes[3 * k] = gw.jk[k];
+        boxes[3 * k + 1] = gw.i1[k];
+        boxes[3 * k + 2] = gw.i2[k];
+    }
+    return CJT_OK;
+}
+
 int cjt_error_bound(cjt_plan_t p, int direction, double *bound) {
     if (!p || !bound) return CJT_EINVAL;
     if (direction != CJT_FWD && direction != CJT_INV) return CJT_EINVAL;

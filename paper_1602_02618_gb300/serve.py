@@ -14,8 +14,10 @@ Every transform runs in the library's kernels through the C ABI
 (cjt_plan, cjt_forward_ws / cjt_inverse_ws); this module only schedules.
 Admission by memory: before a planner builds a new plan, plans not in use are
 evicted least-recently-used until the resident plans, the slot arenas and I/O
-buffers and the new plan's estimate fit in `mem_budget`; while plans in use fill
-it, the planner waits for them to be released.  Slot arenas grow to the largest
+buffers, the estimates of the plans other planners are building and the new
+plan's estimate fit in `mem_budget`; the estimate stays reserved until the plan is
+registered (or its build fails); while plans in use fill the budget, the planner
+waits for them to be released.  Slot arenas grow to the largest
 workspace their slot has served; they count against the budget but are not
 gated themselves (at most slots x the largest workspace).
 """
@@ -94,6 +96,7 @@ class Server:
         self.plans = collections.OrderedDict()   # key -> [Plan, bytes, users]
         self.plan_bytes = 0
         self.slot_bytes = 0
+        self.pending_bytes = 0.0   # estimates of the plans being built
         self.completed = []
         self.max_inflight = 0
         self._stop = False
@@ -158,17 +161,25 @@ class Server:
                         self.plans.move_to_end(key)
                 if ent is None:
                     est = 4000.0 * (r.N + 1)   # conservative device bytes of one plan's tables
-                    self._make_room(est)
-                    p = cjt.Plan(r.N, r.alpha, r.beta, precision=self.precision, directions=r.direction,
-                                 shared_workspace=True, stream=stream.cuda_stream, **self.plan_options(r.N))
+                    self._make_room(est)       # reserves est as pending bytes
+                    try:
+                        p = cjt.Plan(r.N, r.alpha, r.beta, precision=self.precision, directions=r.direction,
+                                     shared_workspace=True, stream=stream.cuda_stream, **self.plan_options(r.N))
+                    except Exception:
+                        with self.cv:
+                            self.pending_bytes -= est
+                            self.cv.notify_all()
+                        raise
                     nbytes = p.info()["device_bytes"]
-                    with self.lock:
+                    with self.cv:
+                        self.pending_bytes -= est
                         if key in self.plans:           # another planner made it meanwhile
                             self.plans[key][2] += 1
                             p.close()
                         else:
                             self.plans[key] = [p, nbytes, 1]
                             self.plan_bytes += nbytes
+                        self.cv.notify_all()
             except Exception as e:  # bad request: report it on the request, keep serving
                 r.error = str(e)
                 r.t_done = time.perf_counter()
@@ -179,8 +190,12 @@ class Server:
                 self.cv.notify_all()
 
     def _make_room(self, need):
+        """Evict unused plans until the resident plans, the slots, the plans being built by
+        other planners (their reserved estimates) and `need` fit the budget, then reserve
+        `need` as pending bytes until the caller registers its plan."""
         with self.cv:
-            while self.plan_bytes + self.slot_bytes + need > self.mem_budget and not self._stop:
+            while (self.plan_bytes + self.slot_bytes + self.pending_bytes + need > self.mem_budget
+                   and not self._stop):
                 victim = next((k for k, v in self.plans.items() if v[2] == 0), None)
                 if victim is None:
                     self.cv.wait(timeout=0.05)
@@ -188,6 +203,7 @@ class Server:
                 p, nbytes, _ = self.plans.pop(victim)
                 p.close()
                 self.plan_bytes -= nbytes
+            self.pending_bytes += need
 
     # -------------------------------------------------------------- executor
     def _executor(self):
