@@ -320,6 +320,19 @@ def run_batched(ctx, big=False, steps=None):
     else:
         items = inputs.batch_workload(args.batch_count, seed=seed)
         precision = precision_code(cjt, args.precision)
+    # transform launch configuration: tuned per length class the batch uses (process-wide,
+    # before the graph is captured)
+    fft_tune = None
+    if not args.no_autotune:
+        from paper_1602_02618_gb300 import autotune
+        t0 = time.perf_counter()
+        Gs = sorted({1 << max(1, int(math.ceil(math.log2(N)))) for N, *_ in items})
+        lens = sorted({int(math.log2(2 * G)) for G in Gs} | {int(math.log2(4 * G)) for G in Gs})
+        fft_tune = {"precision": args.precision if not big else "mixed",
+                    "lengths": autotune.tune_fft(precision, lens), "tune_s": None}
+        if precision != cjt.CJT_FP64:   # the DCT-I and the front end stay in FP64
+            fft_tune["fp64_lengths"] = autotune.tune_fft(cjt.CJT_FP64, lens)
+        fft_tune["tune_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     tune = None
     if big or args.batch_fixed:
@@ -476,6 +489,7 @@ def run_batched(ctx, big=False, steps=None):
                 "h2d_bytes_per_step": coeffs * 8, "d2h_bytes_per_step": coeffs * 8,
                 "via": "cjt_batch_launch_host (C ABI, pinned host buffers)"},
         "kernels_per_step": int(binfo["kernels"]), "gpu_launches": int(binfo["kernels"]) * steps,
+        "fft_autotune": fft_tune,
         "setup": {"plan_s": plan_s, "graph_create_s": graph_s,
                   "plan_bytes": sum(p.info()["device_bytes"] for p in plans),
                   "rec_store_bytes": sum(p.info()["rec_store_bytes"] for p in plans),

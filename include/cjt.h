@@ -398,6 +398,26 @@ int cjt_get_profile(cjt_plan_t plan, double *ms, int64_t *counts, int n);
 int cjt_microbench_fma(int kind, double *flops, void *stream);
 
 /*
+ * Transform launch configuration (for the autotuner; no counterpart in the paper).  The
+ * DCT-I/DST-I sums of every stage run as batched complex FFTs of power-of-two length L;
+ * per precision (CJT_FP64, CJT_MIXED: float, CJT_DFLOAT: double-float) and log2 L:
+ *   ctas_per_sm      CTAs per SM the tile size (sequences per CTA) aims at (1..32, default 4);
+ *   split            four-step factorisation L = L1 L2 above one pass: 0 (default) the larger
+ *                    factor first (L1 = 2^ceil(log2 L / 2)), 1 the smaller first;
+ *   single_max_log2  12 (default) or 13: longest transform run in one shared-memory pass.
+ * The configuration holds for the process and for every later launch (a captured graph keeps
+ * the configuration of its capture).  ctas_per_sm changes only the work split; split and
+ * single_max_log2 change the order of the arithmetic, so results differ in rounding between
+ * configurations (within the tolerances).  Errors: CJT_EINVAL.
+ * cjt_fft_time runs `batch` transforms of length 2^log2L (log2L <= 22, at most 8 GB of data)
+ * under the current configuration and stores the average milliseconds of `reps` runs after a
+ * warm-up (CUDA events on `stream`); it allocates and frees its own buffers.
+ */
+int cjt_fft_set_config(int precision, int log2L, int ctas_per_sm, int split, int single_max_log2);
+int cjt_fft_get_config(int precision, int log2L, int *ctas_per_sm, int *split, int *single_max_log2);
+int cjt_fft_time(int precision, int log2L, int64_t batch, int reps, double *ms, void *stream);
+
+/*
  * Allocation-free Chebyshev coefficients from values (no counterpart in the
  * paper; it is the forward transform's last step, c = T_N^{-1} y, offered for
  * callers that cannot call cudaMalloc: code running under a host framework's

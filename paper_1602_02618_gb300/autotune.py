@@ -241,3 +241,49 @@ def build_batch_plans(items, precision: int = 0, plan_budget_bytes: float = 200e
                                    "items": len(v["members"])} for k, v in cls.items()},
               "plan_bytes": used, "plan_budget_bytes": plan_budget_bytes, "stored_items": stored}
     return plans, opts, report
+
+
+# ---------------------------------------------------------------------------
+# Transforms: launch configuration per (precision, length)
+# ---------------------------------------------------------------------------
+FFT_CTAS = (2, 4, 8)
+
+
+def fft_candidates(log2L: int):
+    """(ctas_per_sm, split, single_max_log2) worth timing for transforms of length 2^log2L:
+    the tile occupancy target always; the four-step split above one pass; one pass or two at
+    2^13."""
+    out = []
+    for ctas in FFT_CTAS:
+        if log2L <= 12:
+            out.append((ctas, 0, 12))
+        elif log2L == 13:
+            out += [(ctas, 0, 12), (ctas, 1, 12), (ctas, 0, 13)]
+        else:
+            out += [(ctas, 0, 12), (ctas, 1, 12)]
+    return out
+
+
+def tune_fft(precision: int, log2Ls, points: int = 1 << 24, reps: int = 3) -> dict:
+    """For each length 2^log2L, time the candidates of fft_candidates on a batch of about
+    `points` points (cjt_fft_time) and keep the fastest with cjt_fft_set_config.  Returns
+    {log2L: {"config": (ctas_per_sm, split, single_max_log2), "ms": best, "default_ms": ...}}."""
+    from . import cjt
+    out = {}
+    for lg in sorted(set(int(v) for v in log2Ls)):
+        batch = max(1, points >> lg)
+        res = []
+        for ctas, split, single in fft_candidates(lg):
+            cjt.fft_set_config(precision, lg, ctas, split, single)
+            try:
+                res.append((cjt.fft_time(precision, lg, batch, reps), (ctas, split, single)))
+            except cjt.CJTError:
+                continue
+        if not res:
+            cjt.fft_set_config(precision, lg)
+            continue
+        best = min(res)
+        default = [t for t, c in res if c == (4, 0, 12)]
+        cjt.fft_set_config(precision, lg, *best[1])
+        out[lg] = {"config": best[1], "ms": best[0], "default_ms": default[0] if default else None, "batch": batch}
+    return out

@@ -69,7 +69,8 @@ EXPORTED = ["cjt_plan_opts_default", "cjt_plan", "cjt_destroy", "cjt_get_info", 
             "cjt_forward_ws", "cjt_inverse_ws", "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info",
             "cjt_batch_destroy", "cjt_jacobi_to_jacobi", "cjt_asy_coefficient", "cjt_asy_eval",
             "cjt_rec_coefficients", "cjt_error_bound", "cjt_batch_launch_host", "cjt_batch_set_profiling",
-            "cjt_batch_get_profile", "cjt_get_partition"]
+            "cjt_batch_get_profile", "cjt_get_partition", "cjt_fft_set_config", "cjt_fft_get_config",
+            "cjt_fft_time"]
 
 NOALLOC_MAX_N = 65536
 
@@ -133,6 +134,9 @@ def load(path: str = LIB_PATH):
         lib.cjt_batch_get_profile.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64), i]
         lib.cjt_error_bound.argtypes = [vp, i, ctypes.POINTER(d)]
         lib.cjt_get_partition.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
+        lib.cjt_fft_set_config.argtypes = [i, i, i, i, i]
+        lib.cjt_fft_get_config.argtypes = [i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        lib.cjt_fft_time.argtypes = [i, i, i64, i, ctypes.POINTER(d), vp]
         lib.cjt_strerror.argtypes = [i]
         lib.cjt_strerror.restype = ctypes.c_char_p
         lib.cjt_last_cuda_error.restype = ctypes.c_char_p
@@ -143,7 +147,7 @@ def load(path: str = LIB_PATH):
                      "cjt_batch_create", "cjt_batch_launch", "cjt_batch_info", "cjt_jacobi_to_jacobi",
                      "cjt_asy_coefficient", "cjt_asy_eval", "cjt_rec_coefficients", "cjt_error_bound",
                      "cjt_batch_launch_host", "cjt_batch_set_profiling", "cjt_batch_get_profile",
-                     "cjt_get_partition"):
+                     "cjt_get_partition", "cjt_fft_set_config", "cjt_fft_get_config", "cjt_fft_time"):
             getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -306,6 +310,27 @@ def cjt_inverse_ws(plan: Plan, c_cheb, c_jac, workspace, stream=None):
                                  ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
                                  _stream_handle(stream)), "cjt_inverse_ws")
     return c_jac
+
+
+def fft_set_config(precision: int, log2L: int, ctas_per_sm: int = 4, split: int = 0, single_max_log2: int = 12):
+    """Launch configuration of the transforms of one (precision, length) class (process-wide)."""
+    _check(load().cjt_fft_set_config(int(precision), int(log2L), int(ctas_per_sm), int(split), int(single_max_log2)),
+           "cjt_fft_set_config")
+
+
+def fft_get_config(precision: int, log2L: int):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().cjt_fft_get_config(int(precision), int(log2L), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "cjt_fft_get_config")
+    return {"ctas_per_sm": a.value, "split": b.value, "single_max_log2": c.value}
+
+
+def fft_time(precision: int, log2L: int, batch: int, reps: int = 3, stream=None) -> float:
+    """Milliseconds of `batch` transforms of length 2^log2L under the current configuration."""
+    v = ctypes.c_double()
+    _check(load().cjt_fft_time(int(precision), int(log2L), int(batch), int(reps), ctypes.byref(v),
+                               _stream_handle(stream)), "cjt_fft_time")
+    return v.value
 
 
 def partition(plan: Plan, direction: int):

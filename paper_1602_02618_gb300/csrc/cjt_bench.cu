@@ -84,3 +84,48 @@ extern "C" int cjt_microbench_fma(int kind, double *flops, void *stream) {
     if (kind == 2) return run<DfTag>(flops, (cudaStream_t)stream);
     return CJT_EINVAL;
 }
+
+// Transform microbenchmark for the autotuner: `batch` transforms of length 2^log2L in the
+// precision's transform type (complex double, float or double-float), under the current
+// cjt_fft_set_config of that class, timed with CUDA events on `stream` (average of `reps`
+// after one warm-up).  The tables are built as a plan builds them; the buffers are freed
+// before returning.
+extern "C" int cjt_fft_time(int precision, int log2L, int64_t batch, int reps, double *ms, void *stream) {
+    if (!ms || log2L < 1 || log2L > 22 || batch < 1 || reps < 1) return CJT_EINVAL;
+    if (precision != CJT_FP64 && precision != CJT_MIXED && precision != CJT_DFLOAT) return CJT_EINVAL;
+    const int pa = precision == CJT_MIXED ? PREC_F32 : precision == CJT_DFLOAT ? PREC_DF : PREC_F64;
+    const int64_t L = 1LL << log2L;
+    if ((double)batch * (double)L * 16.0 > 8e9) return CJT_EUNSUPPORTED;   // at most 8 GB of data
+    cudaStream_t st = (cudaStream_t)stream;
+    cjt_plan_s tmp;
+    tmp.Ltab = L;
+    int rc = cjt_build_twiddles(&tmp, pa, st);
+    void *data = nullptr, *scratch = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const size_t bytes = (size_t)(batch * L * prec_cbytes(pa));
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        if (data) cudaFree(data);
+        if (scratch) cudaFree(scratch);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        for (void *v : tmp.allocs) cudaFree(v);
+        tmp.allocs.clear();
+    };
+    if (!rc && cudaMalloc(&data, bytes) != cudaSuccess) rc = CJT_ENOMEM;
+    if (!rc && L > 4096 && cudaMalloc(&scratch, bytes) != cudaSuccess) rc = CJT_ENOMEM;
+    if (!rc && (cudaMemsetAsync(data, 0, bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+                cudaEventCreate(&e1) != cudaSuccess))
+        rc = CJT_ECUDA;
+    const Twiddles tw = tmp.twiddles(pa);
+    if (!rc) rc = cjt_fft_pow2(data, scratch, L, batch, tw, pa, st);
+    if (!rc && cudaEventRecord(e0, st) != cudaSuccess) rc = CJT_ECUDA;
+    for (int r = 0; r < reps && !rc; ++r) rc = cjt_fft_pow2(data, scratch, L, batch, tw, pa, st);
+    if (!rc && cudaEventRecord(e1, st) != cudaSuccess) rc = CJT_ECUDA;
+    float t = 0.f;
+    if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        rc = CJT_ECUDA;
+    if (!rc) *ms = (double)t / reps;
+    cleanup();
+    return rc;
+}

@@ -34,6 +34,19 @@ int cjt_fft_prime();
 
 namespace {
 
+// Launch configuration of the transforms of one (precision, log2 L) class, set by the
+// autotuner through cjt_fft_set_config and read when a transform is enqueued:
+//   ctas     CTAs per SM the tile size aims at when there is enough work (tiles are powers
+//            of two, at most 64 columns and ~64 KB of shared memory);
+//   split    four-step factorisation L = L1 L2: 0 -> L1 = 2^ceil(log2 L / 2), 1 -> 2^floor;
+//   single   largest log2 L transformed in one pass in shared memory (12 or 13).
+// ctas changes only the work split between CTAs; split and single change the order of
+// the arithmetic (results differ in rounding), so one configuration holds for a process.
+struct FftCfg {
+    std::atomic<int> ctas{4}, split{0}, single{12};
+};
+FftCfg g_fft_cfg[3][32];
+
 struct dfloat {};   // tag of the double-float transform (complex type dfc)
 template <typename T> struct cplx;
 template <> struct cplx<double> { using t = double2; };
@@ -301,7 +314,7 @@ int ilog2(int64_t v) {
 template <typename R>
 int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batch, int64_t in_es, int64_t in_cs,
                int64_t in_ts, int64_t out_ks, int64_t out_cs, int64_t out_ts, const void *tw, int logLtab,
-               int post_log, const void *stw, const void *fmat, cudaStream_t st) {
+               int post_log, const void *stw, const void *fmat, cudaStream_t st, int ctas) {
     using V = typename cplx<R>::t;
     const int Ls = 1 << logLs;
     // Columns per CTA: at most ~64 KB of shared memory (32 KB double-float), and few
@@ -322,9 +335,9 @@ int launch_sub(const void *in, void *out, int logLs, int64_t ncols, int64_t batc
     // double-float: half the tile, so that more CTAs (and warps) share an SM
     const int64_t budget_elems = (int64_t)((std::is_same<R, dfloat>::value ? 32768 : 65536) / sizeof(V));
     int64_t tile64 = std::min<int64_t>(std::min<int64_t>(ncols, 64), std::max<int64_t>(1, budget_elems / Ls));
-    // at least four CTAs per SM when there is enough work (fewer, larger CTAs leave a
+    // at least `ctas` CTAs per SM when there is enough work (fewer, larger CTAs leave a
     // partly empty last wave), and a power of two (shift/mask indexing)
-    tile64 = std::min<int64_t>(tile64, std::max<int64_t>(1, ncols * batch / (4 * sms)));
+    tile64 = std::min<int64_t>(tile64, std::max<int64_t>(1, ncols * batch / ((int64_t)ctas * sms)));
     int tile = 1;
     while ((int64_t)tile * 2 <= tile64) tile *= 2;
     size_t smem = (size_t)tile * (Ls + SMEM_PAD) * sizeof(V);
@@ -354,18 +367,24 @@ int fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles
     if (L <= 1 || batch <= 0) return CJT_OK;
     const int logL = ilog2(L), logLtab = ilog2(Ltab);
     if ((1LL << logL) != L || L > Ltab) return CJT_EINVAL;
-    if (logL <= 12) {
+    const int pr = std::is_same<R, float>::value ? 1 : std::is_same<R, dfloat>::value ? 2 : 0;
+    const FftCfg &cfg = g_fft_cfg[pr][logL];
+    const int ctas = cfg.ctas.load(std::memory_order_relaxed);
+    // one pass up to 2^12 points, or 2^13 when so configured and the stage tables (if any)
+    // reach that level
+    const bool tables13 = (stw == nullptr && fmat == nullptr) || T.lmax >= 13;
+    if (logL <= 12 || (logL == 13 && cfg.single.load(std::memory_order_relaxed) >= 13 && tables13)) {
         // direct: each "column" is one whole transform
-        return launch_sub<R>(data, data, logL, batch, 1, 1, L, 0, 1, L, 0, tw, logLtab, -1, stw, fmat, st);
+        return launch_sub<R>(data, data, logL, batch, 1, 1, L, 0, 1, L, 0, tw, logLtab, -1, stw, fmat, st, ctas);
     }
     if (logL > 24 || scratch == nullptr) return CJT_EUNSUPPORTED;
-    const int log1 = (logL + 1) / 2, log2 = logL - log1;
+    const int log1 = cfg.split.load(std::memory_order_relaxed) ? logL / 2 : (logL + 1) / 2, log2 = logL - log1;
     const int64_t L1 = 1LL << log1, L2 = 1LL << log2;
     // pass A: columns n2 (L2 of them), elements n1 at stride L2
-    int rc = launch_sub<R>(data, scratch, log1, L2, batch, L2, 1, L, L2, 1, L, tw, logLtab, logL, stw, fmat, st);
+    int rc = launch_sub<R>(data, scratch, log1, L2, batch, L2, 1, L, L2, 1, L, tw, logLtab, logL, stw, fmat, st, ctas);
     if (rc) return rc;
     // pass B: rows k1 (L1 of them), elements n2 contiguous, output X[k1 + L1 k2]
-    return launch_sub<R>(scratch, data, log2, L1, batch, 1, L2, L, L1, 1, L, tw, logLtab, -1, stw, fmat, st);
+    return launch_sub<R>(scratch, data, log2, L1, batch, 1, L2, L, L1, 1, L, tw, logLtab, -1, stw, fmat, st, ctas);
 }
 
 // ---------------------------------------------------------------------------
@@ -517,6 +536,32 @@ int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twid
 }
 
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch) { return L > 4096 ? L * batch : 0; }
+
+namespace {
+int prec_index(int precision) {
+    return precision == CJT_FP64 ? 0 : precision == CJT_MIXED ? 1 : precision == CJT_DFLOAT ? 2 : -1;
+}
+}  // namespace
+
+extern "C" int cjt_fft_set_config(int precision, int log2L, int ctas_per_sm, int split, int single_max_log2) {
+    const int pr = prec_index(precision);
+    if (pr < 0 || log2L < 1 || log2L > 24 || ctas_per_sm < 1 || ctas_per_sm > 32 || (split != 0 && split != 1) ||
+        (single_max_log2 != 12 && single_max_log2 != 13))
+        return CJT_EINVAL;
+    g_fft_cfg[pr][log2L].ctas.store(ctas_per_sm);
+    g_fft_cfg[pr][log2L].split.store(split);
+    g_fft_cfg[pr][log2L].single.store(single_max_log2);
+    return CJT_OK;
+}
+
+extern "C" int cjt_fft_get_config(int precision, int log2L, int *ctas_per_sm, int *split, int *single_max_log2) {
+    const int pr = prec_index(precision);
+    if (pr < 0 || log2L < 1 || log2L > 24 || !ctas_per_sm || !split || !single_max_log2) return CJT_EINVAL;
+    *ctas_per_sm = g_fft_cfg[pr][log2L].ctas.load();
+    *split = g_fft_cfg[pr][log2L].split.load();
+    *single_max_log2 = g_fft_cfg[pr][log2L].single.load();
+    return CJT_OK;
+}
 
 // Function attributes, set once per device (they belong to the device's context), so
 // that later launches (possibly under stream capture) make no configuration calls.

@@ -193,6 +193,7 @@ struct Twiddles {
     int64_t Ltab = 0;
     const void *stw = nullptr;
     const void *fma = nullptr;   // FP64 only: TwFma tables of the decimation-in-time stages
+    int lmax = 0;                // the stage tables cover block lengths up to 2^lmax
 };
 __host__ __device__ inline int64_t stw_base(int lb) { return 3 * ((1LL << (lb - 2)) - 1); }
 
@@ -268,12 +269,14 @@ struct cjt_plan_s {
     void *d_twdf = nullptr;       // dfc[Ltab]
     void *d_stw64 = nullptr, *d_stw32 = nullptr, *d_stwdf = nullptr;   // stage tables (Twiddles)
     void *d_twfma = nullptr;      // TwFma tables (FP64 decimation-in-time stages)
+    int stw_lmax = 0;             // the stage tables' top level (block length 2^stw_lmax)
     Twiddles twiddles(int prec) const {
         Twiddles t;
         t.Ltab = Ltab;
         t.tw = prec == PREC_F32 ? d_tw32 : prec == PREC_DF ? d_twdf : d_tw64;
         t.stw = prec == PREC_F32 ? d_stw32 : prec == PREC_DF ? d_stwdf : d_stw64;
         t.fma = prec == PREC_F64 ? d_twfma : nullptr;
+        t.lmax = stw_lmax;
         return t;
     }
     int prec_asy = PREC_F64;      // element type of the asymptotic transforms
@@ -590,6 +593,7 @@ int64_t cjt_dft_work_bytes(const Dft &d, int64_t batch);
 int64_t cjt_dft_scratch_bytes(const Dft &d, int64_t batch);
 
 int cjt_plan_build(cjt_plan_s *p, cudaStream_t st);
+int cjt_build_twiddles(cjt_plan_s *p, int pa, cudaStream_t st);
 Workspace cjt_carve(const cjt_plan_s *p, void *base);
 int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st);
 int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st);

@@ -984,6 +984,42 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
 
 }  // namespace
 
+// Twiddle tables of a plan (p->Ltab set): omega_{Ltab}^k in FP64 and in the precision pa
+// of its asymptotic transforms, the stage tables and the FP64 fused multiply-add forms.
+int cjt_build_twiddles(cjt_plan_s *p, int pa, cudaStream_t st) {
+    TRY(dalloc(p, (double2 **)&p->d_tw64, p->Ltab));
+    if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_tw32, p->Ltab));
+    if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_twdf, p->Ltab));   // dfc: 16 bytes
+    k_twiddles<<<blocks_for(p->Ltab, 256), 256, 0, st>>>(p->Ltab, (double2 *)p->d_tw64, (float2 *)p->d_tw32,
+                                                         (dfc *)p->d_twdf);
+    CJT_CUDA_TRY(cudaGetLastError());
+    {
+        int logLtab = 0;
+        while ((1LL << logLtab) < p->Ltab) ++logLtab;
+        // stage tables to block length 2^13: one-pass transforms of up to 8192 points
+        // (cjt_fft_set_config)
+        const int lmax = std::min(13, logLtab);
+        p->stw_lmax = lmax;
+        if (lmax >= 2) {
+            const int64_t n = stw_base(lmax + 1);
+            TRY(dalloc(p, (double2 **)&p->d_stw64, n));
+            if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_stw32, n));
+            if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_stwdf, n));   // dfc: 16 bytes
+            k_stage_twiddles<<<blocks_for(n, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)p->d_tw64,
+                                                                 (double2 *)p->d_stw64, (float2 *)p->d_stw32,
+                                                                 (dfc *)p->d_stwdf);
+            CJT_CUDA_TRY(cudaGetLastError());
+            // every plan has FP64 transforms (final DCT-I, inverse front end)
+            const int64_t nf = twfma_base(lmax + 1);
+            TRY(dalloc(p, (TwFma **)&p->d_twfma, nf));
+            k_fma_twiddles<<<blocks_for(nf, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)p->d_tw64,
+                                                               (TwFma *)p->d_twfma);
+            CJT_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    return CJT_OK;
+}
+
 int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     PlanTrace tr(st);
     TRY(cjt_fft_prime());
@@ -1066,33 +1102,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     }
     p->Ltab = 2;
     for (auto &u : used) p->Ltab = std::max(p->Ltab, u.first->fft_len());
-    TRY(dalloc(p, (double2 **)&p->d_tw64, p->Ltab));
-    if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_tw32, p->Ltab));
-    if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_twdf, p->Ltab));   // dfc: 16 bytes
-    k_twiddles<<<blocks_for(p->Ltab, 256), 256, 0, st>>>(p->Ltab, (double2 *)p->d_tw64, (float2 *)p->d_tw32,
-                                                         (dfc *)p->d_twdf);
-    CJT_CUDA_TRY(cudaGetLastError());
-    {
-        int logLtab = 0;
-        while ((1LL << logLtab) < p->Ltab) ++logLtab;
-        const int lmax = std::min(12, logLtab);
-        if (lmax >= 2) {
-            const int64_t n = stw_base(lmax + 1);
-            TRY(dalloc(p, (double2 **)&p->d_stw64, n));
-            if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_stw32, n));
-            if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_stwdf, n));   // dfc: 16 bytes
-            k_stage_twiddles<<<blocks_for(n, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)p->d_tw64,
-                                                                 (double2 *)p->d_stw64, (float2 *)p->d_stw32,
-                                                                 (dfc *)p->d_stwdf);
-            CJT_CUDA_TRY(cudaGetLastError());
-            // every plan has FP64 transforms (final DCT-I, inverse front end)
-            const int64_t nf = twfma_base(lmax + 1);
-            TRY(dalloc(p, (TwFma **)&p->d_twfma, nf));
-            k_fma_twiddles<<<blocks_for(nf, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)p->d_tw64,
-                                                               (TwFma *)p->d_twfma);
-            CJT_CUDA_TRY(cudaGetLastError());
-        }
-    }
+    TRY(cjt_build_twiddles(p, pa, st));
     int64_t work = 0, scratch = 0;
     for (auto &u : used) {
         Dft &d = *u.first;

@@ -99,6 +99,9 @@ def test_without_a_device_calls_fail_loudly():
     assert lib.cjt_sync(None) == cjt.CJT_ECUDA
     assert lib.cjt_error_bound(None, cjt.CJT_FWD, None) == cjt.CJT_EINVAL
     assert lib.cjt_get_partition(None, cjt.CJT_FWD, 0, None, None) == cjt.CJT_EINVAL
+    assert lib.cjt_fft_set_config(cjt.CJT_FP64, 40, 4, 0, 12) == cjt.CJT_EINVAL
+    assert lib.cjt_fft_set_config(cjt.CJT_FP64, 16, 4, 0, 14) == cjt.CJT_EINVAL
+    assert lib.cjt_fft_time(cjt.CJT_FP64, 16, 1, 1, None, None) == cjt.CJT_EINVAL
     assert lib.cjt_batch_launch_host(None, None, None, None) == cjt.CJT_EINVAL
     assert lib.cjt_batch_set_profiling(None, 1) == cjt.CJT_EINVAL
     assert lib.cjt_batch_get_profile(None, None, None, 0) == cjt.CJT_EINVAL
