@@ -373,7 +373,9 @@ def run_batched(ctx, big=False, steps=None):
     for k in range(steps):
         ctx.flush.zero_()
         evs[k][0].record(stream)
+        torch.cuda.nvtx.range_push("timed_batch")
         batch.launch()
+        torch.cuda.nvtx.range_pop()
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     multirank.barrier(ctx.dist)

@@ -156,7 +156,12 @@ __global__ void __launch_bounds__(GE_THREADS) k_g_elem(const GDesc *__restrict__
     const int64_t n = Elem<OP>::size(sd);
     const int64_t i0 = (int64_t)e.blk * GE_CHUNK, i1 = min(n, i0 + GE_CHUNK);
     PairCache pc;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += GE_THREADS) Elem<OP>::template apply<V, R>(sd, i, pc);
+    // a fixed trip count, unrolled, so that the loads of several elements are in flight
+#pragma unroll
+    for (int u = 0; u < GE_CHUNK / GE_THREADS; ++u) {
+        const int64_t i = i0 + threadIdx.x + (int64_t)u * GE_THREADS;
+        if (i < i1) Elem<OP>::template apply<V, R>(sd, i, pc);
+    }
 }
 
 // ---------------------------------------------------------------------------

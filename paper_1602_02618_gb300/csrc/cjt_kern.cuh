@@ -9,6 +9,8 @@
 // on which kind of launch computed it (bit for bit).
 #pragma once
 
+#include <type_traits>
+
 #include "cjt_df.cuh"
 #include "cjt_internal.cuh"
 
@@ -231,25 +233,48 @@ struct PairScale {
     int m0, m1;          // terms of items 2p and 2p+1 (m1 < 0: no second item)
     int k0, k1;          // their blocks
     double s0, s1;       // scale[2q] of each
+    int e0, e1;          // s0 = 2^e0, s1 = 2^e1 (exact powers of two)
 };
+__device__ __forceinline__ int pow2_exponent(double s) {
+    return (int)((__double_as_longlong(s) >> 52) & 0x7ff) - 1023;
+}
 __device__ __forceinline__ PairScale pair_scale(int p, int M, int nq, const double *__restrict__ scale) {
     PairScale ps;
     const int q = 2 * p;
     ps.k0 = q / M;
     ps.m0 = q - ps.k0 * M;
     ps.s0 = scale[2 * q];
+    ps.e0 = pow2_exponent(ps.s0);
     if (q + 1 < nq) {
         ps.k1 = (q + 1) / M;
         ps.m1 = q + 1 - ps.k1 * M;
         ps.s1 = scale[2 * (q + 1)];
+        ps.e1 = pow2_exponent(ps.s1);
     } else {
         ps.k1 = 0;
         ps.m1 = -1;
         ps.s1 = 0.0;
+        ps.e1 = 0;
     }
     return ps;
 }
 
+// x 2^k, exact, for s = 2^k: the exponent field is moved by integer arithmetic (the FP64
+// pipe, a few lanes per clock on this GPU, is the scarce resource of these kernels); zeros,
+// subnormals, infinities, NaNs and results outside the normal range take the multiply,
+// which gives the same value
+__device__ __forceinline__ double mul_pow2(double x, int k, double s) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff), ek = e + k;
+    if (e == 0 || e == 0x7ff || ek <= 0 || ek >= 0x7ff) return x * s;
+    return __longlong_as_double(b + ((long long)k << 52));
+}
+__device__ __forceinline__ double neg_if(double x, bool neg) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+}
+
+// FP64 transforms: s_q C_{n,m} c_n formed as (C_{n,m} c_n) s_q, the same value (the scale
+// is a power of two); other precisions: the scaled factor is rounded to R first
 template <typename V, typename R>
 __device__ __forceinline__ void asy_pack_fwd_elem(int64_t n, int p, const PairScale &ps, int64_t N, int64_t L,
                                                   const int *__restrict__ box3, const double *__restrict__ Cnm,
@@ -258,13 +283,21 @@ __device__ __forceinline__ void asy_pack_fwd_elem(int64_t n, int p, const PairSc
     o.x = 0;
     o.y = 0;
     if (n <= N) {
-        const R cn = (R)c[n];
-        o.x = (R)(n >= box3[3 * ps.k0] ? Cnm[ps.m0 * (N + 1) + n] * ps.s0 : 0.0) * cn;
-        if (ps.m1 >= 0) o.y = (R)(n >= box3[3 * ps.k1] ? Cnm[ps.m1 * (N + 1) + n] * ps.s1 : 0.0) * cn;
+        if constexpr (std::is_same<R, double>::value) {
+            const double cn = c[n];
+            if (n >= box3[3 * ps.k0]) o.x = mul_pow2(Cnm[ps.m0 * (N + 1) + n] * cn, ps.e0, ps.s0);
+            if (ps.m1 >= 0 && n >= box3[3 * ps.k1]) o.y = mul_pow2(Cnm[ps.m1 * (N + 1) + n] * cn, ps.e1, ps.s1);
+        } else {
+            const R cn = (R)c[n];
+            o.x = (R)(n >= box3[3 * ps.k0] ? Cnm[ps.m0 * (N + 1) + n] * ps.s0 : 0.0) * cn;
+            if (ps.m1 >= 0) o.y = (R)(n >= box3[3 * ps.k1] ? Cnm[ps.m1 * (N + 1) + n] * ps.s1 : 0.0) * cn;
+        }
     }
     buf[(int64_t)p * L + n] = o;
 }
 
+// Inverse: item q contributes s_q u_m(theta_i) g_i / 2 (real) and +-s_q v_m(theta_i) g_i / 2
+// (imaginary) on its box's rows; FP64 transforms form (u_m g_i) s_q / 2, the same value.
 template <typename V, typename R>
 __device__ __forceinline__ void asy_pack_inv_elem(int64_t idx, int p, const PairScale &ps, int64_t Ng, int64_t L,
                                                   const int *__restrict__ box3, const double *__restrict__ u,
@@ -273,24 +306,45 @@ __device__ __forceinline__ void asy_pack_inv_elem(int64_t idx, int p, const Pair
     // H(idx) = (z(idx) + conj z(L - idx)) / 2: the box rows lie in [1, Ng - 1]
     const bool lo = idx <= Ng;
     const int64_t i = lo ? idx : L - idx;
-    const R gi = (R)g[i];
-    const R sgn = lo ? (R)1 : (R)-1;
     const bool in0 = i >= box3[3 * ps.k0 + 1] && i <= box3[3 * ps.k0 + 2];
-    const double sc0 = 0.5 * ps.s0;
-    const R u0 = (R)(in0 ? sc0 * u[ps.m0 * (Ng + 1) + i] : 0.0), v0 = (R)(in0 ? sc0 * v[ps.m0 * (Ng + 1) + i] : 0.0);
-    const R h0r = u0 * gi, h0i = sgn * v0 * gi;
-    R h1r = 0, h1i = 0;
-    if (ps.m1 >= 0) {
-        const bool in1 = i >= box3[3 * ps.k1 + 1] && i <= box3[3 * ps.k1 + 2];
-        const double sc1 = 0.5 * ps.s1;
-        const R u1 = (R)(in1 ? sc1 * u[ps.m1 * (Ng + 1) + i] : 0.0);
-        const R v1 = (R)(in1 ? sc1 * v[ps.m1 * (Ng + 1) + i] : 0.0);
-        h1r = u1 * gi;
-        h1i = sgn * v1 * gi;
-    }
+    const bool in1 = ps.m1 >= 0 && i >= box3[3 * ps.k1 + 1] && i <= box3[3 * ps.k1 + 2];
     V o;
-    o.x = h0r - h1i;
-    o.y = h0i + h1r;
+    if constexpr (std::is_same<R, double>::value) {
+        // every load is issued whether or not the row is in the box (0 <= i <= Ng, so it is
+        // within the tables), so that the loads of consecutive elements overlap; the box
+        // selects afterwards
+        const int m1 = ps.m1 >= 0 ? ps.m1 : ps.m0;
+        const double gi = __ldg(g + i);
+        const double a0 = __ldg(u + ps.m0 * (Ng + 1) + i), b0 = __ldg(v + ps.m0 * (Ng + 1) + i);
+        const double a1 = __ldg(u + m1 * (Ng + 1) + i), b1 = __ldg(v + m1 * (Ng + 1) + i);
+        double h0r = 0.0, h0i = 0.0, h1r = 0.0, h1i = 0.0;
+        if (in0) {
+            h0r = mul_pow2(a0 * gi, ps.e0 - 1, 0.5 * ps.s0);
+            h0i = neg_if(mul_pow2(b0 * gi, ps.e0 - 1, 0.5 * ps.s0), !lo);
+        }
+        if (in1) {
+            h1r = mul_pow2(a1 * gi, ps.e1 - 1, 0.5 * ps.s1);
+            h1i = neg_if(mul_pow2(b1 * gi, ps.e1 - 1, 0.5 * ps.s1), !lo);
+        }
+        o.x = h0r - h1i;
+        o.y = h0i + h1r;
+    } else {
+        const R gi = (R)g[i];
+        const R sgn = lo ? (R)1 : (R)-1;
+        const double sc0 = 0.5 * ps.s0;
+        const R u0 = (R)(in0 ? sc0 * u[ps.m0 * (Ng + 1) + i] : 0.0), v0 = (R)(in0 ? sc0 * v[ps.m0 * (Ng + 1) + i] : 0.0);
+        const R h0r = u0 * gi, h0i = sgn * v0 * gi;
+        R h1r = 0, h1i = 0;
+        if (ps.m1 >= 0) {
+            const double sc1 = 0.5 * ps.s1;
+            const R u1 = (R)(in1 ? sc1 * u[ps.m1 * (Ng + 1) + i] : 0.0);
+            const R v1 = (R)(in1 ? sc1 * v[ps.m1 * (Ng + 1) + i] : 0.0);
+            h1r = u1 * gi;
+            h1i = sgn * v1 * gi;
+        }
+        o.x = h0r - h1i;
+        o.y = h0i + h1r;
+    }
     buf[(int64_t)p * L + idx] = o;
 }
 
