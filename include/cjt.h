@@ -120,15 +120,17 @@ typedef struct {
                          formula, alpha or beta = +-1/2 collapses each term to one cosine
                          (App. B.2-B.3) in either case.                                  */
     int grid;         /* Lobatto grid of the evaluation.  -1: the paper's, x_j = cos(pi j/N)
-                         (forward) and cos(pi j/(2N)) (inverse), so that for N not a power
-                         of two every transform is a Bluestein transform.  1: G, the least
-                         power of two >= N, in place of N: x_j = cos(pi j/G) and
-                         cos(pi j/(2G)).  The result is the same map (to rounding): a
-                         polynomial of degree N <= G is interpolated exactly by the
-                         inverse DCT-I on G+1 points, whose coefficients above N vanish,
-                         and the (2G+1)-point Clenshaw--Curtis rule is exact wherever the
-                         (2N+1)-point rule is.  0 (default): the power-of-two grid when N
-                         is not a power of two (identical to -1 otherwise).              */
+                         (forward) and cos(pi j/(2N)) (inverse); transforms of lengths 2N and
+                         4N are then direct when N is 2^a or 3 2^a, and Bluestein transforms
+                         otherwise.  1: G, the least power of two >= N, in place of N:
+                         x_j = cos(pi j/G) and cos(pi j/(2G)).  0 (default): G, the least
+                         integer >= N of the forms 2^a and 3 2^a (at most 4N/3; N itself when N
+                         has that form); transforms of length 3 2^b take one radix-3 step and
+                         power-of-two FFTs.  Every grid gives the same map (to rounding): a
+                         polynomial of degree N <= G is interpolated exactly by the inverse
+                         DCT-I on G+1 points, whose coefficients above N vanish, and the
+                         (2G+1)-point Clenshaw--Curtis rule is exact wherever the
+                         (2N+1)-point rule is.                                            */
     int overlap;      /* scheduling of an execution's two concurrent chains, the
                          asymptotic blocks (pack, transforms; Eq. "PNASY") and the
                          recurrence (Sec. 4.2), which run on separate streams and join

@@ -388,6 +388,87 @@ int fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles
 }
 
 // ---------------------------------------------------------------------------
+// Lengths L = 3 L2, L2 = 2^b: X[k1 + 3 k2] = sum_{n2} omega_{L2}^{n2 k2} (omega_L^{n2 k1}
+// sum_{n1 < 3} x[n1 L2 + n2] omega_3^{n1 k1}): one radix-3 step with its twiddles, then the
+// power-of-two FFTs of the three rows, whose stores put X in natural order.
+// ---------------------------------------------------------------------------
+template <typename V> __device__ __forceinline__ V cconst(double re, double im) { V r; r.x = re; r.y = im; return r; }
+template <> __device__ __forceinline__ dfc cconst<dfc>(double re, double im) { return dfc_make(df_from(re), df_from(im)); }
+
+// for each sequence and n2 < L2: the 3-point DFT of x[n2], x[n2 + L2], x[n2 + 2 L2]
+// (omega_3 = -1/2 - i sqrt(3)/2), outputs 1 and 2 times omega_L^{n2} and omega_L^{2 n2},
+// stored at n2 + k1 L2 of `out` (which may be `in`: each thread reads and writes its own
+// three slots)
+template <typename R>
+__global__ void k_fft_r3(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__restrict__ out, int logL2,
+                         int64_t total, const typename cplx<R>::t *__restrict__ tw3, int64_t tstride) {
+    using V = typename cplx<R>::t;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int64_t L2 = 1LL << logL2;
+    const int64_t t = i >> logL2, n2 = i & (L2 - 1);
+    const int64_t base = t * 3 * L2 + n2;
+    const V x0 = in[base], x1 = in[base + L2], x2 = in[base + 2 * L2];
+    const V sum = cadd(x1, x2), dif = csub(x1, x2);
+    const V y0 = cadd(x0, sum);
+    const V mid = csub(x0, cscale(sum, 0.5));                                           // x0 - (x1 + x2)/2
+    const V rot = cmul(dif, cconst<V>(0.0, -0.86602540378443864676372317075294));      // -i sqrt(3)/2 (x1 - x2)
+    const V y1 = cadd(mid, rot), y2 = csub(mid, rot);
+    out[base] = y0;
+    out[base + L2] = cmul(y1, tw3[n2 * tstride]);
+    out[base + 2 * L2] = cmul(y2, tw3[2 * n2 * tstride]);
+}
+
+template <typename R>
+int fft_r3(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &T, cudaStream_t st) {
+    using V = typename cplx<R>::t;
+    const int64_t L2 = L / 3;
+    const int logL2 = ilog2(L2), logLtab = ilog2(T.Ltab);
+    if (!T.tw3 || T.Ltab3 <= 0 || T.Ltab3 % L != 0 || L2 > T.Ltab || !scratch) return CJT_EINVAL;
+    const int64_t total = batch * L2, ts = T.Ltab3 / L;
+    const int pr = std::is_same<R, float>::value ? 1 : std::is_same<R, dfloat>::value ? 2 : 0;
+    const FftCfg &cfg = g_fft_cfg[pr][logL2];
+    const int ctas = cfg.ctas.load(std::memory_order_relaxed);
+    const unsigned nb = (unsigned)((total + 255) / 256);
+    if (L2 <= 4096) {
+        // radix-3 step into the scratch buffer, then the rows (three columns of length L2 per
+        // sequence) in one pass, stored at X[k1 + 3 k2]
+        k_fft_r3<R><<<nb, 256, 0, st>>>((const V *)data, (V *)scratch, logL2, total, (const V *)T.tw3, ts);
+        CJT_CUDA_TRY(cudaGetLastError());
+        if (L2 == 1) {
+            CJT_CUDA_TRY(cudaMemcpyAsync(data, scratch, sizeof(V) * 3 * batch, cudaMemcpyDeviceToDevice, st));
+            return CJT_OK;
+        }
+        return launch_sub<R>(scratch, data, logL2, 3, batch, 1, L2, L, 3, 1, L, T.tw, logLtab, -1, T.stw, T.fma, st,
+                             ctas);
+    }
+    // radix-3 step in place; the four-step transform of the 3 batch rows (contiguous, stride
+    // L2): pass A over all rows into the scratch buffer, pass B per row k1 into X[k1 + 3 k]
+    k_fft_r3<R><<<nb, 256, 0, st>>>((const V *)data, (V *)data, logL2, total, (const V *)T.tw3, ts);
+    CJT_CUDA_TRY(cudaGetLastError());
+    if (logL2 > 24) return CJT_EUNSUPPORTED;
+    const int log1 = cfg.split.load(std::memory_order_relaxed) ? logL2 / 2 : (logL2 + 1) / 2, log2 = logL2 - log1;
+    const int64_t A1 = 1LL << log1, A2 = 1LL << log2;
+    int rc = launch_sub<R>(data, scratch, log1, A2, 3 * batch, A2, 1, L2, A2, 1, L2, T.tw, logLtab, logL2, T.stw, T.fma,
+                           st, ctas);
+    if (rc) return rc;
+    for (int k1 = 0; k1 < 3; ++k1) {
+        rc = launch_sub<R>((const V *)scratch + k1 * L2, (V *)data + k1, log2, A1, batch, 1, A2, L, 3 * A1, 3, L, T.tw,
+                           logLtab, -1, T.stw, T.fma, st, ctas);
+        if (rc) return rc;
+    }
+    return CJT_OK;
+}
+
+template <typename R>
+int fft_any(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &T, cudaStream_t st) {
+    if (L <= 1 || batch <= 0) return CJT_OK;
+    if ((L & (L - 1)) == 0) return fft_pow2<R>(data, scratch, L, batch, T, st);
+    if (cjt_is_3pow2(L)) return fft_r3<R>(data, scratch, L, batch, T, st);
+    return CJT_EINVAL;
+}
+
+// ---------------------------------------------------------------------------
 // Bluestein
 // ---------------------------------------------------------------------------
 template <typename V>
@@ -456,7 +537,7 @@ template <typename R>
 int dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch, const Twiddles &tw, cudaStream_t st) {
     using V = typename cplx<R>::t;
     if (batch <= 0 || d.L <= 1) return CJT_OK;
-    if (!d.P) return fft_pow2<R>(data, scratch, d.L, batch, tw, st);
+    if (!d.P) return fft_any<R>(data, scratch, d.L, batch, tw, st);
     dim3 g(nblk(d.P, 256), (unsigned)batch);
     k_blue_pre<V><<<g, 256, 0, st>>>(d.L, d.S, d.P, (const V *)data, (const V *)d.chirp, (V *)work);
     CJT_CUDA_TRY(cudaGetLastError());
@@ -476,7 +557,7 @@ int dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch,
 }  // namespace
 
 int64_t cjt_dft_padded(int64_t L, int64_t S, int64_t K) {
-    if (L <= 1 || (L & (L - 1)) == 0) return 0;
+    if (L <= 1 || (L & (L - 1)) == 0 || cjt_is_3pow2(L)) return 0;
     int64_t P = 1;
     while (P < S + K - 1) P <<= 1;
     return P;
@@ -535,7 +616,15 @@ int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twid
     return fft_pow2<double>(data, scratch, L, batch, tw, st);
 }
 
-int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch) { return L > 4096 ? L * batch : 0; }
+int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch) {
+    return (L > 4096 || cjt_is_3pow2(L)) ? L * batch : 0;
+}
+
+int cjt_fft_any(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &tw, int prec, cudaStream_t st) {
+    if (prec == PREC_F32) return fft_any<float>(data, scratch, L, batch, tw, st);
+    if (prec == PREC_DF) return fft_any<dfloat>(data, scratch, L, batch, tw, st);
+    return fft_any<double>(data, scratch, L, batch, tw, st);
+}
 
 namespace {
 int prec_index(int precision) {

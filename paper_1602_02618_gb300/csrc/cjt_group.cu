@@ -22,7 +22,7 @@
 // kernels (cjt_kern.cuh), so each result is bit-identical to the transform run alone.
 //
 // Eligible items: N >= 1, FP64 or mixed (FP32 transforms) precision, no parameter shift,
-// power-of-two transform lengths (the default grid).  The batch runs the others (double-
+// transform lengths 2^b or 3 2^b (the default grids).  The batch runs the others (double-
 // float form, shifted parameters, Bluestein lengths) one chain per item on its lanes.
 #include <cuda_runtime.h>
 
@@ -48,7 +48,7 @@ inline int ilog2_exact(int64_t v) {
 // Everything one transform's stage kernels read or write.
 struct __align__(16) GDesc {
     int64_t N, G, Ng, L;      // degree; forward grid G; grid of this direction (G or 2G); ASY length
-    int logL, M, nblk, nq, npair, seg_len, pad0, pad1;
+    int logL, M, nblk, nq, npair, seg_len, l3, pad1;   // L = 2^logL, or 3 2^logL when l3
     RecTables rt;
     const RecItem *items;
     int64_t nitems;
@@ -106,18 +106,23 @@ template <> struct Elem<OP_INV_G> {
         cjt_kern::inv_g_elem(i, d.dct, d.w, d.g);
     }
 };
+// the transform (pair) of element idx of a pack's index space, and the element within it
+__device__ __forceinline__ int pair_of(const GDesc &d, int64_t idx) {
+    return d.l3 ? (int)((idx >> d.logL) / 3) : (int)(idx >> d.logL);
+}
 template <> struct Elem<OP_PACK_FWD> {
     static __host__ __device__ int64_t size(const GDesc &d) { return (int64_t)d.npair * d.L; }
     template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t idx, PairCache &pc) {
-        const int p = (int)(idx >> d.logL);
-        cjt_kern::asy_pack_fwd_elem<V, R>(idx & (d.L - 1), p, pc.of(p, d), d.N, d.L, d.box, d.Cnm, d.in, (V *)d.fft);
+        const int p = pair_of(d, idx);
+        cjt_kern::asy_pack_fwd_elem<V, R>(idx - (int64_t)p * d.L, p, pc.of(p, d), d.N, d.L, d.box, d.Cnm, d.in,
+                                          (V *)d.fft);
     }
 };
 template <> struct Elem<OP_PACK_INV> {
     static __host__ __device__ int64_t size(const GDesc &d) { return (int64_t)d.npair * d.L; }
     template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t idx, PairCache &pc) {
-        const int p = (int)(idx >> d.logL);
-        cjt_kern::asy_pack_inv_elem<V, R>(idx & (d.L - 1), p, pc.of(p, d), d.Ng, d.L, d.box, d.u, d.v, d.g,
+        const int p = pair_of(d, idx);
+        cjt_kern::asy_pack_inv_elem<V, R>(idx - (int64_t)p * d.L, p, pc.of(p, d), d.Ng, d.L, d.box, d.u, d.v, d.g,
                                           (V *)d.fft);
     }
 };
@@ -432,8 +437,8 @@ int run_step(cjt_group_s *g, const Step &s, int pair, cudaStream_t st) {
             return CJT_OK;
         case ST_FFT: {
             unsigned char *base = (unsigned char *)g->arena[pair];
-            return cjt_fft_pow2(base + s.data, s.L > 4096 ? base + s.scratch : nullptr, s.L, s.count, s.tw, s.prec,
-                                st);
+            return cjt_fft_any(base + s.data, cjt_fft_scratch_elems(s.L, 1) ? base + s.scratch : nullptr, s.L, s.count,
+                               s.tw, s.prec, st);
         }
         case ST_RECORD:
             CJT_CUDA_TRY(cudaEventRecord(g->ev[pair][s.event], st));
@@ -527,7 +532,7 @@ int64_t plan_wave(cjt_group_s *g, const std::vector<int> &items, const std::vect
             const int64_t bytes = c.total * c.L * prec_cbytes(c.prec);
             c.off = (size_t)off;
             off = align256(off + bytes);
-            if (c.L > 4096) scr = std::max(scr, bytes);
+            if (cjt_fft_scratch_elems(c.L, 1)) scr = std::max(scr, bytes);
         }
     };
     place(asy_f, scr_side);
@@ -648,7 +653,8 @@ GDesc make_desc(const cjt_plan_s *p, int dir, const double *in, double *out) {
     d.G = p->Gf;
     d.Ng = gw.Ng;
     d.L = f ? p->Lf : p->Li;
-    d.logL = ilog2_exact(std::max<int64_t>(d.L, 1));
+    d.l3 = cjt_is_3pow2(d.L) ? 1 : 0;
+    d.logL = ilog2_exact(std::max<int64_t>(d.l3 ? d.L / 3 : d.L, 1));
     d.M = p->M;
     d.nblk = gw.nblk;
     d.nq = gw.nblk * p->M;
@@ -715,7 +721,7 @@ int cjt_group_create(cjt_group_t *out, const std::vector<int> &idx, const cjt_pl
         auto est = [&]() {
             int64_t scr[2] = {0, 0};
             for (auto &c : cls)
-                if (c.L > 4096) scr[c.kind >> 1] = std::max(scr[c.kind >> 1], c.bytes);
+                if (cjt_fft_scratch_elems(c.L, 1)) scr[c.kind >> 1] = std::max(scr[c.kind >> 1], c.bytes);
             return sum + 256 * (int64_t)cls.size() + scr[0] + scr[1] + 1024;
         };
         auto add_cls = [&](std::vector<Acc> &v, int kind, int64_t L, int prec, int64_t bytes) {

@@ -194,7 +194,15 @@ struct Twiddles {
     const void *stw = nullptr;
     const void *fma = nullptr;   // FP64 only: TwFma tables of the decimation-in-time stages
     int lmax = 0;                // the stage tables cover block lengths up to 2^lmax
+    const void *tw3 = nullptr;   // omega_{Ltab3}^k, k < Ltab3, for the radix-3 step of lengths 3 2^b
+    int64_t Ltab3 = 0;           // a multiple of every such length (0: none)
 };
+// L = 3 2^b (b >= 0): transforms of such lengths take one radix-3 step and power-of-two FFTs
+__host__ __device__ inline bool cjt_is_3pow2(int64_t L) {
+    if (L < 3 || L % 3 != 0) return false;
+    const int64_t r = L / 3;
+    return (r & (r - 1)) == 0;
+}
 __host__ __device__ inline int64_t stw_base(int lb) { return 3 * ((1LL << (lb - 2)) - 1); }
 
 // Radix-4 decimation-in-time twiddles in fused multiply-add form (FP64 transforms).  For a
@@ -269,6 +277,8 @@ struct cjt_plan_s {
     void *d_twdf = nullptr;       // dfc[Ltab]
     void *d_stw64 = nullptr, *d_stw32 = nullptr, *d_stwdf = nullptr;   // stage tables (Twiddles)
     void *d_twfma = nullptr;      // TwFma tables (FP64 decimation-in-time stages)
+    int64_t Ltab3 = 0;            // radix-3 twiddles omega_{Ltab3}^k (grids 3 2^a): 4G, or 2G
+    void *d_tw3_64 = nullptr, *d_tw3_32 = nullptr, *d_tw3df = nullptr;
     int stw_lmax = 0;             // the stage tables' top level (block length 2^stw_lmax)
     Twiddles twiddles(int prec) const {
         Twiddles t;
@@ -277,6 +287,8 @@ struct cjt_plan_s {
         t.stw = prec == PREC_F32 ? d_stw32 : prec == PREC_DF ? d_stwdf : d_stw64;
         t.fma = prec == PREC_F64 ? d_twfma : nullptr;
         t.lmax = stw_lmax;
+        t.tw3 = prec == PREC_F32 ? d_tw3_32 : prec == PREC_DF ? d_tw3df : d_tw3_64;
+        t.Ltab3 = Ltab3;
         return t;
     }
     int prec_asy = PREC_F64;      // element type of the asymptotic transforms
@@ -581,6 +593,8 @@ inline int64_t cjt_asy_nM(const AsyExp &e, int M, double eps) {
 // launchers implemented in the .cu files
 // ---------------------------------------------------------------------------
 int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &tw, int prec, cudaStream_t st);
+// L a power of two or 3 2^b (scratch of cjt_fft_scratch_elems(L, batch) elements)
+int cjt_fft_any(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &tw, int prec, cudaStream_t st);
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch);
 int cjt_fft_prime();
 // Bluestein length (0 when L is a power of two)

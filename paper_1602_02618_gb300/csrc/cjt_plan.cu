@@ -987,6 +987,14 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
 // Twiddle tables of a plan (p->Ltab set): omega_{Ltab}^k in FP64 and in the precision pa
 // of its asymptotic transforms, the stage tables and the FP64 fused multiply-add forms.
 int cjt_build_twiddles(cjt_plan_s *p, int pa, cudaStream_t st) {
+    if (p->Ltab3 > 0) {
+        TRY(dalloc(p, (double2 **)&p->d_tw3_64, p->Ltab3));
+        if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_tw3_32, p->Ltab3));
+        if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_tw3df, p->Ltab3));   // dfc: 16 bytes
+        k_twiddles<<<blocks_for(p->Ltab3, 256), 256, 0, st>>>(p->Ltab3, (double2 *)p->d_tw3_64, (float2 *)p->d_tw3_32,
+                                                              (dfc *)p->d_tw3df);
+        CJT_CUDA_TRY(cudaGetLastError());
+    }
     TRY(dalloc(p, (double2 **)&p->d_tw64, p->Ltab));
     if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_tw32, p->Ltab));
     if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_twdf, p->Ltab));   // dfc: 16 bytes
@@ -1064,9 +1072,16 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     {
         const bool pow2 = (N & (N - 1)) == 0;
         int64_t G = N;
-        if (p->opts.grid == 1 || (p->opts.grid == 0 && !pow2)) {
-            G = 1;
-            while (G < N) G <<= 1;
+        int64_t G2 = 1;
+        while (G2 < N) G2 <<= 1;
+        if (p->opts.grid == 1) {
+            G = G2;
+        } else if (p->opts.grid == 0 && !pow2 && !cjt_is_3pow2(N)) {
+            // the least G >= N of the forms 2^a and 3 2^a: transforms of lengths 2G and 4G
+            // then take one radix-3 step at most, and the grid is at most 4/3 N
+            int64_t G3 = 3;
+            while (G3 < N) G3 <<= 1;
+            G = std::min(G2, G3);
         }
         p->Gf = p->Gi = G;
     }
@@ -1100,8 +1115,23 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         if (p->npair_i) used.push_back({&p->dft_i, p->npair_i});
         used.push_back({&p->dft_cc, 1});
     }
+    // twiddle tables: powers of two up to the longest power-of-two (sub-)transform, and for
+    // lengths 3 2^b the radix-3 table of the longest such length (a multiple of the others)
     p->Ltab = 2;
-    for (auto &u : used) p->Ltab = std::max(p->Ltab, u.first->fft_len());
+    p->Ltab3 = 0;
+    for (auto &u : used) {
+        const Dft &d = *u.first;
+        if (d.P) {
+            p->Ltab = std::max(p->Ltab, d.P);
+        } else if (cjt_is_3pow2(d.L)) {
+            p->Ltab = std::max(p->Ltab, d.L / 3);
+            p->Ltab3 = std::max(p->Ltab3, d.L);
+        } else {
+            p->Ltab = std::max(p->Ltab, d.L);
+        }
+    }
+    for (auto &u : used)
+        if (!u.first->P && cjt_is_3pow2(u.first->L) && p->Ltab3 % u.first->L != 0) return CJT_EUNSUPPORTED;
     TRY(cjt_build_twiddles(p, pa, st));
     int64_t work = 0, scratch = 0;
     for (auto &u : used) {

@@ -200,18 +200,28 @@ def test_identity_at_N0(cjt):
     assert run_inv(cjt, p, np.array([-1.5]))[0] == -1.5
 
 
-@pytest.mark.parametrize("grid", [0, -1])
+def default_grid(N):
+    """The least G >= N of the forms 2^a and 3 2^a."""
+    G2 = 1 << (N - 1).bit_length() if N > 1 else 1
+    G3 = 3
+    while G3 < N:
+        G3 <<= 1
+    return min(G2, G3)
+
+
+@pytest.mark.parametrize("grid", [0, 1, -1])
 @pytest.mark.parametrize("alpha,beta", [(0.1, -0.3), (0.45, 0.45), (-0.5, 0.5)])
 @pytest.mark.parametrize("N", [3, 5, 6, 7, 100, 1000, 1023, 1025, 3001, 10007])
 def test_general_N_matches_oracle(cjt, orc, N, alpha, beta, grid):
-    """N not a power of two: by default the evaluation runs on the power-of-two Lobatto grid
-    G >= N (grid 0); on the paper's grid (grid -1) the DCT-I/DST-I sums go through
-    Bluestein's chirp-z form."""
+    """N not a power of two: by default the evaluation runs on the least Lobatto grid G >= N
+    of the forms 2^a and 3 2^a (grid 0: transforms of lengths 3 2^b take one radix-3 step),
+    on the power-of-two grid with grid 1; on the paper's grid (grid -1) the DCT-I/DST-I sums
+    go through Bluestein's chirp-z form unless N is 3 2^a."""
     c = inputs.decaying_coefficients(N, 1.0, inputs.BASE_SEED + 3 * N)
     plan = cjt.Plan(N, alpha, beta, grid=grid)
     info = plan.info()
-    G = 1 << (N - 1).bit_length()
-    assert info["grid_fwd"] == (G if grid == 0 else N) and info["grid_inv"] == 2 * info["grid_fwd"]
+    want = {0: default_grid(N), 1: 1 << (N - 1).bit_length(), -1: N}[grid]
+    assert info["grid_fwd"] == want and info["grid_inv"] == 2 * info["grid_fwd"]
     assert info["fft_len_fwd"] == 2 * info["grid_fwd"] and info["fft_len_inv"] == 2 * info["grid_inv"]
     assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, alpha, beta))) <= TOL * l1(c)
     assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, alpha, beta))) <= TOL * l1(c)
@@ -233,11 +243,12 @@ def test_power_of_two_grid_forced(cjt, orc, N, opts):
 
 def test_power_of_two_grid_large(cjt, orc):
     """N = 40000 (grid 65536) and N = 70001 (grid 131072): the power-of-two grid against the
-    paper's grid (Bluestein) and sampled oracle values; N = 3 * 2^20 + 1 plans on 2^22."""
+    paper's grid (Bluestein) and sampled oracle values; N = 3 * 2^20 + 1 plans on 2^22 by
+    default (the smaller of 2^22 and 3 2^21)."""
     for N in (40000, 70001):
         c = inputs.decaying_coefficients(N, 1.5, 5000 + N)
         a, b = 0.3, -0.1
-        pg = cjt.Plan(N, a, b, M=13, rec_store=1)
+        pg = cjt.Plan(N, a, b, M=13, rec_store=1, grid=1)
         pb = cjt.Plan(N, a, b, M=13, rec_store=1, grid=-1)
         assert pg.info()["grid_fwd"] == 1 << (N - 1).bit_length() and pb.info()["grid_fwd"] == N
         fg = run_fwd(cjt, pg, c)
@@ -248,6 +259,13 @@ def test_power_of_two_grid_large(cjt, orc):
         assert np.max(np.abs(run_inv(cjt, pg, fg) - c)) <= TOL * l1(c)
     big = cjt.Plan(3 * (1 << 20) + 1, 0.1, 0.2, directions=cjt.CJT_FWD, M=13)
     assert big.info()["grid_fwd"] == 1 << 22
+    # and a grid 3 2^a at large size: N = 40000 plans on 49152 = 3 2^14 by default
+    c = inputs.decaying_coefficients(40000, 1.5, 5000 + 40000)
+    p3 = cjt.Plan(40000, 0.3, -0.1, M=13, rec_store=1)
+    p2 = cjt.Plan(40000, 0.3, -0.1, M=13, rec_store=1, grid=1)
+    assert p3.info()["grid_fwd"] == 3 << 14 and p3.info()["fft_len_inv"] == 3 << 16
+    assert np.max(np.abs(run_fwd(cjt, p3, c) - run_fwd(cjt, p2, c))) <= TOL * l1(c)
+    assert np.max(np.abs(run_inv(cjt, p3, c) - run_inv(cjt, p2, c))) <= TOL * l1(c)
     with pytest.raises(cjt.CJTError) as e:
         cjt.Plan(3 * (1 << 20) + 1, 0.1, 0.2, grid=-1)
     assert e.value.code == cjt.CJT_EUNSUPPORTED
