@@ -119,6 +119,7 @@ void free_plan(cjt_plan_s *p) {
     for (auto e : p->prof_pool) cudaEventDestroy(e);
     for (void *v : p->allocs) cudaFree(v);
     p->allocs.clear();
+    cjt_release_twiddles(p);
     if (p->done) cudaEventDestroy(p->done);
     delete p;
 }

@@ -88,7 +88,7 @@ extern "C" int cjt_microbench_fma(int kind, double *flops, void *stream) {
 // Transform microbenchmark for the autotuner: `batch` transforms of length 2^log2L in the
 // precision's transform type (complex double, float or double-float), under the current
 // cjt_fft_set_config of that class, timed with CUDA events on `stream` (average of `reps`
-// after one warm-up).  The tables are built as a plan builds them; the buffers are freed
+// after one warm-up).  The tables are taken as a plan takes them; the buffers are freed
 // before returning.
 extern "C" int cjt_fft_time(int precision, int log2L, int64_t batch, int reps, double *ms, void *stream) {
     if (!ms || log2L < 1 || log2L > 22 || batch < 1 || reps < 1) return CJT_EINVAL;
@@ -111,6 +111,7 @@ extern "C" int cjt_fft_time(int precision, int log2L, int64_t batch, int reps, d
         if (e1) cudaEventDestroy(e1);
         for (void *v : tmp.allocs) cudaFree(v);
         tmp.allocs.clear();
+        cjt_release_twiddles(&tmp);
     };
     if (!rc && cudaMalloc(&data, bytes) != cudaSuccess) rc = CJT_ENOMEM;
     if (!rc && L > 4096 && cudaMalloc(&scratch, bytes) != cudaSuccess) rc = CJT_ENOMEM;

@@ -92,10 +92,10 @@ template <typename V, typename R>
 __global__ void k_asy_pack_inv_s(int64_t Ng, int64_t L, int M, int nq, const int *__restrict__ box3,
                                  const double *__restrict__ u, const double *__restrict__ v,
                                  const double *__restrict__ scale, const double *__restrict__ g, V *__restrict__ buf) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= L) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // row, 0 <= i < Ng = L / 2
+    if (i >= Ng) return;
     const cjt_kern::PairScale ps = cjt_kern::pair_scale(blockIdx.y, M, nq, scale);
-    cjt_kern::asy_pack_inv_elem<V, R>(idx, blockIdx.y, ps, Ng, L, box3, u, v, g, buf);
+    cjt_kern::asy_pack_inv_elem<V, R>(i, blockIdx.y, ps, Ng, L, box3, u, v, g, buf);
 }
 
 // ---------------------------------------------------------------------------
@@ -573,7 +573,8 @@ int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, doubl
         if (sr != st) CJT_CUDA_TRY(cudaStreamWaitEvent(sr, oc->fork, 0));
     }
     if (nq > 0) {
-        dim3 gp(blocks_for(L, 256), p->npair_i);
+        // the double-float pack takes one element per thread, the others one row (two elements)
+        dim3 gp(blocks_for(dfm ? L : Ng, 256), p->npair_i);
         StageTimer tm(p, sa, CJT_STAGE_INV_PACK);
         if (dfm)
             k_asy_pack_inv_df<<<gp, 256, 0, sa>>>(Ng, L, nq, (const dfs *)gw.d_Us, (const dfs *)gw.d_Vs, gdf,

@@ -118,11 +118,12 @@ template <> struct Elem<OP_PACK_FWD> {
                                           (V *)d.fft);
     }
 };
+// one element per row i < Ng = L / 2 of each pair (the row's two transform inputs)
 template <> struct Elem<OP_PACK_INV> {
-    static __host__ __device__ int64_t size(const GDesc &d) { return (int64_t)d.npair * d.L; }
+    static __host__ __device__ int64_t size(const GDesc &d) { return (int64_t)d.npair * d.Ng; }
     template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t idx, PairCache &pc) {
-        const int p = pair_of(d, idx);
-        cjt_kern::asy_pack_inv_elem<V, R>(idx - (int64_t)p * d.L, p, pc.of(p, d), d.Ng, d.L, d.box, d.u, d.v, d.g,
+        const int p = d.l3 ? (int)((idx >> (d.logL - 1)) / 3) : (int)(idx >> (d.logL - 1));
+        cjt_kern::asy_pack_inv_elem<V, R>(idx - (int64_t)p * d.Ng, p, pc.of(p, d), d.Ng, d.L, d.box, d.u, d.v, d.g,
                                           (V *)d.fft);
     }
 };

@@ -280,6 +280,7 @@ struct cjt_plan_s {
     int64_t Ltab3 = 0;            // radix-3 twiddles omega_{Ltab3}^k (grids 3 2^a): 4G, or 2G
     void *d_tw3_64 = nullptr, *d_tw3_32 = nullptr, *d_tw3df = nullptr;
     int stw_lmax = 0;             // the stage tables' top level (block length 2^stw_lmax)
+    void *twc = nullptr;          // the shared twiddle tables the fields above point into
     Twiddles twiddles(int prec) const {
         Twiddles t;
         t.Ltab = Ltab;
@@ -607,7 +608,11 @@ int64_t cjt_dft_work_bytes(const Dft &d, int64_t batch);
 int64_t cjt_dft_scratch_bytes(const Dft &d, int64_t batch);
 
 int cjt_plan_build(cjt_plan_s *p, cudaStream_t st);
+// The plan's twiddle tables (from p->Ltab, p->Ltab3 and the transform precision pa): taken
+// from a per-device cache of tables shared by plans, built on `st` when absent.  A plan
+// that took tables gives them back with cjt_release_twiddles.
 int cjt_build_twiddles(cjt_plan_s *p, int pa, cudaStream_t st);
+void cjt_release_twiddles(cjt_plan_s *p);
 Workspace cjt_carve(const cjt_plan_s *p, void *base);
 int cjt_exec_forward(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st);
 int cjt_exec_inverse(cjt_plan_s *p, const Workspace &ws, const double *in, double *out, cudaStream_t st);

@@ -298,21 +298,20 @@ __device__ __forceinline__ void asy_pack_fwd_elem(int64_t n, int p, const PairSc
 
 // Inverse: item q contributes s_q u_m(theta_i) g_i / 2 (real) and +-s_q v_m(theta_i) g_i / 2
 // (imaginary) on its box's rows; FP64 transforms form (u_m g_i) s_q / 2, the same value.
+// The transform input H(idx) = (z(idx) + conj z(L - idx)) / 2, L = 2 Ng, takes row i at
+// idx = i and at idx = L - i with the imaginary parts negated, so one call computes row i's
+// products once and writes both: rows 1 .. Ng - 1 at i and L - i; the call for i = 0 also
+// writes rows 0 and Ng (the ends of the grid, in no box).
 template <typename V, typename R>
-__device__ __forceinline__ void asy_pack_inv_elem(int64_t idx, int p, const PairScale &ps, int64_t Ng, int64_t L,
-                                                  const int *__restrict__ box3, const double *__restrict__ u,
-                                                  const double *__restrict__ v, const double *__restrict__ g,
-                                                  V *__restrict__ buf) {
-    // H(idx) = (z(idx) + conj z(L - idx)) / 2: the box rows lie in [1, Ng - 1]
-    const bool lo = idx <= Ng;
-    const int64_t i = lo ? idx : L - idx;
+__device__ __forceinline__ void inv_pack_row(int64_t i, const PairScale &ps, int64_t Ng, const int *__restrict__ box3,
+                                             const double *__restrict__ u, const double *__restrict__ v,
+                                             const double *__restrict__ g, V &lo, V &hi) {
     const bool in0 = i >= box3[3 * ps.k0 + 1] && i <= box3[3 * ps.k0 + 2];
     const bool in1 = ps.m1 >= 0 && i >= box3[3 * ps.k1 + 1] && i <= box3[3 * ps.k1 + 2];
-    V o;
     if constexpr (std::is_same<R, double>::value) {
         // every load is issued whether or not the row is in the box (0 <= i <= Ng, so it is
-        // within the tables), so that the loads of consecutive elements overlap; the box
-        // selects afterwards
+        // within the tables), so that the loads of consecutive rows overlap; the box selects
+        // afterwards
         const int m1 = ps.m1 >= 0 ? ps.m1 : ps.m0;
         const double gi = __ldg(g + i);
         const double a0 = __ldg(u + ps.m0 * (Ng + 1) + i), b0 = __ldg(v + ps.m0 * (Ng + 1) + i);
@@ -320,32 +319,51 @@ __device__ __forceinline__ void asy_pack_inv_elem(int64_t idx, int p, const Pair
         double h0r = 0.0, h0i = 0.0, h1r = 0.0, h1i = 0.0;
         if (in0) {
             h0r = mul_pow2(a0 * gi, ps.e0 - 1, 0.5 * ps.s0);
-            h0i = neg_if(mul_pow2(b0 * gi, ps.e0 - 1, 0.5 * ps.s0), !lo);
+            h0i = mul_pow2(b0 * gi, ps.e0 - 1, 0.5 * ps.s0);
         }
         if (in1) {
             h1r = mul_pow2(a1 * gi, ps.e1 - 1, 0.5 * ps.s1);
-            h1i = neg_if(mul_pow2(b1 * gi, ps.e1 - 1, 0.5 * ps.s1), !lo);
+            h1i = mul_pow2(b1 * gi, ps.e1 - 1, 0.5 * ps.s1);
         }
-        o.x = h0r - h1i;
-        o.y = h0i + h1r;
+        lo.x = h0r - h1i;
+        lo.y = h0i + h1r;
+        hi.x = h0r + h1i;
+        hi.y = h1r - h0i;
     } else {
         const R gi = (R)g[i];
-        const R sgn = lo ? (R)1 : (R)-1;
         const double sc0 = 0.5 * ps.s0;
         const R u0 = (R)(in0 ? sc0 * u[ps.m0 * (Ng + 1) + i] : 0.0), v0 = (R)(in0 ? sc0 * v[ps.m0 * (Ng + 1) + i] : 0.0);
-        const R h0r = u0 * gi, h0i = sgn * v0 * gi;
+        const R h0r = u0 * gi, h0i = v0 * gi;
         R h1r = 0, h1i = 0;
         if (ps.m1 >= 0) {
             const double sc1 = 0.5 * ps.s1;
             const R u1 = (R)(in1 ? sc1 * u[ps.m1 * (Ng + 1) + i] : 0.0);
             const R v1 = (R)(in1 ? sc1 * v[ps.m1 * (Ng + 1) + i] : 0.0);
             h1r = u1 * gi;
-            h1i = sgn * v1 * gi;
+            h1i = v1 * gi;
         }
-        o.x = h0r - h1i;
-        o.y = h0i + h1r;
+        lo.x = h0r - h1i;
+        lo.y = h0i + h1r;
+        hi.x = h0r + h1i;
+        hi.y = h1r - h0i;
     }
-    buf[(int64_t)p * L + idx] = o;
+}
+// pair p's transform input at rows i (0 <= i < Ng) and L - i, and at 0 and Ng for i = 0
+template <typename V, typename R>
+__device__ __forceinline__ void asy_pack_inv_elem(int64_t i, int p, const PairScale &ps, int64_t Ng, int64_t L,
+                                                  const int *__restrict__ box3, const double *__restrict__ u,
+                                                  const double *__restrict__ v, const double *__restrict__ g,
+                                                  V *__restrict__ buf) {
+    V *row = buf + (int64_t)p * L;
+    V lo, hi;
+    inv_pack_row<V, R>(i, ps, Ng, box3, u, v, g, lo, hi);
+    row[i] = lo;
+    if (i > 0) {
+        row[L - i] = hi;
+    } else {
+        inv_pack_row<V, R>(Ng, ps, Ng, box3, u, v, g, lo, hi);
+        row[Ng] = lo;
+    }
 }
 
 // transform output components as doubles

@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "cjt_df.cuh"
 #include "cjt_internal.cuh"
@@ -986,46 +988,171 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
 
 // Twiddle tables of a plan (p->Ltab set): omega_{Ltab}^k in FP64 and in the precision pa
 // of its asymptotic transforms, the stage tables and the FP64 fused multiply-add forms.
-int cjt_build_twiddles(cjt_plan_s *p, int pa, cudaStream_t st) {
-    if (p->Ltab3 > 0) {
-        TRY(dalloc(p, (double2 **)&p->d_tw3_64, p->Ltab3));
-        if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_tw3_32, p->Ltab3));
-        if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_tw3df, p->Ltab3));   // dfc: 16 bytes
-        k_twiddles<<<blocks_for(p->Ltab3, 256), 256, 0, st>>>(p->Ltab3, (double2 *)p->d_tw3_64, (float2 *)p->d_tw3_32,
-                                                              (dfc *)p->d_tw3df);
+// ------------------------------------------------------------------------
+// Twiddle tables shared by plans.  They depend only on (device, Ltab, Ltab3, transform
+// precision), so plans of the same lengths take one copy: a plan built while a copy exists
+// waits for its construction on its own stream (an event) and launches nothing.  Unused
+// copies stay cached up to CJT_TWIDDLE_CACHE_MB (default 1024) and are freed least
+// recently used first beyond that.
+// ------------------------------------------------------------------------
+namespace {
+struct TwShared {
+    int dev = 0, pa = 0;
+    int64_t Ltab = 0, Ltab3 = 0;
+    void *tw64 = nullptr, *tw32 = nullptr, *twdf = nullptr;
+    void *stw64 = nullptr, *stw32 = nullptr, *stwdf = nullptr, *twfma = nullptr;
+    void *tw3_64 = nullptr, *tw3_32 = nullptr, *tw3df = nullptr;
+    int lmax = 0;
+    int64_t bytes = 0;
+    int refs = 0;
+    uint64_t last = 0;
+    cudaEvent_t ready = nullptr;
+    std::vector<void *> allocs;
+};
+std::mutex g_tw_mu;
+std::vector<TwShared *> g_tw;
+uint64_t g_tw_clock = 0;
+
+void tw_free(TwShared *e) {
+    if (e->ready) {
+        cudaEventSynchronize(e->ready);
+        cudaEventDestroy(e->ready);
+    }
+    for (void *v : e->allocs) cudaFree(v);
+    delete e;
+}
+
+template <typename T> int tw_alloc(TwShared *e, void **ptr, int64_t count) {
+    *ptr = nullptr;
+    if (count <= 0) return CJT_OK;
+    void *v = nullptr;
+    cudaError_t rc = cudaMalloc(&v, (size_t)count * sizeof(T));
+    if (rc != cudaSuccess) {
+        cjt_internal_set_cuda_error(rc, "cudaMalloc");
+        return CJT_ENOMEM;
+    }
+    e->allocs.push_back(v);
+    e->bytes += (int64_t)count * (int64_t)sizeof(T);
+    *ptr = v;
+    return CJT_OK;
+}
+
+int tw_build(TwShared *e, cudaStream_t st) {
+    const int pa = e->pa;
+    if (e->Ltab3 > 0) {
+        TRY(tw_alloc<double2>(e, &e->tw3_64, e->Ltab3));
+        if (pa == PREC_F32) TRY(tw_alloc<float2>(e, &e->tw3_32, e->Ltab3));
+        if (pa == PREC_DF) TRY(tw_alloc<double2>(e, &e->tw3df, e->Ltab3));   // dfc: 16 bytes
+        k_twiddles<<<blocks_for(e->Ltab3, 256), 256, 0, st>>>(e->Ltab3, (double2 *)e->tw3_64, (float2 *)e->tw3_32,
+                                                              (dfc *)e->tw3df);
         CJT_CUDA_TRY(cudaGetLastError());
     }
-    TRY(dalloc(p, (double2 **)&p->d_tw64, p->Ltab));
-    if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_tw32, p->Ltab));
-    if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_twdf, p->Ltab));   // dfc: 16 bytes
-    k_twiddles<<<blocks_for(p->Ltab, 256), 256, 0, st>>>(p->Ltab, (double2 *)p->d_tw64, (float2 *)p->d_tw32,
-                                                         (dfc *)p->d_twdf);
+    TRY(tw_alloc<double2>(e, &e->tw64, e->Ltab));
+    if (pa == PREC_F32) TRY(tw_alloc<float2>(e, &e->tw32, e->Ltab));
+    if (pa == PREC_DF) TRY(tw_alloc<double2>(e, &e->twdf, e->Ltab));   // dfc: 16 bytes
+    k_twiddles<<<blocks_for(e->Ltab, 256), 256, 0, st>>>(e->Ltab, (double2 *)e->tw64, (float2 *)e->tw32,
+                                                         (dfc *)e->twdf);
     CJT_CUDA_TRY(cudaGetLastError());
-    {
-        int logLtab = 0;
-        while ((1LL << logLtab) < p->Ltab) ++logLtab;
-        // stage tables to block length 2^13: one-pass transforms of up to 8192 points
-        // (cjt_fft_set_config)
-        const int lmax = std::min(13, logLtab);
-        p->stw_lmax = lmax;
-        if (lmax >= 2) {
-            const int64_t n = stw_base(lmax + 1);
-            TRY(dalloc(p, (double2 **)&p->d_stw64, n));
-            if (pa == PREC_F32) TRY(dalloc(p, (float2 **)&p->d_stw32, n));
-            if (pa == PREC_DF) TRY(dalloc(p, (double2 **)&p->d_stwdf, n));   // dfc: 16 bytes
-            k_stage_twiddles<<<blocks_for(n, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)p->d_tw64,
-                                                                 (double2 *)p->d_stw64, (float2 *)p->d_stw32,
-                                                                 (dfc *)p->d_stwdf);
-            CJT_CUDA_TRY(cudaGetLastError());
-            // every plan has FP64 transforms (final DCT-I, inverse front end)
-            const int64_t nf = twfma_base(lmax + 1);
-            TRY(dalloc(p, (TwFma **)&p->d_twfma, nf));
-            k_fma_twiddles<<<blocks_for(nf, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)p->d_tw64,
-                                                               (TwFma *)p->d_twfma);
-            CJT_CUDA_TRY(cudaGetLastError());
-        }
+    int logLtab = 0;
+    while ((1LL << logLtab) < e->Ltab) ++logLtab;
+    // stage tables to block length 2^13: one-pass transforms of up to 8192 points
+    // (cjt_fft_set_config)
+    const int lmax = std::min(13, logLtab);
+    e->lmax = lmax;
+    if (lmax >= 2) {
+        const int64_t n = stw_base(lmax + 1);
+        TRY(tw_alloc<double2>(e, &e->stw64, n));
+        if (pa == PREC_F32) TRY(tw_alloc<float2>(e, &e->stw32, n));
+        if (pa == PREC_DF) TRY(tw_alloc<double2>(e, &e->stwdf, n));   // dfc: 16 bytes
+        k_stage_twiddles<<<blocks_for(n, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)e->tw64,
+                                                             (double2 *)e->stw64, (float2 *)e->stw32,
+                                                             (dfc *)e->stwdf);
+        CJT_CUDA_TRY(cudaGetLastError());
+        // every plan has FP64 transforms (final DCT-I, inverse front end)
+        const int64_t nf = twfma_base(lmax + 1);
+        TRY(tw_alloc<TwFma>(e, &e->twfma, nf));
+        k_fma_twiddles<<<blocks_for(nf, 256), 256, 0, st>>>(lmax, logLtab, (const double2 *)e->tw64,
+                                                           (TwFma *)e->twfma);
+        CJT_CUDA_TRY(cudaGetLastError());
     }
+    CJT_CUDA_TRY(cudaEventCreateWithFlags(&e->ready, cudaEventDisableTiming));
+    CJT_CUDA_TRY(cudaEventRecord(e->ready, st));
     return CJT_OK;
+}
+
+int64_t tw_cache_cap() {
+    const char *v = getenv("CJT_TWIDDLE_CACHE_MB");
+    const long long mb = v ? atoll(v) : 1024;
+    return (int64_t)std::max(0LL, mb) << 20;
+}
+
+// with g_tw_mu held: free unused copies, least recently used first, beyond the cap
+void tw_trim_locked() {
+    const int64_t cap = tw_cache_cap();
+    for (;;) {
+        int64_t unused = 0;
+        TwShared *victim = nullptr;
+        for (TwShared *e : g_tw) {
+            if (e->refs > 0) continue;
+            unused += e->bytes;
+            if (!victim || e->last < victim->last) victim = e;
+        }
+        if (!victim || unused <= cap) return;
+        g_tw.erase(std::find(g_tw.begin(), g_tw.end(), victim));
+        tw_free(victim);
+    }
+}
+}  // namespace
+
+int cjt_build_twiddles(cjt_plan_s *p, int pa, cudaStream_t st) {
+    int dev = 0;
+    CJT_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    TwShared *e = nullptr;
+    for (TwShared *c : g_tw)
+        if (c->dev == dev && c->pa == pa && c->Ltab == p->Ltab && c->Ltab3 == p->Ltab3) e = c;
+    if (e) {
+        CJT_CUDA_TRY(cudaStreamWaitEvent(st, e->ready, 0));
+    } else {
+        e = new TwShared;
+        e->dev = dev;
+        e->pa = pa;
+        e->Ltab = p->Ltab;
+        e->Ltab3 = p->Ltab3;
+        const int rc = tw_build(e, st);
+        if (rc) {
+            cudaStreamSynchronize(st);
+            tw_free(e);
+            return rc;
+        }
+        g_tw.push_back(e);
+    }
+    ++e->refs;
+    e->last = ++g_tw_clock;
+    p->twc = e;
+    p->d_tw64 = e->tw64;
+    p->d_tw32 = e->tw32;
+    p->d_twdf = e->twdf;
+    p->d_stw64 = e->stw64;
+    p->d_stw32 = e->stw32;
+    p->d_stwdf = e->stwdf;
+    p->d_twfma = e->twfma;
+    p->d_tw3_64 = e->tw3_64;
+    p->d_tw3_32 = e->tw3_32;
+    p->d_tw3df = e->tw3df;
+    p->stw_lmax = e->lmax;
+    p->device_bytes += e->bytes;   // counted in every plan that uses them (an upper bound)
+    return CJT_OK;
+}
+
+void cjt_release_twiddles(cjt_plan_s *p) {
+    if (!p->twc) return;
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    TwShared *e = (TwShared *)p->twc;
+    p->twc = nullptr;
+    --e->refs;
+    e->last = ++g_tw_clock;
+    tw_trim_locked();
 }
 
 int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {

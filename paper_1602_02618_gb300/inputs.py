@@ -122,3 +122,13 @@ def continuous_coefficients(N: int, seed: int = BASE_SEED) -> np.ndarray:
     right; (n+1) so that c_0 is finite)."""
     n = np.arange(N + 1, dtype=np.float64)
     return rng(seed).uniform(-1.0, 1.0, N + 1) / _power(n + 1.0, 2)
+
+
+SHIFTED_PARAMETERS = ((1.5, 0.25), (0.1, 1.3))
+
+
+def shifted_workload(N: int = 1 << 16, seed: int = BASE_SEED):
+    """Transforms with one parameter in (1/2, 3/2] (reached by one integer shift, Sec. 1.2):
+    [(N, alpha, beta, c)] for each pair of SHIFTED_PARAMETERS, c_n = g_n/(n+1)^1.5."""
+    c = decaying_coefficients(N, 1.5, seed + 77)
+    return [(N, a, b, c) for a, b in SHIFTED_PARAMETERS]

@@ -11,6 +11,8 @@ Items:
     (alpha, beta) and coefficients c_n = g_n/(n+1)^1.5): the forward transform
     (Eq. "CJT") of c, and the inverse transform (Eq. "iCJT") of the same vector
     read as Chebyshev coefficients; double-double oracle, every output entry;
+  * the inverse transform at N = 2^16 for the two shifted parameter pairs (one of
+    alpha, beta in (1/2, 3/2], Sec. 1.2), double-double oracle, every output entry;
   * the first two items of the large mixed-precision workload (64 x N = 2^20):
     item 0 (forward) by the double-double oracle, item 1 (inverse) by the
     plain-double oracle (orc_inverse_f64; the double-double inverse at 2^20 takes
@@ -21,7 +23,8 @@ Items:
 An empty `idx` array means the fixture holds every output entry in order.
 
 Run:  python tests/golden/make_fullsize.py [--only NAME ...] [--threads T]
-Fixture names: fwd_N4096 ... inv_N262144, fwd_N1048576, inv_N1048576.
+Fixture names: fwd_N4096 ... inv_N262144, shift0_inv_N65536, shift1_inv_N65536,
+fwd_N1048576, inv_N1048576.
 """
 import argparse
 import hashlib
@@ -59,6 +62,9 @@ def items():
         desc = "single-transform workload, c_n = g_n/(n+1)^1.5"
         out.append(("fwd_N%d" % N, N, a, b, 1, c, "double-double", desc))
         out.append(("inv_N%d" % N, N, a, b, -1, c, "double-double", desc + " read as Chebyshev coefficients"))
+    for t, (N, a, b, c) in enumerate(inputs.shifted_workload()):
+        out.append(("shift%d_inv_N%d" % (t, N), N, a, b, -1, c, "double-double",
+                    "shifted parameters (%g, %g), c_n = g_n/(n+1)^1.5, read as Chebyshev coefficients" % (a, b)))
     big = inputs.mixed_large_workload(2, BIG_N, seed=inputs.BASE_SEED)
     (N0, a0, b0, d0, c0), (N1, a1, b1, d1, c1) = big
     desc = "mixed-precision workload (64 x N = 2^20), item %d, c_n = g_n/(n+1)"

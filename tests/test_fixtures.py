@@ -73,6 +73,24 @@ def test_inverse_fixture(orc, N):
         assert abs(lhs - rhs) <= 4e-16 * float(np.abs(out * P).sum()) + 1e-15 * np.abs(c).sum()
 
 
+@pytest.mark.parametrize("t", [0, 1])
+def test_shifted_inverse_fixture(orc, t):
+    """Inverse at N = 2^16 with one parameter in (1/2, 3/2]: the same identities."""
+    N, a, b, c = inputs.shifted_workload()[t]
+    fx = load("shift%d_inv_N%d" % (t, N))
+    assert str(fx["input_sha256"]) == digest(c) and int(fx["N"]) == N and int(fx["direction"]) == -1
+    assert float(fx["alpha"]) == a and float(fx["beta"]) == b and fx["idx"].size == 0
+    out = fx["out"]
+    assert out.shape == (N + 1,)
+    mu = orc.moments(N, a, b)
+    assert abs(out[0] - np.dot(c, mu) / mu[0]) <= 1e-15 * np.abs(c).sum()
+    for j in inputs.rng(N + 17 + t).integers(N // 8, 7 * N // 8, 6):
+        lhs = orc.jacobi_series(out, a, b, [int(j)], N)[0]
+        rhs = orc.cheb_series(c, [int(j)], N)[0]
+        P = orc.jacobi_values(N, a, b, int(j), N)
+        assert abs(lhs - rhs) <= 4e-16 * float(np.abs(out * P).sum()) + 1e-15 * np.abs(c).sum()
+
+
 @pytest.mark.parametrize("name", ["fwd_N1048576", "inv_N1048576"])
 def test_sampled_fixtures(name):
     fx = load(name)

@@ -88,7 +88,9 @@ def test_dfloat_16384_elementwise(cjt, orc):
 @pytest.mark.parametrize("logN", [16, 18])
 def test_dfloat_full_size(cjt, orc, logN):
     """At full size: sampled value identities (double-double oracle), c_jac_0 from the
-    moments, round trips, and agreement with the FP64 GPU form."""
+    moments, the forward-then-inverse round trip, and agreement with the FP64 GPU form.
+    Every coefficient of both directions is compared with the double-double oracle at these
+    sizes by the full-size parity tests."""
     N = 1 << logN
     a, b = inputs.jacobi_parameters(inputs.BASE_SEED + 3000 + logN)
     c = inputs.decaying_coefficients(N, 1.5, inputs.BASE_SEED + 30 + logN)
@@ -101,8 +103,6 @@ def test_dfloat_full_size(cjt, orc, logN):
     mu = orc.moments(N, a, b)
     assert abs(inv[0] - np.dot(c, mu) / mu[0]) <= TOL * l1(c)
     assert np.max(np.abs(run(cjt, plan, fwd, cjt.CJT_INV) - c)) <= TOL * l1(c)
-    # inverse then forward: two transforms, each held to TOL times its own input's l1 norm
-    assert np.max(np.abs(run(cjt, plan, inv, cjt.CJT_FWD) - c)) <= TOL * (l1(c) + l1(inv))
     p64 = cjt.Plan(N, a, b, M=13, rec_store=1)
     assert np.max(np.abs(fwd - run(cjt, p64, c, cjt.CJT_FWD))) <= TOL * l1(c)
     assert np.max(np.abs(inv - run(cjt, p64, c, cjt.CJT_INV))) <= TOL * l1(c)

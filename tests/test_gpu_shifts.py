@@ -4,6 +4,9 @@ bidiagonal solve on the input) and after the inverse transform (a bidiagonal pro
 the output).  GPU (through the C ABI) against the oracle, which evaluates the definitions
 at the caller's parameters directly.
 """
+import hashlib
+import os
+
 import numpy as np
 import pytest
 
@@ -14,6 +17,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 SHIFTED = [(1.5, 0.25), (0.75, -0.4), (1.2, -0.5), (0.3, 1.5), (1.4, 1.1), (-0.5, 0.9)]
 
 
@@ -55,13 +59,14 @@ def test_shifted_parameters_match_oracle(cjt, orc, N, alpha, beta, precision):
     assert np.max(np.abs(run(cjt, plan, c, cjt.CJT_INV) - orc.inverse(c, alpha, beta))) <= TOL * l1(c)
 
 
-@pytest.mark.parametrize("alpha,beta", [(1.5, 0.25), (0.1, 1.3)])
-def test_shifted_parameters_full_size(cjt, orc, alpha, beta):
-    """N = 2^16 with stored recurrence values: sampled value identities (double-double
-    oracle), each within TOL times the sum of the absolute terms sum_n |c_n P_n(x_j)| (which
-    grows like N^(1+beta-1/2)... near x = -1 for beta > 1/2), and round trips."""
-    N = 1 << 16
-    c = inputs.decaying_coefficients(N, 1.5, inputs.BASE_SEED + 77)
+@pytest.mark.parametrize("t", [0, 1])
+def test_shifted_parameters_full_size(cjt, orc, t):
+    """N = 2^16 with stored recurrence values.  Forward: sampled value identities
+    (double-double oracle), each within TOL times the sum of the absolute terms
+    sum_n |c_n P_n(x_j)|, which grows like N^(beta+1/2) near x = -1 for beta > 1/2.
+    Inverse: every coefficient against the stored double-double oracle output.  And the
+    forward-then-inverse round trip."""
+    N, alpha, beta, c = inputs.shifted_workload()[t]
     plan = cjt.Plan(N, alpha, beta, M=13, rec_store=1)
     j = np.unique(np.concatenate([np.arange(0, 12), N - np.arange(0, 12), inputs.rng(9).integers(0, N + 1, 40)]))
     fwd = run(cjt, plan, c, cjt.CJT_FWD)
@@ -70,9 +75,9 @@ def test_shifted_parameters_full_size(cjt, orc, alpha, beta):
         scale = float(np.abs(c * orc.jacobi_values(N, alpha, beta, int(jj), N)).sum())
         assert err[q] <= TOL * max(l1(c), scale)
     assert np.max(np.abs(run(cjt, plan, fwd, cjt.CJT_INV) - c)) <= TOL * l1(c)
-    inv = run(cjt, plan, c, cjt.CJT_INV)
-    # inverse then forward: two transforms, each held to TOL times its own input's l1 norm
-    assert np.max(np.abs(run(cjt, plan, inv, cjt.CJT_FWD) - c)) <= TOL * (l1(c) + l1(inv))
+    fx = np.load(os.path.join(GOLDEN, "oracle_shift%d_inv_N%d.npz" % (t, N)))
+    assert str(fx["input_sha256"]) == hashlib.sha256(np.ascontiguousarray(c).tobytes()).hexdigest()
+    assert np.max(np.abs(run(cjt, plan, c, cjt.CJT_INV) - fx["out"])) <= TOL * l1(c)
 
 
 def test_shifted_in_a_batch_equals_alone(cjt):
