@@ -70,6 +70,16 @@ def precision_code(cjt, name):
     return {"fp64": cjt.CJT_FP64, "mixed": cjt.CJT_MIXED, "df": cjt.CJT_DFLOAT}[name]
 
 
+def default_grid(N):
+    """The Lobatto grid a plan takes by default: the least G >= N of the forms 2^a, 3 2^a."""
+    g2, g3 = 1, 3
+    while g2 < N:
+        g2 <<= 1
+    while g3 < N:
+        g3 <<= 1
+    return min(g2, g3)
+
+
 def lg2(v):
     return max(math.log2(max(v, 2)), 1.0)
 
@@ -326,8 +336,14 @@ def run_batched(ctx, big=False, steps=None):
     if not args.no_autotune:
         from paper_1602_02618_gb300 import autotune
         t0 = time.perf_counter()
-        Gs = sorted({1 << max(1, int(math.ceil(math.log2(N)))) for N, *_ in items})
-        lens = sorted({int(math.log2(2 * G)) for G in Gs} | {int(math.log2(4 * G)) for G in Gs})
+        # the power-of-two transform lengths the plans run: 2G and 4G, or their power-of-two
+        # factors when G = 3 2^a (the default grid: the least 2^a or 3 2^a >= N)
+        lens = set()
+        for N, *_ in items:
+            G = default_grid(N)
+            for L in (2 * G, 4 * G):
+                lens.add(int(math.log2(L // 3 if L % 3 == 0 else L)))
+        lens = sorted(lens)
         fft_tune = {"precision": args.precision if not big else "mixed",
                     "lengths": autotune.tune_fft(precision, lens), "tune_s": None}
         if precision != cjt.CJT_FP64:   # the DCT-I and the front end stay in FP64

@@ -575,9 +575,9 @@ int cjt_dft_setup(Dft &d, const void *tw64, int64_t Ltab, cudaStream_t st) {
     if (!d.P) return CJT_OK;
     const int64_t nw = std::max(d.S, d.K);
     double2 *w64 = nullptr, *b64 = nullptr, *scr = nullptr;
-    CJT_CUDA_TRY(cudaMallocAsync((void **)&w64, sizeof(double2) * nw, st));
-    CJT_CUDA_TRY(cudaMallocAsync((void **)&b64, sizeof(double2) * d.P, st));
-    if (d.P > 4096) CJT_CUDA_TRY(cudaMallocAsync((void **)&scr, sizeof(double2) * d.P, st));
+    CJT_CUDA_TRY(cjt_tmp_alloc((void **)&w64, sizeof(double2) * nw, st));
+    CJT_CUDA_TRY(cjt_tmp_alloc((void **)&b64, sizeof(double2) * d.P, st));
+    if (d.P > 4096) CJT_CUDA_TRY(cjt_tmp_alloc((void **)&scr, sizeof(double2) * d.P, st));
     k_blue_chirp<<<nblk(nw, 256), 256, 0, st>>>(d.L, nw, w64, nullptr);
     k_blue_b<<<nblk(d.P, 256), 256, 0, st>>>(d.S, d.K, d.P, w64, b64);
     CJT_CUDA_TRY(cudaGetLastError());

@@ -147,7 +147,6 @@ struct GridWork {
     int64_t nstate = 0;
     int64_t npartials = 0;        // recurrence partial sums (in the workspace)
     // state computation rows
-    int *d_srow = nullptr;        // rows needing states: row, J, mode, chunk_state_base, lane, nseg
     int64_t nsrow = 0;
     // inverse combine: CSR over degree segments
     int64_t nsegs = 0;
@@ -510,20 +509,26 @@ __host__ __device__ inline double cjt_asy_C(const AsyExp &e, int64_t n, int m) {
 
 // Envelope of |term m| / C_{n,m} at theta = pi i / Ng, 0 < i < Ng: Hahn's g_m (Sec. 2.2),
 // or 1/sin^{m+lambda}(theta) (App. B.1)
+// Hahn's terms at theta = pi i / Ng share powers of S = 1/sin(theta/2) and C = 1/cos(theta/2):
+// the l-th term of order m has the magnitude h_l(a) h_{m-l}(b) S^(l+a+1/2) C^(m-l+b+1/2)
+// = P_m h_l(a) h_{m-l}(b) t^l with P_m = S^(a+1/2) C^(m+b+1/2) and t = S / C = cot(theta/2),
+// so the sums over l are polynomials in t, evaluated by Horner's rule (their coefficients
+// are non-negative for |a|, |b| <= 1/2), with one exponential and two logarithms per (row, m).
 __host__ __device__ inline double cjt_asy_env(const AsyExp &e, int m, int64_t i, int64_t Ng) {
     if (e.ultra) return exp(-(m + e.lam) * log(cjt_sinpi_((double)i / (double)Ng)));
     const double half = (double)i / (2.0 * (double)Ng);
-    const double ls = log(cjt_sinpi_(half)), lc = log(cjt_cospi_(half));
+    const double sh = cjt_sinpi_(half), ch = cjt_cospi_(half);
+    const double P = exp(-(e.a + 0.5) * log(sh) - (m + e.b + 0.5) * log(ch));
+    const double t = ch / sh;
     double s = 0.0;
-    for (int l = 0; l <= m; ++l) {
-        const double coef = e.ha[l] * e.hb[m - l];
-        if (coef == 0.0) continue;
-        s += coef * exp(-(l + e.a + 0.5) * ls - (m - l + e.b + 0.5) * lc);
-    }
-    return s;
+    for (int l = m; l >= 0; --l) s = fma(s, t, e.ha[l] * e.hb[m - l]);
+    return P * s;
 }
 
-// u_m and v_m at theta = pi i / Ng, 0 < i < Ng
+// u_m and v_m at theta = pi i / Ng, 0 < i < Ng.  The l-th term's phase is
+// phi_{m,l} / pi = (a + l + 1/2)/2 - (a + b + m + 1) theta / (2 pi) = phi_{m,0} / pi + l / 2, so
+// u_m + i v_m = P_m e^{i phi_{m,0}} sum_l h_l(a) h_{m-l}(b) (i t)^l = P_m e^{i phi_{m,0}} (A + i B),
+// A and B the even and odd parts, polynomials in -t^2.
 __host__ __device__ inline void cjt_asy_uv(const AsyExp &e, int m, int64_t i, int64_t Ng, double *u, double *v) {
     if (e.ultra) {
         const double x = (double)i / (double)Ng;
@@ -535,21 +540,17 @@ __host__ __device__ inline void cjt_asy_uv(const AsyExp &e, int m, int64_t i, in
         return;
     }
     const double half = (double)i / (2.0 * (double)Ng);
-    const double ls = log(cjt_sinpi_(half)), lc = log(cjt_cospi_(half));
-    double su = 0.0, sv = 0.0;
-    for (int l = 0; l <= m; ++l) {
-        const double coef = e.ha[l] * e.hb[m - l];
-        if (coef == 0.0) continue;
-        const double mag = coef * exp(-(l + e.a + 0.5) * ls - (m - l + e.b + 0.5) * lc);
-        // phi_{m,l} / pi = (a + l + 1/2)/2 - (a + b + m + 1) theta / (2 pi)
-        const double ph = 0.5 * (e.a + l + 0.5) - (e.a + e.b + m + 1.0) * half;
-        double s, c;
-        cjt_sincospi_(ph, &s, &c);
-        su = fma(mag, c, su);
-        sv = fma(mag, s, sv);
-    }
-    *u = su;
-    *v = sv;
+    const double sh = cjt_sinpi_(half), ch = cjt_cospi_(half);
+    const double P = exp(-(e.a + 0.5) * log(sh) - (m + e.b + 0.5) * log(ch));
+    const double t = ch / sh, w = -t * t;
+    double A = 0.0, B = 0.0;
+    for (int l = m - (m & 1); l >= 0; l -= 2) A = fma(A, w, e.ha[l] * e.hb[m - l]);
+    for (int l = (m & 1) ? m : m - 1; l >= 1; l -= 2) B = fma(B, w, e.ha[l] * e.hb[m - l]);
+    B *= t;
+    double s, c;
+    cjt_sincospi_(0.5 * (e.a + 0.5) - (e.a + e.b + m + 1.0) * half, &s, &c);
+    *u = P * (A * c - B * s);
+    *v = P * (A * s + B * c);
 }
 
 // The expansion for (a, b) in [-1/2, 1/2]^2 and the plan option (CJT_EXPANSION_*):
@@ -608,6 +609,9 @@ int64_t cjt_dft_work_bytes(const Dft &d, int64_t batch);
 int64_t cjt_dft_scratch_bytes(const Dft &d, int64_t batch);
 
 int cjt_plan_build(cjt_plan_s *p, cudaStream_t st);
+// Stream-ordered temporary device memory for plan building, from a library-owned pool per
+// device that keeps up to 1 GiB of freed memory for the next plans (free with cudaFreeAsync).
+cudaError_t cjt_tmp_alloc(void **ptr, size_t bytes, cudaStream_t st);
 // The plan's twiddle tables (from p->Ltab, p->Ltab3 and the transform precision pa): taken
 // from a per-device cache of tables shared by plans, built on `st` when absent.  A plan
 // that took tables gives them back with cjt_release_twiddles.

@@ -448,7 +448,7 @@ __device__ __forceinline__ void inv_g_elem(int64_t i, const double2 *__restrict_
 // the l-th, the warp broadcasts them by shuffles, and eight partial loads are in flight;
 // four interleaved accumulators; the warp sums are added in warp order.  Block `blk`
 // covers the 32 consecutive degrees from 32 blk.
-constexpr int RED_WARPS = 32;
+constexpr int RED_WARPS = 8;
 __device__ __forceinline__ void inv_reduce_block(int64_t blk, int64_t N, int seg_len,
                                                  const int64_t *__restrict__ seg_ptr,
                                                  const int64_t *__restrict__ seg_out, const int *__restrict__ seg_b,

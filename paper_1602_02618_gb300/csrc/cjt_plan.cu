@@ -99,93 +99,35 @@ __global__ void k_rowk(int64_t Ng, int nblk, const int *box3, int *rowk) {
     rowk[i] = kk;
 }
 
-// --------------------------------------------------------------------------
-// forward-recurrence state at every degree-segment start (plain or
-// Reinsch-modified forward recurrence, Sec. 4.2).  One thread per row.
-//   srow = {row, J, mode, state_base, lane, nseg}
-// --------------------------------------------------------------------------
-__global__ void k_rec_states(int64_t nrows, const int *srow, int64_t Ng, int seg_len, RecTables t, double *states) {
-    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= nrows) return;
-    const int *r = srow + 6 * q;
-    const int row = r[0], mode = r[2], base = r[3], lane = r[4], nseg = r[5];
-    if (mode == REC_PLAIN) {
-        const double x = cospi((double)row / (double)Ng);
-        double pm = 0.0, p = 1.0;
-        for (int s = 1; s < nseg; ++s) {
-            const int64_t n0 = (int64_t)(s - 1) * seg_len;
-#pragma unroll 8
-            for (int k = 0; k < seg_len; ++k) {
-                const int64_t n = n0 + k;
-                const double pn = fma(fma(__ldg(t.A + n), x, __ldg(t.B + n)), p, -__ldg(t.C + n) * pm);
-                pm = p;
-                p = pn;
-            }
-            double *st = states + ((int64_t)(base + s - 1) * 32 + lane) * 2;
-            st[0] = p;
-            st[1] = pm;
-        }
-    } else {
-        const bool plus = (mode == REC_REINSCH_P1);
-        // delta = x - x0: -2 sin^2(theta/2) at x0 = 1, 2 cos^2(theta/2) at x0 = -1 (Sec. 4.2)
-        double delta;
-        if (plus) {
-            const double sv = sinpi((double)row / (2.0 * (double)Ng));
-            delta = -2.0 * sv * sv;
-        } else {
-            const double sv = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
-            delta = 2.0 * sv * sv;
-        }
-        const double *Ce = plus ? t.Ce_p : t.Ce_m;
-        const double *rf = plus ? t.rf_p : t.rf_m;
-        double p = 1.0, e = 0.0;
-        for (int s = 1; s < nseg; ++s) {
-            const int64_t n0 = (int64_t)(s - 1) * seg_len;
-#pragma unroll 8
-            for (int k = 0; k < seg_len; ++k) {
-                const int64_t n = n0 + k;
-                const double en = fma(__ldg(t.A + n) * delta, p, __ldg(Ce + n) * e);
-                p = fma(p, __ldg(rf + n), en);
-                e = en;
-            }
-            double *st = states + ((int64_t)(base + s - 1) * 32 + lane) * 2;
-            st[0] = p;
-            st[1] = e;
-        }
-    }
-}
-
-// Long rows (many segments): the states at the segment starts by a chunked scan.  The
-// recurrence is linear in its two-term state, so segment k maps the state at degree kS to
-// the state at degree (k+1)S by a 2x2 matrix: k_rec_seg_maps runs the same recurrence as
-// k_rec_states over segment k from the two unit states (its columns), one thread per
-// (row, segment); k_rec_seg_carry then applies the matrices in order, one thread per row.
-// The chain of S-step segments runs in parallel instead of one N-step chain per row.
-__device__ __forceinline__ void rec_row_setup(int row, int mode, int64_t Ng, const RecTables &t, double &x,
-                                              double &delta, const double *&Ce, const double *&rf) {
+// x (plain rows) or delta = x - x0 (Reinsch rows: -2 sin^2(theta/2) at x0 = 1, 2 cos^2(theta/2)
+// at x0 = -1, Sec. 4.2) of grid row `row`
+__device__ __forceinline__ void rec_row_point(int row, int mode, int64_t Ng, double &x, double &delta) {
     x = 0.0;
     delta = 0.0;
-    Ce = rf = nullptr;
     if (mode == REC_PLAIN) {
         x = cospi((double)row / (double)Ng);
+    } else if (mode == REC_REINSCH_P1) {
+        const double sv = sinpi((double)row / (2.0 * (double)Ng));
+        delta = -2.0 * sv * sv;
     } else {
-        const bool plus = (mode == REC_REINSCH_P1);
-        if (plus) {
-            const double sv = sinpi((double)row / (2.0 * (double)Ng));
-            delta = -2.0 * sv * sv;
-        } else {
-            const double sv = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
-            delta = 2.0 * sv * sv;
-        }
-        Ce = plus ? t.Ce_p : t.Ce_m;
-        rf = plus ? t.rf_p : t.rf_m;
+        const double sv = sinpi((double)(Ng - row) / (2.0 * (double)Ng));
+        delta = 2.0 * sv * sv;
     }
 }
 
-// lsrow: {row, mode, state_base, lane, nseg} per long row; loff[q] = first map of row q
-// (prefix sum of nseg - 1); maps[(loff[q] + k) * 4] = the two columns of segment k's map
+// --------------------------------------------------------------------------
+// Forward-recurrence state (plain or Reinsch-modified, Sec. 4.2) at every degree-segment
+// start of the rows with more than one segment, by a chunked scan.  The recurrence is
+// linear in its two-term state, so a run of `len` degrees maps the state at its start to the
+// state at its end by a 2x2 matrix: k_rec_seg_maps runs the recurrence over run k from the
+// two unit states (the matrix's columns), one thread per (row, run); k_rec_seg_carry then
+// applies the matrices in order, one thread per row, and stores the state at every segment
+// start.  The runs (len divides the segment length, at most 512 degrees) are shorter than a
+// segment: a dependent FP64 chain is slow, so many short chains beat few long ones.
+//   lsrow = {row, mode, state_base, lane, nseg} per row; loff[q] = first run of row q
+// --------------------------------------------------------------------------
 __global__ void k_rec_seg_maps(int64_t nlong, int64_t nmaps, const int *__restrict__ lsrow,
-                               const int64_t *__restrict__ loff, int64_t Ng, int seg_len, RecTables t,
+                               const int64_t *__restrict__ loff, int64_t Ng, int len, RecTables t,
                                double *__restrict__ maps) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= nmaps) return;
@@ -198,14 +140,13 @@ __global__ void k_rec_seg_maps(int64_t nlong, int64_t nmaps, const int *__restri
     const int *r = lsrow + 5 * q;
     const int row = r[0], mode = r[1];
     double x, delta;
-    const double *Ce, *rf;
-    rec_row_setup(row, mode, Ng, t, x, delta, Ce, rf);
-    const int64_t n0 = k * seg_len;
+    rec_row_point(row, mode, Ng, x, delta);
+    const int64_t n0 = k * len;
     // columns: state (1, 0) and (0, 1) at degree n0
     double p0 = 1.0, q0 = 0.0, p1 = 0.0, q1 = 1.0;
     if (mode == REC_PLAIN) {
 #pragma unroll 4
-        for (int kk = 0; kk < seg_len; ++kk) {
+        for (int kk = 0; kk < len; ++kk) {
             const int64_t n = n0 + kk;
             const double an = fma(__ldg(t.A + n), x, __ldg(t.B + n)), cn = __ldg(t.C + n);
             const double pn0 = fma(an, p0, -cn * q0), pn1 = fma(an, p1, -cn * q1);
@@ -213,8 +154,10 @@ __global__ void k_rec_seg_maps(int64_t nlong, int64_t nmaps, const int *__restri
             q1 = p1; p1 = pn1;
         }
     } else {
+        const double *Ce = mode == REC_REINSCH_P1 ? t.Ce_p : t.Ce_m;
+        const double *rf = mode == REC_REINSCH_P1 ? t.rf_p : t.rf_m;
 #pragma unroll 4
-        for (int kk = 0; kk < seg_len; ++kk) {
+        for (int kk = 0; kk < len; ++kk) {
             const int64_t n = n0 + kk;
             const double ad = __ldg(t.A + n) * delta, ce = __ldg(Ce + n), f = __ldg(rf + n);
             const double e0 = fma(ad, p0, ce * q0), e1 = fma(ad, p1, ce * q1);
@@ -227,20 +170,32 @@ __global__ void k_rec_seg_maps(int64_t nlong, int64_t nmaps, const int *__restri
 }
 
 __global__ void k_rec_seg_carry(int64_t nlong, const int *__restrict__ lsrow, const int64_t *__restrict__ loff,
-                                const double *__restrict__ maps, double *__restrict__ states) {
+                                int per, const double *__restrict__ maps, double *__restrict__ states) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nlong) return;
     const int *r = lsrow + 5 * q;
     const int base = r[2], lane = r[3], nseg = r[4];
+    struct Map { double x, y, z, w; };
+    const Map *mp = reinterpret_cast<const Map *>(maps) + loff[q];
+    const int nrun = (nseg - 1) * per;   // `per` runs per segment
     double a = 1.0, b = 0.0;   // (p, second state) at degree 0
-    for (int k = 0; k < nseg - 1; ++k) {
-        const double *m = maps + (loff[q] + k) * 4;
-        const double na = fma(a, m[0], b * m[2]), nb = fma(a, m[1], b * m[3]);
-        a = na;
-        b = nb;
-        double *st = states + ((int64_t)(base + k) * 32 + lane) * 2;
-        st[0] = a;
-        st[1] = b;
+    for (int k0 = 0; k0 < nrun; k0 += 8) {
+        Map m[8];   // loaded ahead: the maps do not depend on the carried state
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m[j] = k0 + j < nrun ? mp[k0 + j] : Map{0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = k0 + j;
+            if (k >= nrun) break;
+            const double na = fma(a, m[j].x, b * m[j].z), nb = fma(a, m[j].y, b * m[j].w);
+            a = na;
+            b = nb;
+            if ((k + 1) % per == 0) {   // the start of segment (k + 1) / per
+                double *st = states + ((int64_t)(base + (k + 1) / per - 1) * 32 + lane) * 2;
+                st[0] = a;
+                st[1] = b;
+            }
+        }
     }
 }
 
@@ -341,8 +296,8 @@ __global__ void k_rec_fill(const RecItem *__restrict__ items, int64_t nitems, in
 // The recurrence for k >= 1 is the linear map (mu_{k-1}, mu_k) -> (mu_k, mu_{k+1}) with
 //   mu_{k+1} = c1_k mu_k + c0_k mu_{k-1},  c1_k = -2(a-b)/(a+b+k+2),  c0_k = -(a+b-k+2)/(a+b+k+2).
 // It is evaluated as a chunked scan: each chunk of kMomChunk steps forms its 2x2 transfer
-// matrix in parallel, one thread carries the true state across the chunks, and every chunk
-// then reruns its steps from that state.  The forward recurrence is stable in the square
+// matrix in parallel, a block-wide scan of the matrices gives the true state at every chunk
+// start, and every chunk then reruns its steps from that state.  The forward recurrence is stable in the square
 // (Sec. 3.1), so the basis solutions carried by the transfer matrices do not outgrow mu.
 constexpr int kMomChunk = 64;
 
@@ -372,10 +327,41 @@ __global__ void k_mom_transfer(int64_t Ng, double a, double b, int64_t nchunk, M
     T[c] = Mat2{x0, x1, y0, y1};
 }
 
-__global__ void k_mom_carry(int64_t nchunk, double mu0, double mu1, const Mat2 *T, double2 *start) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+// The state at every chunk start: start[c] = T[c-1] ... T[0] (mu0, mu1).  One block: thread
+// j multiplies the maps of its run of consecutive chunks, the block scans those products in
+// shared memory (Hillis--Steele, later runs' products on the left), and each thread then
+// carries the state through its own run from the product of all earlier runs.
+constexpr int kMomScanThreads = 1024;
+__device__ __forceinline__ Mat2 mat2_mul(const Mat2 &l, const Mat2 &r) {   // l r
+    return Mat2{fma(l.x0, r.x0, l.x1 * r.y0), fma(l.x0, r.x1, l.x1 * r.y1), fma(l.y0, r.x0, l.y1 * r.y0),
+                fma(l.y0, r.x1, l.y1 * r.y1)};
+}
+__global__ void __launch_bounds__(kMomScanThreads) k_mom_carry(int64_t nchunk, double mu0, double mu1,
+                                                               const Mat2 *__restrict__ T,
+                                                               double2 *__restrict__ start) {
+    __shared__ Mat2 sc[kMomScanThreads];
+    const int j = threadIdx.x;
+    const int64_t per = (nchunk + kMomScanThreads - 1) / kMomScanThreads;
+    const int64_t c0 = min((int64_t)j * per, nchunk), c1 = min(c0 + per, nchunk);
+    Mat2 prod{1.0, 0.0, 0.0, 1.0};
+    for (int64_t c = c0; c < c1; ++c) prod = mat2_mul(T[c], prod);
+    sc[j] = prod;
+    __syncthreads();
+    for (int d = 1; d < kMomScanThreads; d <<= 1) {
+        const Mat2 mine = sc[j];
+        const Mat2 earlier = j >= d ? sc[j - d] : Mat2{1.0, 0.0, 0.0, 1.0};
+        __syncthreads();
+        sc[j] = mat2_mul(mine, earlier);
+        __syncthreads();
+    }
+    // state at c0: the product of all earlier runs applied to (mu0, mu1)
     double u = mu0, v = mu1;
-    for (int64_t c = 0; c < nchunk; ++c) {
+    if (j > 0) {
+        const Mat2 e = sc[j - 1];
+        u = fma(e.x0, mu0, e.x1 * mu1);
+        v = fma(e.y0, mu0, e.y1 * mu1);
+    }
+    for (int64_t c = c0; c < c1; ++c) {
         start[c] = make_double2(u, v);
         const Mat2 m = T[c];
         const double nu = fma(m.x0, u, m.x1 * v), nv = fma(m.y0, u, m.y1 * v);
@@ -687,9 +673,9 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
         if (!js.empty()) {
             double *d_g = nullptr, *d_thr = nullptr;
             int *d_b2 = nullptr;
-            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_g, sizeof(double) * (Ng + 1), st));
-            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_thr, sizeof(double) * thr.size(), st));
-            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_b2, sizeof(int) * 2 * thr.size(), st));
+            CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_g, sizeof(double) * (Ng + 1), st));
+            CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_thr, sizeof(double) * thr.size(), st));
+            CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_b2, sizeof(int) * 2 * thr.size(), st));
             k_envelope<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, M, h, d_g);
             CJT_CUDA_TRY(cudaMemcpyAsync(d_thr, thr.data(), sizeof(double) * thr.size(), cudaMemcpyHostToDevice, st));
             k_box_init<<<1, 64, 0, st>>>((int)thr.size(), d_b2);
@@ -817,26 +803,40 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
     // with the parity fold, chunks of the rows 2i < Ng stand also for their mirror rows
     // Ng - i (same J by the symmetric boxes); the middle row (Ng even) is a chunk of its own
     const int64_t ilast = gw.fold ? (Ng - 1) / 2 : Ng;
-    for (int64_t i = 0; i <= ilast;) {
-        int64_t J = J_of(i);
-        int md = mode_of(i);
-        Chunk c{i, 1, J, md, gw.fold ? 1 : 0};
-        int64_t k = i + 1;
-        while (k <= ilast && c.nrows < 32 && J_of(k) == J && mode_of(k) == md) { ++c.nrows; ++k; }
-        chunks.push_back(c);
-        i = k;
+    {
+        // J(i) and the mode are constant between the rows where a box begins or ends and the
+        // two mode breakpoints: runs of equal (J, mode) are cut into chunks of 32 rows from
+        // their first row (the rows one by one would give the same chunks)
+        std::vector<int64_t> cut = {0, ilast + 1, (Ng + 4) / 4, (3 * Ng + 3) / 4};
+        for (int k = 0; k < gw.nblk; ++k) {
+            cut.push_back(gw.i1[k]);
+            cut.push_back(gw.i2[k] + 1);
+        }
+        std::sort(cut.begin(), cut.end());
+        cut.erase(std::unique(cut.begin(), cut.end()), cut.end());
+        int64_t run0 = 0;
+        for (size_t t = 0; t + 1 < cut.size() && cut[t] <= ilast; ++t) {
+            const int64_t b0 = cut[t], b1 = std::min(cut[t + 1], ilast + 1);
+            if (b1 <= ilast && J_of(b1) == J_of(b0) && mode_of(b1) == mode_of(b0)) continue;   // the run goes on
+            const int64_t J = J_of(run0);
+            const int md = mode_of(run0);
+            for (int64_t i = run0; i < b1; i += 32)
+                chunks.push_back(Chunk{i, (int)std::min<int64_t>(32, b1 - i), J, md, gw.fold ? 1 : 0});
+            run0 = b1;
+        }
     }
     if (gw.fold && Ng % 2 == 0) chunks.push_back(Chunk{Ng / 2, 1, J_of(Ng / 2), mode_of(Ng / 2), 0});
     gw.nchunks = (int64_t)chunks.size();
     std::vector<RecItem> items;
-    std::vector<int> row_nseg(Ng + 1);
-    std::vector<int64_t> row_base(Ng + 1);
+    // the forward combine's per-row segment counts and partial offsets (not used inverse)
+    std::vector<int> row_nseg(inverse ? 0 : Ng + 1);
+    std::vector<int64_t> row_base(inverse ? 0 : Ng + 1);
     std::vector<int> srow;
     int64_t out_f = 0, out_i = 0, nstate = 0, steps = 0, eoff = 0;
     for (size_t c = 0; c < chunks.size(); ++c) {
         const Chunk &ch = chunks[c];
         int nseg = (int)((ch.J + S - 1) / S);
-        for (int r = 0; r < ch.nrows; ++r) {
+        for (int r = 0; r < ch.nrows && !inverse; ++r) {
             row_nseg[ch.row0 + r] = nseg;
             row_base[ch.row0 + r] = out_f + r;
             if (ch.mirror) {   // the mirrored rows' partials follow the chunk's own
@@ -886,13 +886,16 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
     // inverse: contributions to each degree segment, in a fixed order
     if (inverse) {
         gw.nsegs = (gw.Jcap + S - 1) / S;
-        std::vector<std::vector<size_t>> per(gw.nsegs);
-        for (size_t q = 0; q < items.size(); ++q) per[items[q].a / S].push_back(q);
-        std::vector<int64_t> ptr(gw.nsegs + 1, 0), sout;
-        std::vector<int> sb;
-        for (int64_t s = 0; s < gw.nsegs; ++s) {
-            for (size_t q : per[s]) { sout.push_back(items[q].out); sb.push_back(items[q].b); }
-            ptr[s + 1] = (int64_t)sout.size();
+        // items grouped by degree segment, in item order within a segment (a counting sort)
+        std::vector<int64_t> ptr(gw.nsegs + 1, 0), sout(items.size());
+        std::vector<int> sb(items.size());
+        for (const RecItem &it : items) ++ptr[it.a / S + 1];
+        for (int64_t s = 0; s < gw.nsegs; ++s) ptr[s + 1] += ptr[s];
+        std::vector<int64_t> at(ptr.begin(), ptr.end() - 1);
+        for (const RecItem &it : items) {
+            const int64_t q = at[it.a / S]++;
+            sout[q] = it.out;
+            sb[q] = it.b;
         }
         TRY(dalloc(p, &gw.d_seg_ptr, gw.nsegs + 1));
         TRY(dalloc(p, &gw.d_seg_out, (int64_t)sout.size()));
@@ -913,59 +916,54 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
         CJT_CUDA_TRY(cudaStreamSynchronize(st));
     }
     tr.mark(inverse ? "inv: host work lists" : "fwd: host work lists");
-    // longest items first: the block scheduler then balances the SMs
-    std::stable_sort(items.begin(), items.end(),
-                     [](const RecItem &x, const RecItem &y) { return (x.b - x.a) > (y.b - y.a); });
+    // longest items first: the block scheduler then balances the SMs (a stable counting sort
+    // by length, 1 .. S)
+    {
+        std::vector<int64_t> cnt(S + 2, 0);
+        for (const RecItem &it : items) ++cnt[S - (it.b - it.a) + 1];
+        for (int l = 0; l <= S; ++l) cnt[l + 1] += cnt[l];
+        std::vector<RecItem> sorted(items.size());
+        for (const RecItem &it : items) sorted[cnt[S - (it.b - it.a)]++] = it;
+        items.swap(sorted);
+    }
     gw.nitems = (int64_t)items.size();
     TRY(dalloc(p, &gw.d_items, gw.nitems));
     if (gw.nitems)
         CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_items, items.data(), sizeof(RecItem) * items.size(), cudaMemcpyHostToDevice, st));
     TRY(dalloc(p, &gw.d_states, std::max<int64_t>(nstate * 64, 1)));
     CJT_CUDA_TRY(cudaMemsetAsync(gw.d_states, 0, sizeof(double) * std::max<int64_t>(nstate * 64, 1), st));
+    tr.mark(inverse ? "inv: items sorted, uploaded" : "fwd: items sorted, uploaded");
     if (gw.nsrow > 0) {
-        // rows with up to kShortSegs segments: one sequential chain per row (k_rec_states);
-        // longer rows: the chunked scan (k_rec_seg_maps, k_rec_seg_carry)
-        constexpr int kShortSegs = 16;
-        std::vector<int> shortrow, longrow;
+        // every row with more than one segment: runs of len degrees, `per` to a segment
+        int per = (S + 511) / 512;
+        while (S % per) ++per;
+        const int len = S / per;
+        std::vector<int> longrow;
         std::vector<int64_t> loff;
         int64_t nmaps = 0;
         for (int64_t q = 0; q < gw.nsrow; ++q) {
             const int *v = srow.data() + 6 * q;
-            if (v[5] <= kShortSegs) {
-                shortrow.insert(shortrow.end(), v, v + 6);
-            } else {
-                const int w[5] = {v[0], v[2], v[3], v[4], v[5]};
-                longrow.insert(longrow.end(), w, w + 5);
-                loff.push_back(nmaps);
-                nmaps += v[5] - 1;
-            }
+            const int w[5] = {v[0], v[2], v[3], v[4], v[5]};
+            longrow.insert(longrow.end(), w, w + 5);
+            loff.push_back(nmaps);
+            nmaps += (int64_t)(v[5] - 1) * per;
         }
-        const int64_t nshort = (int64_t)shortrow.size() / 6, nlong = (int64_t)longrow.size() / 5;
-        if (nshort > 0) {
-            TRY(dalloc(p, &gw.d_srow, (int64_t)shortrow.size()));
-            CJT_CUDA_TRY(cudaMemcpyAsync(gw.d_srow, shortrow.data(), sizeof(int) * shortrow.size(),
-                                         cudaMemcpyHostToDevice, st));
-            // one row per thread; 32-thread blocks spread the chains over the SMs
-            k_rec_states<<<blocks_for(nshort, 32), 32, 0, st>>>(nshort, gw.d_srow, Ng, S, p->rt, gw.d_states);
-            CJT_CUDA_TRY(cudaGetLastError());
-        }
-        if (nlong > 0) {
-            int *d_l = nullptr;
-            int64_t *d_off = nullptr;
-            double *d_maps = nullptr;
-            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_l, sizeof(int) * longrow.size(), st));
-            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_off, sizeof(int64_t) * loff.size(), st));
-            CJT_CUDA_TRY(cudaMallocAsync((void **)&d_maps, sizeof(double) * 4 * nmaps, st));
-            CJT_CUDA_TRY(cudaMemcpyAsync(d_l, longrow.data(), sizeof(int) * longrow.size(), cudaMemcpyHostToDevice, st));
-            CJT_CUDA_TRY(cudaMemcpyAsync(d_off, loff.data(), sizeof(int64_t) * loff.size(), cudaMemcpyHostToDevice, st));
-            k_rec_seg_maps<<<blocks_for(nmaps, 128), 128, 0, st>>>(nlong, nmaps, d_l, d_off, Ng, S, p->rt, d_maps);
-            k_rec_seg_carry<<<blocks_for(nlong, 64), 64, 0, st>>>(nlong, d_l, d_off, d_maps, gw.d_states);
-            CJT_CUDA_TRY(cudaGetLastError());
-            CJT_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors above go out of scope
-            cudaFreeAsync(d_maps, st);
-            cudaFreeAsync(d_off, st);
-            cudaFreeAsync(d_l, st);
-        }
+        const int64_t nlong = (int64_t)longrow.size() / 5;
+        int *d_l = nullptr;
+        int64_t *d_off = nullptr;
+        double *d_maps = nullptr;
+        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_l, sizeof(int) * longrow.size(), st));
+        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_off, sizeof(int64_t) * loff.size(), st));
+        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_maps, sizeof(double) * 4 * nmaps, st));
+        CJT_CUDA_TRY(cudaMemcpyAsync(d_l, longrow.data(), sizeof(int) * longrow.size(), cudaMemcpyHostToDevice, st));
+        CJT_CUDA_TRY(cudaMemcpyAsync(d_off, loff.data(), sizeof(int64_t) * loff.size(), cudaMemcpyHostToDevice, st));
+        k_rec_seg_maps<<<blocks_for(nmaps, 128), 128, 0, st>>>(nlong, nmaps, d_l, d_off, Ng, len, p->rt, d_maps);
+        k_rec_seg_carry<<<blocks_for(nlong, 64), 64, 0, st>>>(nlong, d_l, d_off, per, d_maps, gw.d_states);
+        CJT_CUDA_TRY(cudaGetLastError());
+        CJT_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors above go out of scope
+        cudaFreeAsync(d_maps, st);
+        cudaFreeAsync(d_off, st);
+        cudaFreeAsync(d_l, st);
     }
     gw.nE = eoff;
     if (p->opts.rec_store && gw.nitems > 0) {
@@ -988,6 +986,35 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
 
 // Twiddle tables of a plan (p->Ltab set): omega_{Ltab}^k in FP64 and in the precision pa
 // of its asymptotic transforms, the stage tables and the FP64 fused multiply-add forms.
+cudaError_t cjt_tmp_alloc(void **ptr, size_t bytes, cudaStream_t st) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaMallocAsync(ptr, bytes, st);
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&pools[dev], &props);
+            if (e != cudaSuccess) {
+                pools[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = 1ull << 30;   // freed memory kept for reuse (the pool is ours alone)
+            cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+}
+
 // ------------------------------------------------------------------------
 // Twiddle tables shared by plans.  They depend only on (device, Ltab, Ltab3, transform
 // precision), so plans of the same lengths take one copy: a plan built while a copy exists
@@ -1316,9 +1343,15 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
     if (inv && N >= 1) {
         const int64_t Ng = 2 * p->Gi;
         Workspace ws = p->ws;
-        if (p->shared_ws) {   // a temporary arena for the weights
-            CJT_CUDA_TRY(cudaMallocAsync(&tmp_ws, p->ws_bytes, st));
-            ws = cjt_carve(p, tmp_ws);
+        if (p->shared_ws) {   // temporary buffers for the weights' transform (DCT, work, scratch)
+            const int64_t a0 = (p->ws_size[WS_DCT] + 255) / 256 * 256, a1 = (p->ws_size[WS_WORK] + 255) / 256 * 256;
+            const int64_t a2 = (p->ws_size[WS_SCRATCH] + 255) / 256 * 256;
+            CJT_CUDA_TRY(cjt_tmp_alloc(&tmp_ws, (size_t)(a0 + a1 + a2), st));
+            unsigned char *b = (unsigned char *)tmp_ws;
+            ws = Workspace{};
+            ws.dct = (double *)b;
+            ws.work = p->ws_size[WS_WORK] ? b + a0 : nullptr;
+            ws.scratch = p->ws_size[WS_SCRATCH] ? b + a0 + a1 : nullptr;
         }
         TRY(dalloc(p, &p->d_w, Ng + 1));
         TRY(dalloc(p, &p->d_s, N + 1));
@@ -1328,10 +1361,10 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         const int64_t nchunk = std::max<int64_t>(1, (Ng - 1 + kMomChunk - 1) / kMomChunk);
         Mat2 *T = nullptr;
         double2 *start = nullptr;
-        CJT_CUDA_TRY(cudaMallocAsync((void **)&T, sizeof(Mat2) * nchunk, st));
-        CJT_CUDA_TRY(cudaMallocAsync((void **)&start, sizeof(double2) * nchunk, st));
+        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&T, sizeof(Mat2) * nchunk, st));
+        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&start, sizeof(double2) * nchunk, st));
         k_mom_transfer<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, T);
-        k_mom_carry<<<1, 1, 0, st>>>(nchunk, mu0, mu1, T, start);
+        k_mom_carry<<<1, kMomScanThreads, 0, st>>>(nchunk, mu0, mu1, T, start);
         k_mom_fill<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, start, (double2 *)ws.dct);
         CJT_CUDA_TRY(cudaGetLastError());
         cudaFreeAsync(T, st);
@@ -1347,14 +1380,14 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         // bound on the FP32 transforms' error (see k_err_fwd): two maxima read back once
         double *acc = nullptr, *U = nullptr;
         const int nqi = p->iv.nblk * M;
-        CJT_CUDA_TRY(cudaMallocAsync((void **)&acc, 2 * sizeof(double), st));
+        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&acc, 2 * sizeof(double), st));
         CJT_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
         if (fwd && p->fw.nblk > 0)
             k_err_fwd<<<blocks_for(p->Gf + 1, 256), 256, 0, st>>>(N, p->Gf, M, p->fw.nblk * M, p->fw.d_rowk,
                                                                    p->fw.d_box, p->d_Cnm, p->fw.d_scale, p->fw.d_u,
                                                                    p->fw.d_v, acc);
         if (inv && nqi > 0) {
-            CJT_CUDA_TRY(cudaMallocAsync((void **)&U, nqi * sizeof(double), st));
+            CJT_CUDA_TRY(cjt_tmp_alloc((void **)&U, nqi * sizeof(double), st));
             k_err_inv_U<<<nqi, 256, 0, st>>>(2 * p->Gi, M, p->iv.d_box, p->d_w, p->iv.d_u, p->iv.d_v, U);
             k_err_inv<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, M, p->iv.nblk, nqi, p->iv.d_box, p->d_Cnm,
                                                                p->iv.d_scale, U, p->d_s, acc + 1);

@@ -147,7 +147,10 @@ class Server:
     def _planner(self):
         torch = self.torch
         torch.cuda.set_device(self.dev)
-        stream = torch.cuda.Stream(device=self.dev)
+        # plan kernels are small and each plan waits for them several times (its partition
+        # and work lists come back to the host): the highest priority lets them take SMs as
+        # the executing transforms' CTAs retire instead of queueing behind them
+        stream = torch.cuda.Stream(device=self.dev, priority=-100)
         while not self._stop:
             r = self.incoming.get()
             if r is None:
