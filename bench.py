@@ -292,11 +292,46 @@ def batch_plan_options(N, big, precision, cjt):
     return o
 
 
+# DRAM traffic of one replay of the 4096-item FP64 batch, summed over its transform launches
+# (k_fft_sub, k_fft_r3) in the one-pass ncu capture summarised in
+# profiles/traffic_batched_fp64_4096.md.  It stands for the code it was taken on: while the
+# transform kernels' and the grouped executor's sources hash to the digests below.
+FFT_TRAFFIC = {
+    "read": 135.844e9, "write": 107.348e9, "bytes_per_step": 243.193e9,
+    "profile": "profiles/traffic_batched_fp64_4096.md",
+    "sources": {"paper_1602_02618_gb300/csrc/cjt_fft.cu":
+                "316ab94ad081e3e5911b525e546fd835445ab92d418af00c6d6a2bf47cfeac7d",
+                "paper_1602_02618_gb300/csrc/cjt_group.cu":
+                "494bfc35b343a11d48034978b85140fc19e797236251eaf8771f7f723cbc8d62"},
+}
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return None
+
+
+def measured_fft_traffic(args, precision, cjt):
+    """FFT_TRAFFIC when this run is the captured workload on the captured code, else None."""
+    import hashlib
+    if args.batch_count != 4096 or precision != cjt.CJT_FP64 or args.batch_fixed:
+        return None
+    for rel, digest in FFT_TRAFFIC["sources"].items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return FFT_TRAFFIC
+
+
 def batch_work(plans, dirs):
     """Algorithmic FP64-pipe work of one batch replay per stage kind (flop) from the plans:
     transforms 5 L log2 L per complex transform of length L (2.5 L log2 L per real item);
     recurrence at execution 8 flop per step; stored values 2 flop (one multiply-add)."""
     w = {"fft_asy": 0.0, "fft_dct": 0.0, "rec": 0.0, "rec_stored": 0.0}
+    points = 0.0   # complex points of all transforms (for their algorithmic bytes)
     for p, d in zip(plans, dirs):
         inf = p.info()
         f = d == 1
@@ -305,10 +340,12 @@ def batch_work(plans, dirs):
         steps = inf["rec_steps_fwd"] if f else inf["rec_steps_inv"]
         w["fft_asy"] += npair * 5.0 * L * lg2(L)
         w["fft_dct"] += 5.0 * L * lg2(L)
+        points += (npair + 1) * L
         if inf["rec_store_bytes"] > 0:
             w["rec_stored"] += 2.0 * steps
         else:
             w["rec"] += 8.0 * steps
+    w["fft_points"] = points
     return w
 
 
@@ -429,12 +466,26 @@ def run_batched(ctx, big=False, steps=None):
                        "rec": "k_g_rec_fwd / k_g_rec_inv (recurrences at execution)",
                        "rec_stored": "k_g_rec_fwd_stored / k_g_rec_inv_stored"}.get(dom, dom),
             "stage": dom, "bound": "alu", "unit": "TFLOP/s", "traffic": None,
-            "serialised_ms_per_step": live, "time_share": live[dom] / sum(live.values()), "work_tflop_per_step": {k: v / 1e12 for k, v in work.items()}}
+            "serialised_ms_per_step": live, "time_share": live[dom] / sum(live.values()), "work_tflop_per_step": {k: v / 1e12 for k, v in work.items() if k != "fft_points"}}
     if dom in t_peak and live[dom] > 0:
         pk = asy_peak if dom == "fft_asy" else peak
         ach = (t_peak[dom] * pk) / (live[dom] * 1e-3)
         roof.update({"achieved": ach / 1e12, "peak": pk / 1e12, "frac": ach / pk,
                      "peak_source": P64_SOURCE if pk == peak else "measured multiply-add rate of the ASY form"})
+    # DRAM traffic of the transform launches, from the one-pass capture of this workload
+    tr = measured_fft_traffic(args, precision, cjt)
+    if tr is not None:
+        tsec = 1e-3 * (live.get("fft_asy", 0.0) + live.get("fft_dct", 0.0))
+        roof["traffic"] = tr["bytes_per_step"]
+        roof["traffic_detail"] = {
+            "kernels": "all transform launches of one replay (k_fft_sub, k_fft_r3; asymptotic blocks, DCT-I and "
+                       "front end together): dram__bytes_read.sum + dram__bytes_write.sum",
+            "read": tr["read"], "write": tr["write"], "profile": tr["profile"],
+            "algorithmic_bytes": 32.0 * work["fft_points"],
+            "note": "algorithmic bytes: every complex point read once and written once (16 B each way)",
+            "traffic_over_algorithmic": tr["bytes_per_step"] / (32.0 * work["fft_points"]),
+            "achieved_gbs": tr["bytes_per_step"] / tsec / 1e9 if tsec > 0 else None,
+            "hbm_gbs": measured_hbm_gbs()}
     roof["step"] = {"frac": sum(t_peak.values()) / step_s, "ms_at_peak": 1e3 * sum(t_peak.values()),
                     "ms_per_step": 1e3 * step_s,
                     "note": "all stage kinds at their pipe's peak, summed (they share the FP64 pipe)"}
