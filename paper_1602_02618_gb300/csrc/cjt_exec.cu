@@ -36,7 +36,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // single-transform launches of the bodies in cjt_kern.cuh
 // ---------------------------------------------------------------------------
 using cjt_kern::SW;
-using cjt_kern::RED_WARPS;
+constexpr int RED_WARPS = 32;   // one large transform: few blocks carry the heavy segments
 using cjt_kern::re_d;
 using cjt_kern::im_d;
 
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(32 * RED_WARPS) k_inv_reduce(int64_t N, int se
                                                                const int *__restrict__ seg_b,
                                                                const double *__restrict__ partials,
                                                                double *__restrict__ y) {
-    cjt_kern::inv_reduce_block(blockIdx.x, N, seg_len, seg_ptr, seg_out, seg_b, partials, y);
+    cjt_kern::inv_reduce_block<RED_WARPS>(blockIdx.x, N, seg_len, seg_ptr, seg_out, seg_b, partials, y);
 }
 
 template <typename V>

@@ -228,11 +228,12 @@ __global__ void __launch_bounds__(32 * cjt_kern::SW) k_g_rec_inv_stored(const GD
     cjt_kern::rec_inv_stored_cta(it, d.Ng, d.g, d.E, d.part);
 }
 
-__global__ void __launch_bounds__(32 * cjt_kern::RED_WARPS) k_g_inv_reduce(const GDesc *__restrict__ D,
+constexpr int GRED_WARPS = 8;   // many small transforms: more blocks resident per SM
+__global__ void __launch_bounds__(32 * GRED_WARPS) k_g_inv_reduce(const GDesc *__restrict__ D,
                                                                            const GTab *__restrict__ tab) {
     const GTab e = tab[blockIdx.x];
     const GDesc &d = D[e.item];
-    cjt_kern::inv_reduce_block(e.blk, d.N, d.seg_len, d.seg_ptr, d.seg_out, d.seg_b, d.part, d.y);
+    cjt_kern::inv_reduce_block<GRED_WARPS>(e.blk, d.N, d.seg_len, d.seg_ptr, d.seg_out, d.seg_b, d.part, d.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -432,7 +433,7 @@ int run_step(cjt_group_s *g, const Step &s, int pair, cudaStream_t st) {
             return CJT_OK;
         }
         case ST_REDUCE:
-            k_g_inv_reduce<<<(unsigned)s.grid, 32 * cjt_kern::RED_WARPS, 0, st>>>(
+            k_g_inv_reduce<<<(unsigned)s.grid, 32 * GRED_WARPS, 0, st>>>(
                 D, reinterpret_cast<const GTab *>(T + s.tab));
             CJT_CUDA_TRY(cudaGetLastError());
             return CJT_OK;

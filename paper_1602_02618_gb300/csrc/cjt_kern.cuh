@@ -442,50 +442,56 @@ __device__ __forceinline__ void inv_g_elem(int64_t i, const double2 *__restrict_
     g[i] = w[i] * F[i].x;
 }
 
-// Sum of the recurrence partials of every item covering degree n, in a fixed order:
-// warp w takes items w, w + RED_WARPS, w + 2 RED_WARPS, ... (round robin, so that short
-// segments spread over all warps), 32 of them at a time: lane l loads the descriptor of
-// the l-th, the warp broadcasts them by shuffles, and eight partial loads are in flight;
-// four interleaved accumulators; the warp sums are added in warp order.  Block `blk`
-// covers the 32 consecutive degrees from 32 blk.
-constexpr int RED_WARPS = 8;
+// Sum of the recurrence partials of every item covering degree n, in a fixed order that
+// does not depend on the block's size: logical warp k (0 <= k < 32) takes items k, k + 32,
+// k + 64, ... (round robin, so that short segments spread over all of them), 32 at a time:
+// lane l loads the descriptor of the l-th, the warp broadcasts them by shuffles, and eight
+// partial loads are in flight; four interleaved accumulators; the 32 logical warps' sums are
+// added in order.  A block of W warps runs logical warps w, w + W, ... on warp w: W = 32 for
+// one large transform (its heavy segments have few blocks), fewer for the grouped batch's
+// many small ones; every W gives the same bits.  Block `blk` covers the degrees from 32 blk.
+constexpr int RED_LOGICAL = 32;
+template <int W>
 __device__ __forceinline__ void inv_reduce_block(int64_t blk, int64_t N, int seg_len,
                                                  const int64_t *__restrict__ seg_ptr,
                                                  const int64_t *__restrict__ seg_out, const int *__restrict__ seg_b,
                                                  const double *__restrict__ partials, double *__restrict__ y) {
-    __shared__ double red[RED_WARPS][33];
+    static_assert(RED_LOGICAL % W == 0, "the logical warps are shared out evenly");
+    __shared__ double red[RED_LOGICAL][33];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n0 = blk * 32, n = n0 + lane;
     const int64_t s = n0 / seg_len, off = n - s * seg_len;
     const int64_t q0 = seg_ptr[s], q1 = seg_ptr[s + 1];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const int64_t kmax = q1 - q0 > w ? (q1 - q0 - w + RED_WARPS - 1) / RED_WARPS : 0;   // this warp's items
-    for (int64_t kb = 0; kb < kmax; kb += 32) {
-        const int64_t qq = q0 + w + (int64_t)RED_WARPS * (kb + lane);
-        const bool ok = kb + lane < kmax;
-        const int64_t so = ok ? seg_out[qq] : 0;
-        const int sb = ok ? seg_b[qq] : 0;
-        const int cnt = (int)min((int64_t)32, kmax - kb);
-        int j = 0;
-        for (; j + 8 <= cnt; j += 8) {
+    for (int lw = w; lw < RED_LOGICAL; lw += W) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        const int64_t kmax = q1 - q0 > lw ? (q1 - q0 - lw + RED_LOGICAL - 1) / RED_LOGICAL : 0;   // its items
+        for (int64_t kb = 0; kb < kmax; kb += 32) {
+            const int64_t qq = q0 + lw + (int64_t)RED_LOGICAL * (kb + lane);
+            const bool ok = kb + lane < kmax;
+            const int64_t so = ok ? seg_out[qq] : 0;
+            const int sb = ok ? seg_b[qq] : 0;
+            const int cnt = (int)min((int64_t)32, kmax - kb);
+            int j = 0;
+            for (; j + 8 <= cnt; j += 8) {
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int64_t o = __shfl_sync(0xffffffffu, so, j + t);
-                const int b = __shfl_sync(0xffffffffu, sb, j + t);
-                if (n < b) acc[t & 3] += partials[o + off];
+                for (int t = 0; t < 8; ++t) {
+                    const int64_t o = __shfl_sync(0xffffffffu, so, j + t);
+                    const int b = __shfl_sync(0xffffffffu, sb, j + t);
+                    if (n < b) acc[t & 3] += partials[o + off];
+                }
+            }
+            for (; j < cnt; ++j) {
+                const int64_t o = __shfl_sync(0xffffffffu, so, j);
+                const int b = __shfl_sync(0xffffffffu, sb, j);
+                if (n < b) acc[0] += partials[o + off];
             }
         }
-        for (; j < cnt; ++j) {
-            const int64_t o = __shfl_sync(0xffffffffu, so, j);
-            const int b = __shfl_sync(0xffffffffu, sb, j);
-            if (n < b) acc[0] += partials[o + off];
-        }
+        red[lw][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
-    red[w][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     __syncthreads();
     if (w == 0 && n <= N) {
         double t = 0.0;
-        for (int k = 0; k < RED_WARPS; ++k) t += red[k][lane];
+        for (int k = 0; k < RED_LOGICAL; ++k) t += red[k][lane];
         y[n] = t;
     }
 }
