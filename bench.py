@@ -280,10 +280,9 @@ class Ctx:
 
 
 def batch_plan_options(N, big, precision, cjt):
-    """Plan options of the batched workloads.  Batch of 4096: the power-of-two Lobatto grid
-    (no Bluestein transforms), M = 13 and block ratio 0.1; stored recurrence values up to
-    N = 16384 (the stored matrices of all larger items would not fit beside the rest).
-    Large mixed batch: M = 16, segment length 1024."""
+    """Fixed plan options of the batched workloads (--batch-fixed; otherwise
+    autotune.build_batch_plans chooses).  Batch of 4096: M = 13 and block ratio 0.1; stored
+    recurrence values up to N = 16384.  Large mixed batch: M = 16, segment length 1024."""
     if big:
         return {"M": 16, "seg_len": 1024}
     o = {"M": 13, "seg_len": 256, "ratio": 0.1}
@@ -388,7 +387,7 @@ def run_batched(ctx, big=False, steps=None):
         fft_tune["tune_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     tune = None
-    if big or args.batch_fixed:
+    if args.batch_fixed:
         plans = []
         for N, a, b, d, c in items:
             plans.append(cjt.Plan(N, a, b, precision=precision, directions=cjt.CJT_FWD if d == 1 else cjt.CJT_INV,
@@ -546,8 +545,9 @@ def run_batched(ctx, big=False, steps=None):
                      "CUDA graph per step" % ("double-float" if precision == cjt.CJT_DFLOAT else "FP32"))
         if big else BATCH_DESC % PREC_NAMES[args.precision],
         "coefficients_per_step": coeffs,
-        "plan_options": "M=16, seg_len=1024" if big else (
-            "M=13, seg_len=256, ratio=0.1, power-of-two grid, rec_store for N <= 16384" if args.batch_fixed else
+        "plan_options": (
+            ("M=16, seg_len=1024" if big else "M=13, seg_len=256, ratio=0.1, rec_store for N <= 16384")
+            if args.batch_fixed else
             {"autotuner": "autotune.build_batch_plans: per size class (M, ratio) by the modelled FP64-pipe work "
                           "of candidate plans; stored recurrence values in increasing N while the plans fit %.0f GB"
                           % ((tune["plan_budget_bytes"] if tune else 0) / 1e9), "classes": tune["classes"] if tune else None,

@@ -135,19 +135,25 @@ def best_options(N: int, alpha: float, beta: float, precision: int = 0, directio
 # Measured fractions of the FP64 pipe peak of the grouped stage kernels (grouped batch,
 # serialised launches on GB300): recurrence at execution, stored values, transforms.
 ETA_REC, ETA_STORED, ETA_FFT = 0.75, 0.85, 0.82
+# The mixed form runs the asymptotic blocks' transforms on the FP32 pipe (64 times the FP64
+# rate on GB300, but the transforms then wait on memory and latency): they are modelled at a
+# tenth of their FP64 cost; its final DCT-I / inverse front end stay FP64.
+MIXED_ASY_FFT_FACTOR = 0.1
 BATCH_CANDIDATES = [{"M": M, "ratio": r} for M in (7, 10, 13, 16) for r in (0.0, 0.1, 0.05)]
 
 
-def _work_model(info, direction):
+def _work_model(info, direction, precision=0):
     """Modelled FP64-pipe seconds-at-peak factors of one execution: (recurrence steps,
     transform flop / ETA_FFT), from a plan's summary."""
     import math
+    from . import cjt
     f = direction == 1
     L = info["fft_len_fwd"] if f else info["fft_len_inv"]
     nfft = info["nfft_fwd"] if f else info["nfft_inv"]
     steps = info["rec_steps_fwd"] if f else info["rec_steps_inv"]
     lg = max(math.log2(max(L, 2)), 1.0)
-    return float(steps), nfft * 5.0 * L * lg / ETA_FFT
+    asy = max(nfft - 1, 0) * (MIXED_ASY_FFT_FACTOR if precision == cjt.CJT_MIXED else 1.0)
+    return float(steps), (asy + 1.0) * 5.0 * L * lg / ETA_FFT
 
 
 def batch_class_options(items, precision: int = 0, samples: int = 2, seed: int = 0):
@@ -180,7 +186,7 @@ def batch_class_options(items, precision: int = 0, samples: int = 2, seed: int =
                     break
                 inf = p.info()
                 p.close()
-                steps, fft = _work_model(inf, d)
+                steps, fft = _work_model(inf, d, precision)
                 t_rec += 8.0 * steps / ETA_REC + fft
                 t_sto += 2.0 * steps / ETA_STORED + fft
                 tab += inf["device_bytes"]

@@ -228,13 +228,15 @@ __global__ void __launch_bounds__(32 * cjt_kern::SW) k_g_rec_inv_stored(const GD
     cjt_kern::rec_inv_stored_cta(it, d.Ng, d.g, d.E, d.part);
 }
 
-constexpr int GRED_WARPS = 8;   // many small transforms: more blocks resident per SM
-__global__ void __launch_bounds__(32 * GRED_WARPS) k_g_inv_reduce(const GDesc *__restrict__ D,
-                                                                           const GTab *__restrict__ tab) {
+// W warps per block: 8 for small transforms (more blocks resident per SM), 32 for large ones,
+// whose heavy low-degree segments have few blocks (the bits are the same for every W)
+template <int W>
+__global__ void __launch_bounds__(32 * W) k_g_inv_reduce(const GDesc *__restrict__ D, const GTab *__restrict__ tab) {
     const GTab e = tab[blockIdx.x];
     const GDesc &d = D[e.item];
-    cjt_kern::inv_reduce_block<GRED_WARPS>(e.blk, d.N, d.seg_len, d.seg_ptr, d.seg_out, d.seg_b, d.part, d.y);
+    cjt_kern::inv_reduce_block<W>(e.blk, d.N, d.seg_len, d.seg_ptr, d.seg_out, d.seg_b, d.part, d.y);
 }
+constexpr int64_t kReduceWideRows = 1 << 19;   // inverse grids of at least this many rows: W = 32
 
 // ---------------------------------------------------------------------------
 // host side
@@ -358,16 +360,21 @@ void add_rec(cjt_group_s *g, std::vector<Step> &out, const std::vector<int> &sel
 }
 
 void add_reduce(cjt_group_s *g, std::vector<Step> &out, const std::vector<int> &sel) {
-    std::vector<GTab> tab;
-    for (int t : sel)
-        for (int64_t b = 0; b * 32 < g->desc[t].N + 1; ++b) tab.push_back({t, (int)b});
-    if (tab.empty()) return;
-    Step s;
-    s.type = ST_REDUCE;
-    s.cat = CJT_BSTAGE_REDUCE;
-    s.tab = push_table(g->tables, tab);
-    s.grid = (int64_t)tab.size();
-    out.push_back(s);
+    for (int wide = 0; wide < 2; ++wide) {
+        std::vector<GTab> tab;
+        for (int t : sel) {
+            if ((g->desc[t].Ng >= kReduceWideRows) != (wide == 1)) continue;
+            for (int64_t b = 0; b * 32 < g->desc[t].N + 1; ++b) tab.push_back({t, (int)b});
+        }
+        if (tab.empty()) continue;
+        Step s;
+        s.type = ST_REDUCE;
+        s.op = wide ? 32 : 8;
+        s.cat = CJT_BSTAGE_REDUCE;
+        s.tab = push_table(g->tables, tab);
+        s.grid = (int64_t)tab.size();
+        out.push_back(s);
+    }
 }
 
 Step ev_step(int type, int e) {
@@ -433,8 +440,10 @@ int run_step(cjt_group_s *g, const Step &s, int pair, cudaStream_t st) {
             return CJT_OK;
         }
         case ST_REDUCE:
-            k_g_inv_reduce<<<(unsigned)s.grid, 32 * GRED_WARPS, 0, st>>>(
-                D, reinterpret_cast<const GTab *>(T + s.tab));
+            if (s.op == 32)
+                k_g_inv_reduce<32><<<(unsigned)s.grid, 32 * 32, 0, st>>>(D, reinterpret_cast<const GTab *>(T + s.tab));
+            else
+                k_g_inv_reduce<8><<<(unsigned)s.grid, 32 * 8, 0, st>>>(D, reinterpret_cast<const GTab *>(T + s.tab));
             CJT_CUDA_TRY(cudaGetLastError());
             return CJT_OK;
         case ST_FFT: {
