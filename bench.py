@@ -71,13 +71,15 @@ def precision_code(cjt, name):
 
 
 def default_grid(N):
-    """The Lobatto grid a plan takes by default: the least G >= N of the forms 2^a, 3 2^a."""
-    g2, g3 = 1, 3
-    while g2 < N:
-        g2 <<= 1
-    while g3 < N:
-        g3 <<= 1
-    return min(g2, g3)
+    """The Lobatto grid a plan takes by default: the least G >= N of the forms 2^a, 3 2^a,
+    5 2^a."""
+    best = None
+    for q in (1, 3, 5):
+        g = q
+        while g < N:
+            g <<= 1
+        best = g if best is None else min(best, g)
+    return best
 
 
 def lg2(v):
@@ -373,12 +375,13 @@ def run_batched(ctx, big=False, steps=None):
         from paper_1602_02618_gb300 import autotune
         t0 = time.perf_counter()
         # the power-of-two transform lengths the plans run: 2G and 4G, or their power-of-two
-        # factors when G = 3 2^a (the default grid: the least 2^a or 3 2^a >= N)
+        # factors when G = 3 2^a or 5 2^a (the default grid: the least of 2^a, 3 2^a, 5 2^a >= N)
         lens = set()
         for N, *_ in items:
             G = default_grid(N)
+            q = 3 if G % 3 == 0 else 5 if G % 5 == 0 else 1
             for L in (2 * G, 4 * G):
-                lens.add(int(math.log2(L // 3 if L % 3 == 0 else L)))
+                lens.add(int(math.log2(L // q)))
         lens = sorted(lens)
         fft_tune = {"precision": args.precision if not big else "mixed",
                     "lengths": autotune.tune_fft(precision, lens), "tune_s": None}
@@ -875,7 +878,7 @@ def main():
     ap.add_argument("--planners", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--lanes", type=int, default=16)
-    ap.add_argument("--batch-plan-gb", type=float, default=230.0,
+    ap.add_argument("--batch-plan-gb", type=float, default=250.0,
                     help="device memory the batched workload's plans may take (autotuned options)")
     ap.add_argument("--batch-fixed", action="store_true",
                     help="batched workload with fixed options (M=13, ratio=0.1, stored values for N <= 16384)")

@@ -121,12 +121,12 @@ typedef struct {
                          (App. B.2-B.3) in either case.                                  */
     int grid;         /* Lobatto grid of the evaluation.  -1: the paper's, x_j = cos(pi j/N)
                          (forward) and cos(pi j/(2N)) (inverse); transforms of lengths 2N and
-                         4N are then direct when N is 2^a or 3 2^a, and Bluestein transforms
-                         otherwise.  1: G, the least power of two >= N, in place of N:
-                         x_j = cos(pi j/G) and cos(pi j/(2G)).  0 (default): G, the least
-                         integer >= N of the forms 2^a and 3 2^a (at most 4N/3; N itself when N
-                         has that form); transforms of length 3 2^b take one radix-3 step and
-                         power-of-two FFTs.  Every grid gives the same map (to rounding): a
+                         4N are then direct when N is 2^a, 3 2^a or 5 2^a, and Bluestein
+                         transforms otherwise.  1: G, the least power of two >= N, in place of
+                         N: x_j = cos(pi j/G) and cos(pi j/(2G)).  0 (default): G, the least
+                         integer >= N of the forms 2^a, 3 2^a and 5 2^a (at most 4N/3; N itself
+                         when N has one of them); transforms of lengths 3 2^b and 5 2^b take one
+                         radix-3 or radix-5 step and power-of-two FFTs.  Every grid gives the same map (to rounding): a
                          polynomial of degree N <= G is interpolated exactly by the inverse
                          DCT-I on G+1 points, whose coefficients above N vanish, and the
                          (2G+1)-point Clenshaw--Curtis rule is exact wherever the

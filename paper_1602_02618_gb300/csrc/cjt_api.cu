@@ -197,7 +197,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     if (o.overlap < CJT_OVERLAP_AUTO || o.overlap > CJT_OVERLAP_REC_FIRST) return CJT_EINVAL;
     if (o.overlap == CJT_OVERLAP_AUTO) o.overlap = CJT_OVERLAP_ASY_FIRST;
     if (o.seg_len < 32 || o.seg_len > (1 << 20) || (o.seg_len % 32) != 0) return CJT_EINVAL;
-    if (N > (1LL << 21) && !is_pow2(N) && !cjt_is_3pow2(N) && o.grid == -1)
+    if (N > (1LL << 21) && !is_pow2(N) && !cjt_is_3pow2(N) && !cjt_is_5pow2(N) && o.grid == -1)
         return CJT_EUNSUPPORTED;   // Bluestein lengths <= 2^24
 
     cjt_plan_s *p = new (std::nothrow) cjt_plan_s();

@@ -388,72 +388,106 @@ int fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles
 }
 
 // ---------------------------------------------------------------------------
-// Lengths L = 3 L2, L2 = 2^b: X[k1 + 3 k2] = sum_{n2} omega_{L2}^{n2 k2} (omega_L^{n2 k1}
-// sum_{n1 < 3} x[n1 L2 + n2] omega_3^{n1 k1}): one radix-3 step with its twiddles, then the
-// power-of-two FFTs of the three rows, whose stores put X in natural order.
+// Lengths L = q L2, L2 = 2^b, q = 3 or 5: X[k1 + q k2] = sum_{n2} omega_{L2}^{n2 k2}
+// (omega_L^{n2 k1} sum_{n1 < q} x[n1 L2 + n2] omega_q^{n1 k1}): one radix-q step with its
+// twiddles, then the power-of-two FFTs of the q rows, whose stores put X in natural order.
 // ---------------------------------------------------------------------------
 template <typename V> __device__ __forceinline__ V cconst(double re, double im) { V r; r.x = re; r.y = im; return r; }
 template <> __device__ __forceinline__ dfc cconst<dfc>(double re, double im) { return dfc_make(df_from(re), df_from(im)); }
 
-// for each sequence and n2 < L2: the 3-point DFT of x[n2], x[n2 + L2], x[n2 + 2 L2]
-// (omega_3 = -1/2 - i sqrt(3)/2), outputs 1 and 2 times omega_L^{n2} and omega_L^{2 n2},
-// stored at n2 + k1 L2 of `out` (which may be `in`: each thread reads and writes its own
-// three slots)
-template <typename R>
-__global__ void k_fft_r3(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__restrict__ out, int logL2,
-                         int64_t total, const typename cplx<R>::t *__restrict__ tw3, int64_t tstride) {
+// the q-point DFT of x[0..q-1] (omega_q = exp(-2 pi i / q)) into y[0..q-1]
+template <typename V, int Q> struct SmallDft;
+template <typename V> struct SmallDft<V, 3> {
+    // omega_3 = -1/2 - i sqrt(3)/2
+    static __device__ __forceinline__ void run(const V *x, V *y) {
+        const V sum = cadd(x[1], x[2]), dif = csub(x[1], x[2]);
+        y[0] = cadd(x[0], sum);
+        const V mid = csub(x[0], cscale(sum, 0.5));                                      // x0 - (x1 + x2)/2
+        const V rot = cmul(dif, cconst<V>(0.0, -0.86602540378443864676372317075294));   // -i sqrt(3)/2 (x1 - x2)
+        y[1] = cadd(mid, rot);
+        y[2] = csub(mid, rot);
+    }
+};
+// a times a real constant c (any c: the double-float form's cscale takes powers of two only)
+template <typename V> __device__ __forceinline__ V cmul_real(V a, double c) { return cscale(a, c); }
+template <> __device__ __forceinline__ dfc cmul_real<dfc>(dfc a, double c) { return cmul(a, cconst<dfc>(c, 0.0)); }
+template <typename V> struct SmallDft<V, 5> {
+    // with s = x1 + x4, t = x2 + x3, d = x1 - x4, e = x2 - x3, c_k = cos(2 pi k/5),
+    // s_k = sin(2 pi k/5): X1, X4 = x0 + c1 s + c2 t -+ i (s1 d + s2 e) and
+    // X2, X3 = x0 + c2 s + c1 t -+ i (s2 d - s1 e)
+    static __device__ __forceinline__ void run(const V *x, V *y) {
+        const double c1 = 0.30901699437494742410229341718282, c2 = -0.80901699437494742410229341718282;
+        const double s1 = 0.95105651629515357211643933337938, s2 = 0.58778525229247312916870595463907;
+        const V sp = cadd(x[1], x[4]), tp = cadd(x[2], x[3]), dm = csub(x[1], x[4]), em = csub(x[2], x[3]);
+        y[0] = cadd(x[0], cadd(sp, tp));
+        const V a1 = cadd(x[0], cadd(cmul_real(sp, c1), cmul_real(tp, c2)));
+        const V a2 = cadd(x[0], cadd(cmul_real(sp, c2), cmul_real(tp, c1)));
+        const V b1 = cadd(cmul_real(dm, s1), cmul_real(em, s2));   // X1 = a1 - i b1
+        const V b2 = csub(cmul_real(dm, s2), cmul_real(em, s1));   // X2 = a2 - i b2
+        const V mib1 = cmul_mi(b1), mib2 = cmul_mi(b2);
+        y[1] = cadd(a1, mib1);
+        y[4] = csub(a1, mib1);
+        y[2] = cadd(a2, mib2);
+        y[3] = csub(a2, mib2);
+    }
+};
+
+// for each sequence and n2 < L2: the q-point DFT of x[n2 + n1 L2], n1 < q, its output k1
+// times omega_L^{k1 n2}, stored at n2 + k1 L2 of `out` (which may be `in`: each thread reads
+// and writes its own q slots)
+template <typename R, int Q>
+__global__ void k_fft_rq(const typename cplx<R>::t *__restrict__ in, typename cplx<R>::t *__restrict__ out, int logL2,
+                         int64_t total, const typename cplx<R>::t *__restrict__ twq, int64_t tstride) {
     using V = typename cplx<R>::t;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= total) return;
     const int64_t L2 = 1LL << logL2;
     const int64_t t = i >> logL2, n2 = i & (L2 - 1);
-    const int64_t base = t * 3 * L2 + n2;
-    const V x0 = in[base], x1 = in[base + L2], x2 = in[base + 2 * L2];
-    const V sum = cadd(x1, x2), dif = csub(x1, x2);
-    const V y0 = cadd(x0, sum);
-    const V mid = csub(x0, cscale(sum, 0.5));                                           // x0 - (x1 + x2)/2
-    const V rot = cmul(dif, cconst<V>(0.0, -0.86602540378443864676372317075294));      // -i sqrt(3)/2 (x1 - x2)
-    const V y1 = cadd(mid, rot), y2 = csub(mid, rot);
-    out[base] = y0;
-    out[base + L2] = cmul(y1, tw3[n2 * tstride]);
-    out[base + 2 * L2] = cmul(y2, tw3[2 * n2 * tstride]);
+    const int64_t base = t * Q * L2 + n2;
+    V x[Q], y[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) x[k] = in[base + k * L2];
+    SmallDft<V, Q>::run(x, y);
+    out[base] = y[0];
+#pragma unroll
+    for (int k = 1; k < Q; ++k) out[base + k * L2] = cmul(y[k], twq[k * n2 * tstride]);
 }
 
-template <typename R>
-int fft_r3(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &T, cudaStream_t st) {
+template <typename R, int Q>
+int fft_rq(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &T, cudaStream_t st) {
     using V = typename cplx<R>::t;
-    const int64_t L2 = L / 3;
+    const int64_t L2 = L / Q;
     const int logL2 = ilog2(L2), logLtab = ilog2(T.Ltab);
-    if (!T.tw3 || T.Ltab3 <= 0 || T.Ltab3 % L != 0 || L2 > T.Ltab || !scratch) return CJT_EINVAL;
-    const int64_t total = batch * L2, ts = T.Ltab3 / L;
+    if (!T.twq || T.Ltabq <= 0 || T.Ltabq % L != 0 || L2 > T.Ltab || !scratch) return CJT_EINVAL;
+    const int64_t total = batch * L2, ts = T.Ltabq / L;
     const int pr = std::is_same<R, float>::value ? 1 : std::is_same<R, dfloat>::value ? 2 : 0;
     const FftCfg &cfg = g_fft_cfg[pr][logL2];
     const int ctas = cfg.ctas.load(std::memory_order_relaxed);
     const unsigned nb = (unsigned)((total + 255) / 256);
     if (L2 <= 4096) {
-        // radix-3 step into the scratch buffer, then the rows (three columns of length L2 per
-        // sequence) in one pass, stored at X[k1 + 3 k2]
-        k_fft_r3<R><<<nb, 256, 0, st>>>((const V *)data, (V *)scratch, logL2, total, (const V *)T.tw3, ts);
+        // radix-q step into the scratch buffer, then the rows (q columns of length L2 per
+        // sequence) in one pass, stored at X[k1 + q k2]
+        k_fft_rq<R, Q><<<nb, 256, 0, st>>>((const V *)data, (V *)scratch, logL2, total, (const V *)T.twq, ts);
         CJT_CUDA_TRY(cudaGetLastError());
         if (L2 == 1) {
-            CJT_CUDA_TRY(cudaMemcpyAsync(data, scratch, sizeof(V) * 3 * batch, cudaMemcpyDeviceToDevice, st));
+            CJT_CUDA_TRY(cudaMemcpyAsync(data, scratch, sizeof(V) * Q * batch, cudaMemcpyDeviceToDevice, st));
             return CJT_OK;
         }
-        return launch_sub<R>(scratch, data, logL2, 3, batch, 1, L2, L, 3, 1, L, T.tw, logLtab, -1, T.stw, T.fma, st,
+        return launch_sub<R>(scratch, data, logL2, Q, batch, 1, L2, L, Q, 1, L, T.tw, logLtab, -1, T.stw, T.fma, st,
                              ctas);
     }
-    // radix-3 step in place; the four-step transform of the 3 batch rows (contiguous, stride
-    // L2): pass A over all rows into the scratch buffer, pass B per row k1 into X[k1 + 3 k]
-    k_fft_r3<R><<<nb, 256, 0, st>>>((const V *)data, (V *)data, logL2, total, (const V *)T.tw3, ts);
+    // radix-q step in place; the four-step transform of the q batch rows (contiguous, stride
+    // L2): pass A over all rows into the scratch buffer, pass B per row k1 into X[k1 + q k]
+    k_fft_rq<R, Q><<<nb, 256, 0, st>>>((const V *)data, (V *)data, logL2, total, (const V *)T.twq, ts);
     CJT_CUDA_TRY(cudaGetLastError());
     if (logL2 > 24) return CJT_EUNSUPPORTED;
     const int log1 = cfg.split.load(std::memory_order_relaxed) ? logL2 / 2 : (logL2 + 1) / 2, log2 = logL2 - log1;
     const int64_t A1 = 1LL << log1, A2 = 1LL << log2;
-    int rc = launch_sub<R>(data, scratch, log1, A2, 3 * batch, A2, 1, L2, A2, 1, L2, T.tw, logLtab, logL2, T.stw, T.fma,
+    int rc = launch_sub<R>(data, scratch, log1, A2, Q * batch, A2, 1, L2, A2, 1, L2, T.tw, logLtab, logL2, T.stw, T.fma,
                            st, ctas);
     if (rc) return rc;
-    for (int k1 = 0; k1 < 3; ++k1) {
-        rc = launch_sub<R>((const V *)scratch + k1 * L2, (V *)data + k1, log2, A1, batch, 1, A2, L, 3 * A1, 3, L, T.tw,
+    for (int k1 = 0; k1 < Q; ++k1) {
+        rc = launch_sub<R>((const V *)scratch + k1 * L2, (V *)data + k1, log2, A1, batch, 1, A2, L, Q * A1, Q, L, T.tw,
                            logLtab, -1, T.stw, T.fma, st, ctas);
         if (rc) return rc;
     }
@@ -464,7 +498,8 @@ template <typename R>
 int fft_any(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &T, cudaStream_t st) {
     if (L <= 1 || batch <= 0) return CJT_OK;
     if ((L & (L - 1)) == 0) return fft_pow2<R>(data, scratch, L, batch, T, st);
-    if (cjt_is_3pow2(L)) return fft_r3<R>(data, scratch, L, batch, T, st);
+    if (cjt_is_3pow2(L)) return fft_rq<R, 3>(data, scratch, L, batch, T, st);
+    if (cjt_is_5pow2(L)) return fft_rq<R, 5>(data, scratch, L, batch, T, st);
     return CJT_EINVAL;
 }
 
@@ -557,7 +592,7 @@ int dft_exec(const Dft &d, void *data, void *work, void *scratch, int64_t batch,
 }  // namespace
 
 int64_t cjt_dft_padded(int64_t L, int64_t S, int64_t K) {
-    if (L <= 1 || (L & (L - 1)) == 0 || cjt_is_3pow2(L)) return 0;
+    if (L <= 1 || cjt_odd_radix(L) > 0) return 0;
     int64_t P = 1;
     while (P < S + K - 1) P <<= 1;
     return P;
@@ -617,7 +652,7 @@ int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twid
 }
 
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch) {
-    return (L > 4096 || cjt_is_3pow2(L)) ? L * batch : 0;
+    return (L > 4096 || cjt_odd_radix(L) > 1) ? L * batch : 0;
 }
 
 int cjt_fft_any(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &tw, int prec, cudaStream_t st) {

@@ -22,7 +22,7 @@
 // kernels (cjt_kern.cuh), so each result is bit-identical to the transform run alone.
 //
 // Eligible items: N >= 1, FP64 or mixed (FP32 transforms) precision, no parameter shift,
-// transform lengths 2^b or 3 2^b (the default grids).  The batch runs the others (double-
+// transform lengths 2^b, 3 2^b or 5 2^b (the default grids).  The batch runs the others (double-
 // float form, shifted parameters, Bluestein lengths) one chain per item on its lanes.
 #include <cuda_runtime.h>
 
@@ -48,7 +48,7 @@ inline int ilog2_exact(int64_t v) {
 // Everything one transform's stage kernels read or write.
 struct __align__(16) GDesc {
     int64_t N, G, Ng, L;      // degree; forward grid G; grid of this direction (G or 2G); ASY length
-    int logL, M, nblk, nq, npair, seg_len, l3, pad1;   // L = 2^logL, or 3 2^logL when l3
+    int logL, M, nblk, nq, npair, seg_len, q, pad1;   // L = q 2^logL, q = 1, 3 or 5
     RecTables rt;
     const RecItem *items;
     int64_t nitems;
@@ -108,7 +108,7 @@ template <> struct Elem<OP_INV_G> {
 };
 // the transform (pair) of element idx of a pack's index space, and the element within it
 __device__ __forceinline__ int pair_of(const GDesc &d, int64_t idx) {
-    return d.l3 ? (int)((idx >> d.logL) / 3) : (int)(idx >> d.logL);
+    return d.q > 1 ? (int)((idx >> d.logL) / d.q) : (int)(idx >> d.logL);
 }
 template <> struct Elem<OP_PACK_FWD> {
     static __host__ __device__ int64_t size(const GDesc &d) { return (int64_t)d.npair * d.L; }
@@ -122,7 +122,7 @@ template <> struct Elem<OP_PACK_FWD> {
 template <> struct Elem<OP_PACK_INV> {
     static __host__ __device__ int64_t size(const GDesc &d) { return (int64_t)d.npair * d.Ng; }
     template <typename V, typename R> static __device__ void apply(const GDesc &d, int64_t idx, PairCache &pc) {
-        const int p = d.l3 ? (int)((idx >> (d.logL - 1)) / 3) : (int)(idx >> (d.logL - 1));
+        const int p = d.q > 1 ? (int)((idx >> (d.logL - 1)) / d.q) : (int)(idx >> (d.logL - 1));
         cjt_kern::asy_pack_inv_elem<V, R>(idx - (int64_t)p * d.Ng, p, pc.of(p, d), d.Ng, d.L, d.box, d.u, d.v, d.g,
                                           (V *)d.fft);
     }
@@ -664,8 +664,8 @@ GDesc make_desc(const cjt_plan_s *p, int dir, const double *in, double *out) {
     d.G = p->Gf;
     d.Ng = gw.Ng;
     d.L = f ? p->Lf : p->Li;
-    d.l3 = cjt_is_3pow2(d.L) ? 1 : 0;
-    d.logL = ilog2_exact(std::max<int64_t>(d.l3 ? d.L / 3 : d.L, 1));
+    d.q = std::max(cjt_odd_radix(d.L), 1);
+    d.logL = ilog2_exact(std::max<int64_t>(d.L / d.q, 1));
     d.M = p->M;
     d.nblk = gw.nblk;
     d.nq = gw.nblk * p->M;

@@ -193,14 +193,22 @@ struct Twiddles {
     const void *stw = nullptr;
     const void *fma = nullptr;   // FP64 only: TwFma tables of the decimation-in-time stages
     int lmax = 0;                // the stage tables cover block lengths up to 2^lmax
-    const void *tw3 = nullptr;   // omega_{Ltab3}^k, k < Ltab3, for the radix-3 step of lengths 3 2^b
-    int64_t Ltab3 = 0;           // a multiple of every such length (0: none)
+    const void *twq = nullptr;   // omega_{Ltabq}^k, k < Ltabq, for the odd-radix step of lengths q 2^b
+    int64_t Ltabq = 0;           // a multiple of every such length (0: none)
 };
-// L = 3 2^b (b >= 0): transforms of such lengths take one radix-3 step and power-of-two FFTs
-__host__ __device__ inline bool cjt_is_3pow2(int64_t L) {
-    if (L < 3 || L % 3 != 0) return false;
-    const int64_t r = L / 3;
+// L = q 2^b (b >= 0, q = 3 or 5): transforms of such lengths take one radix-q step and
+// power-of-two FFTs
+__host__ __device__ inline bool cjt_is_qpow2(int64_t L, int q) {
+    if (L < q || L % q != 0) return false;
+    const int64_t r = L / q;
     return (r & (r - 1)) == 0;
+}
+__host__ __device__ inline bool cjt_is_3pow2(int64_t L) { return cjt_is_qpow2(L, 3); }
+__host__ __device__ inline bool cjt_is_5pow2(int64_t L) { return cjt_is_qpow2(L, 5); }
+// the odd factor q of L = q 2^b (3 or 5), 1 for a power of two, 0 for any other length
+__host__ __device__ inline int cjt_odd_radix(int64_t L) {
+    if (L >= 1 && (L & (L - 1)) == 0) return 1;
+    return cjt_is_3pow2(L) ? 3 : cjt_is_5pow2(L) ? 5 : 0;
 }
 __host__ __device__ inline int64_t stw_base(int lb) { return 3 * ((1LL << (lb - 2)) - 1); }
 
@@ -276,8 +284,8 @@ struct cjt_plan_s {
     void *d_twdf = nullptr;       // dfc[Ltab]
     void *d_stw64 = nullptr, *d_stw32 = nullptr, *d_stwdf = nullptr;   // stage tables (Twiddles)
     void *d_twfma = nullptr;      // TwFma tables (FP64 decimation-in-time stages)
-    int64_t Ltab3 = 0;            // radix-3 twiddles omega_{Ltab3}^k (grids 3 2^a): 4G, or 2G
-    void *d_tw3_64 = nullptr, *d_tw3_32 = nullptr, *d_tw3df = nullptr;
+    int64_t Ltabq = 0;            // odd-radix twiddles omega_{Ltabq}^k (grids q 2^a, q = 3, 5): 4G, or 2G
+    void *d_twq_64 = nullptr, *d_twq_32 = nullptr, *d_twqdf = nullptr;
     int stw_lmax = 0;             // the stage tables' top level (block length 2^stw_lmax)
     void *twc = nullptr;          // the shared twiddle tables the fields above point into
     Twiddles twiddles(int prec) const {
@@ -287,8 +295,8 @@ struct cjt_plan_s {
         t.stw = prec == PREC_F32 ? d_stw32 : prec == PREC_DF ? d_stwdf : d_stw64;
         t.fma = prec == PREC_F64 ? d_twfma : nullptr;
         t.lmax = stw_lmax;
-        t.tw3 = prec == PREC_F32 ? d_tw3_32 : prec == PREC_DF ? d_tw3df : d_tw3_64;
-        t.Ltab3 = Ltab3;
+        t.twq = prec == PREC_F32 ? d_twq_32 : prec == PREC_DF ? d_twqdf : d_twq_64;
+        t.Ltabq = Ltabq;
         return t;
     }
     int prec_asy = PREC_F64;      // element type of the asymptotic transforms
@@ -595,7 +603,7 @@ inline int64_t cjt_asy_nM(const AsyExp &e, int M, double eps) {
 // launchers implemented in the .cu files
 // ---------------------------------------------------------------------------
 int cjt_fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &tw, int prec, cudaStream_t st);
-// L a power of two or 3 2^b (scratch of cjt_fft_scratch_elems(L, batch) elements)
+// L a power of two, 3 2^b or 5 2^b (scratch of cjt_fft_scratch_elems(L, batch) elements)
 int cjt_fft_any(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &tw, int prec, cudaStream_t st);
 int64_t cjt_fft_scratch_elems(int64_t L, int64_t batch);
 int cjt_fft_prime();
@@ -612,7 +620,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st);
 // Stream-ordered temporary device memory for plan building, from a library-owned pool per
 // device that keeps up to 1 GiB of freed memory for the next plans (free with cudaFreeAsync).
 cudaError_t cjt_tmp_alloc(void **ptr, size_t bytes, cudaStream_t st);
-// The plan's twiddle tables (from p->Ltab, p->Ltab3 and the transform precision pa): taken
+// The plan's twiddle tables (from p->Ltab, p->Ltabq and the transform precision pa): taken
 // from a per-device cache of tables shared by plans, built on `st` when absent.  A plan
 // that took tables gives them back with cjt_release_twiddles.
 int cjt_build_twiddles(cjt_plan_s *p, int pa, cudaStream_t st);

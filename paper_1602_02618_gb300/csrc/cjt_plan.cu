@@ -1016,7 +1016,7 @@ cudaError_t cjt_tmp_alloc(void **ptr, size_t bytes, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------------
-// Twiddle tables shared by plans.  They depend only on (device, Ltab, Ltab3, transform
+// Twiddle tables shared by plans.  They depend only on (device, Ltab, Ltabq, transform
 // precision), so plans of the same lengths take one copy: a plan built while a copy exists
 // waits for its construction on its own stream (an event) and launches nothing.  Unused
 // copies stay cached up to CJT_TWIDDLE_CACHE_MB (default 1024) and are freed least
@@ -1025,10 +1025,10 @@ cudaError_t cjt_tmp_alloc(void **ptr, size_t bytes, cudaStream_t st) {
 namespace {
 struct TwShared {
     int dev = 0, pa = 0;
-    int64_t Ltab = 0, Ltab3 = 0;
+    int64_t Ltab = 0, Ltabq = 0;
     void *tw64 = nullptr, *tw32 = nullptr, *twdf = nullptr;
     void *stw64 = nullptr, *stw32 = nullptr, *stwdf = nullptr, *twfma = nullptr;
-    void *tw3_64 = nullptr, *tw3_32 = nullptr, *tw3df = nullptr;
+    void *twq_64 = nullptr, *twq_32 = nullptr, *twqdf = nullptr;
     int lmax = 0;
     int64_t bytes = 0;
     int refs = 0;
@@ -1066,12 +1066,12 @@ template <typename T> int tw_alloc(TwShared *e, void **ptr, int64_t count) {
 
 int tw_build(TwShared *e, cudaStream_t st) {
     const int pa = e->pa;
-    if (e->Ltab3 > 0) {
-        TRY(tw_alloc<double2>(e, &e->tw3_64, e->Ltab3));
-        if (pa == PREC_F32) TRY(tw_alloc<float2>(e, &e->tw3_32, e->Ltab3));
-        if (pa == PREC_DF) TRY(tw_alloc<double2>(e, &e->tw3df, e->Ltab3));   // dfc: 16 bytes
-        k_twiddles<<<blocks_for(e->Ltab3, 256), 256, 0, st>>>(e->Ltab3, (double2 *)e->tw3_64, (float2 *)e->tw3_32,
-                                                              (dfc *)e->tw3df);
+    if (e->Ltabq > 0) {
+        TRY(tw_alloc<double2>(e, &e->twq_64, e->Ltabq));
+        if (pa == PREC_F32) TRY(tw_alloc<float2>(e, &e->twq_32, e->Ltabq));
+        if (pa == PREC_DF) TRY(tw_alloc<double2>(e, &e->twqdf, e->Ltabq));   // dfc: 16 bytes
+        k_twiddles<<<blocks_for(e->Ltabq, 256), 256, 0, st>>>(e->Ltabq, (double2 *)e->twq_64, (float2 *)e->twq_32,
+                                                              (dfc *)e->twqdf);
         CJT_CUDA_TRY(cudaGetLastError());
     }
     TRY(tw_alloc<double2>(e, &e->tw64, e->Ltab));
@@ -1137,7 +1137,7 @@ int cjt_build_twiddles(cjt_plan_s *p, int pa, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_tw_mu);
     TwShared *e = nullptr;
     for (TwShared *c : g_tw)
-        if (c->dev == dev && c->pa == pa && c->Ltab == p->Ltab && c->Ltab3 == p->Ltab3) e = c;
+        if (c->dev == dev && c->pa == pa && c->Ltab == p->Ltab && c->Ltabq == p->Ltabq) e = c;
     if (e) {
         CJT_CUDA_TRY(cudaStreamWaitEvent(st, e->ready, 0));
     } else {
@@ -1145,7 +1145,7 @@ int cjt_build_twiddles(cjt_plan_s *p, int pa, cudaStream_t st) {
         e->dev = dev;
         e->pa = pa;
         e->Ltab = p->Ltab;
-        e->Ltab3 = p->Ltab3;
+        e->Ltabq = p->Ltabq;
         const int rc = tw_build(e, st);
         if (rc) {
             cudaStreamSynchronize(st);
@@ -1164,9 +1164,9 @@ int cjt_build_twiddles(cjt_plan_s *p, int pa, cudaStream_t st) {
     p->d_stw32 = e->stw32;
     p->d_stwdf = e->stwdf;
     p->d_twfma = e->twfma;
-    p->d_tw3_64 = e->tw3_64;
-    p->d_tw3_32 = e->tw3_32;
-    p->d_tw3df = e->tw3df;
+    p->d_twq_64 = e->twq_64;
+    p->d_twq_32 = e->twq_32;
+    p->d_twqdf = e->twqdf;
     p->stw_lmax = e->lmax;
     p->device_bytes += e->bytes;   // counted in every plan that uses them (an upper bound)
     return CJT_OK;
@@ -1230,12 +1230,14 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         while (G2 < N) G2 <<= 1;
         if (p->opts.grid == 1) {
             G = G2;
-        } else if (p->opts.grid == 0 && !pow2 && !cjt_is_3pow2(N)) {
-            // the least G >= N of the forms 2^a and 3 2^a: transforms of lengths 2G and 4G
-            // then take one radix-3 step at most, and the grid is at most 4/3 N
-            int64_t G3 = 3;
+        } else if (p->opts.grid == 0 && !pow2 && !cjt_is_3pow2(N) && !cjt_is_5pow2(N)) {
+            // the least G >= N of the forms 2^a, 3 2^a and 5 2^a: transforms of lengths 2G
+            // and 4G then take one radix-3 or radix-5 step at most, and the grid is at most
+            // 4/3 N
+            int64_t G3 = 3, G5 = 5;
             while (G3 < N) G3 <<= 1;
-            G = std::min(G2, G3);
+            while (G5 < N) G5 <<= 1;
+            G = std::min(G2, std::min(G3, G5));
         }
         p->Gf = p->Gi = G;
     }
@@ -1270,22 +1272,24 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         used.push_back({&p->dft_cc, 1});
     }
     // twiddle tables: powers of two up to the longest power-of-two (sub-)transform, and for
-    // lengths 3 2^b the radix-3 table of the longest such length (a multiple of the others)
+    // lengths q 2^b (q = 3 or 5, one q per plan) the radix-q table of the longest such length
+    // (a multiple of the others)
     p->Ltab = 2;
-    p->Ltab3 = 0;
+    p->Ltabq = 0;
     for (auto &u : used) {
         const Dft &d = *u.first;
+        const int q = d.P ? 1 : cjt_odd_radix(d.L);
         if (d.P) {
             p->Ltab = std::max(p->Ltab, d.P);
-        } else if (cjt_is_3pow2(d.L)) {
-            p->Ltab = std::max(p->Ltab, d.L / 3);
-            p->Ltab3 = std::max(p->Ltab3, d.L);
+        } else if (q > 1) {
+            p->Ltab = std::max(p->Ltab, d.L / q);
+            p->Ltabq = std::max(p->Ltabq, d.L);
         } else {
             p->Ltab = std::max(p->Ltab, d.L);
         }
     }
     for (auto &u : used)
-        if (!u.first->P && cjt_is_3pow2(u.first->L) && p->Ltab3 % u.first->L != 0) return CJT_EUNSUPPORTED;
+        if (!u.first->P && cjt_odd_radix(u.first->L) > 1 && p->Ltabq % u.first->L != 0) return CJT_EUNSUPPORTED;
     TRY(cjt_build_twiddles(p, pa, st));
     int64_t work = 0, scratch = 0;
     for (auto &u : used) {

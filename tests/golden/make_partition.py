@@ -1,7 +1,7 @@
 """Writes tests/golden/partition_ref.json: the paper's partition (Sec. 2.2) of the forward
 grid (Ng = G) and of the inverse transform's 2G grid for a few (N, alpha, beta, M), computed
 by oracle/partition.py (mpmath, 40 digits) and nothing else.  G is the grid a plan evaluates
-on: for N of the forms 2^a and 3 2^a, N itself; otherwise the least integer >= N of those
+on: for N of the forms 2^a, 3 2^a and 5 2^a, N itself; otherwise the least integer >= N of those
 forms (the default, plan option grid = 0) and the least power of two >= N (grid = 1).
 Run:  python tests/golden/make_partition.py
 """
@@ -24,10 +24,13 @@ def main():
         G2 = 1
         while G2 < N:
             G2 <<= 1
-        G3 = 3
+        G3, G5 = 3, 5
         while G3 < N:
             G3 <<= 1
-        grids = [(0, min(G2, G3))] + ([(1, G2)] if G3 < G2 else [])
+        while G5 < N:
+            G5 <<= 1
+        G0 = min(G2, G3, G5)
+        grids = [(0, G0)] + ([(1, G2)] if G0 < G2 else [])
         for grid, G in grids:
             for direction, Ng in (("forward", G), ("inverse", 2 * G)):
                 nM, r, blocks = P.partition(Ng, N, M, a, b)

@@ -201,12 +201,14 @@ def test_identity_at_N0(cjt):
 
 
 def default_grid(N):
-    """The least G >= N of the forms 2^a and 3 2^a."""
+    """The least G >= N of the forms 2^a, 3 2^a and 5 2^a."""
     G2 = 1 << (N - 1).bit_length() if N > 1 else 1
-    G3 = 3
+    G3, G5 = 3, 5
     while G3 < N:
         G3 <<= 1
-    return min(G2, G3)
+    while G5 < N:
+        G5 <<= 1
+    return min(G2, G3, G5)
 
 
 @pytest.mark.parametrize("grid", [0, 1, -1])
@@ -214,9 +216,10 @@ def default_grid(N):
 @pytest.mark.parametrize("N", [3, 5, 6, 7, 100, 1000, 1023, 1025, 3001, 10007])
 def test_general_N_matches_oracle(cjt, orc, N, alpha, beta, grid):
     """N not a power of two: by default the evaluation runs on the least Lobatto grid G >= N
-    of the forms 2^a and 3 2^a (grid 0: transforms of lengths 3 2^b take one radix-3 step),
-    on the power-of-two grid with grid 1; on the paper's grid (grid -1) the DCT-I/DST-I sums
-    go through Bluestein's chirp-z form unless N is 3 2^a."""
+    of the forms 2^a, 3 2^a and 5 2^a (grid 0: transforms of lengths 3 2^b or 5 2^b take one
+    radix-3 or radix-5 step), on the power-of-two grid with grid 1; on the paper's grid
+    (grid -1) the DCT-I/DST-I sums go through Bluestein's chirp-z form unless N is 3 2^a or
+    5 2^a."""
     c = inputs.decaying_coefficients(N, 1.0, inputs.BASE_SEED + 3 * N)
     plan = cjt.Plan(N, alpha, beta, grid=grid)
     info = plan.info()
@@ -259,13 +262,15 @@ def test_power_of_two_grid_large(cjt, orc):
         assert np.max(np.abs(run_inv(cjt, pg, fg) - c)) <= TOL * l1(c)
     big = cjt.Plan(3 * (1 << 20) + 1, 0.1, 0.2, directions=cjt.CJT_FWD, M=13)
     assert big.info()["grid_fwd"] == 1 << 22
-    # and a grid 3 2^a at large size: N = 40000 plans on 49152 = 3 2^14 by default
-    c = inputs.decaying_coefficients(40000, 1.5, 5000 + 40000)
-    p3 = cjt.Plan(40000, 0.3, -0.1, M=13, rec_store=1)
-    p2 = cjt.Plan(40000, 0.3, -0.1, M=13, rec_store=1, grid=1)
-    assert p3.info()["grid_fwd"] == 3 << 14 and p3.info()["fft_len_inv"] == 3 << 16
-    assert np.max(np.abs(run_fwd(cjt, p3, c) - run_fwd(cjt, p2, c))) <= TOL * l1(c)
-    assert np.max(np.abs(run_inv(cjt, p3, c) - run_inv(cjt, p2, c))) <= TOL * l1(c)
+    # and grids q 2^a at large size: N = 45000 plans on 49152 = 3 2^14 and N = 40000 on
+    # 40960 = 5 2^13 by default
+    for N, G in ((45000, 3 << 14), (40000, 5 << 13)):
+        c = inputs.decaying_coefficients(N, 1.5, 5000 + N)
+        pq = cjt.Plan(N, 0.3, -0.1, M=13, rec_store=1)
+        p2 = cjt.Plan(N, 0.3, -0.1, M=13, rec_store=1, grid=1)
+        assert pq.info()["grid_fwd"] == G and pq.info()["fft_len_inv"] == 4 * G
+        assert np.max(np.abs(run_fwd(cjt, pq, c) - run_fwd(cjt, p2, c))) <= TOL * l1(c)
+        assert np.max(np.abs(run_inv(cjt, pq, c) - run_inv(cjt, p2, c))) <= TOL * l1(c)
     with pytest.raises(cjt.CJTError) as e:
         cjt.Plan(3 * (1 << 20) + 1, 0.1, 0.2, grid=-1)
     assert e.value.code == cjt.CJT_EUNSUPPORTED

@@ -2,7 +2,7 @@
 partition evaluated independently in mpmath (tests/golden/partition_ref.json, written by
 tests/golden/make_partition.py from oracle/partition.py): n_M, the block ratio alpha_N and
 every block (j_k, i_k^1, i_k^2), on the forward grid and on the inverse transform's 2G grid,
-for the default grid (2^a or 3 2^a) and, for N of neither form, the power-of-two grid.
+for the default grid (2^a, 3 2^a or 5 2^a) and, for N of none of these forms, the power-of-two grid.
 A correct but more conservative partition (more recurrence, smaller boxes) fails here."""
 import json
 import os
