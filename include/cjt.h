@@ -405,7 +405,10 @@ int cjt_microbench_fma(int kind, double *flops, void *stream);
  * per precision (CJT_FP64, CJT_MIXED: float, CJT_DFLOAT: double-float) and log2 L:
  *   ctas_per_sm      CTAs per SM the tile size (sequences per CTA) aims at (1..32, default 4);
  *   split            four-step factorisation L = L1 L2 above one pass: 0 (default) the larger
- *                    factor first (L1 = 2^ceil(log2 L / 2)), 1 the smaller first;
+ *                    factor first (L1 = 2^ceil(log2 L / 2)), 1 the smaller first, 2 a first
+ *                    factor smaller by one more power of two (L1 = 2^(floor(log2 L / 2) - 1):
+ *                    the strided first pass then reads wider runs of adjacent columns; taken
+ *                    only where the second pass stays within one shared-memory pass, else 0);
  *   single_max_log2  12 (default) or 13: longest transform run in one shared-memory pass.
  * The configuration holds for the process and for every later launch (a captured graph keeps
  * the configuration of its capture).  ctas_per_sm changes only the work split; split and

@@ -257,8 +257,8 @@ FFT_CTAS = (2, 4, 8)
 
 def fft_candidates(log2L: int):
     """(ctas_per_sm, split, single_max_log2) worth timing for transforms of length 2^log2L:
-    the tile occupancy target always; the four-step split above one pass; one pass or two at
-    2^13."""
+    the tile occupancy target always; the four-step splits above one pass (split 2, the
+    narrower first pass, from 2^14); one pass or two at 2^13."""
     out = []
     for ctas in FFT_CTAS:
         if log2L <= 12:
@@ -266,7 +266,7 @@ def fft_candidates(log2L: int):
         elif log2L == 13:
             out += [(ctas, 0, 12), (ctas, 1, 12), (ctas, 0, 13)]
         else:
-            out += [(ctas, 0, 12), (ctas, 1, 12)]
+            out += [(ctas, 0, 12), (ctas, 1, 12), (ctas, 2, 12)]
     return out
 
 

@@ -38,7 +38,9 @@ namespace {
 // autotuner through cjt_fft_set_config and read when a transform is enqueued:
 //   ctas     CTAs per SM the tile size aims at when there is enough work (tiles are powers
 //            of two, at most 64 columns and ~64 KB of shared memory);
-//   split    four-step factorisation L = L1 L2: 0 -> L1 = 2^ceil(log2 L / 2), 1 -> 2^floor;
+//   split    four-step factorisation L = L1 L2: 0 -> L1 = 2^ceil(log2 L / 2), 1 -> 2^floor,
+//            2 -> 2^(floor - 1) (narrower first-pass columns: each CTA then reads more
+//            adjacent columns, whole 64-byte segments of the strided first pass);
 //   single   largest log2 L transformed in one pass in shared memory (12 or 13).
 // ctas changes only the work split between CTAs; split and single change the order of
 // the arithmetic (results differ in rounding), so one configuration holds for a process.
@@ -46,6 +48,13 @@ struct FftCfg {
     std::atomic<int> ctas{4}, split{0}, single{12};
 };
 FftCfg g_fft_cfg[3][32];
+
+// log2 L1 of the four-step split of a length 2^logL; a split whose second pass would exceed
+// 2^max2 points falls back to split 0
+inline int four_step_log1(int logL, int split, int max2) {
+    const int l1 = split == 2 ? logL / 2 - 1 : split == 1 ? logL / 2 : (logL + 1) / 2;
+    return (l1 >= 1 && logL - l1 <= max2) ? l1 : (logL + 1) / 2;
+}
 
 struct dfloat {};   // tag of the double-float transform (complex type dfc)
 template <typename T> struct cplx;
@@ -378,7 +387,8 @@ int fft_pow2(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles
         return launch_sub<R>(data, data, logL, batch, 1, 1, L, 0, 1, L, 0, tw, logLtab, -1, stw, fmat, st, ctas);
     }
     if (logL > 24 || scratch == nullptr) return CJT_EUNSUPPORTED;
-    const int log1 = cfg.split.load(std::memory_order_relaxed) ? logL / 2 : (logL + 1) / 2, log2 = logL - log1;
+    const int log1 = four_step_log1(logL, cfg.split.load(std::memory_order_relaxed), tables13 ? 13 : 12),
+              log2 = logL - log1;
     const int64_t L1 = 1LL << log1, L2 = 1LL << log2;
     // pass A: columns n2 (L2 of them), elements n1 at stride L2
     int rc = launch_sub<R>(data, scratch, log1, L2, batch, L2, 1, L, L2, 1, L, tw, logLtab, logL, stw, fmat, st, ctas);
@@ -481,7 +491,9 @@ int fft_rq(void *data, void *scratch, int64_t L, int64_t batch, const Twiddles &
     k_fft_rq<R, Q><<<nb, 256, 0, st>>>((const V *)data, (V *)data, logL2, total, (const V *)T.twq, ts);
     CJT_CUDA_TRY(cudaGetLastError());
     if (logL2 > 24) return CJT_EUNSUPPORTED;
-    const int log1 = cfg.split.load(std::memory_order_relaxed) ? logL2 / 2 : (logL2 + 1) / 2, log2 = logL2 - log1;
+    const bool tables13 = (T.stw == nullptr && T.fma == nullptr) || T.lmax >= 13;
+    const int log1 = four_step_log1(logL2, cfg.split.load(std::memory_order_relaxed), tables13 ? 13 : 12),
+              log2 = logL2 - log1;
     const int64_t A1 = 1LL << log1, A2 = 1LL << log2;
     int rc = launch_sub<R>(data, scratch, log1, A2, Q * batch, A2, 1, L2, A2, 1, L2, T.tw, logLtab, logL2, T.stw, T.fma,
                            st, ctas);
@@ -669,7 +681,7 @@ int prec_index(int precision) {
 
 extern "C" int cjt_fft_set_config(int precision, int log2L, int ctas_per_sm, int split, int single_max_log2) {
     const int pr = prec_index(precision);
-    if (pr < 0 || log2L < 1 || log2L > 24 || ctas_per_sm < 1 || ctas_per_sm > 32 || (split != 0 && split != 1) ||
+    if (pr < 0 || log2L < 1 || log2L > 24 || ctas_per_sm < 1 || ctas_per_sm > 32 || split < 0 || split > 2 ||
         (single_max_log2 != 12 && single_max_log2 != 13))
         return CJT_EINVAL;
     g_fft_cfg[pr][log2L].ctas.store(ctas_per_sm);

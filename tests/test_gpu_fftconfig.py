@@ -1,7 +1,8 @@
 """Transform launch configurations (cjt_fft_set_config, set by the autotuner): the tile
 occupancy target changes only the work split between CTAs, so results stay bit-identical;
-the four-step split and the one-pass 8192-point transform change the order of the arithmetic,
-and results stay within the library's tolerance of the oracle.  The default configuration is
+the four-step splits (0, 1 and the narrower first pass 2) and the one-pass 8192-point
+transform change the order of the arithmetic, and results stay within the library's tolerance
+of the oracle.  The default configuration is
 restored afterwards."""
 import numpy as np
 import pytest
@@ -61,6 +62,23 @@ def test_fft_configurations(cjt, orc, precision):
             p.close()
             l1 = np.abs(c).sum()
             assert np.max(np.abs(got[0] - fwd)) <= bf * l1 and np.max(np.abs(got[1] - inv)) <= bi * l1
+        # the narrower first pass (split 2), on power-of-two and radix-5 grids (N = 9000 plans
+        # on 10240 = 5 2^11: rows of 4096 and 8192 points)
+        for pr in {0, precision}:
+            for lg in lens:
+                cjt.fft_set_config(pr, lg, 4, 2, 12)
+        for n, sd in ((N, 321), (9000, 322)):
+            cn = c if n == N else inputs.decaying_coefficients(n, 1.0, sd)
+            got = run(cjt, n, a, b, cn, opts)
+            fwd, inv = orc.forward(cn, a, b), orc.inverse(cn, a, b)
+            l1 = np.abs(cn).sum()
+            if precision == 0:
+                bf = bi = TOL
+            else:
+                p = cjt.Plan(n, a, b, **opts)
+                bf, bi = cjt.error_bound(p, cjt.CJT_FWD), cjt.error_bound(p, cjt.CJT_INV)
+                p.close()
+            assert np.max(np.abs(got[0] - fwd)) <= bf * l1 and np.max(np.abs(got[1] - inv)) <= bi * l1, n
         assert cjt.fft_time(precision, 16, 64) > 0
     finally:
         for (pr, lg), v in ((k, v) for k, v in [((pr, lg), saved[lg]) for pr in (0, precision) for lg in lens]):
