@@ -294,16 +294,16 @@ def batch_plan_options(N, big, precision, cjt):
 
 
 # DRAM traffic of one replay of the 4096-item FP64 batch, summed over its transform launches
-# (k_fft_sub, k_fft_r3) in the one-pass ncu capture summarised in
+# (k_fft_sub, k_fft_rq) in the one-pass ncu capture summarised in
 # profiles/traffic_batched_fp64_4096.md.  It stands for the code it was taken on: while the
 # transform kernels' and the grouped executor's sources hash to the digests below.
 FFT_TRAFFIC = {
-    "read": 135.844e9, "write": 107.348e9, "bytes_per_step": 243.193e9,
+    "read": 117.722e9, "write": 92.575e9, "bytes_per_step": 210.296e9, "plan_budget_gb": 250.0,
     "profile": "profiles/traffic_batched_fp64_4096.md",
     "sources": {"paper_1602_02618_gb300/csrc/cjt_fft.cu":
-                "316ab94ad081e3e5911b525e546fd835445ab92d418af00c6d6a2bf47cfeac7d",
+                "c6caedc1d33a40905e296ef093376fdfed8582969fe9c12e5381c585fa410e82",
                 "paper_1602_02618_gb300/csrc/cjt_group.cu":
-                "494bfc35b343a11d48034978b85140fc19e797236251eaf8771f7f723cbc8d62"},
+                "b6cca996de421e246f1361fb3eff42c54c6de599949f3175fa067cd808f93725"},
 }
 
 
@@ -318,7 +318,8 @@ def measured_hbm_gbs():
 def measured_fft_traffic(args, precision, cjt):
     """FFT_TRAFFIC when this run is the captured workload on the captured code, else None."""
     import hashlib
-    if args.batch_count != 4096 or precision != cjt.CJT_FP64 or args.batch_fixed:
+    if (args.batch_count != 4096 or precision != cjt.CJT_FP64 or args.batch_fixed
+            or args.batch_plan_gb != FFT_TRAFFIC["plan_budget_gb"]):
         return None
     for rel, digest in FFT_TRAFFIC["sources"].items():
         with open(os.path.join(ROOT, rel), "rb") as f:
@@ -480,7 +481,7 @@ def run_batched(ctx, big=False, steps=None):
         tsec = 1e-3 * (live.get("fft_asy", 0.0) + live.get("fft_dct", 0.0))
         roof["traffic"] = tr["bytes_per_step"]
         roof["traffic_detail"] = {
-            "kernels": "all transform launches of one replay (k_fft_sub, k_fft_r3; asymptotic blocks, DCT-I and "
+            "kernels": "all transform launches of one replay (k_fft_sub, k_fft_rq; asymptotic blocks, DCT-I and "
                        "front end together): dram__bytes_read.sum + dram__bytes_write.sum",
             "read": tr["read"], "write": tr["write"], "profile": tr["profile"],
             "algorithmic_bytes": 32.0 * work["fft_points"],
