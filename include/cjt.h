@@ -217,7 +217,12 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
              void *stream);
 
 /* Release a plan and all device memory it owns.  NULL is ignored.  The caller
- * must ensure no work using the plan is still running. */
+ * must ensure no work using the plan is still running.
+ * Memory the library keeps beyond its plans, per device: the twiddle tables, which plans of
+ * the same transform lengths and precision share (tables no plan uses stay cached, least
+ * recently used freed first, up to CJT_TWIDDLE_CACHE_MB, default 1024 MiB), and a pool of
+ * plan-building temporaries that keeps up to 1 GiB of freed memory for the next plans.  A
+ * plan's device_bytes (cjt_get_info) counts the shared tables it uses. */
 void cjt_destroy(cjt_plan_t plan);
 
 /* Copy the plan summary into *info. */
