@@ -141,6 +141,11 @@ typedef struct {
                          at normal priority.  CJT_OVERLAP_REC_FIRST: the recurrence on a
                          stream of the highest priority.  CJT_OVERLAP_AUTO (0, default):
                          the library's choice for the plan's precision.                   */
+    int seg_whole;    /* rows whose recurrence spans at most this many degrees run as one
+                         work item of that length instead of seg_len segments, so the plan
+                         computes no segment states for them (cheaper plans, longer items
+                         at execution; for one-shot plans such as a server's).  0 (default):
+                         every row is cut into segments of seg_len.                       */
 } cjt_plan_opts;
 
 /* Summary of a plan (for reports and tests). Sizes are per direction. */

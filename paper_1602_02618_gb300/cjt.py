@@ -43,7 +43,8 @@ class cjt_plan_opts(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("eps", ctypes.c_double), ("precision", ctypes.c_int),
                 ("directions", ctypes.c_int), ("ratio", ctypes.c_double), ("seg_len", ctypes.c_int),
                 ("use_asy", ctypes.c_int), ("shared_workspace", ctypes.c_int), ("rec_store", ctypes.c_int),
-                ("expansion", ctypes.c_int), ("grid", ctypes.c_int), ("overlap", ctypes.c_int)]
+                ("expansion", ctypes.c_int), ("grid", ctypes.c_int), ("overlap", ctypes.c_int),
+                ("seg_whole", ctypes.c_int)]
 
 
 class cjt_plan_info(ctypes.Structure):
@@ -193,10 +194,10 @@ class Plan:
     def __init__(self, N: int, alpha: float, beta: float, M: int = 0, eps: float = 0.0, precision: int = CJT_FP64,
                  directions: int = 0, ratio: float = 0.0, seg_len: int = 0, use_asy: int = 0,
                  shared_workspace: bool = False, rec_store: int = 0, expansion: int = CJT_EXPANSION_AUTO,
-                 grid: int = 0, overlap: int = CJT_OVERLAP_AUTO, stream=None):
+                 grid: int = 0, overlap: int = CJT_OVERLAP_AUTO, seg_whole: int = 0, stream=None):
         lib = load()
         o = cjt_plan_opts(M, eps, precision, directions, ratio, seg_len, use_asy, 1 if shared_workspace else 0,
-                          int(rec_store), int(expansion), int(grid), int(overlap))
+                          int(rec_store), int(expansion), int(grid), int(overlap), int(seg_whole))
         h = ctypes.c_void_p()
         _check(lib.cjt_plan(ctypes.byref(h), int(N), float(alpha), float(beta), ctypes.byref(o),
                             _stream_handle(stream)), "cjt_plan")

@@ -184,6 +184,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
         o.expansion = opts->expansion;
         o.grid = opts->grid;
         o.overlap = opts->overlap;
+        o.seg_whole = opts->seg_whole;
     }
     if (o.M < 1 || o.M > 20) return CJT_EINVAL;
     if (!(o.eps > 0.0 && o.eps < 1.0)) return CJT_EINVAL;
@@ -197,6 +198,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     if (o.overlap < CJT_OVERLAP_AUTO || o.overlap > CJT_OVERLAP_REC_FIRST) return CJT_EINVAL;
     if (o.overlap == CJT_OVERLAP_AUTO) o.overlap = CJT_OVERLAP_ASY_FIRST;
     if (o.seg_len < 32 || o.seg_len > (1 << 20) || (o.seg_len % 32) != 0) return CJT_EINVAL;
+    if (o.seg_whole < 0 || o.seg_whole > (1 << 23)) return CJT_EINVAL;
     if (N > (1LL << 21) && !is_pow2(N) && !cjt_is_3pow2(N) && !cjt_is_5pow2(N) && o.grid == -1)
         return CJT_EUNSUPPORTED;   // Bluestein lengths <= 2^24
 

@@ -835,7 +835,9 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
     int64_t out_f = 0, out_i = 0, nstate = 0, steps = 0, eoff = 0;
     for (size_t c = 0; c < chunks.size(); ++c) {
         const Chunk &ch = chunks[c];
-        int nseg = (int)((ch.J + S - 1) / S);
+        // rows whose recurrence is short enough run as one item (no segment states)
+        const int64_t Sc = (p->opts.seg_whole > 0 && ch.J <= p->opts.seg_whole) ? std::max<int64_t>(ch.J, 1) : S;
+        int nseg = (int)((ch.J + Sc - 1) / Sc);
         for (int r = 0; r < ch.nrows && !inverse; ++r) {
             row_nseg[ch.row0 + r] = nseg;
             row_base[ch.row0 + r] = out_f + r;
@@ -850,8 +852,8 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
             RecItem it;
             it.row0 = (int)ch.row0;
             it.nrows = ch.nrows;
-            it.a = s * S;
-            it.b = (int)std::min<int64_t>((int64_t)(s + 1) * S, ch.J);
+            it.a = (int)(s * Sc);
+            it.b = (int)std::min<int64_t>((int64_t)(s + 1) * Sc, ch.J);
             it.mode = ch.mode;
             it.state = s == 0 ? -1 : state_base + s - 1;
             it.mirror = ch.mirror;
@@ -886,16 +888,22 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
     // inverse: contributions to each degree segment, in a fixed order
     if (inverse) {
         gw.nsegs = (gw.Jcap + S - 1) / S;
-        // items grouped by degree segment, in item order within a segment (a counting sort)
-        std::vector<int64_t> ptr(gw.nsegs + 1, 0), sout(items.size());
-        std::vector<int> sb(items.size());
-        for (const RecItem &it : items) ++ptr[it.a / S + 1];
+        // items grouped by degree segment of S, in item order within a segment (a counting
+        // sort); an item of a whole row is listed in every segment it spans, with its
+        // partials' base shifted to the segment's first degree
+        std::vector<int64_t> ptr(gw.nsegs + 1, 0);
+        for (const RecItem &it : items)
+            for (int64_t s = it.a / S; s <= (int64_t)(it.b - 1) / S; ++s) ++ptr[s + 1];
         for (int64_t s = 0; s < gw.nsegs; ++s) ptr[s + 1] += ptr[s];
+        std::vector<int64_t> sout(ptr[gw.nsegs]);
+        std::vector<int> sb(ptr[gw.nsegs]);
         std::vector<int64_t> at(ptr.begin(), ptr.end() - 1);
         for (const RecItem &it : items) {
-            const int64_t q = at[it.a / S]++;
-            sout[q] = it.out;
-            sb[q] = it.b;
+            for (int64_t s = it.a / S; s <= (int64_t)(it.b - 1) / S; ++s) {
+                const int64_t q = at[s]++;
+                sout[q] = it.out + (s * S - it.a);
+                sb[q] = it.b;
+            }
         }
         TRY(dalloc(p, &gw.d_seg_ptr, gw.nsegs + 1));
         TRY(dalloc(p, &gw.d_seg_out, (int64_t)sout.size()));
@@ -917,13 +925,15 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
     }
     tr.mark(inverse ? "inv: host work lists" : "fwd: host work lists");
     // longest items first: the block scheduler then balances the SMs (a stable counting sort
-    // by length, 1 .. S)
+    // by length, 1 .. the longest)
     {
-        std::vector<int64_t> cnt(S + 2, 0);
-        for (const RecItem &it : items) ++cnt[S - (it.b - it.a) + 1];
-        for (int l = 0; l <= S; ++l) cnt[l + 1] += cnt[l];
+        int64_t lmax = S;
+        for (const RecItem &it : items) lmax = std::max<int64_t>(lmax, it.b - it.a);
+        std::vector<int64_t> cnt(lmax + 2, 0);
+        for (const RecItem &it : items) ++cnt[lmax - (it.b - it.a) + 1];
+        for (int64_t l = 0; l <= lmax; ++l) cnt[l + 1] += cnt[l];
         std::vector<RecItem> sorted(items.size());
-        for (const RecItem &it : items) sorted[cnt[S - (it.b - it.a)]++] = it;
+        for (const RecItem &it : items) sorted[cnt[lmax - (it.b - it.a)]++] = it;
         items.swap(sorted);
     }
     gw.nitems = (int64_t)items.size();

@@ -87,7 +87,10 @@ class Server:
         self.dev = torch.device("cuda", device)
         self.precision = precision
         self.mem_budget = float(mem_budget)
-        self.plan_options = plan_options or (lambda N: {"M": 13 if N >= 16384 else 10, "seg_len": 256})
+        # one-shot plans: rows whose recurrence spans at most 8192 degrees run as one item, so
+        # the plan computes no segment states for them (planning bounds the loop's throughput)
+        self.plan_options = plan_options or (lambda N: {"M": 13 if N >= 16384 else 10, "seg_len": 256,
+                                                        "seg_whole": 8192})
         self.slots = [_Slot(torch, self.dev) for _ in range(slots)]
         self.incoming = queue.Queue()
         self.ready = collections.deque()

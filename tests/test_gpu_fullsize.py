@@ -11,9 +11,9 @@ in the fixture, runs the CUDA path through the C ABI and compares every stored e
                                 (cjt_error_bound: the componentwise FP32 transform error
                                 carried through C_{n,m}, u_m, v_m, the weights and 1/A_n)
 
-Option sets: the defaults and the option sets the autotuner picks for the single-transform
+Option sets: the defaults, the option sets the autotuner picks for the single-transform
 benchmark (stored recurrence values, coarse block ratio), so the configuration the benchmark
-times is the one checked here.
+times is the one checked here, and the serving loop's one-shot options (whole rows).
 """
 import hashlib
 import os
@@ -32,7 +32,8 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 SINGLE = [1 << 12, 1 << 14, 1 << 16, 1 << 18]
 FP64_OPTIONS = [dict(), dict(M=10, ratio=0.05, rec_store=1, seg_len=1024),
-                dict(M=13, ratio=0.05, rec_store=1, seg_len=1024), dict(M=16, seg_len=256)]
+                dict(M=13, ratio=0.05, rec_store=1, seg_len=1024), dict(M=16, seg_len=256),
+                dict(M=13, seg_len=256, seg_whole=8192)]
 DF_OPTIONS = [dict(), dict(M=13, ratio=0.05, rec_store=1, seg_len=1024)]
 
 

@@ -32,7 +32,8 @@ def diverse_items(cjt, seed):
             (3001, {"rec_store": 1}), (4096, {"M": 13, "ratio": 0.05}), (8191, {"precision": cjt.CJT_MIXED}),
             (20000, {"rec_store": 1, "seg_len": 256}), (65536, {"M": 10, "seg_len": 1024}),
             (5000, {"precision": cjt.CJT_DFLOAT}), (777, {"grid": -1}), (1500, {"shift": (1.2, 0.3)}),
-            (2048, {"fold": True}), (12000, {"precision": cjt.CJT_MIXED, "rec_store": 1}), (300, {"M": 20})]
+            (2048, {"fold": True}), (12000, {"precision": cjt.CJT_MIXED, "rec_store": 1}), (300, {"M": 20}),
+            (30000, {"M": 13, "seg_len": 256, "seg_whole": 8192}), (5000, {"seg_len": 256, "seg_whole": 2048})]
     items = []
     for t in range(3 * len(base)):
         N, opts = base[t % len(base)]

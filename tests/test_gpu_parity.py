@@ -86,6 +86,25 @@ def test_options_do_not_change_the_result(cjt, orc, opts):
     assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, a, b))) <= TOL * l1(c), info
 
 
+@pytest.mark.parametrize("opts", [dict(seg_whole=1024), dict(seg_whole=8192, M=13),
+                                  dict(seg_whole=1 << 22, rec_store=1), dict(seg_whole=2048, precision=2),
+                                  dict(seg_whole=2048, precision=2, rec_store=1), dict(seg_whole=700, fold_check=1)])
+@pytest.mark.parametrize("N", [4096, 6000])
+def test_whole_rows_match_oracle(cjt, orc, N, opts):
+    """seg_whole: rows whose recurrence spans at most that many degrees run as one work item
+    (no segment states); the transposed items of such rows span several of the reduction's
+    degree segments.  The result stays within the tolerance of the oracle (alpha = beta adds
+    the parity fold with stored values)."""
+    opts = dict(opts, seg_len=256)
+    a, b = (0.2, 0.2) if opts.pop("fold_check", 0) else (0.1, -0.3)
+    if a == b:
+        opts["rec_store"] = 1
+    c = inputs.decaying_coefficients(N, 1.5, 4100 + N)
+    plan = cjt.Plan(N, a, b, **opts)
+    assert np.max(np.abs(run_fwd(cjt, plan, c) - orc.forward(c, a, b))) <= TOL * l1(c), opts
+    assert np.max(np.abs(run_inv(cjt, plan, c) - orc.inverse(c, a, b))) <= TOL * l1(c), opts
+
+
 def test_partition_matches_paper_shape(cjt):
     """N = 1024, (0.1, -0.3), M = 7: two asymptotic blocks and most of the matrix by ASY."""
     plan = cjt.Plan(1024, 0.1, -0.3, M=7)
