@@ -842,7 +842,7 @@ def run_serving(ctx, precision_name):
                 for N, a, b, d, c in inputs.serving_requests(
                     args.requests, seed=multirank.rank_seed(inputs.BASE_SEED, ctx.rank) + 100 * k)]
         sampler = ClockSampler(ctx.local).start()
-        server = serve.Server(slots=16, mem_budget=40e9, precision=precision, planners=args.planners)
+        server = serve.Server(slots=args.slots, mem_budget=40e9, precision=precision, planners=args.planners)
         serve.poisson_run(server, reqs, rate=rate, seed=k)
         st = server.stats()
         server.close()
@@ -858,7 +858,7 @@ def run_serving(ctx, precision_name):
             "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "dtype": DTYPES[precision_name],
             "workload": "serving: Poisson arrivals, %d requests per rate, N log-uniform in [128, 2^18], "
                         "alpha,beta~U[-0.45,0.45], random direction, c_n=g_n/(n+1); plan built per request "
-                        "(device-resident, reused on repeats); 16 slots, 40 GB budget" % args.requests,
+                        "(device-resident, reused on repeats); %d slots, 40 GB budget" % (args.requests, args.slots),
             "per_rate": results}
 
 
@@ -877,6 +877,7 @@ def main():
     ap.add_argument("--rates", default="50,200,800,3200")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--planners", type=int, default=8)
+    ap.add_argument("--slots", type=int, default=16, help="serving: concurrent requests on the device")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--lanes", type=int, default=16)
     ap.add_argument("--batch-plan-gb", type=float, default=250.0,
