@@ -298,7 +298,7 @@ def batch_plan_options(N, big, precision, cjt):
 # profiles/traffic_batched_fp64_4096.md.  It stands for the code it was taken on: while the
 # transform kernels' and the grouped executor's sources hash to the digests below.
 FFT_TRAFFIC = {
-    "read": 117.722e9, "write": 92.575e9, "bytes_per_step": 210.296e9, "plan_budget_gb": 250.0,
+    "read": 114.990e9, "write": 90.675e9, "bytes_per_step": 205.664e9, "plan_budget_gb": 260.0,
     "profile": "profiles/traffic_batched_fp64_4096.md",
     "sources": {"paper_1602_02618_gb300/csrc/cjt_fft.cu":
                 "c6caedc1d33a40905e296ef093376fdfed8582969fe9c12e5381c585fa410e82",
@@ -398,10 +398,10 @@ def run_batched(ctx, big=False, steps=None):
                                   shared_workspace=True, **batch_plan_options(N, big, precision, cjt)))
     else:
         from paper_1602_02618_gb300 import autotune
-        # the plans may take the budget, within the device memory free now less 30 GB for the
-        # arenas (about 9 GB), the I/O buffers and the runtime
+        # the plans may take the budget, within the device memory free now less 20 GB for the
+        # arenas (about 9 GB), the I/O buffers, the per-call comparison and the runtime
         free, _ = torch.cuda.mem_get_info(dev)
-        budget = min(args.batch_plan_gb * 1e9, free - 30e9)
+        budget = min(args.batch_plan_gb * 1e9, free - 20e9)
         plans, _, tune = autotune.build_batch_plans(items, precision, plan_budget_bytes=budget)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
@@ -880,7 +880,7 @@ def main():
     ap.add_argument("--slots", type=int, default=16, help="serving: concurrent requests on the device")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--lanes", type=int, default=16)
-    ap.add_argument("--batch-plan-gb", type=float, default=250.0,
+    ap.add_argument("--batch-plan-gb", type=float, default=260.0,
                     help="device memory the batched workload's plans may take (autotuned options)")
     ap.add_argument("--batch-fixed", action="store_true",
                     help="batched workload with fixed options (M=13, ratio=0.1, stored values for N <= 16384)")
