@@ -73,3 +73,48 @@ def test_autotune_cache_roundtrip(tmp_path, monkeypatch):
     assert autotune._load() == {}
     # small N never times anything
     assert autotune.best_options(100, 0.1, -0.3) == {"M": 7, "seg_len": 256}
+
+
+def test_bench_default_grid_and_traffic_gate(monkeypatch):
+    """bench.default_grid is the least G >= N of the forms 2^a, 3 2^a, 5 2^a (brute force), and
+    the recorded transform traffic is reported only for the captured workload, plan budget and
+    sources: any other digest, budget or workload gives null."""
+    import argparse
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    def smooth(g):
+        while g % 2 == 0:
+            g //= 2
+        return g in (1, 3, 5)
+
+    for N in list(range(1, 300)) + [3001, 40000, 45000, 65536, 65537]:
+        G = bench.default_grid(N)
+        assert G >= N and smooth(G) and all(not smooth(g) for g in range(N, G)), N
+
+    class FakeCJT:
+        CJT_FP64, CJT_MIXED = 0, 1
+
+    args = argparse.Namespace(batch_count=4096, batch_fixed=False, batch_plan_gb=bench.FFT_TRAFFIC["plan_budget_gb"])
+    ok = bench.measured_fft_traffic(args, FakeCJT.CJT_FP64, FakeCJT)
+    assert ok is None or ok["bytes_per_step"] > 0
+    assert bench.measured_fft_traffic(args, FakeCJT.CJT_MIXED, FakeCJT) is None
+    assert bench.measured_fft_traffic(argparse.Namespace(**dict(vars(args), batch_count=48)), 0, FakeCJT) is None
+    assert bench.measured_fft_traffic(argparse.Namespace(**dict(vars(args), batch_plan_gb=1.0)), 0, FakeCJT) is None
+    monkeypatch.setitem(bench.FFT_TRAFFIC, "sources", {k: "0" * 64 for k in bench.FFT_TRAFFIC["sources"]})
+    assert bench.measured_fft_traffic(args, FakeCJT.CJT_FP64, FakeCJT) is None
+
+
+def test_mixed_work_model_discounts_fp32_transforms():
+    """The batch autotuner's work model counts the mixed form's asymptotic transforms at a
+    tenth of their FP64 cost and its final DCT-I / front end in full."""
+    from paper_1602_02618_gb300 import cjt
+    info = {"fft_len_fwd": 1 << 12, "fft_len_inv": 1 << 13, "nfft_fwd": 11, "nfft_inv": 13,
+            "rec_steps_fwd": 1000, "rec_steps_inv": 2000}
+    s64, f64 = autotune._work_model(info, 1, cjt.CJT_FP64)
+    s32, f32 = autotune._work_model(info, 1, cjt.CJT_MIXED)
+    assert s64 == s32 == 1000.0
+    one = 5.0 * 4096 * 12 / autotune.ETA_FFT
+    assert abs(f64 - 11 * one) < 1e-6 * f64 and abs(f32 - (10 * autotune.MIXED_ASY_FFT_FACTOR + 1) * one) < 1e-6 * f32
