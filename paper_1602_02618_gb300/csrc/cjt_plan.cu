@@ -1050,12 +1050,16 @@ std::mutex g_tw_mu;
 std::vector<TwShared *> g_tw;
 uint64_t g_tw_clock = 0;
 
+// frees a copy's tables on the device that holds them (the caller's device is restored)
 void tw_free(TwShared *e) {
+    int cur = -1;
+    const bool other = cudaGetDevice(&cur) == cudaSuccess && cur != e->dev && cudaSetDevice(e->dev) == cudaSuccess;
     if (e->ready) {
         cudaEventSynchronize(e->ready);
         cudaEventDestroy(e->ready);
     }
     for (void *v : e->allocs) cudaFree(v);
+    if (other) cudaSetDevice(cur);
     delete e;
 }
 
