@@ -101,7 +101,8 @@ typedef struct {
                          min(1/log(N/n_M), 1/2)                                            */
     int seg_len;      /* degree-segment length of the recurrence work items; 0 -> 2048    */
     int use_asy;      /* 1 (default when 0): partition as in Sec. 2.2;
-                         -1: recurrence only (no asymptotic blocks)                        */
+                         -1: recurrence only (no asymptotic blocks); other values:
+                         CJT_EINVAL                                                        */
     int shared_workspace; /* 0: the plan owns its execution workspace (default);
                          1: it owns only its tables, and executions borrow a workspace
                          (cjt_forward_ws / cjt_inverse_ws, or the batched executor), so
@@ -204,7 +205,9 @@ int cjt_plan_opts_default(cjt_plan_opts *opts);
  * partition n_M, alpha_N, K, j_k, i_k^1, i_k^2 (Sec. 2.2), transform twiddles,
  * and for the inverse the Clenshaw--Curtis weights (Eq. "CCweights") and
  * 1/A_n (Eq. "Anabasy").  Runs on `stream` and synchronises it once (the box
- * indices are read back to size the launches).
+ * indices are read back to size the launches).  The plan belongs to the device that is
+ * current at this call: every call that executes it (and every batch made of it) must
+ * run with that device current, else it returns CJT_EINVAL and launches nothing.
  *   out    : receives the plan handle (NULL on failure)
  *   N      : degree, N >= 0 (N = 0 is the identity map); N <= 2^22
  *   alpha, beta : Jacobi parameters in [-1/2, 3/2] (else CJT_EDOMAIN).  The method itself
@@ -268,14 +271,14 @@ int cjt_get_partition(cjt_plan_t plan, int direction, int cap, int64_t *boxes, i
 /*
  * Forward transform (Eq. "CJT"): c_cheb_dev[k], k = 0..N, from c_jac_dev[n].
  * Both are device arrays of N+1 doubles; they may alias.
- * Errors: CJT_EINVAL (null), CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA.
+ * Errors: CJT_EINVAL (null, another device current), CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA.
  */
 int cjt_forward(cjt_plan_t plan, const double *c_jac_dev, double *c_cheb_dev, void *stream);
 
 /*
  * Inverse transform (Eq. "iCJT" through Eq. "CJTT"): c_jac_dev from c_cheb_dev.
  * Both are device arrays of N+1 doubles; they may alias.
- * Errors: CJT_EINVAL (null), CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA.
+ * Errors: CJT_EINVAL (null, another device current), CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA.
  */
 int cjt_inverse(cjt_plan_t plan, const double *c_cheb_dev, double *c_jac_dev, void *stream);
 
@@ -328,7 +331,7 @@ int cjt_execute_host(cjt_plan_t plan, int direction, const double *in_host, doub
  * capture that would need a larger arena returns CJT_EBUSY).  An outgrown arena
  * is kept, not freed, until the process exits, so that a graph captured from an
  * earlier call stays valid.  A plan may appear at most once per call; in_dev
- * and out_dev must not overlap.
+ * and out_dev must not overlap.  Every plan must belong to the current device.
  * Errors: CJT_EINVAL, CJT_EDIRECTION, CJT_EBUSY, CJT_ECUDA, CJT_ENOMEM.
  */
 int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, const int64_t *offsets,
@@ -339,7 +342,8 @@ int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, c
  * given items and buffers into one CUDA graph and instantiates it; cjt_batch_launch
  * replays it on `stream` with a single graph launch.  Plans and buffers must outlive
  * the batch.  cjt_batch_info reports the kernel launches of one replay and the bytes
- * of the batch's private workspace arenas.
+ * of the batch's private workspace arenas.  cjt_batch_launch (and _host) return
+ * CJT_EINVAL unless the plans' device is current.
  *   Grouped execution (Sec. 4: one plan machinery over many coefficient sets): items
  * in FP64 or the mixed form with power-of-two transform lengths and no parameter
  * shift run stage by stage, one launch per stage over many items, and one batched

@@ -36,6 +36,8 @@ def candidates(N: int, max_store_bytes: float):
     if 3 * 8.0 * (N + 1) ** 2 <= max_store_bytes:
         out.append({"M": 7, "seg_len": 1024, "rec_store": 1, "use_asy": -1})
     return out
+
+
 _lock = threading.Lock()
 
 
@@ -119,6 +121,8 @@ def best_options(N: int, alpha: float, beta: float, precision: int = 0, directio
             continue
         results.append((time_plan(p, x, y), opts))
         p.close()
+    if not results:
+        raise RuntimeError("no candidate plan could be built for N=%d, alpha=%g, beta=%g" % (N, alpha, beta))
     results.sort(key=lambda r: r[0])
     best = results[0][1]
     with _lock:

@@ -19,6 +19,16 @@ bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
 }  // namespace
 
+int cjt_internal_check_device(const cjt_plan_s *p) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cjt_internal_set_cuda_error(e, "cudaGetDevice");
+        return CJT_ECUDA;
+    }
+    return dev == p->dev ? CJT_OK : CJT_EINVAL;
+}
+
 int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st) {
     // a shared-workspace plan holds only read-only tables: any number of streams may use
     // it at once, each with its own workspace
@@ -191,6 +201,7 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     if (o.precision != CJT_FP64 && o.precision != CJT_MIXED && o.precision != CJT_DFLOAT) return CJT_EINVAL;
     if (o.directions < 1 || o.directions > 3) return CJT_EINVAL;
     if (!(o.ratio == 0.0 || (o.ratio > 0.0 && o.ratio < 1.0))) return CJT_EINVAL;
+    if (o.use_asy != 1 && o.use_asy != -1) return CJT_EINVAL;
     if (o.rec_store != 0 && o.rec_store != 1) return CJT_EINVAL;
     if (o.expansion < CJT_EXPANSION_AUTO || o.expansion > CJT_EXPANSION_ULTRASPHERICAL) return CJT_EINVAL;
     if (o.expansion == CJT_EXPANSION_ULTRASPHERICAL && alpha != beta) return CJT_EINVAL;
@@ -205,6 +216,14 @@ int cjt_plan(cjt_plan_t *out, int64_t N, double alpha, double beta, const cjt_pl
     cjt_plan_s *p = new (std::nothrow) cjt_plan_s();
     if (!p) return CJT_ENOMEM;
     p->N = N;
+    {
+        cudaError_t e = cudaGetDevice(&p->dev);
+        if (e != cudaSuccess) {
+            cjt_internal_set_cuda_error(e, "cudaGetDevice");
+            delete p;
+            return CJT_ECUDA;
+        }
+    }
     // one unit step down into the square [-1/2, 1/2]^2 for a parameter in (1/2, 3/2]
     // (Sec. 1.2; alpha - 1 is exact there)
     auto shift_of = [](double v) { return v > 0.5 ? 1 : 0; };
@@ -407,7 +426,9 @@ static int run_one(cjt_plan_t p, int direction, const double *in, double *out, c
     if (!p || !in || !out) return CJT_EINVAL;
     if (!(p->opts.directions & direction)) return CJT_EDIRECTION;
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = cjt_internal_begin_use(p, st);
+    int rc = cjt_internal_check_device(p);
+    if (rc) return rc;
+    rc = cjt_internal_begin_use(p, st);
     if (rc) return rc;
     rc = direction == CJT_FWD ? cjt_exec_forward_shifted(p, ws, in, out, st)
                               : cjt_exec_inverse_shifted(p, ws, in, out, st);
@@ -449,7 +470,9 @@ int cjt_execute_host(cjt_plan_t p, int direction, const double *in_host, double 
     if (!(p->opts.directions & direction)) return CJT_EDIRECTION;
     if (p->shared_ws && p->N > 0) return CJT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = cjt_internal_begin_use(p, st);
+    int rc = cjt_internal_check_device(p);
+    if (rc) return rc;
+    rc = cjt_internal_begin_use(p, st);
     if (rc) return rc;
     const size_t bytes = sizeof(double) * (size_t)(p->N + 1);
     CJT_CUDA_TRY(cudaMemcpyAsync(p->d_in, in_host, bytes, cudaMemcpyHostToDevice, st));

@@ -111,8 +111,11 @@ int validate(int count, const cjt_plan_t *plans, const int8_t *dir, const int64_
     if (count < 0) return CJT_EINVAL;
     if (count == 0) return CJT_OK;
     if (!plans || !dir || !offsets || !in || !out) return CJT_EINVAL;
+    int dev = -1;
+    CJT_CUDA_TRY(cudaGetDevice(&dev));
     for (int t = 0; t < count; ++t) {
         if (!plans[t] || offsets[t] < 0) return CJT_EINVAL;
+        if (plans[t]->dev != dev) return CJT_EINVAL;   // every plan on the current device
         if (dir[t] != CJT_FWD && dir[t] != CJT_INV) return CJT_EINVAL;
         if (!(plans[t]->opts.directions & dir[t])) return CJT_EDIRECTION;
     }
@@ -144,6 +147,7 @@ Context g_ctx[64];
 }  // namespace
 
 struct cjt_batch_s {
+    int dev = -1;   // the device of its plans (current at creation)
     Lanes lanes;
     std::vector<void *> arenas;
     int64_t arena_bytes = 0;
@@ -235,6 +239,7 @@ int cjt_batch_create(cjt_batch_t *out, int count, const cjt_plan_t *plans, const
         cjt_batch_destroy(b);
         return code;
     };
+    b->dev = plans[0]->dev;   // validate: every plan's device is the current one
     // the grouped items, and the rest (one chain of launches per item on the lanes)
     std::vector<int> grouped, rest;
     const bool no_group = getenv("CJT_BATCH_NO_GROUP") != nullptr;
@@ -307,6 +312,9 @@ int cjt_batch_create(cjt_batch_t *out, int count, const cjt_plan_t *plans, const
 
 int cjt_batch_launch(cjt_batch_t b, void *stream) {
     if (!b || !b->exec) return CJT_EINVAL;
+    int dev = -1;
+    CJT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != b->dev) return CJT_EINVAL;   // launched with another device current
     cudaStream_t st = (cudaStream_t)stream;
     if (!b->prof) {
         CJT_CUDA_TRY(cudaGraphLaunch(b->exec, st));
@@ -322,6 +330,9 @@ int cjt_batch_launch(cjt_batch_t b, void *stream) {
 
 int cjt_batch_launch_host(cjt_batch_t b, const double *in_host, double *out_host, void *stream) {
     if (!b || !b->exec || !in_host || !out_host) return CJT_EINVAL;
+    int dev = -1;
+    CJT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != b->dev) return CJT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = sizeof(double) * (size_t)b->total;
     CJT_CUDA_TRY(cudaMemcpyAsync((void *)b->in, in_host, bytes, cudaMemcpyHostToDevice, st));

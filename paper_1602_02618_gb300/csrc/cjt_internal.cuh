@@ -38,6 +38,9 @@ void cjt_internal_set_cuda_error(cudaError_t e, const char *what);
 struct cjt_plan_s;
 int cjt_internal_begin_use(cjt_plan_s *p, cudaStream_t st);
 int cjt_internal_end_use(cjt_plan_s *p, cudaStream_t st);
+// CJT_OK when the plan's device is the current one, CJT_EINVAL when another device is
+// current (its tables would be read from the wrong device), CJT_ECUDA without a device.
+int cjt_internal_check_device(const cjt_plan_s *p);
 // Side streams and events of one execution's two concurrent chains (the asymptotic blocks
 // and the recurrence, option overlap).  Each execution takes a context of its own from a
 // per-device pool for the time it enqueues its work and gives it back at once (cudaEvent
@@ -257,6 +260,7 @@ constexpr int CJT_EXP_BLOCKS = 128;
 
 struct cjt_plan_s {
     int64_t N = 0;
+    int dev = 0;                         // the device current when the plan was built
     double alpha = 0, beta = 0;          // the parameters the method runs on, in [-1/2, 1/2]^2
     double alpha_user = 0, beta_user = 0;// the caller's: alpha + shift_a, beta + shift_b
     int shift_a = 0, shift_b = 0;        // integer shifts (-1, 0, +1), Sec. 1.2

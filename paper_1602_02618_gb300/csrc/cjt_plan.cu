@@ -632,6 +632,25 @@ template <typename T> int dalloc(cjt_plan_s *p, T **ptr, int64_t count) {
     return CJT_OK;
 }
 
+// A temporary device buffer from cjt_tmp_alloc, given back to the pool in stream order when
+// it goes out of scope, so that every early error return releases it too.
+template <typename T> struct TmpBuf {
+    T *ptr = nullptr;
+    cudaStream_t st;
+    explicit TmpBuf(cudaStream_t s) : st(s) {}
+    TmpBuf(const TmpBuf &) = delete;
+    TmpBuf &operator=(const TmpBuf &) = delete;
+    ~TmpBuf() { release(); }
+    cudaError_t alloc(int64_t count) {
+        release();
+        return cjt_tmp_alloc((void **)&ptr, sizeof(T) * (size_t)count, st);
+    }
+    void release() {
+        if (ptr) cudaFreeAsync(ptr, st);
+        ptr = nullptr;
+    }
+};
+
 #define TRY(x)                 \
     do {                       \
         int _rc = (x);         \
@@ -671,21 +690,20 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
             thr.push_back(p->opts.eps / (2.0 * cjt_asy_C(h, j, M)));
         }
         if (!js.empty()) {
-            double *d_g = nullptr, *d_thr = nullptr;
-            int *d_b2 = nullptr;
-            CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_g, sizeof(double) * (Ng + 1), st));
-            CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_thr, sizeof(double) * thr.size(), st));
-            CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_b2, sizeof(int) * 2 * thr.size(), st));
-            k_envelope<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, M, h, d_g);
-            CJT_CUDA_TRY(cudaMemcpyAsync(d_thr, thr.data(), sizeof(double) * thr.size(), cudaMemcpyHostToDevice, st));
-            k_box_init<<<1, 64, 0, st>>>((int)thr.size(), d_b2);
+            TmpBuf<double> d_g(st), d_thr(st);
+            TmpBuf<int> d_b2(st);
+            CJT_CUDA_TRY(d_g.alloc(Ng + 1));
+            CJT_CUDA_TRY(d_thr.alloc((int64_t)thr.size()));
+            CJT_CUDA_TRY(d_b2.alloc(2 * (int64_t)thr.size()));
+            k_envelope<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, M, h, d_g.ptr);
+            CJT_CUDA_TRY(cudaMemcpyAsync(d_thr.ptr, thr.data(), sizeof(double) * thr.size(), cudaMemcpyHostToDevice, st));
+            k_box_init<<<1, 64, 0, st>>>((int)thr.size(), d_b2.ptr);
             unsigned nb = std::min<unsigned>(blocks_for(Ng, 256), 152 * 8);
-            k_boxes<<<nb, 256, 0, st>>>(Ng, d_g, (int)thr.size(), d_thr, d_b2);
+            k_boxes<<<nb, 256, 0, st>>>(Ng, d_g.ptr, (int)thr.size(), d_thr.ptr, d_b2.ptr);
             CJT_CUDA_TRY(cudaGetLastError());
             std::vector<int> hb(2 * thr.size());
-            CJT_CUDA_TRY(cudaMemcpyAsync(hb.data(), d_b2, sizeof(int) * hb.size(), cudaMemcpyDeviceToHost, st));
+            CJT_CUDA_TRY(cudaMemcpyAsync(hb.data(), d_b2.ptr, sizeof(int) * hb.size(), cudaMemcpyDeviceToHost, st));
             CJT_CUDA_TRY(cudaStreamSynchronize(st));
-            cudaFreeAsync(d_g, st); cudaFreeAsync(d_thr, st); cudaFreeAsync(d_b2, st);
             for (size_t k = 0; k < js.size(); ++k) {
                 int lo = hb[2 * k], hi = hb[2 * k + 1];
                 if (hi < lo) break;   // empty box: this and all deeper blocks dropped
@@ -959,21 +977,19 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
             nmaps += (int64_t)(v[5] - 1) * per;
         }
         const int64_t nlong = (int64_t)longrow.size() / 5;
-        int *d_l = nullptr;
-        int64_t *d_off = nullptr;
-        double *d_maps = nullptr;
-        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_l, sizeof(int) * longrow.size(), st));
-        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_off, sizeof(int64_t) * loff.size(), st));
-        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&d_maps, sizeof(double) * 4 * nmaps, st));
-        CJT_CUDA_TRY(cudaMemcpyAsync(d_l, longrow.data(), sizeof(int) * longrow.size(), cudaMemcpyHostToDevice, st));
-        CJT_CUDA_TRY(cudaMemcpyAsync(d_off, loff.data(), sizeof(int64_t) * loff.size(), cudaMemcpyHostToDevice, st));
-        k_rec_seg_maps<<<blocks_for(nmaps, 128), 128, 0, st>>>(nlong, nmaps, d_l, d_off, Ng, len, p->rt, d_maps);
-        k_rec_seg_carry<<<blocks_for(nlong, 64), 64, 0, st>>>(nlong, d_l, d_off, per, d_maps, gw.d_states);
+        TmpBuf<int> d_l(st);
+        TmpBuf<int64_t> d_off(st);
+        TmpBuf<double> d_maps(st);
+        CJT_CUDA_TRY(d_l.alloc((int64_t)longrow.size()));
+        CJT_CUDA_TRY(d_off.alloc((int64_t)loff.size()));
+        CJT_CUDA_TRY(d_maps.alloc(4 * nmaps));
+        CJT_CUDA_TRY(cudaMemcpyAsync(d_l.ptr, longrow.data(), sizeof(int) * longrow.size(), cudaMemcpyHostToDevice, st));
+        CJT_CUDA_TRY(cudaMemcpyAsync(d_off.ptr, loff.data(), sizeof(int64_t) * loff.size(), cudaMemcpyHostToDevice, st));
+        k_rec_seg_maps<<<blocks_for(nmaps, 128), 128, 0, st>>>(nlong, nmaps, d_l.ptr, d_off.ptr, Ng, len, p->rt,
+                                                               d_maps.ptr);
+        k_rec_seg_carry<<<blocks_for(nlong, 64), 64, 0, st>>>(nlong, d_l.ptr, d_off.ptr, per, d_maps.ptr, gw.d_states);
         CJT_CUDA_TRY(cudaGetLastError());
         CJT_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors above go out of scope
-        cudaFreeAsync(d_maps, st);
-        cudaFreeAsync(d_off, st);
-        cudaFreeAsync(d_l, st);
     }
     gw.nE = eoff;
     if (p->opts.rec_store && gw.nitems > 0) {
@@ -994,8 +1010,8 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
 
 }  // namespace
 
-// Twiddle tables of a plan (p->Ltab set): omega_{Ltab}^k in FP64 and in the precision pa
-// of its asymptotic transforms, the stage tables and the FP64 fused multiply-add forms.
+// A pool per device (created on first use) whose freed memory, up to 1 GiB, stays reserved
+// for the next plan build instead of going back to the driver.
 cudaError_t cjt_tmp_alloc(void **ptr, size_t bytes, cudaStream_t st) {
     static std::mutex mu;
     static cudaMemPool_t pools[64] = {};
@@ -1349,7 +1365,7 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         p->ws_bytes = off;
     }
     p->shared_ws = p->opts.shared_workspace != 0;
-    void *tmp_ws = nullptr;
+    TmpBuf<unsigned char> tmp_ws(st);
     if (!p->shared_ws) {
         unsigned char *arena = nullptr;
         TRY(dalloc(p, &arena, p->ws_bytes));
@@ -1364,8 +1380,8 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         if (p->shared_ws) {   // temporary buffers for the weights' transform (DCT, work, scratch)
             const int64_t a0 = (p->ws_size[WS_DCT] + 255) / 256 * 256, a1 = (p->ws_size[WS_WORK] + 255) / 256 * 256;
             const int64_t a2 = (p->ws_size[WS_SCRATCH] + 255) / 256 * 256;
-            CJT_CUDA_TRY(cjt_tmp_alloc(&tmp_ws, (size_t)(a0 + a1 + a2), st));
-            unsigned char *b = (unsigned char *)tmp_ws;
+            CJT_CUDA_TRY(tmp_ws.alloc(a0 + a1 + a2));
+            unsigned char *b = tmp_ws.ptr;
             ws = Workspace{};
             ws.dct = (double *)b;
             ws.work = p->ws_size[WS_WORK] ? b + a0 : nullptr;
@@ -1377,45 +1393,43 @@ int cjt_plan_build(cjt_plan_s *p, cudaStream_t st) {
         // modified moments mu_0..mu_Ng (Sec. 3.1, mu_1 with the sign of the weight's mean)
         const double mu1 = (b - a) / (a + b + 2.0) * mu0;
         const int64_t nchunk = std::max<int64_t>(1, (Ng - 1 + kMomChunk - 1) / kMomChunk);
-        Mat2 *T = nullptr;
-        double2 *start = nullptr;
-        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&T, sizeof(Mat2) * nchunk, st));
-        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&start, sizeof(double2) * nchunk, st));
-        k_mom_transfer<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, T);
-        k_mom_carry<<<1, kMomScanThreads, 0, st>>>(nchunk, mu0, mu1, T, start);
-        k_mom_fill<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, start, (double2 *)ws.dct);
+        TmpBuf<Mat2> T(st);
+        TmpBuf<double2> start(st);
+        CJT_CUDA_TRY(T.alloc(nchunk));
+        CJT_CUDA_TRY(start.alloc(nchunk));
+        k_mom_transfer<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, T.ptr);
+        k_mom_carry<<<1, kMomScanThreads, 0, st>>>(nchunk, mu0, mu1, T.ptr, start.ptr);
+        k_mom_fill<<<blocks_for(nchunk, 128), 128, 0, st>>>(Ng, a, b, nchunk, start.ptr, (double2 *)ws.dct);
         CJT_CUDA_TRY(cudaGetLastError());
-        cudaFreeAsync(T, st);
-        cudaFreeAsync(start, st);
+        T.release();
+        start.release();
         TRY(cjt_dft_exec(p->dft_cc, ws.dct, ws.work, ws.scratch, 1, p->twiddles(PREC_F64), st));
         k_cc_weights<<<blocks_for(Ng + 1, 256), 256, 0, st>>>(Ng, (const double2 *)ws.dct, p->d_w);
         k_inv_norm<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, a, b, p->d_s);
         CJT_CUDA_TRY(cudaGetLastError());
     }
-    if (tmp_ws) cudaFreeAsync(tmp_ws, st);
+    tmp_ws.release();
     tr.mark("buffers, inverse weights");
     if (pa == PREC_F32 && (p->fw.nblk > 0 || p->iv.nblk > 0)) {
         // bound on the FP32 transforms' error (see k_err_fwd): two maxima read back once
-        double *acc = nullptr, *U = nullptr;
+        TmpBuf<double> acc(st), U(st);
         const int nqi = p->iv.nblk * M;
-        CJT_CUDA_TRY(cjt_tmp_alloc((void **)&acc, 2 * sizeof(double), st));
-        CJT_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+        CJT_CUDA_TRY(acc.alloc(2));
+        CJT_CUDA_TRY(cudaMemsetAsync(acc.ptr, 0, 2 * sizeof(double), st));
         if (fwd && p->fw.nblk > 0)
             k_err_fwd<<<blocks_for(p->Gf + 1, 256), 256, 0, st>>>(N, p->Gf, M, p->fw.nblk * M, p->fw.d_rowk,
                                                                    p->fw.d_box, p->d_Cnm, p->fw.d_scale, p->fw.d_u,
-                                                                   p->fw.d_v, acc);
+                                                                   p->fw.d_v, acc.ptr);
         if (inv && nqi > 0) {
-            CJT_CUDA_TRY(cjt_tmp_alloc((void **)&U, nqi * sizeof(double), st));
-            k_err_inv_U<<<nqi, 256, 0, st>>>(2 * p->Gi, M, p->iv.d_box, p->d_w, p->iv.d_u, p->iv.d_v, U);
+            CJT_CUDA_TRY(U.alloc(nqi));
+            k_err_inv_U<<<nqi, 256, 0, st>>>(2 * p->Gi, M, p->iv.d_box, p->d_w, p->iv.d_u, p->iv.d_v, U.ptr);
             k_err_inv<<<blocks_for(N + 1, 256), 256, 0, st>>>(N, M, p->iv.nblk, nqi, p->iv.d_box, p->d_Cnm,
-                                                               p->iv.d_scale, U, p->d_s, acc + 1);
+                                                               p->iv.d_scale, U.ptr, p->d_s, acc.ptr + 1);
         }
         CJT_CUDA_TRY(cudaGetLastError());
         double h[2] = {0.0, 0.0};
-        CJT_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CJT_CUDA_TRY(cudaMemcpyAsync(h, acc.ptr, sizeof(h), cudaMemcpyDeviceToHost, st));
         CJT_CUDA_TRY(cudaStreamSynchronize(st));
-        cudaFreeAsync(acc, st);
-        if (U) cudaFreeAsync(U, st);
         p->err_mixed_fwd = fwd ? 2.0 * mixed_eps_fft(p->Lf) * h[0] : 0.0;
         p->err_mixed_inv = inv ? mixed_eps_fft(p->Li) * h[1] : 0.0;
     }

@@ -111,6 +111,12 @@ class Server:
 
     # ---------------------------------------------------------------- public
     def submit(self, req: Request) -> Request:
+        """Queue a request; a malformed one (coefficients not of length N+1, an unknown
+        direction) raises ValueError here instead of reaching the executor."""
+        if req.direction not in (cjt.CJT_FWD, cjt.CJT_INV):
+            raise ValueError("direction must be CJT_FWD or CJT_INV")
+        if int(req.N) < 0 or np.shape(req.x) != (int(req.N) + 1,):
+            raise ValueError("x must hold N+1 = %d coefficients, got shape %s" % (int(req.N) + 1, np.shape(req.x)))
         with self.lock:
             req.rid = self._next_id
             self._next_id += 1
@@ -126,10 +132,28 @@ class Server:
             self.cv.notify_all()
         for th in self.threads:
             th.join(timeout=30)
+        # requests still queued or planned get an error instead of waiting for ever
+        left = list(self.ready)
+        self.ready.clear()
+        while True:
+            try:
+                r = self.incoming.get_nowait()
+            except queue.Empty:
+                break
+            if r is not None:
+                left.append(r)
+        for r in left:
+            self._fail(r, "server closed before the request ran")
         with self.lock:
             for p, _, _ in self.plans.values():
                 p.close()
             self.plans.clear()
+
+    @staticmethod
+    def _fail(r, msg):
+        r.error = msg
+        r.t_done = time.perf_counter()
+        r.done.set()
 
     def stats(self):
         lat = np.array([r.t_done - r.t_arrival for r in self.completed])
@@ -187,9 +211,7 @@ class Server:
                             self.plan_bytes += nbytes
                         self.cv.notify_all()
             except Exception as e:  # bad request: report it on the request, keep serving
-                r.error = str(e)
-                r.t_done = time.perf_counter()
-                r.done.set()
+                self._fail(r, str(e))
                 continue
             with self.cv:
                 self.ready.append(r)
@@ -243,17 +265,27 @@ class Server:
                     plan = self.plans[key][0]
                 s = free.pop()
                 n = r.N + 1
-                grown = s.ensure(plan.info()["workspace_bytes"], n, self.dev)
-                with self.cv:
-                    self.slot_bytes += grown
-                r.t_admit = time.perf_counter()
-                s.h_in[:n].copy_(torch.from_numpy(np.ascontiguousarray(r.x, dtype=np.float64)))
-                with torch.cuda.stream(s.stream):
-                    s.d_in[:n].copy_(s.h_in[:n], non_blocking=True)
-                    fn = cjt.cjt_forward_ws if r.direction == cjt.CJT_FWD else cjt.cjt_inverse_ws
-                    fn(plan, s.d_in, s.d_out, s.arena, stream=s.stream)
-                    s.h_out[:n].copy_(s.d_out[:n], non_blocking=True)
-                    s.event.record(s.stream)
+                try:
+                    grown = s.ensure(plan.info()["workspace_bytes"], n, self.dev)
+                    with self.cv:
+                        self.slot_bytes += grown
+                    r.t_admit = time.perf_counter()
+                    s.h_in[:n].copy_(torch.from_numpy(np.ascontiguousarray(r.x, dtype=np.float64)))
+                    with torch.cuda.stream(s.stream):
+                        s.d_in[:n].copy_(s.h_in[:n], non_blocking=True)
+                        fn = cjt.cjt_forward_ws if r.direction == cjt.CJT_FWD else cjt.cjt_inverse_ws
+                        fn(plan, s.d_in, s.d_out, s.arena, stream=s.stream)
+                        s.h_out[:n].copy_(s.d_out[:n], non_blocking=True)
+                        s.event.record(s.stream)
+                except Exception as e:   # the request fails; the slot and the loop go on
+                    s.stream.synchronize()
+                    with self.cv:
+                        self.plans[key][2] -= 1
+                        self.cv.notify_all()
+                    self._fail(r, str(e))
+                    free.append(s)
+                    progressed = True
+                    continue
                 s.req, s.plan_key = r, key
                 busy.append(s)
                 self.max_inflight = max(self.max_inflight, len(busy))

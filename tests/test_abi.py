@@ -105,3 +105,35 @@ def test_without_a_device_calls_fail_loudly():
     assert lib.cjt_batch_launch_host(None, None, None, None) == cjt.CJT_EINVAL
     assert lib.cjt_batch_set_profiling(None, 1) == cjt.CJT_EINVAL
     assert lib.cjt_batch_get_profile(None, None, None, 0) == cjt.CJT_EINVAL
+
+
+# one bad value per option; cjt_plan checks them all before it touches the device
+_BAD_OPTIONS = [dict(M=21), dict(M=-1), dict(eps=1.5), dict(eps=-1e-3), dict(precision=7), dict(directions=4),
+                dict(directions=-1), dict(ratio=1.0), dict(ratio=-0.1), dict(seg_len=48), dict(seg_len=16),
+                dict(seg_len=1 << 21), dict(use_asy=2), dict(use_asy=-2), dict(rec_store=2), dict(expansion=3),
+                dict(expansion=-1), dict(grid=2), dict(grid=-2), dict(overlap=4), dict(overlap=-1),
+                dict(seg_whole=-1), dict(seg_whole=(1 << 23) + 1)]
+
+
+@pytest.mark.parametrize("bad", _BAD_OPTIONS, ids=lambda d: "%s=%s" % next(iter(d.items())))
+def test_bad_option_values_are_refused(bad):
+    """Every option outside its documented range returns CJT_EINVAL and no handle, on a
+    machine with or without a GPU (the checks run before any device call)."""
+    from paper_1602_02618_gb300 import cjt
+    lib = cjt.load()
+    o = cjt.default_opts()
+    for k, v in bad.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    assert lib.cjt_plan(ctypes.byref(h), 64, 0.1, -0.3, ctypes.byref(o), None) == cjt.CJT_EINVAL
+    assert h.value is None
+
+
+def test_ultraspherical_expansion_needs_equal_parameters():
+    from paper_1602_02618_gb300 import cjt
+    lib = cjt.load()
+    o = cjt.default_opts()
+    o.expansion = cjt.CJT_EXPANSION_ULTRASPHERICAL
+    h = ctypes.c_void_p()
+    assert lib.cjt_plan(ctypes.byref(h), 64, 0.1, -0.3, ctypes.byref(o), None) == cjt.CJT_EINVAL
+    assert h.value is None

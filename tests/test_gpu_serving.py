@@ -65,3 +65,20 @@ def test_memory_budget_evicts_idle_plans(mods):
     server.close()
     assert st["requests"] == len(reqs)
     assert st["resident_plan_bytes"] + st["slot_bytes"] <= 3e8 + 4000 * 20001
+
+
+def test_bad_requests_fail_alone(mods):
+    """A malformed request is refused at submit; one whose plan cannot be built (alpha
+    outside [-1/2, 3/2]) comes back with an error; the requests around it are served."""
+    cjt, serve = mods
+    server = serve.Server(slots=2, mem_budget=5e9, planners=1)
+    with pytest.raises(ValueError):
+        server.submit(serve.Request(100, 0.1, 0.2, cjt.CJT_FWD, np.ones(100)))
+    with pytest.raises(ValueError):
+        server.submit(serve.Request(100, 0.1, 0.2, 3, np.ones(101)))
+    good = make_requests(serve, n=3, seed=inputs.BASE_SEED + 4200)
+    bad = serve.Request(300, 2.5, 0.0, cjt.CJT_FWD, np.ones(301))
+    serve.poisson_run(server, [good[0], bad, good[1], good[2]], rate=2000.0, seed=3)
+    server.close()
+    assert bad.error and bad.out is None
+    assert all(not r.error and r.out is not None for r in good[:3])
