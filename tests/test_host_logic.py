@@ -1,5 +1,7 @@
-"""Host-side logic that needs no GPU: the seeded workload generators and the
-autotuner's candidate set and cache file."""
+"""Host-side logic that needs no GPU: the seeded workload generators, the autotuner's
+candidate sets, cache file and work model, the bench's grid choice and traffic gate, the
+serving loop's memory admission, and the batch planner's memory budget (the last two with
+fake plans)."""
 import json
 
 import numpy as np
@@ -118,3 +120,127 @@ def test_mixed_work_model_discounts_fp32_transforms():
     assert s64 == s32 == 1000.0
     one = 5.0 * 4096 * 12 / autotune.ETA_FFT
     assert abs(f64 - 11 * one) < 1e-6 * f64 and abs(f32 - (10 * autotune.MIXED_ASY_FFT_FACTOR + 1) * one) < 1e-6 * f32
+
+
+# --------------------------------------------------------------------------------------
+# serving admission (serve.Server._make_room) on a server without threads or a device
+# --------------------------------------------------------------------------------------
+class _FakeServePlan:
+    def __init__(self):
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+def _bare_server(budget):
+    import collections
+    import threading
+    from paper_1602_02618_gb300 import serve
+    s = serve.Server.__new__(serve.Server)      # no planner/executor threads, no streams
+    s.lock = threading.Lock()
+    s.cv = threading.Condition(s.lock)
+    s.plans = collections.OrderedDict()
+    s.plan_bytes = 0
+    s.slot_bytes = 0
+    s.pending_bytes = 0.0
+    s.mem_budget = float(budget)
+    s._stop = False
+    return s
+
+
+def _add_plan(s, key, nbytes, users):
+    p = _FakeServePlan()
+    s.plans[key] = [p, nbytes, users]
+    s.plan_bytes += nbytes
+    return p
+
+
+def test_serving_admission_evicts_idle_plans_lru_and_reserves():
+    s = _bare_server(100)
+    a = _add_plan(s, "a", 30, 0)     # least recently used
+    b = _add_plan(s, "b", 30, 1)     # in use: never evicted
+    c = _add_plan(s, "c", 30, 0)
+    s._make_room(25)                 # 90 + 25 > 100: the idle LRU plan goes
+    assert a.closed and not b.closed and not c.closed
+    assert list(s.plans) == ["b", "c"] and s.plan_bytes == 60 and s.pending_bytes == 25
+    s._make_room(30)                 # 60 + 25 + 30 > 100: the next idle plan goes
+    assert c.closed and not b.closed and s.plan_bytes == 30 and s.pending_bytes == 55
+    s._make_room(10)                 # 30 + 55 + 10 fits: nothing evicted
+    assert list(s.plans) == ["b"] and s.pending_bytes == 65
+
+
+def test_serving_admission_waits_for_plans_in_use():
+    import threading
+    import time
+    s = _bare_server(100)
+    b = _add_plan(s, "b", 50, 1)
+    s.pending_bytes = 20.0
+    t = threading.Thread(target=s._make_room, args=(40,), daemon=True)
+    t.start()
+    time.sleep(0.2)
+    assert t.is_alive() and not b.closed          # 50 + 20 + 40 > 100 and b is in use
+    with s.cv:
+        s.plans["b"][2] = 0                        # the request using b completes
+        s.cv.notify_all()
+    t.join(timeout=5)
+    assert not t.is_alive() and b.closed
+    assert s.plan_bytes == 0 and s.pending_bytes == 60
+
+
+# --------------------------------------------------------------------------------------
+# batch planning under a device-memory budget (autotune.build_batch_plans) with fake plans
+# --------------------------------------------------------------------------------------
+class _FakeBatchPlan:
+    """Plan tables of 64 bytes per coefficient; stored recurrence values of 8 bytes per
+    recurrence step, which grow as N^2 (so stored values cost more per coefficient for
+    larger N)."""
+    made = []
+
+    def __init__(self, N, alpha, beta, precision=0, directions=3, shared_workspace=False, **opts):
+        self.N, self.opts, self.closed = int(N), dict(opts), False
+        _FakeBatchPlan.made.append(self)
+
+    def info(self):
+        N, M = self.N, self.opts.get("M", 7)
+        steps = int(0.05 * N * N / M)
+        return {"fft_len_fwd": 2 * N, "fft_len_inv": 4 * N, "nfft_fwd": 1 + 2 * M, "nfft_inv": 1 + 2 * M,
+                "rec_steps_fwd": steps, "rec_steps_inv": steps,
+                "device_bytes": 64 * (N + 1) + (8 * steps if self.opts.get("rec_store") else 0)}
+
+    def close(self):
+        self.closed = True
+
+
+def _plan_batch(monkeypatch, items, budget):
+    from paper_1602_02618_gb300 import cjt
+    monkeypatch.setattr(cjt, "Plan", _FakeBatchPlan)
+    _FakeBatchPlan.made = []
+    return autotune.build_batch_plans(items, plan_budget_bytes=budget)
+
+
+def test_batch_plans_store_values_within_the_budget(monkeypatch):
+    Ns = [100, 300, 1000, 3000, 10000, 30000, 70, 5000, 20000, 900]
+    items = [(N, 0.1, -0.2, 1 if t % 2 else -1) for t, N in enumerate(Ns)]
+    plain = sum(64 * (N + 1) for N in Ns)
+    est = 1.25 * plain                         # the planner's reserve for the items to come
+
+    plans, opts, rep = _plan_batch(monkeypatch, items, 1e15)
+    assert all(o["rec_store"] == 1 for o in opts) and rep["stored_items"] == len(items)
+
+    plans, opts, rep = _plan_batch(monkeypatch, items, plain)   # no room beyond the tables
+    assert all(o["rec_store"] == 0 for o in opts) and rep["stored_items"] == 0
+    assert [p.N for p in plans] == Ns and not any(p.closed for p in plans)
+
+    budget = est + 8.0 * 0.05 * 3000 ** 2      # room for the stored values of a few small items
+    plans, opts, rep = _plan_batch(monkeypatch, items, budget)
+    stored = sorted(N for N, o in zip(Ns, opts) if o["rec_store"])
+    assert 0 < len(stored) < len(items) and min(Ns) in stored and max(Ns) not in stored
+    used = sum(p.info()["device_bytes"] for p in plans)
+    assert used == rep["plan_bytes"] <= budget
+    assert [p.N for p in plans] == Ns and not any(p.closed for p in plans)
+    # every plan that was tried with stored values and did not fit was closed, not leaked
+    kept = {id(p) for p in plans}
+    assert all(p.closed for p in _FakeBatchPlan.made if id(p) not in kept)
+    # segment length by size, as the grouped executor expects
+    assert all(o["seg_len"] == (256 if N <= 16384 else 1024) for N, o in zip(Ns, opts))
