@@ -151,19 +151,35 @@ def oracle_seconds_estimate(N, d):
     return (N / 4096.0) ** 2 * (0.09 if d == 1 else 0.29) + 1e-3
 
 
-def batched_sample(items, budget_s=1.2):
-    """The batch's transforms, in order, that fit about `budget_s` of oracle time on 8 cores
-    (each item's estimate within what is left of the budget; the large items are skipped)."""
+def batched_sample_indices(items, budget_s=1.2):
+    """Indices of the batch's transforms, in order, that fit about `budget_s` of oracle time
+    on 8 cores (each item's estimate within what is left of the budget; the large items are
+    skipped)."""
     out, t = [], 0.0
-    for N, a, b, d, c in items:
+    for i, (N, a, b, d, c) in enumerate(items):
         e = oracle_seconds_estimate(N, d)
         if t + e > budget_s:
             continue
-        out.append((N, a, b, d, c))
+        out.append(i)
         t += e
         if budget_s - t < 0.01:
             break
     return out
+
+
+def batched_sample(items, budget_s=1.2):
+    """The items of batched_sample_indices, as (N, alpha, beta, direction, coefficients)."""
+    return [tuple(items[i][:5]) for i in batched_sample_indices(items, budget_s)]
+
+
+def sample_outputs(items, offs, out):
+    """{item_key: (output, ||c_in||_1)} of the batch's items that the cpu_baseline leg's
+    sampling rule picks, read from the batch's output array at the items' offsets."""
+    kept = {}
+    for i in batched_sample_indices(items):
+        N, c = items[i][0], items[i][4]
+        kept[item_key(items[i])] = (np.array(out[offs[i]:offs[i] + N + 1]), float(np.abs(c).sum()))
+    return kept
 
 
 def time_oracle_items(forward, inverse, items, nthreads):
@@ -202,20 +218,52 @@ def batch_sample_items():
     return batched_sample(batch_items(4096))
 
 
+def item_key(it):
+    """Identity of a transform item (N, alpha, beta, direction, coefficients' digest)."""
+    import hashlib
+    N, a, b, d, c = it[:5]
+    return (int(N), float(a), float(b), int(d), hashlib.sha256(np.ascontiguousarray(c).tobytes()).hexdigest())
+
+
 def cpu_baseline(config, cores):
-    """The oracle as it stands (double-double) on the bounded sample, on all host cores, and
-    the plain-double O(N^2) routines on all cores and on one core."""
+    """The cpu_baseline leg: the oracle as it stands (double-double) on the bounded sample, on
+    all host cores, and the plain-double O(N^2) routines on all cores and on one core.
+    Returns (the baseline's dict, {item_key: the oracle's output} of the sample's items); the
+    outputs also serve the GPU forms' error against the oracle (oracle_errors)."""
     from oracle import oracle as orc
     orc.build()
     items, desc = cpu_sample(config)
     coeffs = sum(it[0] + 1 for it in items)
-    t, _ = time_oracle_items(orc.forward, orc.inverse, items, cores)
+    t, outs = time_oracle_items(orc.forward, orc.inverse, items, cores)
     t64, _ = time_oracle_items(orc.forward_f64, orc.inverse_f64, items, cores)
     t64_1, _ = time_oracle_items(orc.forward_f64, orc.inverse_f64, items, 1)
-    return {"value": coeffs / t, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
+    base = {"value": coeffs / t, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
             "sample": "oracle (double-double, O(N^2)): %s; %.1f s" % (desc, t),
             "fp64_naive": {"value_all_cores": coeffs / t64, "value_1_core": coeffs / t64_1, "unit": "coeffs/s",
                            "cores": cores, "sample": "plain-double O(N^2) forward/inverse, same sample"}}
+    return base, {item_key(it): np.asarray(y) for it, y in zip(items, outs)}
+
+
+def oracle_errors(form, oracle_out):
+    """Fill the form's error against the oracle from the cpu_baseline leg's outputs: max
+    |c_gpu - c_oracle| / ||c_in||_1 over the sample's items that the form also ran (the GPU
+    outputs the form kept in "_oracle_sample"), then drop the kept outputs."""
+    kept = form.pop("_oracle_sample", None)
+    if kept is None:
+        return
+    err = form.setdefault("error", {})
+    if oracle_out is None:
+        err["vs_oracle"] = "not computed: the cpu_baseline leg did not run"
+        return
+    common = [k for k in kept if k in oracle_out]
+    if not common:
+        err["vs_oracle"] = "not computed: no item in common with the cpu_baseline leg's sample"
+        return
+    errs = [float(np.abs(kept[k][0] - oracle_out[k]).max() / kept[k][1]) for k in common]
+    err["max_abs_over_l1_vs_oracle"] = max(errs)
+    err["items_checked"] = len(common)
+    err["vs_oracle"] = ("the cpu_baseline leg's double-double oracle outputs of %d items (N from %d to %d)"
+                        % (len(common), min(k[0] for k in common), max(k[0] for k in common)))
 
 
 def run_reference(args):
@@ -493,10 +541,11 @@ def run_batched(ctx, big=False, steps=None):
                     "ms_per_step": 1e3 * step_s,
                     "note": "all stage kinds at their pipe's peak, summed (they share the FP64 pipe)"}
 
-    # accuracy: the oracle on the items it computes in well under a second
-    from oracle import oracle as orc
-    orc.build()
+    # accuracy: the mixed batch against the stored oracle fixtures (tests/golden); the FP64
+    # batch keeps its outputs of the cpu_baseline leg's sample items, compared with the
+    # oracle's by oracle_errors once that leg has run
     err = {}
+    kept = None
     if big:
         err64 = []
         for t, ((N, a, b, d, c), off) in enumerate(zip(items, offs)):
@@ -515,19 +564,13 @@ def run_batched(ctx, big=False, steps=None):
             dirn = cjt.CJT_FWD if d == 1 else cjt.CJT_INV
             key = "forward" if d == 1 else "inverse"
             err["stated_bound_" + key] = cjt.error_bound(plans[t], dirn)
-            if fx is not None:
+            if fx is not None and str(fx["input_sha256"]) == item_key(items[t])[4]:   # same input
                 err["vs_oracle_%s_max_abs_over_l1" % key] = float(
                     np.abs(got[fx["idx"]] - fx["out"]).max() / np.abs(c).sum())
                 err["oracle_%s" % key] = "%s, %d sampled coefficients" % (str(fx["oracle"]), fx["idx"].size)
     else:
-        errs = []
-        for (N, a, b, d, c), off in zip(items, offs):
-            if N > 2048 or len(errs) >= 48:
-                continue
-            want = orc.forward(c, a, b) if d == 1 else orc.inverse(c, a, b)
-            errs.append(float(np.abs(o[off:off + N + 1] - want).max() / np.abs(c).sum()))
-        err = {"max_abs_over_l1_vs_oracle": max(errs), "items_checked": len(errs),
-               "stated_bound": max(cjt.error_bound(p, d) for p, d in zip(plans, dirs))}
+        kept = sample_outputs(items, offs, o)
+        err = {"stated_bound": max(cjt.error_bound(p, d) for p, d in zip(plans, dirs))}
 
     # end to end through the C ABI: pinned host input -> device -> replay -> host output
     host_out = torch.empty_like(host_in).pin_memory()
@@ -569,6 +612,8 @@ def run_batched(ctx, big=False, steps=None):
                   "arena_bytes": binfo["arena_bytes"]},
         "clocks": clocks,
     }
+    if kept is not None:
+        form["_oracle_sample"] = kept
 
     if not big:
         # the same transforms one call per transform (the plain form on this workload)
@@ -766,14 +811,12 @@ def run_single(ctx, precision_name=None):
         roof["step"] = {"frac": t_res / step_s, "bound_ms": 1e3 * t_res, "ms_per_step": 1e3 * step_s,
                         "bound_by": res}
 
-    # accuracy: the round trip of one step, and each transform against the oracle (the CPU
-    # oracle at N <= 2^14, the stored oracle fixtures of tests/golden above)
+    # accuracy: the round trip of one step, and each transform against the oracle's outputs
+    # stored in tests/golden (written by tests/golden/make_fullsize.py, for these very inputs)
     err = {"round_trip_max_abs_over_l1": max(float((z - x).abs().max()) / float(x.abs().sum())
                                               for x, z in zip(xs, zs))}
     if ctx.rank == 0 and not args.params:
         import hashlib
-        from oracle import oracle as orc
-        orc.build()
         vs = {}
         for (N, a, b, c), p, x in zip(items, plans, xs):
             dg = hashlib.sha256(np.ascontiguousarray(c).tobytes()).hexdigest()
@@ -781,13 +824,9 @@ def run_single(ctx, precision_name=None):
             fwd_of_c = cjt.cjt_forward(p, x).cpu().numpy()
             for name, got in (("forward", fwd_of_c), ("inverse", inv_of_c)):
                 fx = oracle_fixture(("fwd_N%d" if name == "forward" else "inv_N%d") % N)
-                if fx is not None and str(fx["input_sha256"]) == dg:
-                    ref = fx["out"]             # the oracle's output, stored (tests/golden)
-                elif N <= (1 << 14):
-                    ref = orc.forward(c, a, b) if name == "forward" else orc.inverse(c, a, b)
-                else:
-                    continue
-                vs["%s_N%d" % (name, N)] = float(np.abs(got - ref).max() / np.abs(c).sum())
+                if fx is None or str(fx["input_sha256"]) != dg:
+                    continue                    # no stored oracle output for this input
+                vs["%s_N%d" % (name, N)] = float(np.abs(got - fx["out"]).max() / np.abs(c).sum())
         err["max_abs_over_l1_vs_oracle"] = vs
         err["stated_bound"] = max(cjt.error_bound(p, cjt.CJT_INV) for p in plans)
 
@@ -932,8 +971,14 @@ def main():
                                                "path)" % world) if world > 1 else "single GPU"},
                     "error": head["error"], "roofline": head["roofline"], "e2e": head["e2e"],
                     "gpu_launches": head["gpu_launches"], "clocks": head["clocks"], "forms": forms})
+        oracle_out = None
+        if rank == 0 and not args.no_cpu_baseline:
+            out["cpu_baseline"], oracle_out = cpu_baseline("batched", cores)
+        elif rank == 0:
+            out["cpu_baseline"] = None
+        oracle_errors(forms["batched_fp64"], oracle_out)
+        out["error"] = forms["batched_fp64"]["error"]
         if rank == 0:
-            out["cpu_baseline"] = None if args.no_cpu_baseline else cpu_baseline("batched", cores)
             print(json.dumps(out))
     else:
         if args.config == "single":
@@ -949,9 +994,13 @@ def main():
         out["config"] = {"workload": f["workload"]}
         out.setdefault("steps", args.steps)
         out.setdefault("warmup", args.warmup)
+        oracle_out = None
+        if rank == 0 and args.config in ("single", "batched") and not args.no_cpu_baseline:
+            out["cpu_baseline"], oracle_out = cpu_baseline(args.config, cores)
+        oracle_errors(f, oracle_out)
+        out.pop("_oracle_sample", None)
+        out["error"] = f.get("error")
         if rank == 0:
-            if args.config in ("single", "batched") and not args.no_cpu_baseline:
-                out["cpu_baseline"] = cpu_baseline(args.config, cores)
             print(json.dumps(out))
     if dist:
         dist.barrier()

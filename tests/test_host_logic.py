@@ -244,3 +244,92 @@ def test_batch_plans_store_values_within_the_budget(monkeypatch):
     assert all(p.closed for p in _FakeBatchPlan.made if id(p) not in kept)
     # segment length by size, as the grouped executor expects
     assert all(o["seg_len"] == (256 if N <= 16384 else 1024) for N, o in zip(Ns, opts))
+
+
+def test_bench_oracle_errors_come_from_the_cpu_baseline_leg():
+    """The batched form's error against the oracle is taken from the cpu_baseline leg's
+    outputs of the items both ran (matched by N, parameters, direction and the input's
+    digest); the form's kept GPU outputs never reach the JSON line."""
+    import bench
+    c1, c2 = np.arange(5.0), np.ones(9)
+    it1, it2 = (4, 0.1, -0.2, 1, c1), (8, 0.3, 0.0, -1, c2)
+    k1, k2 = bench.item_key(it1), bench.item_key(it2)
+    assert k1 != bench.item_key((4, 0.1, -0.2, 1, c1 + 1.0)) and k1 != bench.item_key((4, 0.1, -0.2, -1, c1))
+    ref1, ref2 = np.linspace(0, 1, 5), np.linspace(1, 2, 9)
+    form = {"error": {"stated_bound": 1e-12},
+            "_oracle_sample": {k1: (ref1 + 2e-3, float(np.abs(c1).sum())), k2: (ref2 - 9e-3, float(np.abs(c2).sum()))}}
+    bench.oracle_errors(form, {k1: ref1, k2: ref2, ("other",): np.zeros(1)})
+    assert "_oracle_sample" not in form
+    assert form["error"]["items_checked"] == 2
+    assert abs(form["error"]["max_abs_over_l1_vs_oracle"] - 1e-3) < 1e-12      # 9e-3 / 9 > 2e-3 / 10
+    form = {"error": {}, "_oracle_sample": {k1: (ref1, 10.0)}}
+    bench.oracle_errors(form, None)
+    assert "_oracle_sample" not in form and "did not run" in form["error"]["vs_oracle"]
+    form = {"error": {}, "_oracle_sample": {k1: (ref1, 10.0)}}
+    bench.oracle_errors(form, {k2: ref2})
+    assert "no item in common" in form["error"]["vs_oracle"]
+    # the form picks its sample with the leg's own rule, so the same workload gives the same items
+    items = bench.batch_items(64)
+    assert [bench.item_key(it) for it in bench.batched_sample(items)] == \
+        [bench.item_key(it) for it in bench.batched_sample(bench.batch_items(64))]
+
+
+def test_bench_sample_outputs_match_the_legs_items():
+    """The batched form keeps, at each sampled item's offset, exactly that item's output,
+    under the keys of the cpu_baseline leg's own sample of the same workload."""
+    import bench
+    items = bench.batch_items(4096)
+    offs, pos = [], 0
+    for it in items:
+        offs.append(pos)
+        pos += it[0] + 1
+    # a stand-in output: every item's own coefficients, so each slice identifies its item
+    out = np.concatenate([it[4] for it in items])
+    kept = bench.sample_outputs(items, offs, out)
+    leg = bench.cpu_sample("batched")[0]
+    assert list(kept) == [bench.item_key(it) for it in leg] and len(kept) > 10
+    for it in leg:
+        got, l1 = kept[bench.item_key(it)]
+        assert np.array_equal(got, it[4]) and l1 == float(np.abs(it[4]).sum())
+
+
+@pytest.mark.parametrize("config", ["all", "batched"])
+def test_bench_main_line_carries_the_legs_oracle_error(monkeypatch, capsys, config):
+    """bench.main with the GPU forms and the cpu_baseline leg replaced by fakes: the printed
+    line carries the error against the leg's oracle outputs and none of the form's kept
+    arrays."""
+    import sys
+    import torch
+    import bench
+    import __graft_entry__ as ge
+    monkeypatch.setattr(ge, "build", lambda: None)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a, **k: None)
+    monkeypatch.setattr(bench, "Ctx", lambda *a, **k: object())
+    for v in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(v, raising=False)
+    key = (3, 0.1, -0.2, 1, "0" * 64)
+
+    def form(value, kept=None):
+        f = {"value": value, "unit": "coeffs/s", "ms_per_step": 1.0, "p50_ms": 1.0, "p99_ms": 1.0, "dtype": "f64",
+             "workload": "w", "coefficients_per_step": 10, "plan_options": {}, "l2": "flushed",
+             "error": {"stated_bound": 1e-12}, "roofline": {}, "e2e": {}, "gpu_launches": 1, "clocks": {}}
+        if kept is not None:
+            f["_oracle_sample"] = kept
+        return f
+
+    monkeypatch.setattr(bench, "run_batched", lambda ctx, big=False, steps=None:
+                        form(2.0, None) if big else form(1.0, {key: (np.array([1.0, 2.0, 3.0, 4.0]), 4.0)}))
+    monkeypatch.setattr(bench, "run_single", lambda ctx, precision_name=None: form(3.0))
+    monkeypatch.setattr(bench, "run_serving", lambda ctx, precision_name: form(4.0))
+    monkeypatch.setattr(bench, "cpu_baseline", lambda cfg, cores: ({"value": 5.0, "kind": "oracle", "cores": cores},
+                                                                   {key: np.array([1.0, 2.2, 3.0, 4.0])}))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--config", config, "--steps", "3", "--warmup", "3"])
+    bench.main()
+    line = capsys.readouterr().out.strip().splitlines()[-1]
+    assert "_oracle_sample" not in line
+    d = json.loads(line)
+    assert abs(d["error"]["max_abs_over_l1_vs_oracle"] - 0.05) < 1e-12 and d["error"]["items_checked"] == 1
+    assert d["cpu_baseline"]["value"] == 5.0 and d["value"] == 1.0
+    if config == "all":
+        assert d["forms"]["batched_fp64"]["error"]["items_checked"] == 1
+        assert "_oracle_sample" not in d["forms"]["batched_fp64"]
