@@ -345,14 +345,15 @@ int cjt_execute_batched(int count, const cjt_plan_t *plans, const int8_t *dir, c
  * of the batch's private workspace arenas.  cjt_batch_launch (and _host) return
  * CJT_EINVAL unless the plans' device is current.
  *   Grouped execution (Sec. 4: one plan machinery over many coefficient sets): items
- * in FP64 or the mixed form with power-of-two transform lengths and no parameter
- * shift run stage by stage, one launch per stage over many items, and one batched
- * FFT per (length, precision) class.  The items are taken by decreasing cost and
- * packed into waves whose workspace fits CJT_BATCH_ARENA_MB MiB (environment,
- * default 4096); consecutive waves alternate between two such arenas and two pairs
- * of streams.  Every grouped item's result is bit-identical to the same plan run
- * alone.  The other items (double-float form, shifted parameters, Bluestein
- * lengths) run one chain of launches each over `nstreams` lanes (0 -> 16).
+ * in FP64 or the mixed form whose transform lengths are 2^b, 3 2^b or 5 2^b (no
+ * Bluestein transform) and with no parameter shift run stage by stage, one launch per
+ * stage over many items, and one batched FFT per (length, precision) class.  The items
+ * are taken by decreasing cost and packed into waves whose workspace fits
+ * CJT_BATCH_ARENA_MB MiB (environment, default 4096); consecutive waves alternate
+ * between two such arenas and two pairs of streams.  Every grouped item's result is
+ * bit-identical to the same plan run alone.  The other items (double-float form,
+ * shifted parameters, Bluestein lengths) run one chain of launches each over
+ * `nstreams` lanes (0 -> 16).
  */
 typedef struct cjt_batch_s *cjt_batch_t;
 int cjt_batch_create(cjt_batch_t *out, int count, const cjt_plan_t *plans, const int8_t *dir,
