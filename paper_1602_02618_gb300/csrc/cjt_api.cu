@@ -124,13 +124,17 @@ namespace {
 int fft_launches(int64_t L) { return L <= 1 ? 0 : (L <= 4096 ? 1 : 2); }
 int dft_launches(const Dft &d) { return d.L <= 1 ? 0 : (d.P ? 3 + 2 * fft_launches(d.P) : fft_launches(d.L)); }
 
+// frees a plan's events and memory on the plan's device (the caller's device is restored)
 void free_plan(cjt_plan_s *p) {
+    int cur = -1;
+    const bool other = cudaGetDevice(&cur) == cudaSuccess && cur != p->dev && cudaSetDevice(p->dev) == cudaSuccess;
     for (auto &r : p->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : p->prof_pool) cudaEventDestroy(e);
     for (void *v : p->allocs) cudaFree(v);
     p->allocs.clear();
     cjt_release_twiddles(p);
     if (p->done) cudaEventDestroy(p->done);
+    if (other) cudaSetDevice(cur);
     delete p;
 }
 }  // namespace

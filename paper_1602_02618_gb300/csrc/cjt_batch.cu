@@ -367,6 +367,10 @@ int cjt_batch_info(cjt_batch_t b, int64_t *kernels, int64_t *arena_bytes) {
 
 void cjt_batch_destroy(cjt_batch_t b) {
     if (!b) return;
+    // on the batch's device: the synchronisation below must cover its replays
+    int cur = -1;
+    const bool other = b->dev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != b->dev &&
+                       cudaSetDevice(b->dev) == cudaSuccess;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaDeviceSynchronize();
@@ -376,6 +380,7 @@ void cjt_batch_destroy(cjt_batch_t b) {
     for (auto s : b->lanes.streams) cudaStreamDestroy(s);
     for (auto e : b->lanes.join) cudaEventDestroy(e);
     if (b->lanes.fork) cudaEventDestroy(b->lanes.fork);
+    if (other) cudaSetDevice(cur);
     delete b;
 }
 
