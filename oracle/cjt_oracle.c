@@ -3,7 +3,7 @@
  *
  * This file is the plain, slow, obviously-correct reference that the CUDA
  * library is checked against.  Only tests, the smoke check and the benchmark's
- * CPU-baseline leg may load it; the product path never does.  It shares no
+ * CPU-baseline leg and reference arm may load it; the product path never does.  It shares no
  * code, header, table or constant generator with the CUDA library.
  *
  * What it computes (the paper's definitions, written out directly):

@@ -2,8 +2,8 @@
 
 The oracle is a plain, slow, double-double C implementation of the paper's
 definitions (see cjt_oracle.c for the citations).  Only the test-suite, the
-smoke check and the benchmark's CPU-baseline leg may import this module; the
-library itself never does.
+smoke check and the benchmark's CPU-baseline leg and reference arm may import
+this module; the library itself never does.
 
 ``build()`` compiles ``cjt_oracle.c`` with gcc (OpenMP, -ffp-contract=off so
 that the error-free transformations are not contracted into fused
