@@ -62,6 +62,20 @@ extern "C" {
 #define CJT_EUNSUPPORTED (-7)/* request outside what this build implements          */
 #define CJT_EDIRECTION (-8)  /* plan was not built for the requested direction       */
 
+/* Environment variables read by the library (all optional):
+ *   CJT_TWIDDLE_CACHE_MB  MiB of twiddle tables kept cached after no plan uses them
+ *                         (default 1024; see cjt_destroy)
+ *   CJT_BATCH_ARENA_MB    MiB of one workspace arena of a grouped batch (default 4096;
+ *                         see cjt_batch_create)
+ *   CJT_BATCH_STREAMS     lanes of cjt_execute_batched and the default of
+ *                         cjt_batch_create's nstreams (1..64, default 16)
+ *   CJT_BATCH_NO_GROUP    set: cjt_batch_create runs every item as its own chain of
+ *                         launches (the per-item path), with the same results
+ *   CJT_PLAN_TRACE        set: cjt_plan prints the wall time of each planning step to
+ *                         stderr, synchronising the stream after each
+ *   CJT_GROUP_TRACE       set: a grouped batch prints one line per launch step to stderr
+ *                         when it is issued (captured or profiled)                      */
+
 /* precision of the scaled DCT-I/DST-I bulk (Sec. 2.1, Eq. "PNASY") */
 #define CJT_FP64 0           /* everything in IEEE double                            */
 #define CJT_MIXED 1          /* ASY transforms in float; Hahn coefficients, scalings,
