@@ -85,8 +85,9 @@ int make_lanes(Lanes &L, int n) {
 }
 
 // Issues the items over the lanes; arenas[l] (>= a.need[l] bytes) is lane l's workspace.
-int issue(int count, const cjt_plan_t *plans, const int8_t *dir, const int64_t *offsets, const double *in,
-          double *out, const Assignment &a, Lanes &L, const std::vector<void *> &arenas, cudaStream_t st) {
+int issue(int /*count: a.order holds the items*/, const cjt_plan_t *plans, const int8_t *dir,
+          const int64_t *offsets, const double *in, double *out, const Assignment &a, Lanes &L,
+          const std::vector<void *> &arenas, cudaStream_t st) {
     const int nl = (int)a.order.size();
     CJT_CUDA_TRY(cudaEventRecord(L.fork, st));
     for (int l = 0; l < nl; ++l) {
