@@ -59,7 +59,7 @@ extern "C" {
 #define CJT_ECUDA (-4)       /* a CUDA runtime call failed (see cjt_last_cuda_error) */
 #define CJT_ETIMEOUT (-5)    /* a bounded device-side wait gave up                   */
 #define CJT_EBUSY (-6)       /* plan still in use on another stream                  */
-#define CJT_EUNSUPPORTED (-7)/* request outside what this build implements          */
+#define CJT_EUNSUPPORTED (-7)/* request outside what this library implements        */
 #define CJT_EDIRECTION (-8)  /* plan was not built for the requested direction       */
 
 /* Environment variables read by the library (all optional):

@@ -1011,7 +1011,7 @@ int build_grid(cjt_plan_s *p, GridWork &gw, int64_t Ng, bool inverse, const AsyE
 }  // namespace
 
 // A pool per device (created on first use) whose freed memory, up to 1 GiB, stays reserved
-// for the next plan build instead of going back to the driver.
+// for the next plan build instead of going back to the CUDA driver.
 cudaError_t cjt_tmp_alloc(void **ptr, size_t bytes, cudaStream_t st) {
     static std::mutex mu;
     static cudaMemPool_t pools[64] = {};

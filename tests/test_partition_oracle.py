@@ -7,8 +7,8 @@
     alpha_N = min(1/log(Ng/n_M), 1/2) and n_M from the envelope at pi/2;
   * C_{n,m} of Eq. "Cnmab" satisfies the recurrence in m of Eq. "Cnmabrec" and, at a = b = 0,
     the closed form through the central binomial coefficient;
-  * the probe values of the survey of the paper (N = 1024 and 2^14, (0.1, -0.3), M = 7) are
-    reproduced: a cross-check, not the pin.
+  * independently computed probe values of the partition (N = 1024 and 2^14, (0.1, -0.3),
+    M = 7; two blocks at N = 2^18, M = 13) are reproduced: a cross-check, not the pin.
 """
 import json
 import math
@@ -63,7 +63,7 @@ def test_boxes_satisfy_their_definition(case):
         prev = (j, i1, i2)
 
 
-def test_survey_probe_values():
+def test_independent_probe_values():
     got = {(c["N"], c["direction"], c["M"]): (c["n_M"], c["blocks"]) for c in cases()}
     assert got[(1024, "forward", 7)] == (106, [[451, 103, 937], [199, 235, 817]])
     assert got[(16384, "forward", 7)] == (106, [[3250, 235, 16206], [644, 1159, 15424], [127, 6057, 10909]])
