@@ -182,6 +182,29 @@ def _dev_ptr(t, n):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _dev_buf(t, what):
+    """Pointer of a caller's device scratch tensor (any dtype): contiguous, on the current
+    CUDA device, so that the library never receives a host address."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous CUDA tensor" % what)
+    cur = torch.cuda.current_device()
+    if t.device.index != cur:
+        raise ValueError("%s on cuda:%d while cuda:%d is current" % (what, t.device.index, cur))
+    return ctypes.c_void_p(t.data_ptr()), t.numel() * t.element_size()
+
+
+def _host_buf(a, n, what, writable=False):
+    """Pointer of a host float64 array holding at least n values (C-contiguous)."""
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError("%s must be a C-contiguous float64 numpy array" % what)
+    if writable and not a.flags.writeable:
+        raise ValueError("%s is read-only" % what)
+    if a.size < n:
+        raise ValueError("%s has %d values, need %d" % (what, a.size, n))
+    return ctypes.c_void_p(a.ctypes.data)
+
+
 def default_opts() -> cjt_plan_opts:
     o = cjt_plan_opts()
     _check(load().cjt_plan_opts_default(ctypes.byref(o)), "cjt_plan_opts_default")
@@ -267,8 +290,9 @@ def cjt_execute_host(plan: Plan, direction: int, x: np.ndarray, out: np.ndarray 
         raise ValueError("expected %d values" % (plan.N + 1))
     if out is None:
         out = np.empty_like(x)
-    _check(load().cjt_execute_host(plan.handle, int(direction), ctypes.c_void_p(x.ctypes.data),
-                                   ctypes.c_void_p(out.ctypes.data), _stream_handle(stream)), "cjt_execute_host")
+    po = _host_buf(out, plan.N + 1, "out", writable=True)
+    _check(load().cjt_execute_host(plan.handle, int(direction), _host_buf(x, plan.N + 1, "x"), po,
+                                   _stream_handle(stream)), "cjt_execute_host")
     return out
 
 
@@ -299,16 +323,17 @@ def cjt_jacobi_to_jacobi(plan_from: Plan, plan_to: Plan, c_in, c_out=None, strea
 def cjt_forward_ws(plan: Plan, c_jac, c_cheb, workspace, stream=None):
     """Forward transform borrowing `workspace` (a CUDA tensor of >= workspace_bytes bytes)."""
     n = plan.N + 1
-    _check(load().cjt_forward_ws(plan.handle, _dev_ptr(c_jac, n), _dev_ptr(c_cheb, n),
-                                 ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
+    ws, nbytes = _dev_buf(workspace, "workspace")
+    _check(load().cjt_forward_ws(plan.handle, _dev_ptr(c_jac, n), _dev_ptr(c_cheb, n), ws, nbytes,
                                  _stream_handle(stream)), "cjt_forward_ws")
     return c_cheb
 
 
 def cjt_inverse_ws(plan: Plan, c_cheb, c_jac, workspace, stream=None):
+    """Inverse transform borrowing `workspace` (a CUDA tensor of >= workspace_bytes bytes)."""
     n = plan.N + 1
-    _check(load().cjt_inverse_ws(plan.handle, _dev_ptr(c_cheb, n), _dev_ptr(c_jac, n),
-                                 ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
+    ws, nbytes = _dev_buf(workspace, "workspace")
+    _check(load().cjt_inverse_ws(plan.handle, _dev_ptr(c_cheb, n), _dev_ptr(c_jac, n), ws, nbytes,
                                  _stream_handle(stream)), "cjt_inverse_ws")
     return c_jac
 
@@ -365,17 +390,17 @@ class Batch:
                                        _dev_ptr(out_dev, total), int(nstreams)), "cjt_batch_create")
         self._h = h
         self._keep = (plans, x_dev, out_dev)
+        self.total = total
 
     def launch(self, stream=None):
         _check(load().cjt_batch_launch(self._h, _stream_handle(stream)), "cjt_batch_launch")
 
     def launch_host(self, x_host: np.ndarray, out_host: np.ndarray, stream=None):
-        """Host input -> device -> replay -> host output, synchronous (whole-batch arrays)."""
-        if x_host.dtype != np.float64 or out_host.dtype != np.float64 or x_host.size != out_host.size:
-            raise ValueError("float64 host arrays of equal size expected")
-        _check(load().cjt_batch_launch_host(self._h, ctypes.c_void_p(x_host.ctypes.data),
-                                            ctypes.c_void_p(out_host.ctypes.data), _stream_handle(stream)),
-               "cjt_batch_launch_host")
+        """Host input -> device -> replay -> host output, synchronous (whole-batch arrays of
+        at least max_t (offsets[t] + N_t + 1) values)."""
+        px = _host_buf(x_host, self.total, "x_host")
+        po = _host_buf(out_host, self.total, "out_host", writable=True)
+        _check(load().cjt_batch_launch_host(self._h, px, po, _stream_handle(stream)), "cjt_batch_launch_host")
         return out_host
 
     def set_profiling(self, on: bool = True):

@@ -1,9 +1,11 @@
 """The C-ABI library builds for sm_103a, loads without a GPU and exports every
-function that include/cjt.h declares (no compute calls here)."""
+function that include/cjt.h declares; its argument checks and the binding's buffer checks
+refuse bad input before any device call (no compute calls here)."""
 import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -137,3 +139,37 @@ def test_ultraspherical_expansion_needs_equal_parameters():
     h = ctypes.c_void_p()
     assert lib.cjt_plan(ctypes.byref(h), 64, 0.1, -0.3, ctypes.byref(o), None) == cjt.CJT_EINVAL
     assert h.value is None
+
+
+def test_binding_refuses_buffers_that_do_not_fit():
+    """The binding checks the caller's buffers before it calls the library: host arrays
+    too small, of another dtype, non-contiguous or read-only, and a workspace that is not a
+    CUDA tensor, are refused, so that the library never writes past a host array nor gets
+    a host address for device memory."""
+    torch = pytest.importorskip("torch")
+    from paper_1602_02618_gb300 import cjt
+
+    class FakePlan:
+        N = 7
+        handle = ctypes.c_void_p()
+
+    with pytest.raises(ValueError):
+        cjt.cjt_execute_host(FakePlan(), cjt.CJT_FWD, np.zeros(8), out=np.zeros(7))
+    with pytest.raises(TypeError):
+        cjt.cjt_execute_host(FakePlan(), cjt.CJT_FWD, np.zeros(8), out=np.zeros(8, dtype=np.float32))
+    with pytest.raises(TypeError):
+        cjt.cjt_execute_host(FakePlan(), cjt.CJT_FWD, np.zeros(8), out=np.zeros(16)[::2])
+    ro = np.zeros(8)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        cjt.cjt_execute_host(FakePlan(), cjt.CJT_FWD, np.zeros(8), out=ro)
+    for fn in (cjt.cjt_forward_ws, cjt.cjt_inverse_ws):
+        with pytest.raises(TypeError, match="workspace"):
+            fn(FakePlan(), torch.zeros(8, dtype=torch.float64), torch.zeros(8, dtype=torch.float64),
+               torch.zeros(64, dtype=torch.uint8))
+    b = cjt.Batch.__new__(cjt.Batch)          # a batch whose inputs span 10 values
+    b._h, b.total = ctypes.c_void_p(), 10
+    with pytest.raises(ValueError):
+        b.launch_host(np.zeros(9), np.zeros(10))
+    with pytest.raises(ValueError):
+        b.launch_host(np.zeros(10), np.zeros(9))
