@@ -140,12 +140,12 @@ typedef struct {
                          transforms otherwise.  1: G, the least power of two >= N, in place of
                          N: x_j = cos(pi j/G) and cos(pi j/(2G)).  0 (default): G, the least
                          integer >= N of the forms 2^a, 3 2^a and 5 2^a (at most 4N/3; N itself
-                         when N has one of them); transforms of lengths 3 2^b and 5 2^b take one
-                         radix-3 or radix-5 step and power-of-two FFTs.  Every grid gives the same map (to rounding): a
-                         polynomial of degree N <= G is interpolated exactly by the inverse
-                         DCT-I on G+1 points, whose coefficients above N vanish, and the
-                         (2G+1)-point Clenshaw--Curtis rule is exact wherever the
-                         (2N+1)-point rule is.                                            */
+                         when N has one of them); transforms of lengths 3 2^b and 5 2^b take
+                         one radix-3 or radix-5 step and power-of-two FFTs.  Every grid gives
+                         the same map (to rounding): a polynomial of degree N <= G is
+                         interpolated exactly by the inverse DCT-I on G+1 points, whose
+                         coefficients above N vanish, and the (2G+1)-point Clenshaw--Curtis
+                         rule is exact wherever the (2N+1)-point rule is.                 */
     int overlap;      /* scheduling of an execution's two concurrent chains, the
                          asymptotic blocks (pack, transforms; Eq. "PNASY") and the
                          recurrence (Sec. 4.2), which run on separate streams and join
@@ -160,7 +160,8 @@ typedef struct {
                          work item of that length instead of seg_len segments, so the plan
                          computes no segment states for them (cheaper plans, longer items
                          at execution; for one-shot plans such as a server's).  0 (default):
-                         every row is cut into segments of seg_len.                       */
+                         every row is cut into segments of seg_len.  0 .. 2^23, else
+                         CJT_EINVAL.                                                      */
 } cjt_plan_opts;
 
 /* Summary of a plan (for reports and tests). Sizes are per direction. */
@@ -170,10 +171,10 @@ typedef struct {
     int M, precision, directions;
     int64_t n_M;             /* Sec. 2.2, from the envelope g_M(pi/2)                  */
     double ratio;            /* alpha_N actually used                                   */
-    int nblk_fwd, nblk_inv;  /* asymptotic blocks (grid N, grid 2N)                     */
+    int nblk_fwd, nblk_inv;  /* asymptotic blocks (grid G, grid 2G; G = grid_fwd)       */
     int64_t rec_steps_fwd;   /* sum_i J(i): recurrence steps of one forward transform
                                 (with the parity fold: over the rows i <= N/2 only)     */
-    int64_t rec_steps_inv;   /* sum_i min(J(i), N+1) on the 2N grid (likewise)          */
+    int64_t rec_steps_inv;   /* sum_i min(J(i), N+1) on the 2G grid (likewise)          */
     int64_t fft_len_fwd, fft_len_inv;   /* transform lengths used by the ASY blocks:
                                            2 grid_fwd and 2 grid_inv                    */
     int64_t nfft_fwd, nfft_inv;         /* complex transforms per execution             */
