@@ -1,7 +1,8 @@
 """Host-side logic that needs no GPU: the seeded workload generators, the autotuner's
 candidate sets, cache file and work model, the bench's grid choice and traffic gate, the
 serving loop's memory admission, and the batch planner's memory budget (the last two with
-fake plans)."""
+fake plans), the bench's algorithmic-work count behind the roofline, and the
+transform autotuner's choice (with a fake timer)."""
 import json
 
 import numpy as np
@@ -333,3 +334,55 @@ def test_bench_main_line_carries_the_legs_oracle_error(monkeypatch, capsys, conf
     if config == "all":
         assert d["forms"]["batched_fp64"]["error"]["items_checked"] == 1
         assert "_oracle_sample" not in d["forms"]["batched_fp64"]
+
+
+def test_bench_batch_work_counts_the_stated_units():
+    """The roofline's algorithmic work, from plan summaries: 5 L log2 L per complex transform
+    (the pairs of asymptotic items, plus one DCT-I / front-end transform per item), 8 flop per
+    recurrence step at execution, 2 per stored value; points of all transforms for bytes."""
+    import bench
+
+    class P:
+        def __init__(self, **kw):
+            self.kw = kw
+
+        def info(self):
+            return self.kw
+
+    fwd = P(fft_len_fwd=1024, nfft_fwd=4, rec_steps_fwd=1000, rec_store_bytes=8000,
+            fft_len_inv=0, nfft_inv=0, rec_steps_inv=0)
+    inv = P(fft_len_inv=2048, nfft_inv=1, rec_steps_inv=500, rec_store_bytes=0,
+            fft_len_fwd=0, nfft_fwd=0, rec_steps_fwd=0)
+    w = bench.batch_work([fwd, inv], [1, -1])
+    assert w["fft_asy"] == 3 * 5.0 * 1024 * 10
+    assert w["fft_dct"] == 5.0 * 1024 * 10 + 5.0 * 2048 * 11
+    assert w["rec_stored"] == 2.0 * 1000 and w["rec"] == 8.0 * 500
+    assert w["fft_points"] == 4 * 1024 + 1 * 2048
+
+
+def test_tune_fft_keeps_the_fastest_configuration(monkeypatch):
+    """tune_fft times every candidate of a length class, sets the fastest, reports the
+    default's time, and restores the default when no candidate runs."""
+    from paper_1602_02618_gb300 import cjt
+    state = {}
+    calls = []
+
+    def set_config(prec, lg, ctas=4, split=0, single=12):
+        state[(prec, lg)] = (ctas, split, single)
+        calls.append((prec, lg, ctas, split, single))
+
+    def fft_time(prec, lg, batch, reps):
+        ctas, split, single = state[(prec, lg)]
+        if lg == 20:
+            raise cjt.CJTError(cjt.CJT_ENOMEM, "fft_time")
+        return 1.0 + 0.1 * abs(ctas - 2) + 0.05 * split + (0.3 if single == 13 else 0.0)
+
+    monkeypatch.setattr(cjt, "fft_set_config", set_config)
+    monkeypatch.setattr(cjt, "fft_time", fft_time)
+    out = autotune.tune_fft(0, [14, 13, 14, 20], points=1 << 20)
+    assert sorted(out) == [13, 14]                       # 20: every candidate failed
+    for lg in (13, 14):
+        assert out[lg]["config"] == (2, 0, 12) and state[(0, lg)] == (2, 0, 12)
+        assert abs(out[lg]["default_ms"] - 1.2) < 1e-12 and out[lg]["batch"] == max(1, (1 << 20) >> lg)
+        assert len([c for c in calls if c[1] == lg]) == len(autotune.fft_candidates(lg)) + 1
+    assert calls[-1] == (0, 20, 4, 0, 12)                # the default put back
