@@ -386,3 +386,22 @@ def test_tune_fft_keeps_the_fastest_configuration(monkeypatch):
         assert abs(out[lg]["default_ms"] - 1.2) < 1e-12 and out[lg]["batch"] == max(1, (1 << 20) >> lg)
         assert len([c for c in calls if c[1] == lg]) == len(autotune.fft_candidates(lg)) + 1
     assert calls[-1] == (0, 20, 4, 0, 12)                # the default put back
+
+
+def test_serving_submit_refuses_malformed_requests():
+    """Requests whose coefficients are not N+1 long, or whose direction is unknown, are
+    refused at submit and never reach the executor's queue; a good one is queued."""
+    import queue
+    from paper_1602_02618_gb300 import cjt, serve
+    s = _bare_server(1e9)
+    s.incoming = queue.Queue()
+    s._next_id = 0
+    for bad in (serve.Request(100, 0.1, 0.2, cjt.CJT_FWD, np.ones(100)),
+                serve.Request(100, 0.1, 0.2, cjt.CJT_FWD, np.ones((101, 1))),
+                serve.Request(100, 0.1, 0.2, 3, np.ones(101)),
+                serve.Request(-1, 0.1, 0.2, cjt.CJT_INV, np.ones(0))):
+        with pytest.raises(ValueError):
+            s.submit(bad)
+    assert s.incoming.empty()
+    good = s.submit(serve.Request(100, 0.1, 0.2, cjt.CJT_INV, np.ones(101)))
+    assert s.incoming.get_nowait() is good and good.rid == 0
